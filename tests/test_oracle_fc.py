@@ -1,0 +1,130 @@
+"""Pins of the FC-Gram oracle against what the paper and mathematics fix (CPU)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fc, fc_tables
+import synth
+
+
+def test_stored_tables_match_fresh_build(golden_dir):
+    pytest.importorskip("mpmath")
+    for d, C in [(5, 25), (5, 15)]:
+        fresh = fc_tables._to_f64(fc_tables.build_mr_mp(d, C)[0])
+        stored = fc_tables.read_table(fc_tables.table_path(d, C, fc_tables.default_bandwidth(d, C),
+                                                           fc_tables.N_OS, golden_dir))
+        assert np.array_equal(fresh, stored)
+
+
+@pytest.mark.slow
+def test_gram_and_lagrange_constructions_agree():
+    """App. B: M_r = A Q^T is independent of the polynomial basis (d nodes, degree < d)."""
+    mp = pytest.importorskip("mpmath")
+    a, ra = fc_tables.build_mr_mp(5, 25, basis="lagrange")
+    b, rb = fc_tables.build_mr_mp(5, 25, basis="gram")
+    worst = max(abs(x - y) for ra_, rb_ in zip(a, b) for x, y in zip(ra_, rb_))
+    scale = max(abs(x) for r in a for x in r)
+    assert worst / scale < 1e-30
+    assert max(float(r) for r in ra) < 1e-15   # least-squares residual of the fits
+
+
+def test_table_shape_and_count():
+    # App. B: d*C numbers per end ("231 numbers" for d=7, C=33)
+    assert 7 * 33 == 231
+    Mr = fc_tables.fc_matrix(5, 25, table_dir=None) if False else None
+    assert fc_tables.default_bandwidth(5, 25) == 20
+    assert fc_tables.default_bandwidth(7, 33) == 26
+
+
+def test_first_row_is_polynomial_extrapolation(Mr_5_25):
+    """The first continuation point (t = d) follows the matching polynomial: the
+    degree-4 extrapolation weights are the alternating binomials."""
+    np.testing.assert_allclose(Mr_5_25[0], [1, -5, 10, -10, 5], atol=1e-7)
+    # blend to zero next to the left matching set
+    assert np.abs(Mr_5_25[-1]).max() < 1e-7
+    assert Mr_5_25.shape == (25, 5)
+
+
+def test_mirror_symmetry(Mr_5_25):
+    """Reversing a line in z reverses its continuation (J_C M J_d structure, Sec. 3)."""
+    g = np.random.default_rng(0)
+    f = g.standard_normal(40)
+    c = fc.extend(f, Mr_5_25)[40:]
+    cr = fc.extend(f[::-1].copy(), Mr_5_25)[40:]
+    np.testing.assert_allclose(cr, c[::-1], rtol=0, atol=1e-12 * np.abs(c).max())
+
+
+@pytest.mark.parametrize("Nz", [33, 65, 129, 257, 513])
+def test_polynomials_below_degree_d_are_differentiated_exactly(Mr_5_25, Nz):
+    z = synth.z_grid(Nz)
+    for p in range(5):
+        f = z ** p
+        d1 = p * z ** max(p - 1, 0) if p > 0 else 0 * z
+        d2 = p * (p - 1) * z ** max(p - 2, 0) if p > 1 else 0 * z
+        assert np.abs(fc.fc_deriv_z(f, 1.0, Mr_5_25, 1) - d1).max() < 2e-9
+        assert np.abs(fc.fc_deriv_z(f, 1.0, Mr_5_25, 2) - d2).max() < 5e-7
+
+
+def test_boundary_order_of_convergence(Mr_5_25):
+    """High order at the boundaries (Sec. 1/8): observed order >= d-1 for d/dz."""
+    errs1, errs2 = [], []
+    Ns = [65, 129, 257]
+    for Nz in Ns:
+        z = synth.z_grid(Nz)
+        f = np.sin(5 * z)
+        errs1.append(np.abs(fc.fc_deriv_z(f, 1.0, Mr_5_25, 1) - 5 * np.cos(5 * z)).max())
+        errs2.append(np.abs(fc.fc_deriv_z(f, 1.0, Mr_5_25, 2) + 25 * np.sin(5 * z)).max())
+    o1 = [math.log2(errs1[i] / errs1[i + 1]) * (Ns[i + 1] - 1) / (Ns[i + 1] - 1) for i in range(2)]
+    o2 = [math.log2(errs2[i] / errs2[i + 1]) for i in range(2)]
+    assert min(o1) > 3.7 and min(o2) > 2.7
+
+
+def test_interior_spectral_accuracy(Mr_5_25):
+    """Away from the walls the error is far below the boundary error."""
+    Nz = 257
+    z = synth.z_grid(Nz)
+    f = np.sin(5 * z)
+    e = np.abs(fc.fc_deriv_z(f, 1.0, Mr_5_25, 1) - 5 * np.cos(5 * z))
+    assert e[100:157].max() < 1e-3 * e.max()
+
+
+@pytest.mark.parametrize("a,bound", [(1.0, 1e-6), (5.0, 1e-6), (15.0, 5e-5)])
+def test_sine_closed_form(Mr_5_25, a, bound):
+    Nz = 129
+    z = synth.z_grid(Nz)
+    e = np.abs(fc.fc_deriv_z(np.sin(a * z), 1.0, Mr_5_25, 1) - a * np.cos(a * z)).max() / a
+    assert e < bound
+
+
+@pytest.mark.parametrize("Nz", [11, 24, 40])
+def test_dense_bruteforce_operator(Mr_5_25, Nz):
+    """Explicit O(N'^2) DFT sums agree with the FFT path (tiny grids)."""
+    g = np.random.default_rng(Nz)
+    f = g.standard_normal(Nz)
+    for order in (1, 2):
+        D = fc.dense_deriv_operator(Nz, 25, 1.0, Mr_5_25, order)
+        ref = fc.fc_deriv_z(f, 1.0, Mr_5_25, order)
+        assert np.abs(D @ f - ref).max() < 1e-11 * np.abs(D).max() * np.abs(f).max() * Nz
+
+
+def test_fc_demo_function(golden_dir):
+    """Sec. 3 demonstration: 49 points on [0,1], C = 15, d = 5; the continued data
+    is periodic and smooth, so its Fourier coefficients decay without Gibbs tails."""
+    setups = {}
+    for line in open(f"{golden_dir}/paper_setups.txt"):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("#")[0].split("=")
+            setups[k.strip()] = v.strip()
+    N, C, d = int(setups["fc_demo_points"]), int(setups["fc_demo_C"]), int(setups["fc_demo_d"])
+    Mr = fc_tables.fc_matrix(d, C, table_dir=golden_dir)
+    f, df = synth.fc_demo_function(N)
+    fe = fc.extend(f, Mr)
+    assert fe.shape == (N + C,)
+    F = np.abs(np.fft.fft(fe))
+    assert F[20:N + C - 20].max() < 1e-4 * F.max()
+    # a plain (non-continued) periodic transform of the same data has a Gibbs tail
+    G = np.abs(np.fft.fft(f))
+    assert G[12:N - 12].max() > 1e-2 * G.max()
+    e = np.abs(fc.fc_deriv_z(f, 1.0, Mr, 1) - df).max() / np.abs(df).max()
+    assert e < 2e-2

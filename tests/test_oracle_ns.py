@@ -1,0 +1,176 @@
+"""Pins of the Navier-Stokes / Boussinesq oracle (CPU)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ns
+import synth
+
+
+def _zeros_gp(p):
+    return np.zeros((2, 2, p.Ny, p.Kx), dtype=complex)
+
+
+def test_poiseuille_is_a_fixed_point(Mr_5_25):
+    """Sec. 6 laminar solution with F/nu = 10 (runs L1-L3): max U = 1.25 and one
+    RK3 step leaves it unchanged up to the FC second-derivative floor."""
+    nu = 1e-2
+    p = ns.Params(32, 32, 33, nu=nu, forcing_x=10 * nu, Mr=Mr_5_25)
+    v = synth.poiseuille(32, 32, 33, F=10 * nu, nu=nu)
+    assert abs(v[0].max() - 1.25) < 1e-12
+    st = ns.to_spectral(v, p)
+    st2, gp = ns.rk_step(st, _zeros_gp(p), p, 1e-3)
+    v2 = np.stack([ns.to_physical(c, p) for c in st2])
+    assert np.abs(v2 - v).max() < 1e-10 * 1.25
+    rhs = ns.ns_rhs(v, p)
+    assert np.abs(rhs).max() < 1e-8
+
+
+def test_rhs_closed_form(Mr_5_25):
+    """-(v.grad)v + nu lap v for v = (z sin y, z cos x, 0): polynomial z-dependence
+    of degree < d is differentiated exactly, so the RHS has a closed form."""
+    N, Nz, nu = 16, 33, 0.3
+    p = ns.Params(N, N, Nz, nu=nu, Mr=Mr_5_25)
+    x = np.arange(N) * 2 * np.pi / N
+    z = synth.z_grid(Nz)
+    Z, Y, X = np.meshgrid(z, x, x, indexing="ij")
+    v = np.stack([Z * np.sin(Y), Z * np.cos(X), 0 * Z])
+    rhs = ns.ns_rhs(v, p)
+    ex_u = -(Z * np.cos(X) * Z * np.cos(Y)) - nu * Z * np.sin(Y)
+    ex_v = -(Z * np.sin(Y) * (-Z * np.sin(X))) - nu * Z * np.cos(X)
+    assert np.abs(rhs[0] - ex_u).max() < 1e-8
+    assert np.abs(rhs[1] - ex_v).max() < 1e-8
+    assert np.abs(rhs[2]).max() < 1e-8
+
+
+def test_boussinesq_buoyancy_sign_and_theta_source(Mr_5_25):
+    """Sec. 7 with reading B1: dw/dt gets +gamma theta; dtheta/dt gets +gamma w."""
+    N, Nz = 8, 33
+    p = ns.Params(N, N, Nz, nfields=4, nu=1e-3, kappa=0.5, gamma=2.0, Mr=Mr_5_25)
+    z = synth.z_grid(Nz)
+    f = np.zeros((4, Nz, N, N))
+    f[3] = (z * (1 - z))[:, None, None]
+    rhs = ns.ns_rhs(f, p)
+    assert np.abs(rhs[2] - 2.0 * f[3]).max() < 1e-9
+    assert np.abs(rhs[3] - 0.5 * (-2.0)).max() < 1e-8
+    g = np.zeros((4, Nz, N, N))
+    g[2] = 0.25
+    rhs = ns.ns_rhs(g, p)
+    assert np.abs(rhs[3] - 2.0 * 0.25).max() < 1e-9
+
+
+def test_conduction_state_is_exactly_fixed(Mr_5_25):
+    p = ns.Params(16, 16, 33, nfields=4, nu=3.162e-4, kappa=3.162e-4, gamma=1.0, Mr=Mr_5_25)
+    st = np.zeros((4, p.Np, p.Ny, p.Kx), dtype=complex)
+    st2, gp = ns.rk_step(st, _zeros_gp(p), p, 1e-3)
+    assert np.abs(st2).max() == 0.0 and np.abs(gp).max() == 0.0
+    assert ns.nusselt(st2 + 0.0, p) == (1.0, 1.0)
+
+
+def test_projection_wall_normal_velocity_is_roundoff(Mr_5_25):
+    """After projection w = 0 at the walls to round-off (Sec. 6: <w^2|wall> ~ 1e-35)."""
+    p = ns.Params(32, 32, 33, nu=1e-2, Mr=Mr_5_25)
+    v = synth.channel_velocity(32, 32, 33)
+    vp, gp = ns.poisson_project(v, p, 1e-3)
+    assert np.abs(vp[2][[0, -1]]).max() < 1e-14
+    st = ns.to_spectral(v, p)
+    st2, _ = ns.rk_step(st, _zeros_gp(p), p, 1e-3)
+    assert ns.wall_mean_squares(st2, p)[2] < 1e-28
+
+
+def test_projection_reduces_divergence(Mr_5_25):
+    p = ns.Params(32, 32, 33, nu=1e-2, forcing_x=0.1, Mr=Mr_5_25)
+    v = synth.channel_velocity(32, 32, 33)
+    st = ns.to_spectral(v, p)
+    before = (ns.divergence_phys(st, p) ** 2).mean()
+    st2, _ = ns.rk_step(st, _zeros_gp(p), p, 1e-3)
+    after = (ns.divergence_phys(st2, p) ** 2).mean()
+    assert after < 1e-5 * before
+
+
+def _manufactured(N, Nz, Mr, with_u=True):
+    p = ns.Params(N, N, Nz, Mr=Mr)
+    x = np.arange(N) * 2 * np.pi / N
+    z = synth.z_grid(Nz)
+    Z, Y, X = np.meshgrid(z, x, x, indexing="ij")
+    h = Z ** 2 * (1 - Z) ** 2
+    sx = np.cos(X) * np.cos(2 * Y)
+    sy = -2 * np.sin(X) * np.sin(2 * Y)
+    u = np.stack([sy * h, -sx * h, 0 * h]) * (1.0 if with_u else 0.0)
+    gpsi = np.stack([-np.sin(X) * np.cos(2 * Y) * np.cosh(Z),
+                     -2 * np.cos(X) * np.sin(2 * Y) * np.cosh(Z),
+                     np.cos(X) * np.cos(2 * Y) * np.sinh(Z) + 3 * Z ** 2])
+    vs = u + gpsi
+    dt = 1e-3
+    m = ns.xy_forward(vs)
+    gpp = np.zeros((2, 2, p.Ny, p.Kx), complex)
+    gpp[0, 0], gpp[0, 1] = m[0, 0] / dt, m[1, 0] / dt
+    gpp[1, 0], gpp[1, 1] = m[0, -1] / dt, m[1, -1] / dt
+    v, _ = ns.poisson_project(vs, p, dt, gradp_prev=gpp)
+    return np.abs(v - u).max()
+
+
+def test_manufactured_poisson_converges(Mr_5_25):
+    """v* = u + grad psi with u solenoidal and u.z = 0 at the walls: the projection
+    returns u, with errors shrinking fast as Nz grows."""
+    e = [_manufactured(16, Nz, Mr_5_25) for Nz in (17, 33, 65)]
+    assert e[0] < 1e-7 and e[1] < 1e-9 and e[2] < 1e-10
+    assert e[2] < e[1] < e[0]
+    # a pure gradient is annihilated
+    assert _manufactured(16, 65, Mr_5_25, with_u=False) < 1e-10
+
+
+def test_projection_idempotent_with_consistent_injection(Mr_5_25):
+    p = ns.Params(32, 32, 33, Mr=Mr_5_25)
+    v = synth.channel_velocity(32, 32, 33)
+    vp, g = ns.poisson_project(v, p, 1e-3)
+    vp2, _ = ns.poisson_project(vp, p, 1e-3, gradp_prev=-g)
+    assert np.abs(vp2 - vp).max() < 1e-6 * np.abs(vp).max()
+
+
+def test_stage_steps_give_taylor_amplification():
+    """Reading R1: the low-storage stages reproduce exp(z) to order o for y' = lam y."""
+    for o in (1, 2, 3, 4):
+        for zval in (-0.3, 0.2 + 0.5j):
+            y0 = 1.0
+            y = y0
+            for j in range(1, o + 1):
+                y = y0 + ns.stage_dt(1.0, o, j) * zval * y
+            want = sum(zval ** k / math.factorial(k) for k in range(o + 1))
+            assert abs(y - want) < 1e-15
+
+
+def test_rk3_time_convergence_on_diffusion(Mr_5_25):
+    """Third-order global convergence of the full step on theta diffusion."""
+    p = ns.Params(8, 8, 33, nfields=4, nu=1e-3, kappa=2e-3, gamma=0.0, Mr=Mr_5_25)
+    z = synth.z_grid(33)
+    x = np.arange(8) * 2 * np.pi / 8
+    f = np.zeros((4, 33, 8, 8))
+    f[3] = np.sin(np.pi * z)[:, None, None] * (1 + 0.5 * np.cos(x))[None, None, :]
+    st0 = ns.to_spectral(f, p)
+
+    def run(dt, n):
+        st, gp = st0, _zeros_gp(p)
+        for _ in range(n):
+            st, gp = ns.rk_step(st, gp, p, dt)
+        return st[3]
+
+    a, b, c = run(0.04, 5), run(0.02, 10), run(0.01, 20)
+    r = np.abs(a - b).max() / np.abs(b - c).max()
+    assert r > 6.0          # ~8 for third order; ~2 for the printed j dt/o stage steps
+
+
+def test_filter_factor_values():
+    """Sec. 4.3: the Nyquist mode is attenuated by e^{-beta} = 1e-16; the 2/3 mask
+    keeps |n| <= N/3 in x and y."""
+    p = ns.Params(12, 12, 33)
+    F = ns.filter_factor(p)
+    nyq = p.Np // 2
+    assert abs(F[nyq, 0, 0] - 1e-16) < 1e-28
+    assert abs(F[1, 0, 0] - 1.0) < 1e-15
+    assert F[0, 0, 4] == 1.0 and F[0, 0, 5] == 0.0
+    assert F[0, 4, 0] == 1.0 and F[0, 5, 0] == 0.0 and F[0, -4, 0] == 1.0 and F[0, -5, 0] == 0.0
+    p0 = ns.Params(12, 12, 33, filter=0)
+    F0 = ns.filter_factor(p0)
+    assert abs(F0[0, 0, 6] - 1e-16) < 1e-28
