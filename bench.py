@@ -1,0 +1,250 @@
+"""Benchmark of the FC-Gram hot path on one GB300 (or N independent replicas).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Workloads (seeded synthetic fields, no dataset):
+  * fc_deriv_z: batch of 3 fields 512 x 512 x 513 (d = 5, C = 25), first and
+    second z-derivatives, float32 (headline) and float64.
+Inputs (1.6 GB in float32) are larger than the 129 MB L2, so no flush is
+needed between timed iterations.  Kernel time is measured with CUDA events on
+the launching stream; the end-to-end figure goes through the public Python
+API with pinned host buffers, host->device copy of the input and
+device->host copy of both derivatives inside the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("RK-stage grid-points/s and fc_deriv_z HBM GB/s (FP32 batched vs FP64 plain); p50/p99")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._thr = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._thr = threading.Thread(target=self._run, daemon=True)
+        self._thr.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._thr.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 3 + i and s[3 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def deriv_workload(dtype_np, B=3, Nx=512, Ny=512, Nz=513):
+    import synth
+    fields = [synth.SeparableField(Nx, Ny, Nz, seed_offset=b) for b in range(B)]
+    return fields, (B, Nz, Ny, Nx)
+
+
+def bench_deriv(api, torch, dtype_np, steps, warmup, with_e2e=True):
+    """Time fc_deriv_z on the 3 x 512^2 x 513 batch; returns a dict."""
+    fields, shape = deriv_workload(dtype_np)
+    tdt = torch.float32 if dtype_np == np.float32 else torch.float64
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f = torch.empty(shape, dtype=tdt, device=dev)
+    for b, sf in enumerate(fields):
+        f[b] = torch.from_numpy(sf.field(0).astype(dtype_np)).to(dev)
+    d1, d2 = torch.empty_like(f), torch.empty_like(f)
+    plan = api.Plan(5, 25, shape[1])
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        api.fc_deriv_z(plan, f, d1, d2)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(stream)
+    for i in range(steps):
+        ev[i][0].record(stream)
+        api.fc_deriv_z(plan, f, d1, d2)
+        ev[i][1].record(stream)
+    t_all1.record(stream)
+    torch.cuda.synchronize()
+    times = np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3
+    total = t_all0.elapsed_time(t_all1) * 1e-3
+    pts = int(np.prod(shape))
+    es = np.dtype(dtype_np).itemsize
+    alg_bytes = 3 * es * pts
+    res = {
+        "points": pts, "seconds_per_call_mean": float(times.mean()), "p50_ms": float(np.percentile(times, 50) * 1e3),
+        "p99_ms": float(np.percentile(times, 99) * 1e3), "grid_points_per_s": pts * steps / total,
+        "alg_bytes_per_call": alg_bytes, "alg_GBps": alg_bytes * steps / total / 1e9, "launches": steps,
+    }
+    # accuracy vs the FP64 oracle on 64 sampled lines (reported beside the number)
+    from oracle import fc, fc_tables
+    Mr = fc_tables.fc_matrix(5, 25, table_dir=os.path.join(ROOT, "tests", "golden"))
+    g = np.random.default_rng(1)
+    B, Nz, Ny, Nx = shape
+    bs, ys, xs = g.integers(0, B, 64), g.integers(0, Ny, 64), g.integers(0, Nx, 64)
+    lines = f[bs, :, ys, xs].double().cpu().numpy().T
+    for order, out in ((1, d1), (2, d2)):
+        ref = fc.fc_deriv_z(lines, 1.0, Mr, order, axis=0)
+        o = out[bs, :, ys, xs].double().cpu().numpy().T
+        res[f"rel_l2_err_d{order}_vs_oracle"] = float(np.linalg.norm(o - ref) / np.linalg.norm(ref))
+    if with_e2e:
+        hf = f.cpu().pin_memory()
+        h1 = torch.empty(shape, dtype=tdt).pin_memory()
+        h2 = torch.empty(shape, dtype=tdt).pin_memory()
+        n_e2e = max(2, min(steps, 5))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_e2e):
+            f.copy_(hf, non_blocking=True)
+            api.fc_deriv_z(plan, f, d1, d2)
+            h1.copy_(d1, non_blocking=True)
+            h2.copy_(d2, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = e0.elapsed_time(e1) * 1e-3
+        res["e2e"] = {"value": pts * n_e2e / te, "unit": "grid-points/s",
+                      "h2d_bytes_per_step": es * pts, "d2h_bytes_per_step": 2 * es * pts}
+    del f, d1, d2
+    torch.cuda.empty_cache()
+    return res
+
+
+def cpu_baseline_deriv(budget_s=12.0):
+    """The FP64 oracle timed on a bounded sample of the same workload: z-lines of
+    the 3 x 512^2 x 513 batch, as many as fit in ~budget_s seconds."""
+    import synth
+    from oracle import fc, fc_tables
+    Mr = fc_tables.fc_matrix(5, 25, table_dir=os.path.join(ROOT, "tests", "golden"))
+    sf = synth.SeparableField(512, 512, 513, seed_offset=0)
+    Z = sf.z_profiles(0)                                   # [rank][Nz]
+    g = np.random.default_rng(3)
+    X = sf.X.reshape(sf.X.shape[0], -1)
+    lines_per_chunk = 4096
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        idx = g.integers(0, X.shape[1], lines_per_chunk)
+        f = Z.T @ X[:, idx]                                 # [Nz][lines]
+        fc.fc_deriv_z(f, 1.0, Mr, 1, axis=0)
+        fc.fc_deriv_z(f, 1.0, Mr, 2, axis=0)
+        done += lines_per_chunk
+    dt = time.perf_counter() - t0
+    return {"value": done * 513 / dt, "unit": "grid-points/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} z-lines (x 513 points) of the 3x512x512x513 fc_deriv_z batch, FP64 numpy"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = cpu_baseline_deriv(budget_s=max(5.0, min(60.0, 2.0 * args.steps)))
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"],
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "fc_deriv_z 3x512x512x513 d=5 C=25 (oracle, sampled lines)"},
+                          "cpu_baseline": cb,
+                          "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2002_01392_gb300 import api
+    dev_index = torch.cuda.current_device()
+    hbm_peak, peak_kind = _peaks()
+    if world > 1:
+        torch.distributed.barrier()
+    with ClockSampler(dev_index) as clk:
+        r32 = bench_deriv(api, torch, np.float32, args.steps, args.warmup)
+    r64 = bench_deriv(api, torch, np.float64, max(3, args.steps // 4), 2, with_e2e=False)
+    value = r32["grid_points_per_s"]
+    if world > 1:
+        t = torch.tensor([r32["seconds_per_call_mean"]], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        value = r32["points"] * world / float(t.item())
+    out = {
+        "metric": METRIC, "value": value, "unit": "grid-points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r32["seconds_per_call_mean"] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "fc_deriv_z 3x512x512x513 d=5 C=25, d/dz and d2/dz2, FP32 (continuation FP64)",
+                   "l2": "inputs 1.6 GB > L2, no flush", "parallelism": "replicas" if world > 1 else "single"},
+        "p50_ms": r32["p50_ms"], "p99_ms": r32["p99_ms"],
+        "fc_deriv_z": {"fp32": {k: v for k, v in r32.items() if k != "e2e"}, "fp64": r64},
+        "roofline": {"bound": "hbm", "achieved": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9,
+                     "peak": hbm_peak, "unit": "GB/s",
+                     "frac": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9 / hbm_peak,
+                     "traffic": None, "peak_kind": peak_kind, "kernel": "fc_deriv_z conv L=1080 FP32"},
+        "e2e": r32.get("e2e"),
+        "gpu_launches": r32["launches"],
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline_deriv()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

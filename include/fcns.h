@@ -1,0 +1,240 @@
+/*
+ * fcns.h -- C ABI of the GB300 FC-Gram Navier-Stokes library (libfcns.so).
+ *
+ * Method: Fontana, Bruno, Mininni, Dmitruk, "Fourier continuation method for
+ * incompressible fluids with boundaries" (FC-Gram pseudospectral
+ * Navier-Stokes in a cuboid with walls at z = 0, Lz and periodic x, y).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an fc_status; no C++ exception crosses the ABI.
+ *   - Arguments are validated synchronously: FC_ERR_ARG for bad values or
+ *     NULL pointers, FC_ERR_UNSUPPORTED for sizes outside what the compiled
+ *     kernels cover.  A failing call writes nothing.
+ *   - "Device pointer" arguments are caller-owned CUDA device allocations
+ *     (for example PyTorch tensors), contiguous, 16-byte aligned, on the
+ *     current CUDA device.  "Host pointer" arguments are ordinary host memory.
+ *   - Kernels are enqueued on the caller's stream (fc_stream_t is a
+ *     cudaStream_t; NULL means the legacy default stream) and the calls
+ *     return without synchronising unless stated otherwise.  Asynchronous
+ *     CUDA failures surface as FC_ERR_CUDA from the next call that checks.
+ *   - Field layouts are row-major with x fastest:
+ *       physical  [nf][Nz][Ny][Nx] real (float or double),
+ *       spectral  [nf][Nz+C][Ny][Nx/2+1] complex (interleaved re, im).
+ *   - Grids include both walls: z_s = s Lz/(Nz-1), s = 0..Nz-1; the
+ *     continued (periodic) grid has N' = Nz + C points and period
+ *     L'z = N' Lz/(Nz-1).  Forward transforms are unnormalised, inverse
+ *     transforms carry 1/N.
+ */
+#ifndef FCNS_H
+#define FCNS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FC_OK = 0,
+  FC_ERR_ARG = 1,          /* invalid argument or NULL pointer                    */
+  FC_ERR_UNSUPPORTED = 2,  /* size outside the compiled kernel set                 */
+  FC_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed          */
+  FC_ERR_NOMEM = 4,        /* device or host allocation failed / workspace too small */
+  FC_ERR_TIMEOUT = 5,      /* a bounded device wait gave up                        */
+  FC_ERR_NONFINITE = 6,    /* non-finite values detected in an output             */
+  FC_ERR_STATE = 7         /* call not valid in the object's current state         */
+} fc_status;
+
+typedef enum { FC_F32 = 0, FC_F64 = 1 } fc_dtype;
+
+typedef struct fc_plan* fc_plan_t;
+typedef struct ns_sim* ns_sim_t;
+typedef void* fc_stream_t; /* cudaStream_t */
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* fc_status_str(fc_status s);
+
+/* Text of the last error detected on the calling thread (static per thread). */
+const char* fc_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* FC-Gram continuation plan                                                  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * fc_setup -- build the FC-Gram continuation tables for d matching points and
+ * C continuation points (Sec. 3, continuation formula; App. B, Gram basis by
+ * QR of the Vandermonde matrix on the d matching points and oversampled
+ * least-squares Fourier continuations of each Gram polynomial with
+ * periodicity interval [1 - delta_r, 2b - (1 - delta_r)]).  Host only; the
+ * tables are computed in binary128 (_Float128) and rounded to double.
+ *   d   number of matching points, 2 <= d <= 10.
+ *   C   number of continuation points, d <= C <= 64.
+ *   Nz  number of physical z points including both walls, Nz >= 2 d.
+ *   out receives a new plan (owned by the caller, release with fc_destroy).
+ * Uses the bandwidth M = floor(2 (d + C) / 3) and oversampling 20.
+ * Device tables are created lazily, once per device, by the first call that
+ * needs them on that device (that first call allocates and must not be
+ * inside a CUDA graph capture).
+ */
+fc_status fc_setup(int d, int C, int Nz, fc_plan_t* out);
+
+/* As fc_setup with an explicit trigonometric bandwidth M (number of cosine /
+ * sine pairs, 1 <= M) and oversampling factor n_os (>= 1). */
+fc_status fc_setup_ex(int d, int C, int Nz, int M, int n_os, fc_plan_t* out);
+
+/* Copy the right-end continuation matrix M_r = A_r Q_r^T (C rows x d
+ * columns, row-major) to host memory Mr_out (C*d doubles).  Row j gives the
+ * weights of the last d samples f_{Nz-d..Nz-1} for continuation point
+ * Nz + j.  The left-end matrix is its row/column reversal (Sec. 3). */
+fc_status fc_plan_matrix(fc_plan_t plan, double* Mr_out);
+
+/* Sizes of a plan (any output pointer may be NULL); ls_residual is the
+ * largest relative least-squares residual of the continuation fits. */
+fc_status fc_plan_info(fc_plan_t plan, int* d, int* C, int* Nz, int* M, int* n_os,
+                       double* ls_residual);
+
+/* Release a plan and its device tables (synchronises the devices it used). */
+fc_status fc_destroy(fc_plan_t plan);
+
+/*
+ * fc_deriv_z -- first and/or second z-derivative of real fields by FC-Gram
+ * (Sec. 3: continuation of every z-line from its first and last d samples to
+ * N' = Nz + C points; Sec. 4.2: multiplication of the Fourier coefficients by
+ * i k (Nyquist entry zeroed) or -k^2; inverse transform truncated to the Nz
+ * physical points).  The continuation product is always evaluated in double.
+ *   dtype  FC_F32: f, df, d2f are float; FC_F64: double.
+ *   batch, Nx, Ny  field count and horizontal sizes (each >= 1); the line
+ *          count batch*Nx*Ny must stay below 2^31.
+ *   Lz     domain height (> 0); dz = Lz/(Nz-1).
+ *   f      device pointer, [batch][Nz][Ny][Nx].
+ *   df     device pointer for d f/dz, same layout, or NULL.
+ *   d2f    device pointer for d^2 f/dz^2, same layout, or NULL.
+ *          At least one of df, d2f must be non-NULL; outputs must not
+ *          overlap f.
+ *   stream CUDA stream for the launch.
+ * Needs no workspace.  FC_ERR_UNSUPPORTED when N' + Nz - 1 exceeds 1080.
+ */
+fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
+                     const void* f, void* df, void* d2f, fc_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Navier-Stokes / Boussinesq simulation                                     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int Nx, Ny, Nz;        /* physical grid; Nx, Ny even, Nz >= 2 d                  */
+  int d, C;              /* FC-Gram matching / continuation points                  */
+  int nfields;           /* 3: Navier-Stokes (u, v, w); 4: Boussinesq (+ theta)     */
+  int rk_order;          /* o of the time-splitting low-storage RK (1..4)           */
+  double Lx, Ly, Lz;     /* box size                                                */
+  double nu, kappa;      /* viscosity, thermal diffusivity                          */
+  double gamma;          /* Boussinesq coupling (Sec. 7); unused for nfields = 3    */
+  double forcing_x;      /* constant mean-pressure forcing +F x_hat (Sec. 6)        */
+  int filter;            /* 0: exponential filter in x, y, z (Sec. 4.3);
+                            1: sharp 2/3 mask in x, y and exponential in z          */
+  double filter_beta;    /* beta (16 ln 10 for double precision digits)            */
+  double filter_2p;      /* 2p (100)                                                */
+  fc_dtype prec;         /* FC_F32: float transforms and products with the
+                            continuation products, the homogeneous-pressure
+                            coefficients and the mean-flow line in double;
+                            FC_F64: everything in double                           */
+} ns_params;
+
+/* Fill *p with the defaults: d = 5, C = 25, nfields = 3, rk_order = 3,
+ * Lx = Ly = 2 pi, Lz = 1, nu = 1e-2, kappa = gamma = forcing_x = 0,
+ * filter = 1, filter_beta = 16 ln 10, filter_2p = 100, prec = FC_F64.
+ * Nx, Ny, Nz are set to 0 and must be filled in. */
+fc_status ns_params_default(ns_params* p);
+
+/* Device workspace (bytes) that ns_create needs for these parameters. */
+fc_status ns_workspace_bytes(const ns_params* p, size_t* bytes);
+
+/*
+ * ns_create -- create a simulation object holding the spectral state of the
+ * nfields fields, the wall pressure-gradient planes (Sec. 4.4 step 2) and the
+ * tables.  dev_workspace (device pointer, >= ns_workspace_bytes) is used for
+ * every device buffer; if it is NULL the library allocates it itself with
+ * cudaMalloc and frees it in ns_destroy.  Creation uploads tables with
+ * synchronous copies on the current device.
+ */
+fc_status ns_create(const ns_params* p, void* dev_workspace, size_t bytes, ns_sim_t* out);
+
+/* Release the object (synchronises its device). */
+fc_status ns_destroy(ns_sim_t sim);
+
+/* Set the state from physical fields phys (device pointer,
+ * [nf][Nz][Ny][Nx] in the simulation's precision): the state becomes the
+ * FC continuation of phys transformed to (kx, ky, kz) (Sec. 3), and the wall
+ * pressure-gradient planes are reset to zero. */
+fc_status ns_set_fields(ns_sim_t sim, const void* phys, fc_stream_t stream);
+
+/* Physical fields of the current state (first Nz points of the inverse
+ * transforms), device pointer [nf][Nz][Ny][Nx]. */
+fc_status ns_get_fields(ns_sim_t sim, void* phys, fc_stream_t stream);
+
+/* Copy the spectral state to / from a device buffer of
+ * nf * (Nz+C) * Ny * (Nx/2+1) complex values of the simulation's precision
+ * (checkpoint / restore). */
+fc_status ns_get_state(ns_sim_t sim, void* spec, fc_stream_t stream);
+fc_status ns_put_state(ns_sim_t sim, const void* spec, fc_stream_t stream);
+
+/* Wall pressure-gradient planes: [2 walls][2 components][Ny][Nx/2+1] complex
+ * double, device pointer (get copies out, put copies in). */
+fc_status ns_get_wall_gradp(ns_sim_t sim, void* gradp, fc_stream_t stream);
+fc_status ns_put_wall_gradp(ns_sim_t sim, const void* gradp, fc_stream_t stream);
+
+/*
+ * ns_rhs -- right-hand side of the pressureless momentum (and temperature)
+ * equations for the physical fields phys_in (Sec. 4.2 and Sec. 4.4 step 1):
+ * with v^c the FC continuation of phys_in,
+ *   rhs = filter[ -(v.grad)v + F x_hat (+ gamma theta z_hat) ] - nu k^2 v^c
+ * (theta: filter[ -(v.grad)theta + gamma w ] - kappa k^2 theta^c),
+ * returned at the Nz physical points.  Overwrites the simulation's working
+ * buffers (not its state).  phys_in, rhs_out: device pointers
+ * [nf][Nz][Ny][Nx].
+ */
+fc_status ns_rhs(ns_sim_t sim, const void* phys_in, void* rhs_out, fc_stream_t stream);
+
+/*
+ * fc_poisson_project -- pressure solve and projection of a physical
+ * pressureless velocity v* (Sec. 4.1-4.2, Sec. 4.4 steps 2-5) with the
+ * readings phi = dt_stage p:
+ *   inject v*_par = dt_stage grad_par p_prev at z = 0, Lz (p_prev: the
+ *   simulation's wall planes), FC-continue, grad phi^I = k (k.v*)/k^2,
+ *   b, t = w* - d_z phi^I at the walls, homogeneous solution
+ *   A e^{g(z-Lz)} + B e^{-g z} (+ D z for the mean mode, D = (b+t)/2),
+ *   v = v* - grad phi^I - grad phi^H, and stores grad_par p = grad_par phi /
+ *   dt_stage at the walls as the simulation's new wall planes.
+ *   vstar_phys, v_phys  device pointers [3][Nz][Ny][Nx] (velocity only).
+ *   gradp_wall          device pointer for a copy of the new wall planes
+ *                       ([2][2][Ny][Nx/2+1] complex double) or NULL.
+ * Leaves the simulation's spectral state unchanged.
+ */
+fc_status fc_poisson_project(ns_sim_t sim, double dt_stage, const void* vstar_phys, void* v_phys,
+                             void* gradp_wall, fc_stream_t stream);
+
+/*
+ * rk_step -- advance the state by one time step dt with the time-splitting
+ * low-storage Runge-Kutta scheme of order rk_order (Sec. 4.4), stage steps
+ * dt_j = dt / (o + 1 - j).
+ */
+fc_status rk_step(ns_sim_t sim, double dt, fc_stream_t stream);
+
+/*
+ * ns_diagnostics -- scalar diagnostics of the current state, synchronous
+ * (host outputs; any pointer may be NULL):
+ *   div_ms       mean square of div v over the physical grid (Sec. 6),
+ *   wall_u_ms    mean square of u over both walls,  wall_w_ms: of w,
+ *   flow_rate    volume mean of u,
+ *   nusselt      (Nu at z = 0 + Nu at z = Lz)/2 with Nu = 1 - <d_z theta>/gamma
+ *                (Sec. 7; 0 for nfields = 3).
+ */
+fc_status ns_diagnostics(ns_sim_t sim, double* div_ms, double* wall_u_ms, double* wall_w_ms,
+                         double* flow_rate, double* nusselt, fc_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCNS_H */

@@ -168,11 +168,15 @@ def read_table(path: str) -> np.ndarray:
     return np.array(rows, dtype=np.float64)
 
 
+STORED = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden")
+
+
 @lru_cache(maxsize=None)
 def fc_matrix(d: int, C: int, M: int | None = None, n_os: int = N_OS,
-              table_dir: str | None = None) -> np.ndarray:
-    """float64 M_r (C x d).  Uses a stored table written by ``write_table`` when
-    ``table_dir`` holds one (for hosts without mpmath), else builds it."""
+              table_dir: str | None = STORED) -> np.ndarray:
+    """float64 M_r (C x d).  Uses a stored table written by ``write_table`` (by
+    this module, see tests/golden/make_fc_tables.py) when ``table_dir`` holds
+    one, for hosts without mpmath; else builds it."""
     if M is None:
         M = default_bandwidth(d, C)
     if table_dir is not None:

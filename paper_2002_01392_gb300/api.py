@@ -1,0 +1,157 @@
+"""Thin Python binding of the libfcns C ABI (argument marshalling only).
+
+Every numerical step runs in the CUDA kernels of ``libfcns.so``; this module
+checks tensor dtypes / shapes / devices, passes raw device pointers and the
+current CUDA stream, and turns status codes into exceptions.  If the library
+is missing the import fails: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfcns.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libfcns.so not built ({LIB_PATH}); run __graft_entry__.build()")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+FC_F32, FC_F64 = 0, 1
+
+_c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+
+
+class FcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        name = _lib.fc_status_str(status).decode()
+        detail = _lib.fc_last_error().decode()
+        super().__init__(f"{where}: {name} ({detail})")
+        self.status = status
+        self.name = name
+
+
+class NsParams(ctypes.Structure):
+    _fields_ = [("Nx", _c_int), ("Ny", _c_int), ("Nz", _c_int), ("d", _c_int), ("C", _c_int),
+                ("nfields", _c_int), ("rk_order", _c_int),
+                ("Lx", _c_double), ("Ly", _c_double), ("Lz", _c_double),
+                ("nu", _c_double), ("kappa", _c_double), ("gamma", _c_double), ("forcing_x", _c_double),
+                ("filter", _c_int), ("filter_beta", _c_double), ("filter_2p", _c_double),
+                ("prec", _c_int)]
+
+
+def _sig(name, args, res=_c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_lib.fc_status_str.argtypes = [_c_int]
+_lib.fc_status_str.restype = ctypes.c_char_p
+_lib.fc_last_error.argtypes = []
+_lib.fc_last_error.restype = ctypes.c_char_p
+_sig("fc_setup", [_c_int, _c_int, _c_int, ctypes.POINTER(_vp)])
+_sig("fc_setup_ex", [_c_int, _c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_vp)])
+_sig("fc_plan_matrix", [_vp, ctypes.POINTER(_c_double)])
+_sig("fc_plan_info", [_vp] + [ctypes.POINTER(_c_int)] * 5 + [ctypes.POINTER(_c_double)])
+_sig("fc_destroy", [_vp])
+_sig("fc_deriv_z", [_vp, _c_int, _c_int, _c_int, _c_int, _c_double, _vp, _vp, _vp, _vp])
+
+EXPORTED = ["fc_status_str", "fc_last_error", "fc_setup", "fc_setup_ex", "fc_plan_matrix", "fc_plan_info",
+            "fc_destroy", "fc_deriv_z", "ns_params_default", "ns_workspace_bytes", "ns_create", "ns_destroy",
+            "ns_set_fields", "ns_get_fields", "ns_get_state", "ns_put_state", "ns_get_wall_gradp",
+            "ns_put_wall_gradp", "ns_rhs", "fc_poisson_project", "rk_step", "ns_diagnostics"]
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise FcError(status, where)
+
+
+def _stream(stream=None) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return FC_F32
+    if t.dtype == torch.float64:
+        return FC_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+class Plan:
+    """FC-Gram continuation plan (``fc_setup``)."""
+
+    def __init__(self, d: int, C: int, Nz: int, M: int | None = None, n_os: int | None = None):
+        h = _vp()
+        if M is None and n_os is None:
+            _check(_lib.fc_setup(d, C, Nz, ctypes.byref(h)), "fc_setup")
+        else:
+            M = (2 * (d + C)) // 3 if M is None else M
+            n_os = 20 if n_os is None else n_os
+            _check(_lib.fc_setup_ex(d, C, Nz, M, n_os, ctypes.byref(h)), "fc_setup_ex")
+        self.handle = h
+        self.d, self.C, self.Nz = d, C, Nz
+
+    def matrix(self):
+        import numpy as np
+        out = np.empty((self.C, self.d), dtype=np.float64)
+        _check(_lib.fc_plan_matrix(self.handle, out.ctypes.data_as(ctypes.POINTER(_c_double))), "fc_plan_matrix")
+        return out
+
+    def info(self):
+        vals = [_c_int() for _ in range(5)]
+        res = _c_double()
+        _check(_lib.fc_plan_info(self.handle, *[ctypes.byref(v) for v in vals], ctypes.byref(res)), "fc_plan_info")
+        d, C, Nz, M, n_os = (v.value for v in vals)
+        return dict(d=d, C=C, Nz=Nz, M=M, n_os=n_os, ls_residual=res.value)
+
+    def close(self):
+        if self.handle:
+            _lib.fc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fc_setup(d: int, C: int, Nz: int) -> Plan:
+    return Plan(d, C, Nz)
+
+
+def fc_deriv_z(plan: Plan, f, df=None, d2f=None, Lz: float = 1.0, stream=None):
+    """z-derivatives of f [batch][Nz][Ny][Nx] (or [Nz][Ny][Nx]) on the GPU."""
+    if f.dim() == 3:
+        f = f.unsqueeze(0)
+        df = df.unsqueeze(0) if df is not None else None
+        d2f = d2f.unsqueeze(0) if d2f is not None else None
+    if f.dim() != 4 or f.shape[1] != plan.Nz:
+        raise ValueError("f must be [batch][Nz][Ny][Nx] with Nz = plan.Nz")
+    if not f.is_cuda:
+        raise ValueError("f must be a CUDA tensor")
+    for o in (df, d2f):
+        if o is not None and (o.shape != f.shape or o.dtype != f.dtype or o.device != f.device):
+            raise ValueError("outputs must match f in shape, dtype and device")
+    B, _, Ny, Nx = f.shape
+    _check(_lib.fc_deriv_z(plan.handle, _dtype_code(f), B, Nx, Ny, float(Lz), _ptr(f), _ptr(df), _ptr(d2f),
+                           _stream(stream)), "fc_deriv_z")
+    return df, d2f

@@ -1,0 +1,179 @@
+// C ABI of libfcns: argument validation, plan objects, dispatch to launchers.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "host_tables.hpp"
+#include "internal.hpp"
+
+namespace fcns {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+fc_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FC_OK;
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? FC_ERR_NOMEM : FC_ERR_CUDA;
+}
+
+struct PlanHostTables {
+  int L = 0, L1 = 0, L2 = 0;
+  std::vector<std::complex<double>> H, tw;
+};
+
+}  // namespace fcns
+
+struct fc_plan {
+  fcns::PlanData data;
+  fcns::PlanHostTables deriv;
+};
+
+using namespace fcns;
+
+extern "C" {
+
+const char* fc_status_str(fc_status s) {
+  switch (s) {
+    case FC_OK: return "FC_OK";
+    case FC_ERR_ARG: return "FC_ERR_ARG";
+    case FC_ERR_UNSUPPORTED: return "FC_ERR_UNSUPPORTED";
+    case FC_ERR_CUDA: return "FC_ERR_CUDA";
+    case FC_ERR_NOMEM: return "FC_ERR_NOMEM";
+    case FC_ERR_TIMEOUT: return "FC_ERR_TIMEOUT";
+    case FC_ERR_NONFINITE: return "FC_ERR_NONFINITE";
+    case FC_ERR_STATE: return "FC_ERR_STATE";
+  }
+  return "FC_ERR_UNKNOWN";
+}
+
+const char* fc_last_error(void) { return g_last_error.c_str(); }
+
+fc_status fc_setup_ex(int d, int C, int Nz, int M, int n_os, fc_plan_t* out) {
+  if (!out) { set_error("fc_setup: out is NULL"); return FC_ERR_ARG; }
+  *out = nullptr;
+  if (d < 2 || d > 10 || C < d || C > 64 || Nz < 2 * d || M < 1 || n_os < 1 || 2 * M + 1 > 2 * ((d - 1) * n_os + 1)) {
+    set_error("fc_setup: invalid d, C, Nz, M or n_os");
+    return FC_ERR_ARG;
+  }
+  fc_plan* p = new (std::nothrow) fc_plan;
+  if (!p) return FC_ERR_NOMEM;
+  FcTables T;
+  if (!build_fc_tables(d, C, M, n_os, &T)) { delete p; set_error("fc_setup: table construction failed"); return FC_ERR_ARG; }
+  p->data.d = d; p->data.C = C; p->data.Nz = Nz; p->data.Np = Nz + C;
+  p->data.M = M; p->data.n_os = n_os; p->data.ls_residual = T.ls_residual;
+  p->data.Mr = T.Mr;
+  const int need = p->data.Np + Nz - 1;
+  const int L = pick_engine_length(need);
+  if (L > 0) {
+    for (auto& s : engine_shapes())
+      if (s.L == L) { p->deriv.L = L; p->deriv.L1 = s.L1; p->deriv.L2 = s.L2; }
+    deriv_conv_spectrum(Nz, p->data.Np, L, &p->deriv.H);
+    engine_twiddles(p->deriv.L1, p->deriv.L2, &p->deriv.tw);
+  }
+  *out = p;
+  return FC_OK;
+}
+
+fc_status fc_setup(int d, int C, int Nz, fc_plan_t* out) {
+  return fc_setup_ex(d, C, Nz, (2 * (d + C)) / 3, 20, out);
+}
+
+fc_status fc_plan_matrix(fc_plan_t plan, double* Mr_out) {
+  if (!plan || !Mr_out) { set_error("fc_plan_matrix: NULL argument"); return FC_ERR_ARG; }
+  std::memcpy(Mr_out, plan->data.Mr.data(), sizeof(double) * plan->data.Mr.size());
+  return FC_OK;
+}
+
+fc_status fc_plan_info(fc_plan_t plan, int* d, int* C, int* Nz, int* M, int* n_os, double* ls_residual) {
+  if (!plan) { set_error("fc_plan_info: NULL plan"); return FC_ERR_ARG; }
+  if (d) *d = plan->data.d;
+  if (C) *C = plan->data.C;
+  if (Nz) *Nz = plan->data.Nz;
+  if (M) *M = plan->data.M;
+  if (n_os) *n_os = plan->data.n_os;
+  if (ls_residual) *ls_residual = plan->data.ls_residual;
+  return FC_OK;
+}
+
+fc_status fc_destroy(fc_plan_t plan) {
+  if (!plan) return FC_ERR_ARG;
+  int cur = -1;
+  if (!plan->data.dev.empty() && cudaGetDevice(&cur) == cudaSuccess) {
+    for (auto& t : plan->data.dev) {
+      cudaSetDevice(t.device);
+      cudaDeviceSynchronize();
+      cudaFree(t.Mr); cudaFree(t.H32); cudaFree(t.H64); cudaFree(t.tw32); cudaFree(t.tw64);
+    }
+    cudaSetDevice(cur);
+  }
+  delete plan;
+  return FC_OK;
+}
+
+}  // extern "C"
+
+namespace fcns {
+
+template <class C>
+static fc_status upload(const std::vector<std::complex<double>>& v, void** dst) {
+  std::vector<C> h(v.size());
+  for (size_t i = 0; i < v.size(); ++i) { h[i].x = (decltype(h[i].x))v[i].real(); h[i].y = (decltype(h[i].y))v[i].imag(); }
+  fc_status s = cuda_status(cudaMalloc(dst, sizeof(C) * h.size()), "cudaMalloc(tables)");
+  if (s) return s;
+  return cuda_status(cudaMemcpy(*dst, h.data(), sizeof(C) * h.size(), cudaMemcpyHostToDevice), "cudaMemcpy(tables)");
+}
+
+static fc_status deriv_tables_locked(fc_plan* plan, DerivDevTables** out) {
+  int dev = -1;
+  fc_status s = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+  if (s) return s;
+  for (auto& t : plan->data.dev)
+    if (t.device == dev) { *out = &t; return FC_OK; }
+  DerivDevTables t;
+  t.device = dev;
+  t.L = plan->deriv.L;
+  s = cuda_status(cudaMalloc((void**)&t.Mr, sizeof(double) * plan->data.Mr.size()), "cudaMalloc(Mr)");
+  if (!s) s = cuda_status(cudaMemcpy(t.Mr, plan->data.Mr.data(), sizeof(double) * plan->data.Mr.size(),
+                                     cudaMemcpyHostToDevice), "cudaMemcpy(Mr)");
+  if (!s) s = upload<float2>(plan->deriv.H, &t.H32);
+  if (!s) s = upload<double2>(plan->deriv.H, &t.H64);
+  if (!s) s = upload<float2>(plan->deriv.tw, &t.tw32);
+  if (!s) s = upload<double2>(plan->deriv.tw, &t.tw64);
+  if (s) {
+    cudaFree(t.Mr); cudaFree(t.H32); cudaFree(t.H64); cudaFree(t.tw32); cudaFree(t.tw64);
+    return s;
+  }
+  plan->data.dev.push_back(t);
+  *out = &plan->data.dev.back();
+  return FC_OK;
+}
+
+}  // namespace fcns
+
+extern "C" fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
+                                const void* f, void* df, void* d2f, fc_stream_t stream) {
+  if (!plan || !f || (!df && !d2f)) { set_error("fc_deriv_z: NULL plan, input or both outputs"); return FC_ERR_ARG; }
+  if (dtype != FC_F32 && dtype != FC_F64) { set_error("fc_deriv_z: bad dtype"); return FC_ERR_ARG; }
+  if (batch < 1 || Nx < 1 || Ny < 1 || !(Lz > 0) || !std::isfinite(Lz)) { set_error("fc_deriv_z: bad sizes"); return FC_ERR_ARG; }
+  const long long lines = (long long)Nx * Ny;
+  if (lines * batch >= (1LL << 31)) { set_error("fc_deriv_z: too many lines"); return FC_ERR_UNSUPPORTED; }
+  if (plan->deriv.L == 0) { set_error("fc_deriv_z: N' + Nz - 1 exceeds the compiled transform lengths"); return FC_ERR_UNSUPPORTED; }
+  const size_t es = dtype == FC_F32 ? 4 : 8;
+  const size_t bytes = es * (size_t)lines * plan->data.Nz * batch;
+  auto overlap = [&](const void* a, const void* b) {
+    if (!a || !b) return false;
+    const char* x = (const char*)a; const char* y = (const char*)b;
+    return x < y + bytes && y < x + bytes;
+  };
+  if (overlap(f, df) || overlap(f, d2f) || overlap(df, d2f)) { set_error("fc_deriv_z: overlapping buffers"); return FC_ERR_ARG; }
+  DerivDevTables* t = nullptr;
+  fc_status s;
+  {
+    std::lock_guard<std::mutex> lk(plan->data.mtx);
+    s = deriv_tables_locked(plan, &t);
+  }
+  if (s) return s;
+  return launch_deriv_z(*t, plan->data, dtype, batch, lines, Lz, f, df, d2f, (cudaStream_t)stream);
+}

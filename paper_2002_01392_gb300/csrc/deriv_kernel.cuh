@@ -1,0 +1,141 @@
+// fc_deriv_z: FC-Gram first and second z-derivatives of real fields.
+//
+// Per z-line (Sec. 3 continuation + Sec. 4.2 spectral derivative): the N'-point
+// continued line x = [f; M_r f_last + M_l f_first] is convolved circularly with
+// the derivative kernels d1 + i d2 of the N'-periodic grid.  Only outputs
+// n < Nz are needed, so the circular convolution of length N' is computed as a
+// circular convolution of length L >= N' + Nz - 1 (one forward and one inverse
+// FFT of length L, kernel spectrum precomputed), and Re / Im of the result are
+// the first / second derivative.
+//
+// Thread layout: tid = r * LINES + li, li = line within the tile (lines are
+// adjacent in memory, so every global access is coalesced across li).
+// FFT of length L = L1 * L2 in two register passes with one shared-memory
+// exchange each way:  input index n = n2 + L2 n1 lives in thread r = n2;
+// frequency k = k1 + L1 k2 lives in thread r = k1.
+#pragma once
+#include "phases.cuh"
+
+namespace fcns {
+
+template <class T, int L1_, int L2_, int LINES_>
+struct DerivConv {
+  static constexpr int L1 = L1_, L2 = L2_, L = L1 * L2, LINES = LINES_;
+  static constexpr int G = L1 > L2 ? L1 : L2;
+  static constexpr int THREADS = G * LINES;
+  static constexpr int NPHASE = 4;
+  static constexpr int MR_MAX = 640;  // C * d <= 64 * 10
+  static constexpr int DMAX = 10;
+  using C = cx<T>;
+
+  struct Args {
+    const T* f;
+    T* df;
+    T* d2f;
+    int Nz, Np, d, Cc;
+    long long lines;           // lines per field (Nx * Ny)
+    long long tiles;           // tiles per field
+    long long zstride;         // elements between consecutive z
+    long long bstride;         // elements between fields
+    T s1, s2;                  // 1/dz, 1/dz^2
+    const double* Mr;          // C x d
+    const C* H;                // kernel spectrum, natural order, length L
+    const C* tw;               // tw[n2 * L1 + k1] = e^{-2 pi i n2 k1 / L}
+  };
+
+  struct Regs {
+    C v[L1];
+    C u[L2];
+  };
+
+  // shared memory layout
+  static constexpr size_t off_buf = 0;
+  static constexpr size_t off_H = off_buf + sizeof(C) * L * LINES;
+  static constexpr size_t off_tw = off_H + sizeof(C) * L;
+  static constexpr size_t off_M = off_tw + sizeof(C) * L;
+  static constexpr size_t off_E = off_M + sizeof(double) * MR_MAX;
+  static constexpr size_t smem_bytes = off_E + sizeof(double) * LINES * 2 * DMAX;
+
+  static FC_HD int bidx(int k1, int n2, int li) { return (k1 * L2 + n2) * LINES + li; }
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
+    C* buf = reinterpret_cast<C*>(sm + off_buf);
+    C* Hs = reinterpret_cast<C*>(sm + off_H);
+    C* tws = reinterpret_cast<C*>(sm + off_tw);
+    double* Ms = reinterpret_cast<double*>(sm + off_M);
+    double* E = reinterpret_cast<double*>(sm + off_E);
+    const int r = tid / LINES, li = tid % LINES;
+    const long long field = bid / a.tiles;
+    const long long line = (bid % a.tiles) * LINES + li;
+    const bool valid = line < a.lines;
+    const long long base = field * a.bstride + line;
+
+    if constexpr (P == 0) {
+      for (int i = tid; i < L; i += THREADS) { Hs[i] = a.H[i]; tws[i] = a.tw[i]; }
+      for (int i = tid; i < a.Cc * a.d; i += THREADS) Ms[i] = a.Mr[i];
+      if (r < L2) {
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          T x = T(0);
+          if (valid && n < a.Nz) x = a.f[base + (long long)n * a.zstride];
+          R.v[j] = mk<T>(x, T(0));
+          if (n < a.d) E[li * 2 * DMAX + n] = (double)x;
+          if (n >= a.Nz - a.d && n < a.Nz) E[li * 2 * DMAX + DMAX + (n - (a.Nz - a.d))] = (double)x;
+        }
+      }
+    } else if constexpr (P == 1) {
+      if (r < L2) {
+        const double* first = E + li * 2 * DMAX;
+        const double* last = first + DMAX;
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          if (n >= a.Nz && n < a.Np) {
+            const int jj = n - a.Nz;
+            double c = 0.0;
+            for (int i = 0; i < a.d; ++i) {
+              c += Ms[jj * a.d + i] * last[i];
+              c += Ms[(a.Cc - 1 - jj) * a.d + (a.d - 1 - i)] * first[i];
+            }
+            R.v[j] = mk<T>((T)c, T(0));
+          }
+        }
+        dft_reg<L1, -1, T>(R.v);
+#pragma unroll
+        for (int k1 = 0; k1 < L1; ++k1) buf[bidx(k1, r, li)] = cmul(R.v[k1], tws[r * L1 + k1]);
+      }
+    } else if constexpr (P == 2) {
+      if (r < L1) {
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) R.u[n2] = buf[bidx(r, n2, li)];
+        dft_reg<L2, -1, T>(R.u);
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(R.u[k2], Hs[r + L1 * k2]);
+        dft_reg<L2, 1, T>(R.u);
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) buf[bidx(r, n2, li)] = cmulc(R.u[n2], tws[n2 * L1 + r]);
+      }
+    } else if constexpr (P == 3) {
+      if (r < L2) {
+#pragma unroll
+        for (int k1 = 0; k1 < L1; ++k1) R.v[k1] = buf[bidx(k1, r, li)];
+        dft_reg<L1, 1, T>(R.v);
+        if (valid) {
+#pragma unroll
+          for (int j = 0; j < L1; ++j) {
+            const int n = r + L2 * j;
+            if (n < a.Nz) {
+              const long long o = base + (long long)n * a.zstride;
+              if (a.df) a.df[o] = R.v[j].x * a.s1;
+              if (a.d2f) a.d2f[o] = R.v[j].y * a.s2;
+            }
+          }
+        }
+      }
+    }
+  }
+};
+
+}  // namespace fcns

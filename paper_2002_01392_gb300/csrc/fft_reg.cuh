@@ -1,0 +1,193 @@
+// Register-resident small DFTs with compile-time twiddles.
+//
+// A transform of length N = R1 R2 ... Rm is done as m Stockham autosort
+// passes over a register array (all indices compile-time constants after
+// template expansion, so the arrays stay in registers).  Twiddle factors are
+// evaluated at compile time by kcos2pi/ksin2pi (octant reduction + Taylor
+// series written out below), so they become immediates.
+#pragma once
+#include <cuda_runtime.h>
+#include <type_traits>
+#include <utility>
+
+namespace fcns {
+
+template <class T> struct V2;
+template <> struct V2<float> { using t = float2; };
+template <> struct V2<double> { using t = double2; };
+template <class T> using cx = typename V2<T>::t;
+
+template <class T> __host__ __device__ __forceinline__ cx<T> mk(T a, T b) { cx<T> r; r.x = a; r.y = b; return r; }
+template <class C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <class C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <class C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <class C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {  // a * conj(b)
+  C r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
+}
+template <class C, class S> __host__ __device__ __forceinline__ C cscale(C a, S s) { a.x *= s; a.y *= s; return a; }
+// multiply by sign * i
+template <int SIGN, class C> __host__ __device__ __forceinline__ C mul_si(C a) {
+  C r;
+  if (SIGN > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// compile-time cos / sin of 2 pi num / den
+// ---------------------------------------------------------------------------
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+constexpr double taylor_sin(double x) {  // |x| <= pi/4
+  double x2 = x * x, term = x, sum = x;
+  for (int n = 1; n < 14; ++n) { term *= -x2 / double((2 * n) * (2 * n + 1)); sum += term; }
+  return sum;
+}
+constexpr double taylor_cos(double x) {
+  double x2 = x * x, term = 1.0, sum = 1.0;
+  for (int n = 1; n < 14; ++n) { term *= -x2 / double((2 * n - 1) * (2 * n)); sum += term; }
+  return sum;
+}
+// Nearest quarter turn m, residual fraction rho in [-1/8, 1/8] of a turn.
+constexpr void quarter_reduce(long long num, long long den, int& m, double& psi) {
+  long long r = ((num % den) + den) % den;       // [0, den)
+  long long m4 = (4 * r * 2 + den) / (2 * den);  // round(4 r / den)
+  long long resid = 4 * r - m4 * den;            // in [-den/2, den/2]
+  m = int(m4 & 3);
+  psi = kTwoPi * (double(resid) / double(4 * den));
+}
+constexpr double kcos2pi(long long num, long long den) {
+  int m = 0; double psi = 0;
+  quarter_reduce(num, den, m, psi);
+  return m == 0 ? taylor_cos(psi) : m == 1 ? -taylor_sin(psi) : m == 2 ? -taylor_cos(psi) : taylor_sin(psi);
+}
+constexpr double ksin2pi(long long num, long long den) {
+  int m = 0; double psi = 0;
+  quarter_reduce(num, den, m, psi);
+  return m == 0 ? taylor_sin(psi) : m == 1 ? taylor_cos(psi) : m == 2 ? -taylor_sin(psi) : -taylor_cos(psi);
+}
+
+// ---------------------------------------------------------------------------
+// compile-time loops
+// ---------------------------------------------------------------------------
+template <int I, int E> struct SFor {
+  template <class F> __host__ __device__ __forceinline__ static void run(F&& f) {
+    if constexpr (I < E) {
+      f(std::integral_constant<int, I>{});
+      SFor<I + 1, E>::run(f);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// radix butterflies (natural order in / out), SIGN = -1 forward, +1 inverse
+// ---------------------------------------------------------------------------
+template <int R, int SIGN, class T> struct Radix;
+
+template <int SIGN, class T> struct Radix<2, SIGN, T> {
+  __host__ __device__ __forceinline__ static void run(cx<T>* v) {
+    cx<T> a = v[0], b = v[1];
+    v[0] = cadd(a, b); v[1] = csub(a, b);
+  }
+};
+template <int SIGN, class T> struct Radix<3, SIGN, T> {
+  __host__ __device__ __forceinline__ static void run(cx<T>* v) {
+    constexpr T h = T(0.5);
+    constexpr T s = T(0.86602540378443864676372317075294);  // sin(2 pi / 3)
+    cx<T> a = v[0], b = v[1], c = v[2];
+    cx<T> t1 = cadd(b, c);
+    cx<T> t2 = csub(a, cscale(t1, h));
+    cx<T> t3 = cscale(mul_si<SIGN>(csub(b, c)), s);
+    v[0] = cadd(a, t1);
+    v[1] = cadd(t2, t3);
+    v[2] = csub(t2, t3);
+  }
+};
+template <int SIGN, class T> struct Radix<4, SIGN, T> {
+  __host__ __device__ __forceinline__ static void run(cx<T>* v) {
+    cx<T> a = v[0], b = v[1], c = v[2], d = v[3];
+    cx<T> s0 = cadd(a, c), d0 = csub(a, c), s1 = cadd(b, d), d1 = mul_si<SIGN>(csub(b, d));
+    v[0] = cadd(s0, s1); v[2] = csub(s0, s1);
+    v[1] = cadd(d0, d1); v[3] = csub(d0, d1);
+  }
+};
+template <int SIGN, class T> struct Radix<5, SIGN, T> {
+  __host__ __device__ __forceinline__ static void run(cx<T>* v) {
+    constexpr T c1 = T(0.30901699437494742410229341718282);   // cos(2 pi/5)
+    constexpr T c2 = T(-0.80901699437494742410229341718282);  // cos(4 pi/5)
+    constexpr T s1 = T(0.95105651629515357211643933337938);   // sin(2 pi/5)
+    constexpr T s2 = T(0.58778525229247312916870595463907);   // sin(4 pi/5)
+    cx<T> a0 = v[0];
+    cx<T> p1 = cadd(v[1], v[4]), m1 = csub(v[1], v[4]);
+    cx<T> p2 = cadd(v[2], v[3]), m2 = csub(v[2], v[3]);
+    cx<T> r1 = cadd(a0, cadd(cscale(p1, c1), cscale(p2, c2)));
+    cx<T> r2 = cadd(a0, cadd(cscale(p1, c2), cscale(p2, c1)));
+    cx<T> i1 = mul_si<SIGN>(cadd(cscale(m1, s1), cscale(m2, s2)));
+    cx<T> i2 = mul_si<SIGN>(csub(cscale(m1, s2), cscale(m2, s1)));
+    v[0] = cadd(a0, cadd(p1, p2));
+    v[1] = cadd(r1, i1); v[4] = csub(r1, i1);
+    v[2] = cadd(r2, i2); v[3] = csub(r2, i2);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// radix schedule: prefer 4, then 2, 3, 5
+// ---------------------------------------------------------------------------
+constexpr int first_radix(int n) {
+  return (n % 4 == 0 && n != 8) ? 4 : (n % 2 == 0) ? 2 : (n % 3 == 0) ? 3 : (n % 5 == 0) ? 5 : n;
+}
+constexpr bool smooth235(int n) {
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  while (n % 5 == 0) n /= 5;
+  return n == 1;
+}
+
+// One Stockham pass with radix R at stage Ns over arrays in -> out (length N).
+template <int N, int R, int NS, int SIGN, class T>
+__host__ __device__ __forceinline__ void stockham_pass(const cx<T>* in, cx<T>* out) {
+  SFor<0, N / R>::run([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    cx<T> v[R];
+    SFor<0, R>::run([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      v[r] = in[j + r * (N / R)];
+      if constexpr (NS > 1 && r > 0 && ((j % NS) * r) != 0) {
+        constexpr long long num = (long long)r * (j % NS);
+        constexpr long long den = (long long)NS * R;
+        constexpr T c = T(kcos2pi(num, den));
+        constexpr T s = T(SIGN * ksin2pi(num, den));
+        v[r] = cmul(v[r], mk<T>(c, s));
+      }
+    });
+    Radix<R, SIGN, T>::run(v);
+    constexpr int idxD = (j / NS) * NS * R + (j % NS);
+    SFor<0, R>::run([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      out[idxD + r * NS] = v[r];
+    });
+  });
+}
+
+template <int N, int REM, int NS, int SIGN, class T>
+__host__ __device__ __forceinline__ void stockham_all(cx<T>* a) {
+  if constexpr (REM > 1) {
+    constexpr int R = first_radix(REM);
+    static_assert(R == 2 || R == 3 || R == 4 || R == 5, "length must be 2^a 3^b 5^c");
+    cx<T> tmp[N];
+    stockham_pass<N, R, NS, SIGN, T>(a, tmp);
+    SFor<0, N>::run([&](auto ic) { constexpr int i = decltype(ic)::value; a[i] = tmp[i]; });
+    stockham_all<N, REM / R, NS * R, SIGN, T>(a);
+  }
+}
+
+// In-place DFT of length N on a register array, natural order in and out.
+// SIGN = -1: X_k = sum x_n e^{-2 pi i nk/N};  SIGN = +1: unnormalised inverse.
+template <int N, int SIGN, class T>
+__host__ __device__ __forceinline__ void dft_reg(cx<T> (&a)[N]) {
+  static_assert(smooth235(N), "register DFT needs a 2/3/5-smooth length");
+  stockham_all<N, N, 1, SIGN, T>(a);
+}
+
+}  // namespace fcns

@@ -1,0 +1,319 @@
+// Host-side tables in binary128 arithmetic.
+//
+// FC-Gram tables follow App. B of the paper: Gram basis from the QR
+// factorisation of the Vandermonde matrix of the d matching points (the basis
+// orthonormal for the discrete inner product over those points), and
+// blend-to-zero continuations of every Gram polynomial obtained as
+// oversampled least-squares trigonometric fits with periodicity interval
+// [1 - delta_r, 2b - (1 - delta_r)] (2(d + C) grid spacings).  The right-end
+// matrix is M_r = A_r Q_r^T (App. B, eq. Af).
+#include "host_tables.hpp"
+
+#include <cmath>
+
+namespace fcns {
+
+typedef _Float128 q;
+
+static q q_abs(q x) { return x < 0 ? -x : x; }
+
+static q q_sqrt(q x) {
+  if (x <= 0) return 0;
+  q y = (q)std::sqrt((double)x);
+  for (int i = 0; i < 4; ++i) y = (y + x / y) / 2;
+  return y;
+}
+
+// atan(1/x) by its alternating series
+static q q_atan_inv(int x) {
+  q x2 = (q)x * (q)x, term = (q)1 / (q)x, sum = term;
+  const q tiny = (q)1e-40;
+  for (int k = 1; k < 400; ++k) {
+    term /= x2;
+    q t = term / (q)(2 * k + 1);
+    sum += (k & 1) ? -t : t;
+    if (t < tiny) break;
+  }
+  return sum;
+}
+
+static q q_pi() {
+  static const q pi = 16 * q_atan_inv(5) - 4 * q_atan_inv(239);  // Machin's formula
+  return pi;
+}
+
+static q taylor_sin(q x) {
+  q x2 = x * x, term = x, sum = x;
+  for (int n = 1; n < 30; ++n) { term *= -x2 / (q)((2 * n) * (2 * n + 1)); sum += term; }
+  return sum;
+}
+static q taylor_cos(q x) {
+  q x2 = x * x, term = 1, sum = 1;
+  for (int n = 1; n < 30; ++n) { term *= -x2 / (q)((2 * n - 1) * (2 * n)); sum += term; }
+  return sum;
+}
+
+// cos, sin of 2 pi num/den: exact reduction to the nearest quarter turn
+static void q_sincos2pi(long long num, long long den, q* c, q* s) {
+  long long r = ((num % den) + den) % den;
+  long long m4 = (8 * r + den) / (2 * den);
+  long long resid = 4 * r - m4 * den;
+  int m = int(m4 & 3);
+  q psi = 2 * q_pi() * ((q)resid / (q)(4 * den));
+  q cs = taylor_cos(psi), sn = taylor_sin(psi);
+  switch (m) {
+    case 0: *c = cs; *s = sn; break;
+    case 1: *c = -sn; *s = cs; break;
+    case 2: *c = -cs; *s = -sn; break;
+    default: *c = sn; *s = -cs; break;
+  }
+}
+
+void sincos2pi(long long num, long long den, double* c, double* s) {
+  q cq, sq;
+  q_sincos2pi(num, den, &cq, &sq);
+  *c = (double)cq;
+  *s = (double)sq;
+}
+
+// Householder QR least squares: minimise |A x - b| for A (m x n, m >= n),
+// several right-hand sides.  A is overwritten.
+static void lsq_solve(std::vector<q>& A, int m, int n, std::vector<std::vector<q>>& rhs,
+                      std::vector<std::vector<q>>* sol) {
+  std::vector<q> v(m);
+  for (int k = 0; k < n; ++k) {
+    q norm = 0;
+    for (int i = k; i < m; ++i) norm += A[i * n + k] * A[i * n + k];
+    norm = q_sqrt(norm);
+    q alpha = A[k * n + k] > 0 ? -norm : norm;
+    for (int i = 0; i < m; ++i) v[i] = 0;
+    v[k] = A[k * n + k] - alpha;
+    for (int i = k + 1; i < m; ++i) v[i] = A[i * n + k];
+    q vnorm2 = 0;
+    for (int i = k; i < m; ++i) vnorm2 += v[i] * v[i];
+    if (vnorm2 == 0) continue;
+    for (int j = k; j < n; ++j) {
+      q dot = 0;
+      for (int i = k; i < m; ++i) dot += v[i] * A[i * n + j];
+      q f = 2 * dot / vnorm2;
+      for (int i = k; i < m; ++i) A[i * n + j] -= f * v[i];
+    }
+    for (auto& b : rhs) {
+      q dot = 0;
+      for (int i = k; i < m; ++i) dot += v[i] * b[i];
+      q f = 2 * dot / vnorm2;
+      for (int i = k; i < m; ++i) b[i] -= f * v[i];
+    }
+  }
+  sol->assign(rhs.size(), std::vector<q>(n));
+  for (size_t r = 0; r < rhs.size(); ++r) {
+    auto& x = (*sol)[r];
+    for (int k = n - 1; k >= 0; --k) {
+      q s = rhs[r][k];
+      for (int j = k + 1; j < n; ++j) s -= A[k * n + j] * x[j];
+      x[k] = s / A[k * n + k];
+    }
+  }
+}
+
+bool build_fc_tables(int d, int C, int M, int n_os, FcTables* out) {
+  if (d < 2 || d > 10 || C < d || C > 64 || M < 1 || n_os < 1) return false;
+  const int P = 2 * (d + C);  // Fourier period in grid units
+  // --- Gram basis: Householder QR of the Vandermonde V[i][p] = t_i^p, t_i = i
+  std::vector<q> V(d * d);
+  for (int i = 0; i < d; ++i) {
+    q tp = 1;
+    for (int p = 0; p < d; ++p) { V[i * d + p] = tp; tp *= (q)i; }
+  }
+  // modified Gram-Schmidt in binary128 on the columns gives Q (d x d) and R
+  std::vector<q> Qm(d * d), R(d * d, 0);
+  for (int k = 0; k < d; ++k) {
+    std::vector<q> col(d);
+    for (int i = 0; i < d; ++i) col[i] = V[i * d + k];
+    for (int pass = 0; pass < 2; ++pass)  // re-orthogonalise once
+      for (int j = 0; j < k; ++j) {
+        q dot = 0;
+        for (int i = 0; i < d; ++i) dot += Qm[i * d + j] * col[i];
+        R[j * d + k] += dot;
+        for (int i = 0; i < d; ++i) col[i] -= dot * Qm[i * d + j];
+      }
+    q nrm = 0;
+    for (int i = 0; i < d; ++i) nrm += col[i] * col[i];
+    nrm = q_sqrt(nrm);
+    R[k * d + k] = nrm;
+    for (int i = 0; i < d; ++i) Qm[i * d + k] = col[i] / nrm;
+  }
+  // polynomial coefficients of Gram polynomial k: Q = V R^{-1}, so c_k = column k of R^{-1}
+  std::vector<q> Rinv(d * d, 0);
+  for (int k = 0; k < d; ++k) {
+    // solve R x = e_k
+    for (int i = d - 1; i >= 0; --i) {
+      q s = (i == k) ? 1 : 0;
+      for (int j = i + 1; j < d; ++j) s -= R[i * d + j] * Rinv[j * d + k];
+      Rinv[i * d + k] = s / R[i * d + i];
+    }
+  }
+  auto gram_val = [&](int k, q t) {
+    q s = 0, tp = 1;
+    for (int p = 0; p < d; ++p) { s += Rinv[p * d + k] * tp; tp *= t; }
+    return s;
+  };
+  // --- least-squares system: points t = i/n_os on [0, d-1] and d+C + i/n_os
+  const int npt = (d - 1) * n_os + 1;
+  const int m = 2 * npt, n = 2 * M + 1;
+  if (m < n) return false;
+  std::vector<q> A(m * n);
+  std::vector<long long> tnum(m);  // t = tnum / n_os
+  for (int i = 0; i < npt; ++i) { tnum[i] = i; tnum[npt + i] = (long long)(d + C) * n_os + i; }
+  for (int r = 0; r < m; ++r) {
+    A[r * n] = 1;
+    for (int mm = 1; mm <= M; ++mm) {
+      q c, s;
+      q_sincos2pi((long long)mm * tnum[r], (long long)P * n_os, &c, &s);
+      A[r * n + 2 * mm - 1] = c;
+      A[r * n + 2 * mm] = s;
+    }
+  }
+  std::vector<q> Acopy = A;
+  std::vector<std::vector<q>> rhs(d, std::vector<q>(m, 0));
+  for (int k = 0; k < d; ++k)
+    for (int i = 0; i < npt; ++i) rhs[k][i] = gram_val(k, (q)tnum[i] / (q)n_os);
+  std::vector<std::vector<q>> rhs0 = rhs, sol;
+  lsq_solve(A, m, n, rhs, &sol);
+  // residuals
+  double worst = 0;
+  for (int k = 0; k < d; ++k) {
+    q rr = 0, bb = 0;
+    for (int r = 0; r < m; ++r) {
+      q s = 0;
+      for (int j = 0; j < n; ++j) s += Acopy[r * n + j] * sol[k][j];
+      q e = s - rhs0[k][r];
+      rr += e * e;
+      bb += rhs0[k][r] * rhs0[k][r];
+    }
+    double rel = (double)q_sqrt(rr / bb);
+    if (rel > worst) worst = rel;
+  }
+  // --- evaluate the continuations at t = d + j and form M_r = A_r Q^T
+  std::vector<q> Ar(C * d);
+  for (int j = 0; j < C; ++j) {
+    std::vector<q> row(n);
+    row[0] = 1;
+    for (int mm = 1; mm <= M; ++mm) {
+      q c, s;
+      q_sincos2pi((long long)mm * (d + j), P, &c, &s);
+      row[2 * mm - 1] = c;
+      row[2 * mm] = s;
+    }
+    for (int k = 0; k < d; ++k) {
+      q s = 0;
+      for (int jj = 0; jj < n; ++jj) s += row[jj] * sol[k][jj];
+      Ar[j * d + k] = s;
+    }
+  }
+  out->d = d; out->C = C; out->M = M; out->n_os = n_os;
+  out->ls_residual = worst;
+  out->Mr.assign(C * d, 0.0);
+  for (int j = 0; j < C; ++j)
+    for (int i = 0; i < d; ++i) {
+      q s = 0;
+      for (int k = 0; k < d; ++k) s += Ar[j * d + k] * Qm[i * d + k];
+      out->Mr[j * d + i] = (double)s;
+    }
+  return true;
+}
+
+// direct DFT helpers on binary128 with a root table
+struct Roots {
+  int N;
+  std::vector<q> c, s;  // exp(2 pi i m / N) = c[m] + i s[m]
+  explicit Roots(int N_) : N(N_), c(N_), s(N_) {
+    for (int m = 0; m < N; ++m) q_sincos2pi(m, N, &c[m], &s[m]);
+  }
+};
+
+void deriv_conv_spectrum(int Nz, int Np, int L, std::vector<std::complex<double>>* H) {
+  Roots rn(Np), rl(L);
+  const q twopi = 2 * q_pi();
+  // derivative kernels on the Np-periodic unit grid:
+  // d_o(j) = (1/Np) sum_l fac_o(l) e^{2 pi i l j / Np}
+  // fac_1 = i k (Nyquist zeroed), fac_2 = -k^2, k = 2 pi l_s / Np.
+  const int jlo = -(Np - 1), jhi = Nz - 1;
+  std::vector<q> d1(jhi - jlo + 1), d2(jhi - jlo + 1);
+  for (int j = jlo; j <= jhi; ++j) {
+    q s1 = 0, s2 = 0;
+    for (int l = 0; l < Np; ++l) {
+      int ls = (l <= (Np - 1) / 2) ? l : l - Np;  // signed index, Nyquist -> -Np/2
+      q k = twopi * (q)ls / (q)Np;
+      long long m = ((long long)l * j) % Np;
+      if (m < 0) m += Np;
+      // i k e^{i th} = i k (c + i s) -> real part -k s
+      bool nyq = (Np % 2 == 0) && (l == Np / 2);
+      if (!nyq) s1 += -k * rn.s[m];
+      s2 += -k * k * rn.c[m];
+    }
+    d1[j - jlo] = s1 / (q)Np;
+    d2[j - jlo] = s2 / (q)Np;
+  }
+  H->assign(L, std::complex<double>(0, 0));
+  for (int kk = 0; kk < L; ++kk) {
+    q re = 0, im = 0;
+    for (int j = jlo; j <= jhi; ++j) {
+      long long mm = (((long long)j % L) + L) % L;
+      long long e = (mm * kk) % L;  // e^{-2 pi i mm kk / L}
+      q c = rl.c[e], s = -rl.s[e];
+      q hr = d1[j - jlo], hi = d2[j - jlo];
+      re += hr * c - hi * s;
+      im += hr * s + hi * c;
+    }
+    (*H)[kk] = std::complex<double>((double)(re / (q)L), (double)(im / (q)L));
+  }
+}
+
+void bluestein_tables(int Np, int L, std::vector<std::complex<double>>* chirp,
+                      std::vector<std::complex<double>>* Hfwd, std::vector<std::complex<double>>* Hinv) {
+  Roots rl(L);
+  std::vector<q> wc(Np), ws(Np);  // chirp w_n = exp(-i pi n^2/Np) = exp(-2 pi i n^2 / (2 Np))
+  for (int nn = 0; nn < Np; ++nn) {
+    long long num = ((long long)nn * nn) % (2LL * Np);
+    q c, s;
+    q_sincos2pi(num, 2LL * Np, &c, &s);
+    wc[nn] = c;
+    ws[nn] = -s;
+  }
+  chirp->resize(Np);
+  for (int nn = 0; nn < Np; ++nn) (*chirp)[nn] = std::complex<double>((double)wc[nn], (double)ws[nn]);
+  // b[m mod L] = conj(w_|m|) for |m| < Np (forward); binv = w_|m|
+  Hfwd->assign(L, 0);
+  Hinv->assign(L, 0);
+  for (int kk = 0; kk < L; ++kk) {
+    q fr = 0, fi = 0, ir = 0, ii = 0;
+    for (int m = -(Np - 1); m <= Np - 1; ++m) {
+      int a = m < 0 ? -m : m;
+      long long mm = (((long long)m % L) + L) % L;
+      long long e = (mm * kk) % L;
+      q c = rl.c[e], s = -rl.s[e];  // e^{-2 pi i mm kk / L}
+      q br = wc[a], bi = -ws[a];   // conj(w)
+      fr += br * c - bi * s;
+      fi += br * s + bi * c;
+      q vr = wc[a], vi = ws[a];    // w
+      ir += vr * c - vi * s;
+      ii += vr * s + vi * c;
+    }
+    (*Hfwd)[kk] = std::complex<double>((double)(fr / (q)L), (double)(fi / (q)L));
+    (*Hinv)[kk] = std::complex<double>((double)(ir / (q)L), (double)(ii / (q)L));
+  }
+}
+
+void engine_twiddles(int L1, int L2, std::vector<std::complex<double>>* tw) {
+  const int L = L1 * L2;
+  tw->resize(L);
+  for (int n2 = 0; n2 < L2; ++n2)
+    for (int k1 = 0; k1 < L1; ++k1) {
+      q c, s;
+      q_sincos2pi((long long)n2 * k1, L, &c, &s);
+      (*tw)[n2 * L1 + k1] = std::complex<double>((double)c, (double)-s);
+    }
+}
+
+}  // namespace fcns

@@ -1,0 +1,39 @@
+// Host-side table construction in binary128 (_Float128).
+#pragma once
+#include <complex>
+#include <vector>
+
+namespace fcns {
+
+struct FcTables {
+  int d = 0, C = 0, M = 0, n_os = 0;
+  std::vector<double> Mr;  // C x d row-major, right-end continuation matrix
+  double ls_residual = 0;  // largest relative least-squares residual
+};
+
+// Gram-basis FC tables (App. B): QR of the Vandermonde on the d matching
+// points, oversampled trigonometric least squares per Gram polynomial,
+// M_r = A_r Q_r^T.  Returns false on invalid sizes.
+bool build_fc_tables(int d, int C, int M, int n_os, FcTables* out);
+
+// Spectrum (length L, natural frequency order, including the 1/L of the
+// inverse transform) of the length-L circular kernel whose convolution with
+// [f; continuation; 0...] returns, at n < Nz, d1 + i d2 where d1, d2 are the
+// first and second derivatives on the N'-periodic grid with unit spacing.
+// Requires L >= N' + Nz - 1.
+void deriv_conv_spectrum(int Nz, int Np, int L, std::vector<std::complex<double>>* H);
+
+// Bluestein tables for a length-Np DFT done with length-L transforms:
+// chirp[n] = exp(-i pi n^2 / Np) (n < Np) and the spectrum (with 1/L) of the
+// circular kernel b[m mod L] = conj(chirp[|m|]), |m| < Np.  For the inverse
+// DFT use conj(chirp) and the spectrum of chirp[|m|] (Hinv).
+void bluestein_tables(int Np, int L, std::vector<std::complex<double>>* chirp,
+                      std::vector<std::complex<double>>* Hfwd, std::vector<std::complex<double>>* Hinv);
+
+// Twiddles tw[n2 * L1 + k1] = exp(-2 pi i n2 k1 / L), L = L1 L2.
+void engine_twiddles(int L1, int L2, std::vector<std::complex<double>>* tw);
+
+// cos / sin of 2 pi num / den, correctly rounded to double from binary128.
+void sincos2pi(long long num, long long den, double* c, double* s);
+
+}  // namespace fcns

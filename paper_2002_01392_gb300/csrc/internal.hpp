@@ -1,0 +1,47 @@
+// Internal declarations shared by the C ABI and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <complex>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fcns.h"
+
+namespace fcns {
+
+void set_error(const std::string& msg);
+fc_status cuda_status(cudaError_t e, const char* what);
+
+// lengths of the two-pass line engine that are compiled: L = L1 * L2
+struct EngineShape { int L, L1, L2; };
+const std::vector<EngineShape>& engine_shapes();
+// smallest compiled L >= need (0 if none)
+int pick_engine_length(int need);
+
+// per-device copies of the derivative tables of one plan
+struct DerivDevTables {
+  int device = -1;
+  int L = 0;
+  double* Mr = nullptr;
+  void* H32 = nullptr;   // float2[L]
+  void* H64 = nullptr;   // double2[L]
+  void* tw32 = nullptr;  // float2[L]
+  void* tw64 = nullptr;  // double2[L]
+};
+
+struct PlanData {
+  int d, C, Nz, Np, M, n_os;
+  double ls_residual;
+  std::vector<double> Mr;
+  std::mutex mtx;
+  std::vector<DerivDevTables> dev;
+};
+
+fc_status deriv_tables_for_device(PlanData* p, DerivDevTables** out);
+
+fc_status launch_deriv_z(const DerivDevTables& t, const PlanData& p, fc_dtype dtype, int batch,
+                         long long lines, double Lz, const void* f, void* df, void* d2f,
+                         cudaStream_t stream);
+
+}  // namespace fcns

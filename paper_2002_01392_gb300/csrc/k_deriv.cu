@@ -1,0 +1,75 @@
+// Launchers of the fc_deriv_z kernels (float and double, every compiled L).
+#include "deriv_kernel.cuh"
+#include "internal.hpp"
+
+namespace fcns {
+
+namespace {
+
+template <class T, int L1, int L2, int LINES>
+fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long long lines, double Lz,
+                    const void* f, void* df, void* d2f, cudaStream_t stream) {
+  using K = DerivConv<T, L1, L2, LINES>;
+  static_assert(K::smem_bytes <= 227 * 1024, "shared memory budget");
+  typename K::Args a;
+  a.f = static_cast<const T*>(f);
+  a.df = static_cast<T*>(df);
+  a.d2f = static_cast<T*>(d2f);
+  a.Nz = p.Nz; a.Np = p.Np; a.d = p.d; a.Cc = p.C;
+  a.lines = lines;
+  a.tiles = (lines + LINES - 1) / LINES;
+  a.zstride = lines;
+  a.bstride = lines * p.Nz;
+  const double dz = Lz / (p.Nz - 1);
+  a.s1 = T(1.0 / dz);
+  a.s2 = T(1.0 / (dz * dz));
+  a.Mr = t.Mr;
+  a.H = static_cast<const cx<T>*>(sizeof(T) == 4 ? t.H32 : t.H64);
+  a.tw = static_cast<const cx<T>*>(sizeof(T) == 4 ? t.tw32 : t.tw64);
+  auto kern = phased_kernel<K>;
+  static bool attr_done = false;  // per instantiation; the attribute is per device but idempotent
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem_bytes);
+  (void)attr_done;
+  if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(fc_deriv_z)");
+  const long long grid = a.tiles * batch;
+  if (grid > 0x7fffffffLL) return FC_ERR_UNSUPPORTED;
+  kern<<<(unsigned)grid, K::THREADS, K::smem_bytes, stream>>>(a);
+  return cuda_status(cudaGetLastError(), "fc_deriv_z launch");
+}
+
+}  // namespace
+
+const std::vector<EngineShape>& engine_shapes() {
+  static const std::vector<EngineShape> s = {
+      {96, 8, 12}, {160, 10, 16}, {192, 12, 16}, {288, 16, 18}, {320, 16, 20}, {576, 24, 24}, {1080, 30, 36}};
+  return s;
+}
+
+int pick_engine_length(int need) {
+  for (auto& s : engine_shapes())
+    if (s.L >= need) return s.L;
+  return 0;
+}
+
+fc_status launch_deriv_z(const DerivDevTables& t, const PlanData& p, fc_dtype dtype, int batch,
+                         long long lines, double Lz, const void* f, void* df, void* d2f,
+                         cudaStream_t stream) {
+#define FC_CASE(LL, A, B, LF, LD)                                                                 \
+  case LL:                                                                                        \
+    return dtype == FC_F32 ? run_deriv<float, A, B, LF>(t, p, batch, lines, Lz, f, df, d2f, stream) \
+                           : run_deriv<double, A, B, LD>(t, p, batch, lines, Lz, f, df, d2f, stream);
+  switch (t.L) {
+    FC_CASE(96, 8, 12, 32, 16)
+    FC_CASE(160, 10, 16, 32, 16)
+    FC_CASE(192, 12, 16, 32, 16)
+    FC_CASE(288, 16, 18, 32, 16)
+    FC_CASE(320, 16, 20, 32, 16)
+    FC_CASE(576, 24, 24, 16, 8)
+    FC_CASE(1080, 30, 36, 16, 8)
+    default:
+      return FC_ERR_UNSUPPORTED;
+  }
+#undef FC_CASE
+}
+
+}  // namespace fcns

@@ -1,0 +1,82 @@
+"""C ABI: the library loads, exports every declared symbol, host-only calls work (CPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "fcns.h")
+
+
+@pytest.fixture(scope="session")
+def api():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2002_01392_gb300 import api as a
+    return a
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(?:fc_status|const char\*)\s+(\w+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(api):
+    names = declared_functions()
+    assert len(names) >= 20
+    lib = ctypes.CDLL(api.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(api.EXPORTED) == names
+
+
+def test_status_strings(api):
+    for code, name in enumerate(["FC_OK", "FC_ERR_ARG", "FC_ERR_UNSUPPORTED", "FC_ERR_CUDA", "FC_ERR_NOMEM",
+                                 "FC_ERR_TIMEOUT", "FC_ERR_NONFINITE", "FC_ERR_STATE"]):
+        assert api._lib.fc_status_str(code).decode() == name
+
+
+def test_fc_setup_tables_match_oracle(api, Mr_5_25):
+    """Library Gram/QR tables (binary128) vs oracle Lagrange tables (60 digits)."""
+    plan = api.Plan(5, 25, 33)
+    Mr = plan.matrix()
+    assert np.abs(Mr - Mr_5_25).max() / np.abs(Mr_5_25).max() < 1e-14
+    info = plan.info()
+    assert info["M"] == 20 and info["n_os"] == 20 and info["ls_residual"] < 1e-15
+
+
+def test_fc_setup_demo_tables(api, golden_dir):
+    from oracle import fc_tables
+    ref = fc_tables.fc_matrix(5, 15, table_dir=golden_dir)
+    Mr = api.Plan(5, 15, 49).matrix()
+    assert np.abs(Mr - ref).max() / np.abs(ref).max() < 1e-13
+
+
+@pytest.mark.parametrize("args", [(1, 25, 33), (5, 4, 33), (5, 25, 9), (11, 25, 33), (5, 65, 200)])
+def test_fc_setup_rejects_bad_sizes(api, args):
+    with pytest.raises(api.FcError) as e:
+        api.Plan(*args)
+    assert e.value.name == "FC_ERR_ARG"
+
+
+def test_fc_deriv_z_argument_checks_need_no_gpu(api):
+    plan = api.Plan(5, 25, 33)
+    st = api._lib.fc_deriv_z(plan.handle, 0, 1, 4, 4, 1.0, None, None, None, None)
+    assert api._lib.fc_status_str(st).decode() == "FC_ERR_ARG"
+    st = api._lib.fc_deriv_z(plan.handle, 7, 1, 4, 4, 1.0, 16, 32, None, None)
+    assert api._lib.fc_status_str(st).decode() == "FC_ERR_ARG"
+    st = api._lib.fc_deriv_z(plan.handle, 0, 1, 4, 4, -1.0, 16, 32, None, None)
+    assert api._lib.fc_status_str(st).decode() == "FC_ERR_ARG"
+    # overlapping input and output
+    st = api._lib.fc_deriv_z(plan.handle, 0, 1, 4, 4, 1.0, 4096, 4100, None, None)
+    assert api._lib.fc_status_str(st).decode() == "FC_ERR_ARG"
+
+
+def test_unsupported_length(api):
+    plan = api.Plan(5, 25, 700)          # N' + Nz - 1 = 1424 > 1080
+    st = api._lib.fc_deriv_z(plan.handle, 0, 1, 4, 4, 1.0, 16, 1 << 40, None, None)
+    assert api._lib.fc_status_str(st).decode() == "FC_ERR_UNSUPPORTED"

@@ -1,0 +1,51 @@
+"""Kernel index arithmetic checked on the CPU: the host-check library runs the
+same phase functions as the CUDA kernels, block by block, and is compared with
+the oracle (no GPU involved)."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import fc
+from numerics import norm_bound
+import synth
+
+HC = os.path.join(ROOT, "paper_2002_01392_gb300", "libfcns_hostcheck.so")
+
+
+@pytest.fixture(scope="session")
+def hc():
+    import __graft_entry__
+    __graft_entry__.build()
+    return ctypes.CDLL(HC)
+
+
+def _vp(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@pytest.mark.parametrize("Nz,L,Nx,Ny,B", [(33, 96, 5, 7, 2), (10, 96, 33, 1, 1), (65, 160, 40, 3, 1),
+                                           (129, 288, 33, 1, 1), (513, 1080, 17, 2, 1)])
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_deriv_kernel_phases_match_oracle(hc, Mr_5_25, Nz, L, Nx, Ny, B, dtype):
+    sf = synth.SeparableField(Nx, Ny, Nz, rank=3, seed_offset=Nz)
+    f = np.stack([sf.field(0)] * B) * np.arange(1, B + 1)[:, None, None, None]
+    npdt = np.float32 if dtype == 0 else np.float64
+    fin = np.ascontiguousarray(f.astype(npdt))
+    d1, d2 = np.zeros_like(fin), np.zeros_like(fin)
+    rc = hc.fchc_deriv_z(dtype, L, _vp(Mr_5_25), 5, 25, Nz, B, Nx, Ny, ctypes.c_double(1.0),
+                         _vp(fin), _vp(d1), _vp(d2))
+    assert rc == 0
+    Np = Nz + 25
+    kmax = np.pi * (Nz - 1)
+    # scale of the transformed data: the continued lines
+    xnorm = np.linalg.norm(fc.extend(fin.astype(np.float64), Mr_5_25, axis=1))
+    for order, out in ((1, d1), (2, d2)):
+        ref = fc.fc_deriv_z(fin.astype(np.float64), 1.0, Mr_5_25, order, axis=1)
+        en = np.linalg.norm(out - ref) / (xnorm * kmax ** order)
+        assert en < norm_bound(npdt, Nz), (order, en)
+        if dtype == 1:
+            rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+            assert rel < 1e-11 * max(1.0, (Np / 128) ** (2 * (order - 1))), (order, rel)
