@@ -82,7 +82,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def deriv_workload(dtype_np, B=3, Nx=512, Ny=512, Nz=513):
+DERIV_SHAPE = (3, 512, 512, 513)
+
+
+def deriv_workload(dtype_np, B=None, Nx=None, Ny=None, Nz=None):
+    B = B or DERIV_SHAPE[0]
+    Nx = Nx or DERIV_SHAPE[1]
+    Ny = Ny or DERIV_SHAPE[2]
+    Nz = Nz or DERIV_SHAPE[3]
     import synth
     fields = [synth.SeparableField(Nx, Ny, Nz, seed_offset=b) for b in range(B)]
     return fields, (B, Nz, Ny, Nx)
@@ -156,6 +163,72 @@ def bench_deriv(api, torch, dtype_np, steps, warmup, with_e2e=True):
     return res
 
 
+RK_SHAPE = (1024, 1024, 513)
+
+
+def bench_rk(api, torch, steps, warmup, with_e2e=True, shape=None):
+    """Boussinesq Rayleigh-Benard RK3 step (4 fields, FP32 transforms) on
+    1024 x 1024 x 513, Ra = 1e7, Pr = 1 (nu = kappa = sqrt(Pr/Ra) = 3.162e-4,
+    gamma = 1, Lz = 1).  Returns RK-stage grid-points/s = Nx Ny Nz o / t_step."""
+    import synth
+    Nx, Ny, Nz = shape or RK_SHAPE
+    kw = dict(nu=3.162e-4, kappa=3.162e-4, gamma=1.0)
+    p = api.ns_params(Nx=Nx, Ny=Ny, Nz=Nz, nfields=4, prec="f32", rk_order=3, **kw)
+    ws_bytes = api.ns_workspace_bytes(p)
+    sim = api.Sim(p)
+    host = synth.boussinesq_fields(Nx, Ny, Nz, dtype=np.float32)
+    f = torch.from_numpy(host).cuda()
+    sim.set_fields(f)
+    dt = 1e-3
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        sim.step(dt)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for i in range(steps):
+        ev[i][0].record(stream)
+        sim.step(dt)
+        ev[i][1].record(stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    times = np.array([x.elapsed_time(y) for x, y in ev]) * 1e-3
+    total = a0.elapsed_time(a1) * 1e-3
+    pts = Nx * Ny * Nz
+    res = {"grid": [Nx, Ny, Nz], "fields": 4, "rk_order": 3, "points": pts,
+           "seconds_per_step_mean": float(times.mean()), "p50_ms": float(np.percentile(times, 50) * 1e3),
+           "p99_ms": float(np.percentile(times, 99) * 1e3),
+           "rk_stage_grid_points_per_s": pts * 3 * steps / total, "workspace_GB": ws_bytes / 1e9,
+           "launches_per_step": 3 * 6}
+    out = sim.get_fields()
+    res["finite"] = bool(torch.isfinite(out).all().item())
+    res["w_wall_rel"] = float(out[2, [0, -1]].abs().max().item() / max(out[:3].abs().max().item(), 1e-300))
+    if with_e2e:
+        hp = torch.from_numpy(host).pin_memory()
+        ho = torch.empty_like(hp).pin_memory()
+        n_e2e = 2
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_e2e):
+            f.copy_(hp, non_blocking=True)
+            sim.set_fields(f)
+            sim.step(dt)
+            sim.get_fields(out)
+            ho.copy_(out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = e0.elapsed_time(e1) * 1e-3
+        res["e2e"] = {"value": pts * 3 * n_e2e / te, "unit": "RK-stage grid-points/s",
+                      "h2d_bytes_per_step": int(hp.numel() * 4), "d2h_bytes_per_step": int(ho.numel() * 4)}
+        del hp, ho
+    sim.close()
+    del f, out, host
+    torch.cuda.empty_cache()
+    return res
+
+
 def cpu_baseline_deriv(budget_s=12.0):
     """The FP64 oracle timed on a bounded sample of the same workload: z-lines of
     the 3 x 512^2 x 513 batch, as many as fit in ~budget_s seconds."""
@@ -187,6 +260,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--rk-steps", type=int, default=5)
+    ap.add_argument("--no-rk", action="store_true")
+    ap.add_argument("--profile-case", default=None, choices=["deriv32", "deriv64", "rk-small"],
+                    help="small single-kernel case for ncu: fc_deriv_z on 2x256x256x513, no e2e / CPU leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -212,10 +289,22 @@ def main():
     from paper_2002_01392_gb300 import api
     dev_index = torch.cuda.current_device()
     hbm_peak, peak_kind = _peaks()
+    if args.profile_case == "rk-small":
+        r = bench_rk(api, torch, args.steps, args.warmup, with_e2e=False, shape=(256, 256, 257))
+        print(json.dumps({"profile_case": args.profile_case, **r}))
+        return
+    if args.profile_case:
+        global DERIV_SHAPE
+        DERIV_SHAPE = (2, 256, 256, 513)
+        r = bench_deriv(api, torch, np.float32 if args.profile_case == "deriv32" else np.float64,
+                        args.steps, args.warmup, with_e2e=False)
+        print(json.dumps({"profile_case": args.profile_case, **r}))
+        return
     if world > 1:
         torch.distributed.barrier()
     with ClockSampler(dev_index) as clk:
         r32 = bench_deriv(api, torch, np.float32, args.steps, args.warmup)
+        rk = None if args.no_rk else bench_rk(api, torch, args.rk_steps, 3)
     r64 = bench_deriv(api, torch, np.float64, max(3, args.steps // 4), 2, with_e2e=False)
     value = r32["grid_points_per_s"]
     if world > 1:
@@ -230,6 +319,7 @@ def main():
                    "l2": "inputs 1.6 GB > L2, no flush", "parallelism": "replicas" if world > 1 else "single"},
         "p50_ms": r32["p50_ms"], "p99_ms": r32["p99_ms"],
         "fc_deriv_z": {"fp32": {k: v for k, v in r32.items() if k != "e2e"}, "fp64": r64},
+        "rk_stage": rk,
         "roofline": {"bound": "hbm", "achieved": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9,
                      "peak": hbm_peak, "unit": "GB/s",
                      "frac": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9 / hbm_peak,

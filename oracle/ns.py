@@ -43,8 +43,13 @@ inconsistent at these points):
   P4  A = (t - b E)/(gamma (1 - E^2)), B = -(b - t E)/(gamma (1 - E^2)),
       E = exp(-gamma Lz)  (Eqs. A, B).
   K1  odd-order factors (i k, and the k k^T / k^2 projector) use k with the
-      Nyquist entries zeroed; even-order factors (k^2 in the viscous term,
-      gamma^2 = kx^2 + ky^2) keep them.
+      Nyquist entries zeroed; the k^2 of the viscous term keeps them.  The
+      homogeneous solution uses gamma = |k_perp| of the same Nyquist-zeroed
+      wavenumbers as its gradient (i kx Phi, i ky Phi, Phi'), so that
+      grad phi^H is divergence-free at every (kx, ky); where that gamma is 0
+      (the mean mode and the Nyquist-only modes) phi^H = D z with
+      D = (b + t)/2.  With the true Nyquist wavenumber in gamma the x / y
+      Nyquist modes grow by ~1e10 per RK2/RK3 step from round-off.
   B1  buoyancy enters the vertical momentum equation as +gamma theta (with the
       +gamma w source in the theta equation this is the convecting sign).
   B2  Nusselt number Nu = 1 - (1/gamma) <d_z theta> at a wall.
@@ -245,17 +250,19 @@ def inject(mixed: np.ndarray, p: Params, dt_stage: float, gradp_prev: np.ndarray
 
 
 def homogeneous_coefficients(b: np.ndarray, t: np.ndarray, p: Params):
-    """A, B (and D for the mean mode) of Eqs. A, B, D with the P1/P2/P4 readings."""
-    kx, ky, _ = wavenumbers(p)
-    gam = np.sqrt(kx[None, :] ** 2 + ky[:, None] ** 2)           # [Ny][Kx]
+    """A, B (and D where gamma = 0) of Eqs. A, B, D with the P1/P2/P4/K1 readings.
+
+    Returns gamma [Ny][Kx], A, B [Ny][Kx] and D [Ny][Kx] (nonzero only where
+    gamma = 0)."""
+    kxo, kyo, _ = odd_wavenumbers(p)
+    gam = np.sqrt(kxo[None, :] ** 2 + kyo[:, None] ** 2)         # [Ny][Kx]
     E = np.exp(-gam * p.Lz)
+    flat = gam == 0
     with np.errstate(divide="ignore", invalid="ignore"):
         den = gam * (1 - E * E)
-        A = (t - b * E) / den
-        B = -(b - t * E) / den
-    A[0, 0] = 0.0
-    B[0, 0] = 0.0
-    D = 0.5 * (b[0, 0] + t[0, 0])
+        A = np.where(flat, 0.0, (t - b * E) / den)
+        B = np.where(flat, 0.0, -(b - t * E) / den)
+    D = np.where(flat, 0.5 * (b + t), 0.0)
     return gam, A, B, D
 
 
@@ -280,8 +287,7 @@ def project_core(vs: np.ndarray, p: Params, dt_stage: float):
     ep = np.exp(gam[None] * (z[:, None, None] - p.Lz))            # e^{gamma (z - Lz)}
     em = np.exp(-gam[None] * z[:, None, None])                    # e^{-gamma z}
     Phi = A[None] * ep + B[None] * em
-    dPhi = gam[None] * (A[None] * ep - B[None] * em)
-    dPhi[:, 0, 0] += D
+    dPhi = gam[None] * (A[None] * ep - B[None] * em) + D[None]
     kx1 = kxo[None, None, :]
     ky1 = kyo[None, :, None]
     gH_mixed = np.stack([1j * kx1 * Phi, 1j * ky1 * Phi, dPhi])

@@ -155,3 +155,137 @@ def fc_deriv_z(plan: Plan, f, df=None, d2f=None, Lz: float = 1.0, stream=None):
     _check(_lib.fc_deriv_z(plan.handle, _dtype_code(f), B, Nx, Ny, float(Lz), _ptr(f), _ptr(df), _ptr(d2f),
                            _stream(stream)), "fc_deriv_z")
     return df, d2f
+
+_sig("ns_params_default", [ctypes.POINTER(NsParams)])
+_sig("ns_workspace_bytes", [ctypes.POINTER(NsParams), ctypes.POINTER(ctypes.c_size_t)])
+_sig("ns_create", [ctypes.POINTER(NsParams), _vp, ctypes.c_size_t, ctypes.POINTER(_vp)])
+_sig("ns_destroy", [_vp])
+_sig("ns_set_fields", [_vp, _vp, _vp])
+_sig("ns_get_fields", [_vp, _vp, _vp])
+_sig("ns_get_state", [_vp, _vp, _vp])
+_sig("ns_put_state", [_vp, _vp, _vp])
+_sig("ns_get_wall_gradp", [_vp, _vp, _vp])
+_sig("ns_put_wall_gradp", [_vp, _vp, _vp])
+_sig("ns_rhs", [_vp, _vp, _vp, _vp])
+_sig("fc_poisson_project", [_vp, _c_double, _vp, _vp, _vp, _vp])
+_sig("rk_step", [_vp, _c_double, _vp])
+_sig("ns_diagnostics", [_vp] + [ctypes.POINTER(_c_double)] * 5 + [_vp])
+
+
+def ns_params(**kw) -> NsParams:
+    """ns_params with the library defaults, overridden by keyword arguments
+    (prec may be given as 'f32' / 'f64')."""
+    p = NsParams()
+    _check(_lib.ns_params_default(ctypes.byref(p)), "ns_params_default")
+    for k, v in kw.items():
+        if k == "prec" and isinstance(v, str):
+            v = FC_F32 if v == "f32" else FC_F64
+        setattr(p, k, v)
+    return p
+
+
+def ns_workspace_bytes(p: NsParams) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib.ns_workspace_bytes(ctypes.byref(p), ctypes.byref(n)), "ns_workspace_bytes")
+    return n.value
+
+
+class Sim:
+    """Navier-Stokes / Boussinesq simulation object (ns_create ... ns_destroy).
+
+    ``workspace``: optional caller-owned uint8 CUDA tensor of at least
+    ``ns_workspace_bytes(p)`` bytes; otherwise the library allocates."""
+
+    def __init__(self, p: NsParams, workspace=None):
+        import torch
+        self.p = p
+        self.dtype = torch.float32 if p.prec == FC_F32 else torch.float64
+        self.cdtype = torch.complex64 if p.prec == FC_F32 else torch.complex128
+        self.shape = (p.nfields, p.Nz, p.Ny, p.Nx)
+        self.Kx = p.Nx // 2 + 1
+        self._ws = workspace
+        h = _vp()
+        wptr = workspace.data_ptr() if workspace is not None else None
+        wbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        _check(_lib.ns_create(ctypes.byref(p), wptr, wbytes, ctypes.byref(h)), "ns_create")
+        self.handle = h
+
+    def _chk(self, t, shape, dtype=None):
+        if t.shape != shape or t.dtype != (dtype or self.dtype) or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"expected contiguous CUDA tensor {shape} {dtype or self.dtype}, got {tuple(t.shape)} {t.dtype}")
+
+    def set_fields(self, phys, stream=None):
+        self._chk(phys, self.shape)
+        _check(_lib.ns_set_fields(self.handle, phys.data_ptr(), _stream(stream)), "ns_set_fields")
+
+    def get_fields(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        self._chk(out, self.shape)
+        _check(_lib.ns_get_fields(self.handle, out.data_ptr(), _stream(stream)), "ns_get_fields")
+        return out
+
+    def state_shape(self):
+        return (self.p.nfields, self.p.Nz + self.p.C, self.p.Ny, self.Kx)
+
+    def get_state(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.state_shape(), dtype=self.cdtype, device="cuda")
+        self._chk(out, self.state_shape(), self.cdtype)
+        _check(_lib.ns_get_state(self.handle, out.data_ptr(), _stream(stream)), "ns_get_state")
+        return out
+
+    def put_state(self, st, stream=None):
+        self._chk(st, self.state_shape(), self.cdtype)
+        _check(_lib.ns_put_state(self.handle, st.data_ptr(), _stream(stream)), "ns_put_state")
+
+    def wall_gradp(self, stream=None):
+        import torch
+        out = torch.empty((2, 2, self.p.Ny, self.Kx), dtype=torch.complex128, device="cuda")
+        _check(_lib.ns_get_wall_gradp(self.handle, out.data_ptr(), _stream(stream)), "ns_get_wall_gradp")
+        return out
+
+    def put_wall_gradp(self, gp, stream=None):
+        import torch
+        self._chk(gp, (2, 2, self.p.Ny, self.Kx), torch.complex128)
+        _check(_lib.ns_put_wall_gradp(self.handle, gp.data_ptr(), _stream(stream)), "ns_put_wall_gradp")
+
+    def rhs(self, phys, out=None, stream=None):
+        import torch
+        self._chk(phys, self.shape)
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        self._chk(out, self.shape)
+        _check(_lib.ns_rhs(self.handle, phys.data_ptr(), out.data_ptr(), _stream(stream)), "ns_rhs")
+        return out
+
+    def project(self, vstar, dt_stage: float, out=None, gradp_out=None, stream=None):
+        import torch
+        vs = (3, self.p.Nz, self.p.Ny, self.p.Nx)
+        self._chk(vstar, vs)
+        if out is None:
+            out = torch.empty(vs, dtype=self.dtype, device="cuda")
+        self._chk(out, vs)
+        gptr = None
+        if gradp_out is not None:
+            self._chk(gradp_out, (2, 2, self.p.Ny, self.Kx), torch.complex128)
+            gptr = gradp_out.data_ptr()
+        _check(_lib.fc_poisson_project(self.handle, float(dt_stage), vstar.data_ptr(), out.data_ptr(), gptr,
+                                       _stream(stream)), "fc_poisson_project")
+        return out
+
+    def step(self, dt: float, stream=None):
+        _check(_lib.rk_step(self.handle, float(dt), _stream(stream)), "rk_step")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.ns_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -104,7 +104,7 @@ fc_status fc_destroy(fc_plan_t plan) {
     for (auto& t : plan->data.dev) {
       cudaSetDevice(t.device);
       cudaDeviceSynchronize();
-      cudaFree(t.Mr); cudaFree(t.H32); cudaFree(t.H64); cudaFree(t.tw32); cudaFree(t.tw64);
+      cudaFree(t.Mr); cudaFree(t.Mr2); cudaFree(t.H32); cudaFree(t.H64); cudaFree(t.tw32); cudaFree(t.tw64);
     }
     cudaSetDevice(cur);
   }
@@ -137,12 +137,22 @@ static fc_status deriv_tables_locked(fc_plan* plan, DerivDevTables** out) {
   s = cuda_status(cudaMalloc((void**)&t.Mr, sizeof(double) * plan->data.Mr.size()), "cudaMalloc(Mr)");
   if (!s) s = cuda_status(cudaMemcpy(t.Mr, plan->data.Mr.data(), sizeof(double) * plan->data.Mr.size(),
                                      cudaMemcpyHostToDevice), "cudaMemcpy(Mr)");
+  if (!s) {
+    std::vector<std::complex<double>> split(plan->data.Mr.size());
+    for (size_t i = 0; i < split.size(); ++i) {
+      const float hi = (float)plan->data.Mr[i];
+      split[i] = std::complex<double>(hi, (double)(float)(plan->data.Mr[i] - (double)hi));
+    }
+    void* p2 = nullptr;
+    s = upload<float2>(split, &p2);
+    t.Mr2 = (float2*)p2;
+  }
   if (!s) s = upload<float2>(plan->deriv.H, &t.H32);
   if (!s) s = upload<double2>(plan->deriv.H, &t.H64);
   if (!s) s = upload<float2>(plan->deriv.tw, &t.tw32);
   if (!s) s = upload<double2>(plan->deriv.tw, &t.tw64);
   if (s) {
-    cudaFree(t.Mr); cudaFree(t.H32); cudaFree(t.H64); cudaFree(t.tw32); cudaFree(t.tw64);
+    cudaFree(t.Mr); cudaFree(t.Mr2); cudaFree(t.H32); cudaFree(t.H64); cudaFree(t.tw32); cudaFree(t.tw64);
     return s;
   }
   plan->data.dev.push_back(t);

@@ -24,7 +24,13 @@ struct DerivConv {
   static constexpr int G = L1 > L2 ? L1 : L2;
   static constexpr int THREADS = G * LINES;
   static constexpr int NPHASE = 4;
+  static constexpr int MINB = (sizeof(T) == 4 && THREADS <= 512) ? 2 : 1;  // CTAs per SM (register budget)
   static constexpr int MR_MAX = 640;  // C * d <= 64 * 10
+  // row padding of the exchange buffer: a warp touches several k1 rows of
+  // LINES elements; shifting rows by half a 128-byte bank line keeps those
+  // accesses conflict-free when one row chunk is narrower than 128 bytes
+  static constexpr int PAD = (LINES * 2 * (int)sizeof(T) < 128) ? LINES : 0;
+  static constexpr int ROW = L2 * LINES + PAD;
   static constexpr int DMAX = 10;
   using C = cx<T>;
 
@@ -38,7 +44,8 @@ struct DerivConv {
     long long zstride;         // elements between consecutive z
     long long bstride;         // elements between fields
     T s1, s2;                  // 1/dz, 1/dz^2
-    const double* Mr;          // C x d
+    const double* Mr;          // C x d (float64 path)
+    const float2* Mr2;         // C x d as (hi, lo) float pairs (float32 path)
     const C* H;                // kernel spectrum, natural order, length L
     const C* tw;               // tw[n2 * L1 + k1] = e^{-2 pi i n2 k1 / L}
   };
@@ -48,23 +55,23 @@ struct DerivConv {
     C u[L2];
   };
 
-  // shared memory layout
+  // shared memory layout (the kernel spectrum and twiddles are read through
+  // the read-only data cache; every CTA uses the same L entries)
   static constexpr size_t off_buf = 0;
-  static constexpr size_t off_H = off_buf + sizeof(C) * L * LINES;
-  static constexpr size_t off_tw = off_H + sizeof(C) * L;
-  static constexpr size_t off_M = off_tw + sizeof(C) * L;
+  static constexpr size_t off_M = off_buf + sizeof(C) * ROW * L1;
   static constexpr size_t off_E = off_M + sizeof(double) * MR_MAX;
-  static constexpr size_t smem_bytes = off_E + sizeof(double) * LINES * 2 * DMAX;
+  static constexpr size_t smem_bytes = off_E + sizeof(T) * LINES * 2 * DMAX;
 
-  static FC_HD int bidx(int k1, int n2, int li) { return (k1 * L2 + n2) * LINES + li; }
+  static FC_HD int bidx(int k1, int n2, int li) { return k1 * ROW + n2 * LINES + li; }
 
   template <int P>
   static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
     C* buf = reinterpret_cast<C*>(sm + off_buf);
-    C* Hs = reinterpret_cast<C*>(sm + off_H);
-    C* tws = reinterpret_cast<C*>(sm + off_tw);
+    const C* __restrict__ Hs = a.H;
+    const C* __restrict__ tws = a.tw;
     double* Ms = reinterpret_cast<double*>(sm + off_M);
-    double* E = reinterpret_cast<double*>(sm + off_E);
+    float2* Ms2 = reinterpret_cast<float2*>(sm + off_M);
+    T* E = reinterpret_cast<T*>(sm + off_E);
     const int r = tid / LINES, li = tid % LINES;
     const long long field = bid / a.tiles;
     const long long line = (bid % a.tiles) * LINES + li;
@@ -72,8 +79,11 @@ struct DerivConv {
     const long long base = field * a.bstride + line;
 
     if constexpr (P == 0) {
-      for (int i = tid; i < L; i += THREADS) { Hs[i] = a.H[i]; tws[i] = a.tw[i]; }
-      for (int i = tid; i < a.Cc * a.d; i += THREADS) Ms[i] = a.Mr[i];
+      if constexpr (sizeof(T) == 4) {
+        for (int i = tid; i < a.Cc * a.d; i += THREADS) Ms2[i] = a.Mr2[i];
+      } else {
+        for (int i = tid; i < a.Cc * a.d; i += THREADS) Ms[i] = a.Mr[i];
+      }
       if (r < L2) {
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
@@ -81,25 +91,37 @@ struct DerivConv {
           T x = T(0);
           if (valid && n < a.Nz) x = a.f[base + (long long)n * a.zstride];
           R.v[j] = mk<T>(x, T(0));
-          if (n < a.d) E[li * 2 * DMAX + n] = (double)x;
-          if (n >= a.Nz - a.d && n < a.Nz) E[li * 2 * DMAX + DMAX + (n - (a.Nz - a.d))] = (double)x;
+          if (n < a.d) E[li * 2 * DMAX + n] = x;
+          if (n >= a.Nz - a.d && n < a.Nz) E[li * 2 * DMAX + DMAX + (n - (a.Nz - a.d))] = x;
         }
       }
     } else if constexpr (P == 1) {
       if (r < L2) {
-        const double* first = E + li * 2 * DMAX;
-        const double* last = first + DMAX;
+        const T* first = E + li * 2 * DMAX;
+        const T* last = first + DMAX;
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
           if (n >= a.Nz && n < a.Np) {
             const int jj = n - a.Nz;
-            double c = 0.0;
-            for (int i = 0; i < a.d; ++i) {
-              c += Ms[jj * a.d + i] * last[i];
-              c += Ms[(a.Cc - 1 - jj) * a.d + (a.d - 1 - i)] * first[i];
+            if constexpr (sizeof(T) == 4) {
+              // continuation product M_r f_last + M_l f_first in float-float
+              ff c{0.f, 0.f};
+              for (int i = 0; i < a.d; ++i) {
+                const float2 m1 = Ms2[jj * a.d + i];
+                const float2 m2 = Ms2[(a.Cc - 1 - jj) * a.d + (a.d - 1 - i)];
+                ff_fma(c, m1.x, m1.y, (float)last[i]);
+                ff_fma(c, m2.x, m2.y, (float)first[i]);
+              }
+              R.v[j] = mk<T>((T)ff_round(c), T(0));
+            } else {
+              double c = 0.0;
+              for (int i = 0; i < a.d; ++i) {
+                c += Ms[jj * a.d + i] * (double)last[i];
+                c += Ms[(a.Cc - 1 - jj) * a.d + (a.d - 1 - i)] * (double)first[i];
+              }
+              R.v[j] = mk<T>((T)c, T(0));
             }
-            R.v[j] = mk<T>((T)c, T(0));
           }
         }
         dft_reg<L1, -1, T>(R.v);

@@ -1,0 +1,64 @@
+// Two-pass line FFT engine shared by the z, y and x kernels.
+//
+// A transform of length L = L1 * L2 over a tile of LINES lines: input index
+// n = n2 + L2 n1 lives in thread r = n2 (register array v[L1]); output index
+// k = k1 + L1 k2 lives in thread r = k1 (register array u[L2]).  One
+// shared-memory exchange per transform (A: DFT_L1 + twiddle + store, barrier,
+// B: load + DFT_L2).  Thread id = r * LINES + li (lines fastest, so global
+// accesses of a warp are contiguous across lines).
+#pragma once
+#include "phases.cuh"
+
+namespace fcns {
+
+template <class T, int L1_, int L2_, int LINES_>
+struct Eng {
+  static constexpr int L1 = L1_, L2 = L2_, L = L1 * L2, LINES = LINES_;
+  static constexpr int G = L1 > L2 ? L1 : L2;
+  static constexpr int THREADS = G * LINES;
+  static constexpr int PAD = (LINES * 2 * (int)sizeof(T) < 128) ? LINES : 0;
+  static constexpr int ROW = L2 * LINES + PAD;
+  static constexpr size_t BUF = (size_t)ROW * L1;  // elements of one exchange buffer
+  using C = cx<T>;
+
+  static FC_HD int bidx(int k1, int n2, int li) { return k1 * ROW + n2 * LINES + li; }
+
+  // twiddle e^{SIGN 2 pi i n2 k1 / L}; tw holds the SIGN = -1 values
+  template <int SIGN>
+  static FC_HD C twid(const C* tw, int n2, int k1) {
+    C w = tw[n2 * L1 + k1];
+    if (SIGN > 0) w.y = -w.y;
+    return w;
+  }
+
+  // A: thread n2 with v[n1] = x[n2 + L2 n1]
+  template <int SIGN>
+  static FC_HD void A(C (&v)[L1], C* buf, const C* tw, int n2, int li) {
+    dft_reg<L1, SIGN, T>(v);
+#pragma unroll
+    for (int k1 = 0; k1 < L1; ++k1) buf[bidx(k1, n2, li)] = cmul(v[k1], twid<SIGN>(tw, n2, k1));
+  }
+  // B: thread k1 -> u[k2] = X[k1 + L1 k2]
+  template <int SIGN>
+  static FC_HD void B(C (&u)[L2], const C* buf, int k1, int li) {
+#pragma unroll
+    for (int n2 = 0; n2 < L2; ++n2) u[n2] = buf[bidx(k1, n2, li)];
+    dft_reg<L2, SIGN, T>(u);
+  }
+  // inverse-direction B: thread k1 holds u[k2] = X[k1 + L1 k2]; stores for Ai
+  template <int SIGN>
+  static FC_HD void Bi(C (&u)[L2], C* buf, const C* tw, int k1, int li) {
+    dft_reg<L2, SIGN, T>(u);
+#pragma unroll
+    for (int n2 = 0; n2 < L2; ++n2) buf[bidx(k1, n2, li)] = cmul(u[n2], twid<SIGN>(tw, n2, k1));
+  }
+  // inverse-direction A: thread n2 -> v[n1] = x[n2 + L2 n1]
+  template <int SIGN>
+  static FC_HD void Ai(C (&v)[L1], const C* buf, int n2, int li) {
+#pragma unroll
+    for (int k1 = 0; k1 < L1; ++k1) v[k1] = buf[bidx(k1, n2, li)];
+    dft_reg<L1, SIGN, T>(v);
+  }
+};
+
+}  // namespace fcns

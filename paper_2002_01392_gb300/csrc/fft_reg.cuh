@@ -191,3 +191,34 @@ __host__ __device__ __forceinline__ void dft_reg(cx<T> (&a)[N]) {
 }
 
 }  // namespace fcns
+
+namespace fcns {
+
+// ---------------------------------------------------------------------------
+// compensated ("float-float") dot products: a value is hi + lo with |lo| <=
+// ulp(hi)/2.  Used where a float32 path needs float64-level accuracy (the
+// FC continuation product, whose weights reach 4e3 and cancel) without the
+// float64 pipe, which is slow on this part.
+// ---------------------------------------------------------------------------
+struct ff {
+  float hi, lo;
+};
+
+// s += (mhi + mlo) * x, exactly up to float-float rounding.
+__host__ __device__ __forceinline__ void ff_fma(ff& s, float mhi, float mlo, float x) {
+  const float p = mhi * x;
+#if defined(__CUDA_ARCH__)
+  const float e = __fmaf_rn(mhi, x, -p);
+#else
+  const float e = (float)((double)mhi * (double)x - (double)p);  // exact: 48-bit product
+#endif
+  const float t = s.hi + p;
+  const float z = t - s.hi;
+  const float err = (s.hi - (t - z)) + (p - z);
+  s.hi = t;
+  s.lo += err + e + mlo * x;
+}
+
+__host__ __device__ __forceinline__ float ff_round(const ff& s) { return s.hi + s.lo; }
+
+}  // namespace fcns

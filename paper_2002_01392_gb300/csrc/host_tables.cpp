@@ -270,6 +270,71 @@ void deriv_conv_spectrum(int Nz, int Np, int L, std::vector<std::complex<double>
   }
 }
 
+// spectrum of a real kernel h(j), j in [-(Np-1), Nz-1], placed circularly on L
+static void kernel_spectrum(const std::vector<q>& h, int jlo, int L, std::vector<std::complex<double>>* H) {
+  Roots rl(L);
+  const int jhi = jlo + (int)h.size() - 1;
+  H->assign(L, std::complex<double>(0, 0));
+  for (int kk = 0; kk < L; ++kk) {
+    q re = 0, im = 0;
+    for (int j = jlo; j <= jhi; ++j) {
+      long long mm = (((long long)j % L) + L) % L;
+      long long e = (mm * kk) % L;
+      re += h[j - jlo] * rl.c[e];
+      im -= h[j - jlo] * rl.s[e];
+    }
+    (*H)[kk] = std::complex<double>((double)(re / (q)L), (double)(im / (q)L));
+  }
+}
+
+void deriv_conv_spectra(int Nz, int Np, int L, std::vector<std::complex<double>>* H1,
+                        std::vector<std::complex<double>>* H2) {
+  Roots rn(Np);
+  const q twopi = 2 * q_pi();
+  const int jlo = -(Np - 1), jhi = Nz - 1;
+  std::vector<q> d1(jhi - jlo + 1), d2(jhi - jlo + 1);
+  for (int j = jlo; j <= jhi; ++j) {
+    q s1 = 0, s2 = 0;
+    for (int l = 0; l < Np; ++l) {
+      int ls = (l <= (Np - 1) / 2) ? l : l - Np;
+      q k = twopi * (q)ls / (q)Np;
+      long long m = ((long long)l * j) % Np;
+      if (m < 0) m += Np;
+      bool nyq = (Np % 2 == 0) && (l == Np / 2);
+      if (!nyq) s1 += -k * rn.s[m];
+      s2 += -k * k * rn.c[m];
+    }
+    d1[j - jlo] = s1 / (q)Np;
+    d2[j - jlo] = s2 / (q)Np;
+  }
+  kernel_spectrum(d1, jlo, L, H1);
+  kernel_spectrum(d2, jlo, L, H2);
+}
+
+void filter_conv_spectrum(int Nz, int Np, int L, double beta, double two_p,
+                          std::vector<std::complex<double>>* Hf) {
+  Roots rn(Np);
+  std::vector<q> fz(Np);
+  for (int l = 0; l < Np; ++l) {
+    int ls = (l <= (Np - 1) / 2) ? l : l - Np;
+    if (Np % 2 == 0 && l == Np / 2) ls = -Np / 2;
+    const double x = std::fabs((double)ls) / (Np / 2.0);
+    fz[l] = (q)std::exp(-beta * std::pow(x, two_p));
+  }
+  const int jlo = -(Np - 1), jhi = Nz - 1;
+  std::vector<q> h(jhi - jlo + 1);
+  for (int j = jlo; j <= jhi; ++j) {
+    q s = 0;
+    for (int l = 0; l < Np; ++l) {
+      long long m = ((long long)l * j) % Np;
+      if (m < 0) m += Np;
+      s += fz[l] * rn.c[m];  // fz is even in l, so the kernel is real
+    }
+    h[j - jlo] = s / (q)Np;
+  }
+  kernel_spectrum(h, jlo, L, Hf);
+}
+
 void bluestein_tables(int Np, int L, std::vector<std::complex<double>>* chirp,
                       std::vector<std::complex<double>>* Hfwd, std::vector<std::complex<double>>* Hinv) {
   Roots rl(L);

@@ -23,6 +23,16 @@ bool build_fc_tables(int d, int C, int M, int n_os, FcTables* out);
 // Requires L >= N' + Nz - 1.
 void deriv_conv_spectrum(int Nz, int Np, int L, std::vector<std::complex<double>>* H);
 
+// Spectra (length L, with 1/L) of the circular kernels of d/dz and d2/dz2 on
+// the N'-periodic unit grid, for complex input (first Nz outputs valid).
+void deriv_conv_spectra(int Nz, int Np, int L, std::vector<std::complex<double>>* H1,
+                        std::vector<std::complex<double>>* H2);
+
+// Spectrum (length L, with 1/L) of the circular kernel of the z filter
+// fz(l) = exp(-beta (|l_s| / (N'/2))^{2p}) on the N'-periodic grid.
+void filter_conv_spectrum(int Nz, int Np, int L, double beta, double two_p,
+                          std::vector<std::complex<double>>* Hf);
+
 // Bluestein tables for a length-Np DFT done with length-L transforms:
 // chirp[n] = exp(-i pi n^2 / Np) (n < Np) and the spectrum (with 1/L) of the
 // circular kernel b[m mod L] = conj(chirp[|m|]), |m| < Np.  For the inverse

@@ -31,7 +31,9 @@ static int emu_deriv(const double* Mr, int d, int Cc, int Nz, int batch, long lo
   a.zstride = lines; a.bstride = lines * Nz;
   const double dz = Lz / (Nz - 1);
   a.s1 = T(1.0 / dz); a.s2 = T(1.0 / (dz * dz));
-  a.Mr = Mr; a.H = Ht.data(); a.tw = twt.data();
+  std::vector<float2> Mr2(Cc * d);
+  for (int i = 0; i < Cc * d; ++i) { Mr2[i].x = (float)Mr[i]; Mr2[i].y = (float)(Mr[i] - (double)Mr2[i].x); }
+  a.Mr = Mr; a.Mr2 = Mr2.data(); a.H = Ht.data(); a.tw = twt.data();
   phased_emulate<K>(a, a.tiles * batch, K::smem_bytes);
   return 0;
 }
@@ -54,7 +56,60 @@ extern "C" int fchc_deriv_z(int dtype, int L, const double* Mr, int d, int Cc, i
   HC(96, 8, 12, 32, 16)
   HC(160, 10, 16, 32, 16)
   HC(288, 16, 18, 32, 16)
-  HC(1080, 30, 36, 16, 8)
+  HC(1080, 30, 36, 8, 8)
 #undef HC
   return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Navier-Stokes simulation run on the CPU with the same kernel sequence
+// (NsCore with an emulating backend; host memory throughout).
+// ---------------------------------------------------------------------------
+#include <cstdlib>
+#include <cstring>
+
+#include "ns_core.hpp"
+
+namespace fcns {
+void set_error(const std::string&) {}
+fc_status cuda_status(cudaError_t, const char*) { return FC_OK; }
+
+struct EmuBK {
+  template <class K>
+  fc_status run(const typename K::Args& a, long long grid, void*) {
+    phased_emulate<K>(a, grid, K::smem_bytes);
+    return FC_OK;
+  }
+  fc_status alloc(void** p, size_t b) { *p = std::calloc(1, b); return *p ? FC_OK : FC_ERR_NOMEM; }
+  void free(void* p) { std::free(p); }
+  fc_status h2d(void* d, const void* s, size_t b) { std::memcpy(d, s, b); return FC_OK; }
+  fc_status d2d(void* d, const void* s, size_t b, void*) { std::memmove(d, s, b); return FC_OK; }
+  fc_status memset(void* d, int v, size_t b, void*) { std::memset(d, v, b); return FC_OK; }
+  fc_status sync(void*) { return FC_OK; }
+};
+}  // namespace fcns
+
+extern "C" {
+void* fchc_ns_create(const ns_params* p) {
+  auto* c = new NsCore<EmuBK>();
+  if (c->create(*p, nullptr, 0)) { c->destroy(); delete c; return nullptr; }
+  return c;
+}
+void fchc_ns_destroy(void* h) {
+  auto* c = (NsCore<EmuBK>*)h;
+  c->destroy();
+  delete c;
+}
+int fchc_ns_set_fields(void* h, const void* phys) { return ((NsCore<EmuBK>*)h)->set_fields_any(phys, nullptr); }
+int fchc_ns_get_fields(void* h, void* phys) { return ((NsCore<EmuBK>*)h)->get_fields_any(phys, nullptr); }
+int fchc_ns_rhs(void* h, const void* in, void* out) { return ((NsCore<EmuBK>*)h)->rhs_any(in, out, nullptr); }
+int fchc_ns_project(void* h, double dt, const void* in, void* out, void* gp) {
+  return ((NsCore<EmuBK>*)h)->project_any(dt, in, out, gp, nullptr);
+}
+int fchc_ns_step(void* h, double dt) { return ((NsCore<EmuBK>*)h)->step_any(dt, nullptr); }
+int fchc_ns_get_state(void* h, void* out) {
+  auto* c = (NsCore<EmuBK>*)h;
+  std::memcpy(out, c->ws + c->l.X[c->cur], c->state_bytes());
+  return 0;
+}
 }

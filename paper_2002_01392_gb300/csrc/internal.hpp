@@ -24,6 +24,7 @@ struct DerivDevTables {
   int device = -1;
   int L = 0;
   double* Mr = nullptr;
+  float2* Mr2 = nullptr;  // (hi, lo) float split of Mr
   void* H32 = nullptr;   // float2[L]
   void* H64 = nullptr;   // double2[L]
   void* tw32 = nullptr;  // float2[L]

@@ -24,6 +24,7 @@ fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long 
   a.s1 = T(1.0 / dz);
   a.s2 = T(1.0 / (dz * dz));
   a.Mr = t.Mr;
+  a.Mr2 = t.Mr2;
   a.H = static_cast<const cx<T>*>(sizeof(T) == 4 ? t.H32 : t.H64);
   a.tw = static_cast<const cx<T>*>(sizeof(T) == 4 ? t.tw32 : t.tw64);
   auto kern = phased_kernel<K>;
@@ -65,7 +66,7 @@ fc_status launch_deriv_z(const DerivDevTables& t, const PlanData& p, fc_dtype dt
     FC_CASE(288, 16, 18, 32, 16)
     FC_CASE(320, 16, 20, 32, 16)
     FC_CASE(576, 24, 24, 16, 8)
-    FC_CASE(1080, 30, 36, 16, 8)
+    FC_CASE(1080, 30, 36, 8, 8)
     default:
       return FC_ERR_UNSUPPORTED;
   }

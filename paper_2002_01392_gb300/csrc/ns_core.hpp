@@ -1,0 +1,448 @@
+// Orchestration of the Navier-Stokes simulation object: workspace layout,
+// tables, and the kernel sequences of set/get fields, right-hand side,
+// projection and the Runge-Kutta step.  Templated on a backend that runs a
+// kernel (on the GPU for libfcns, on the CPU for the host-check library) and
+// moves memory, so that the same sequence is what the CPU tests check.
+#pragma once
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "../../include/fcns.h"
+#include "host_tables.hpp"
+#include "ns_kernels.cuh"
+#include "shapes.hpp"
+
+namespace fcns {
+
+struct NsLayout {
+  int Nx, Ny, Nz, Np, Kx, nf, L, L1, L2, Lx1, Lx2, Ly1, Ly2;
+  long long lines;
+  size_t es;  // bytes per real
+  // byte offsets inside the workspace
+  size_t X[3], DZ, DZZ, V, DY, NL, gradp;
+  size_t kxo, kyo, kzo, kx, ky, fx, fy, Mr, Mr2, twz, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy;
+  size_t total;
+};
+
+inline bool z_shape_for(int need, int* L, int* L1, int* L2) {
+  int best = 0;
+#define FC_ZPICK(LL, A, B) \
+  if (!best && LL >= need) { best = LL; *L1 = A; *L2 = B; }
+  FC_ZSHAPES(FC_ZPICK)
+#undef FC_ZPICK
+  *L = best;
+  return best > 0;
+}
+
+inline bool xy_shape_for(int N, int* L1, int* L2) {
+  bool ok = false;
+#define FC_XYPICK(NN, A, B) \
+  if (!ok && NN == N) { ok = true; *L1 = A; *L2 = B; }
+  FC_XYSHAPES(FC_XYPICK)
+#undef FC_XYPICK
+  return ok;
+}
+
+inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
+  if (p.Nx < 2 || p.Ny < 2 || p.Nz < 2 * p.d || p.d < 2 || p.d > DMAX || p.C < p.d || p.C > 64 ||
+      (p.nfields != 3 && p.nfields != 4) || p.rk_order < 1 || p.rk_order > 4 || !(p.Lx > 0) || !(p.Ly > 0) ||
+      !(p.Lz > 0) || p.nu < 0 || p.kappa < 0 || (p.filter != 0 && p.filter != 1) || (p.prec != FC_F32 && p.prec != FC_F64))
+    return FC_ERR_ARG;
+  NsLayout& l = *o;
+  l.Nx = p.Nx; l.Ny = p.Ny; l.Nz = p.Nz; l.Np = p.Nz + p.C; l.Kx = p.Nx / 2 + 1; l.nf = p.nfields;
+  l.lines = (long long)p.Ny * l.Kx;
+  l.es = p.prec == FC_F32 ? 4 : 8;
+  const int need = std::max(l.Np + p.Nz - 1, 2 * l.Np - 1);
+  if (!z_shape_for(need, &l.L, &l.L1, &l.L2)) return FC_ERR_UNSUPPORTED;
+  if (!xy_shape_for(p.Nx, &l.Lx1, &l.Lx2) || !xy_shape_for(p.Ny, &l.Ly1, &l.Ly2)) return FC_ERR_UNSUPPORTED;
+  if (p.prec == FC_F64 && (l.L > 576 || p.Nx > 512)) return FC_ERR_UNSUPPORTED;
+  const size_t cs = 2 * l.es;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o2 = off; off += (bytes + 255) / 256 * 256; return o2; };
+  for (int i = 0; i < 3; ++i) l.X[i] = take(cs * l.nf * l.Np * l.lines);
+  l.DZ = take(cs * l.nf * l.Nz * l.lines);
+  l.DZZ = take(cs * l.nf * l.Nz * l.lines);
+  l.V = take(cs * l.nf * l.Nz * l.lines);
+  l.DY = take(cs * l.nf * l.Nz * l.lines);
+  l.NL = take(cs * l.nf * l.Nz * l.lines);
+  l.gradp = take(sizeof(double) * 2 * 4 * l.lines);
+  l.kxo = take(8 * l.Kx); l.kyo = take(8 * p.Ny); l.kzo = take(8 * l.Np);
+  l.kx = take(8 * l.Kx); l.ky = take(8 * p.Ny); l.fx = take(8 * l.Kx); l.fy = take(8 * p.Ny);
+  l.Mr = take(8 * p.C * p.d); l.Mr2 = take(8 * p.C * p.d);
+  l.twz = take(cs * l.L); l.H1 = take(cs * l.L); l.H2 = take(cs * l.L); l.Hf = take(cs * l.L);
+  l.chirp = take(cs * l.Np); l.Hbf = take(cs * l.L); l.Hbi = take(cs * l.L);
+  l.twx = take(cs * p.Nx); l.twy = take(cs * p.Ny);
+  l.total = off;
+  return FC_OK;
+}
+
+template <class BK>
+struct NsCore {
+  BK bk;
+  ns_params p{};
+  NsLayout l{};
+  unsigned char* ws = nullptr;
+  bool own_ws = false;
+  int cur = 0;  // index of the state buffer
+
+  template <class X> X* at(size_t off) const { return reinterpret_cast<X*>(ws + off); }
+
+  // ---------------------------------------------------------------- tables
+  fc_status create(const ns_params& prm, void* dev_ws, size_t bytes) {
+    p = prm;
+    fc_status s = ns_layout(p, &l);
+    if (s) return s;
+    if (dev_ws) {
+      if (bytes < l.total) return FC_ERR_NOMEM;
+      ws = static_cast<unsigned char*>(dev_ws);
+    } else {
+      s = bk.alloc((void**)&ws, l.total);
+      if (s) return s;
+      own_ws = true;
+    }
+    FcTables T;
+    if (!build_fc_tables(p.d, p.C, (2 * (p.d + p.C)) / 3, 20, &T)) return FC_ERR_ARG;
+    const double dz = p.Lz / (p.Nz - 1);
+    const double twopi = 6.283185307179586476925286766559;
+    std::vector<double> kxo(l.Kx), kx(l.Kx), kyo(p.Ny), ky(p.Ny), kzo(l.Np), fx(l.Kx), fy(p.Ny);
+    for (int i = 0; i < l.Kx; ++i) {
+      kx[i] = twopi * i / p.Lx;
+      kxo[i] = (p.Nx % 2 == 0 && i == p.Nx / 2) ? 0.0 : kx[i];
+      fx[i] = p.filter == 1 ? (3 * i <= p.Nx ? 1.0 : 0.0)
+                            : std::exp(-p.filter_beta * std::pow(i / (p.Nx / 2.0), p.filter_2p));
+    }
+    for (int i = 0; i < p.Ny; ++i) {
+      const int is = (i <= (p.Ny - 1) / 2) ? i : i - p.Ny;
+      ky[i] = twopi * is / p.Ly;
+      kyo[i] = (p.Ny % 2 == 0 && i == p.Ny / 2) ? 0.0 : ky[i];
+      fy[i] = p.filter == 1 ? (3 * std::abs(is) <= p.Ny ? 1.0 : 0.0)
+                            : std::exp(-p.filter_beta * std::pow(std::abs(is) / (p.Ny / 2.0), p.filter_2p));
+    }
+    for (int i = 0; i < l.Np; ++i) {
+      const int is = (i <= (l.Np - 1) / 2) ? i : i - l.Np;
+      kzo[i] = (l.Np % 2 == 0 && i == l.Np / 2) ? 0.0 : twopi * is / (l.Np * dz);
+    }
+    std::vector<std::complex<double>> twz, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy;
+    engine_twiddles(l.L1, l.L2, &twz);
+    deriv_conv_spectra(p.Nz, l.Np, l.L, &H1, &H2);
+    filter_conv_spectrum(p.Nz, l.Np, l.L, p.filter_beta, p.filter_2p, &Hf);
+    bluestein_tables(l.Np, l.L, &chirp, &Hbf, &Hbi);
+    engine_twiddles(l.Lx1, l.Lx2, &twx);
+    engine_twiddles(l.Ly1, l.Ly2, &twy);
+    std::vector<float2> mr2(T.Mr.size());
+    for (size_t i = 0; i < mr2.size(); ++i) {
+      mr2[i].x = (float)T.Mr[i];
+      mr2[i].y = (float)(T.Mr[i] - (double)mr2[i].x);
+    }
+    s = put(l.kxo, kxo.data(), 8 * kxo.size());
+    if (!s) s = put(l.kyo, kyo.data(), 8 * kyo.size());
+    if (!s) s = put(l.kzo, kzo.data(), 8 * kzo.size());
+    if (!s) s = put(l.kx, kx.data(), 8 * kx.size());
+    if (!s) s = put(l.ky, ky.data(), 8 * ky.size());
+    if (!s) s = put(l.fx, fx.data(), 8 * fx.size());
+    if (!s) s = put(l.fy, fy.data(), 8 * fy.size());
+    if (!s) s = put(l.Mr, T.Mr.data(), 8 * T.Mr.size());
+    if (!s) s = put(l.Mr2, mr2.data(), 8 * mr2.size());
+    if (!s) s = putc(l.twz, twz);
+    if (!s) s = putc(l.H1, H1);
+    if (!s) s = putc(l.H2, H2);
+    if (!s) s = putc(l.Hf, Hf);
+    if (!s) s = putc(l.chirp, chirp);
+    if (!s) s = putc(l.Hbf, Hbf);
+    if (!s) s = putc(l.Hbi, Hbi);
+    if (!s) s = putc(l.twx, twx);
+    if (!s) s = putc(l.twy, twy);
+    if (!s) s = bk.memset(ws + l.gradp, 0, sizeof(double) * 8 * l.lines, nullptr);
+    if (!s) s = bk.memset(ws + l.X[0], 0, 2 * l.es * l.nf * l.Np * l.lines, nullptr);
+    if (!s) s = bk.sync(nullptr);
+    return s;
+  }
+
+  fc_status destroy() {
+    fc_status s = bk.sync(nullptr);
+    if (own_ws && ws) bk.free(ws);
+    ws = nullptr;
+    return s;
+  }
+
+  fc_status put(size_t off, const void* src, size_t bytes) { return bk.h2d(ws + off, src, bytes); }
+  fc_status putc(size_t off, const std::vector<std::complex<double>>& v) {
+    if (l.es == 8) return put(off, v.data(), 16 * v.size());
+    std::vector<float2> f(v.size());
+    for (size_t i = 0; i < v.size(); ++i) { f[i].x = (float)v[i].real(); f[i].y = (float)v[i].imag(); }
+    return put(off, f.data(), 8 * f.size());
+  }
+
+  template <class T>
+  ZTab<T> ztab() const {
+    ZTab<T> t;
+    t.Mr = at<double>(l.Mr); t.Mr2 = at<float2>(l.Mr2);
+    t.tw = at<cx<T>>(l.twz); t.H1 = at<cx<T>>(l.H1); t.H2 = at<cx<T>>(l.H2); t.Hf = at<cx<T>>(l.Hf);
+    t.chirp = at<cx<T>>(l.chirp); t.Hbf = at<cx<T>>(l.Hbf); t.Hbi = at<cx<T>>(l.Hbi);
+    t.kxo = at<double>(l.kxo); t.kyo = at<double>(l.kyo); t.kzo = at<double>(l.kzo);
+    t.kx = at<double>(l.kx); t.ky = at<double>(l.ky); t.fx = at<double>(l.fx); t.fy = at<double>(l.fy);
+    return t;
+  }
+  ZGeom zgeom(int nf) const {
+    ZGeom g;
+    g.Nz = p.Nz; g.Np = l.Np; g.d = p.d; g.Cc = p.C; g.Kx = l.Kx; g.Ny = p.Ny; g.nf = nf;
+    g.lines = l.lines; g.Lz = p.Lz; g.dz = p.Lz / (p.Nz - 1);
+    return g;
+  }
+
+  // ------------------------------------------------------------ launchers
+  template <class T>
+  fc_status z_deriv(const cx<T>* X, int nf, void* st) {
+    fc_status s = FC_ERR_UNSUPPORTED;
+#define FC_ZD(LL, A, B)                                                        \
+  if (l.L == LL) {                                                            \
+    using K = KZDeriv<T, A, B, z_lines<T, LL>()>;                             \
+    typename K::Args a;                                                       \
+    a.g = zgeom(nf); a.t = ztab<T>(); a.X = X;                                \
+    a.DZ = at<cx<T>>(l.DZ); a.DZZ = at<cx<T>>(l.DZZ);                         \
+    a.tiles = (l.lines + K::E::LINES - 1) / K::E::LINES;                      \
+    const double dz = p.Lz / (p.Nz - 1);                                      \
+    a.s1 = (T)(1.0 / dz); a.s2 = (T)(1.0 / (dz * dz));                        \
+    s = bk.template run<K>(a, a.tiles * nf, st);                              \
+  }
+    FC_ZSHAPES(FC_ZD)
+#undef FC_ZD
+    return s;
+  }
+
+  template <class T>
+  fc_status z_combine(const cx<T>* NL, const cx<T>* Xt, const cx<T>* Xj, cx<T>* Xo, double dtj, int inject,
+                      int nf, void* st) {
+    fc_status s = FC_ERR_UNSUPPORTED;
+#define FC_ZC(LL, A, B)                                                        \
+  if (l.L == LL) {                                                            \
+    using K = KZCombine<T, A, B, z_lines<T, LL>()>;                           \
+    typename K::Args a;                                                       \
+    a.g = zgeom(nf); a.t = ztab<T>(); a.NL = NL; a.Xt = Xt; a.Xj = Xj;        \
+    a.DZZ = at<cx<T>>(l.DZZ); a.Xout = Xo; a.gradp = at<double2>(l.gradp);    \
+    a.dtj = dtj; a.dif[0] = a.dif[1] = a.dif[2] = p.nu; a.dif[3] = p.kappa;   \
+    a.inject = inject;                                                        \
+    a.tiles = (l.lines + K::E::LINES - 1) / K::E::LINES;                      \
+    s = bk.template run<K>(a, a.tiles * nf, st);                              \
+  }
+    FC_ZSHAPES(FC_ZC)
+#undef FC_ZC
+    return s;
+  }
+
+  template <class T>
+  fc_status z_continue(const cx<T>* M, cx<T>* X, int nf, const double2* gradp, double dtj, void* st) {
+    using K = KZContinue<T, 8>;
+    typename K::Args a;
+    a.g = zgeom(nf); a.t = ztab<T>(); a.M = M; a.X = X; a.gradp = gradp; a.dtj = dtj;
+    a.tiles = (l.lines + 7) / 8;
+    return bk.template run<K>(a, a.tiles * nf, st);
+  }
+
+  template <class T>
+  fc_status z_project(cx<T>* X, double dtj, void* st) {
+    fc_status s = FC_ERR_UNSUPPORTED;
+#define FC_ZP(LL, A, B)                                                        \
+  if (l.L == LL) {                                                            \
+    using K = KZProject<T, A, B, zproj_lines<T, LL>()>;                       \
+    typename K::Args a;                                                       \
+    a.g = zgeom(3); a.t = ztab<T>(); a.X = X; a.gradp = at<double2>(l.gradp); \
+    a.dtj = dtj;                                                              \
+    a.tiles = (l.lines + K::E::LINES - 1) / K::E::LINES;                      \
+    s = bk.template run<K>(a, a.tiles, st);                                   \
+  }
+    FC_ZSHAPES(FC_ZP)
+#undef FC_ZP
+    return s;
+  }
+
+  YGeom ygeom() const {
+    YGeom g;
+    g.Ny = p.Ny; g.Kx = l.Kx; g.Nz = p.Nz; g.plane = l.lines;
+    return g;
+  }
+
+  template <class T>
+  fc_status y_inv3(const cx<T>* A, long long a_fstride, int nf, void* st) {
+    fc_status s = FC_ERR_UNSUPPORTED;
+#define FC_YI(NN, A1, B1)                                                      \
+  if (p.Ny == NN) {                                                           \
+    using K = KYInv3<T, A1, B1, y_lines<T, NN>()>;                            \
+    typename K::Args a;                                                       \
+    a.g = ygeom(); a.tw = at<cx<T>>(l.twy); a.kyo = at<double>(l.kyo);        \
+    a.A = A; a.a_fstride = a_fstride;                                         \
+    a.V = at<cx<T>>(l.V); a.DY = at<cx<T>>(l.DY); a.DZ = at<cx<T>>(l.DZ);     \
+    a.tiles = (l.Kx + K::E::LINES - 1) / K::E::LINES;                         \
+    a.scale = (T)(1.0 / p.Ny);                                                \
+    s = bk.template run<K>(a, a.tiles * nf * p.Nz, st);                       \
+  }
+    FC_XYSHAPES(FC_YI)
+#undef FC_YI
+    return s;
+  }
+
+  template <class T, int SIGN>
+  fc_status y_one(const cx<T>* IN, long long in_fs, cx<T>* OUT, long long out_fs, int nf, double scale, void* st) {
+    fc_status s = FC_ERR_UNSUPPORTED;
+#define FC_Y1(NN, A1, B1)                                                      \
+  if (p.Ny == NN) {                                                           \
+    using K = KY1<T, A1, B1, y_lines<T, NN>(), SIGN>;                         \
+    typename K::Args a;                                                       \
+    a.g = ygeom(); a.tw = at<cx<T>>(l.twy);                                   \
+    a.IN = IN; a.in_fstride = in_fs; a.OUT = OUT; a.out_fstride = out_fs;     \
+    a.tiles = (l.Kx + K::E::LINES - 1) / K::E::LINES;                         \
+    a.scale = (T)scale;                                                       \
+    s = bk.template run<K>(a, a.tiles * nf * p.Nz, st);                       \
+  }
+    FC_XYSHAPES(FC_Y1)
+#undef FC_Y1
+    return s;
+  }
+
+  template <class T>
+  fc_status x_pass(void* st) {
+    fc_status s = FC_ERR_UNSUPPORTED;
+    const long long rows = (long long)p.Nz * p.Ny;
+#define FC_XP(NN, A1, B1)                                                      \
+  if (p.Nx == NN) {                                                           \
+    if (l.nf == 3) {                                                          \
+      using K = KXPass<T, A1, B1, 3>;                                         \
+      s = x_pass_run<T, K>(rows, st);                                         \
+    } else {                                                                  \
+      using K = KXPass<T, A1, B1, 4>;                                         \
+      s = x_pass_run<T, K>(rows, st);                                         \
+    }                                                                         \
+  }
+    FC_XYSHAPES(FC_XP)
+#undef FC_XP
+    return s;
+  }
+  template <class T, class K>
+  fc_status x_pass_run(long long rows, void* st) {
+    if (K::smem_bytes > 227 * 1024) return FC_ERR_UNSUPPORTED;
+    typename K::Args a;
+    a.Kx = l.Kx; a.rows = rows; a.tw = at<cx<T>>(l.twx); a.kxo = at<double>(l.kxo);
+    a.V = at<cx<T>>(l.V); a.DY = at<cx<T>>(l.DY); a.DZ = at<cx<T>>(l.DZ); a.NL = at<cx<T>>(l.NL);
+    a.forcing = (T)p.forcing_x; a.gamma = (T)p.gamma; a.scale = (T)(1.0 / p.Nx);
+    return bk.template run<K>(a, rows, st);
+  }
+
+  template <class T, int SIGN>
+  fc_status x_rows(T* R, cx<T>* S, int nf, void* st) {
+    fc_status s = FC_ERR_UNSUPPORTED;
+    const long long pairs = (long long)nf * p.Nz * p.Ny / 2;
+#define FC_XR(NN, A1, B1)                                                      \
+  if (p.Nx == NN) {                                                           \
+    using K = KXRow<T, A1, B1, SIGN, x_jobs<NN>()>;                           \
+    typename K::Args a;                                                       \
+    a.Kx = l.Kx; a.pairs = pairs; a.tw = at<cx<T>>(l.twx); a.R = R; a.S = S;  \
+    a.scale = (T)(SIGN > 0 ? 1.0 / p.Nx : 1.0);                               \
+    s = bk.template run<K>(a, (pairs + x_jobs<NN>() - 1) / x_jobs<NN>(), st); \
+  }
+    FC_XYSHAPES(FC_XR)
+#undef FC_XR
+    return s;
+  }
+
+  // ------------------------------------------------------------- sequences
+  template <class T> cx<T>* Xb(int i) const { return at<cx<T>>(l.X[i]); }
+  template <class T> cx<T>* buf(size_t off) const { return at<cx<T>>(off); }
+
+  // physical [nf][Nz][Ny][Nx] -> extended state X (optionally with injection)
+  template <class T>
+  fc_status phys_to_state(const T* phys, cx<T>* X, int nf, const double2* gradp, double dtj, void* st) {
+    cx<T>* V = buf<T>(l.V);
+    fc_status s = x_rows<T, -1>(const_cast<T*>(phys), V, nf, st);
+    if (!s) s = y_one<T, -1>(V, p.Nz, V, p.Nz, nf, 1.0, st);
+    if (!s) s = z_continue<T>(V, X, nf, gradp, dtj, st);
+    return s;
+  }
+  // extended state X -> physical (first Nz points)
+  template <class T>
+  fc_status state_to_phys(const cx<T>* X, T* phys, int nf, void* st) {
+    cx<T>* V = buf<T>(l.V);
+    fc_status s = y_one<T, 1>(X, l.Np, V, p.Nz, nf, 1.0 / p.Ny, st);
+    if (!s) s = x_rows<T, 1>(phys, V, nf, st);
+    return s;
+  }
+
+  // nonlinear term of the state Xj into NL (mixed, filtered later); DZZ filled
+  template <class T>
+  fc_status nonlinear(const cx<T>* Xj, void* st) {
+    fc_status s = z_deriv<T>(Xj, l.nf, st);
+    if (!s) s = y_inv3<T>(Xj, l.Np, l.nf, st);
+    if (!s) s = x_pass<T>(st);
+    if (!s) s = y_one<T, -1>(buf<T>(l.NL), p.Nz, buf<T>(l.NL), p.Nz, l.nf, 1.0, st);
+    return s;
+  }
+
+  template <class T>
+  fc_status set_fields(const T* phys, void* st) {
+    fc_status s = phys_to_state<T>(phys, Xb<T>(cur), l.nf, nullptr, 0.0, st);
+    if (!s) s = bk.memset(ws + l.gradp, 0, sizeof(double) * 8 * l.lines, st);
+    return s;
+  }
+  template <class T>
+  fc_status get_fields(T* phys, void* st) { return state_to_phys<T>(Xb<T>(cur), phys, l.nf, st); }
+
+  template <class T>
+  fc_status rhs(const T* in, T* out, void* st) {
+    cx<T>* Xs = Xb<T>((cur + 1) % 3);
+    cx<T>* Xo = Xb<T>((cur + 2) % 3);
+    fc_status s = phys_to_state<T>(in, Xs, l.nf, nullptr, 0.0, st);
+    if (!s) s = nonlinear<T>(Xs, st);
+    if (!s) s = z_combine<T>(buf<T>(l.NL), nullptr, Xs, Xo, 1.0, 0, l.nf, st);
+    if (!s) s = state_to_phys<T>(Xo, out, l.nf, st);
+    return s;
+  }
+
+  template <class T>
+  fc_status project(double dtj, const T* vin, T* vout, void* gp_out, void* st) {
+    cx<T>* Xs = Xb<T>((cur + 1) % 3);
+    fc_status s = phys_to_state<T>(vin, Xs, 3, at<double2>(l.gradp), dtj, st);
+    if (!s) s = z_project<T>(Xs, dtj, st);
+    if (!s) s = state_to_phys<T>(Xs, vout, 3, st);
+    if (!s && gp_out) s = bk.d2d(gp_out, ws + l.gradp, sizeof(double) * 8 * l.lines, st);
+    return s;
+  }
+
+  template <class T>
+  fc_status step(double dt, void* st) {
+    const int o = p.rk_order;
+    const int it = cur, ia = (cur + 1) % 3, ib = (cur + 2) % 3;
+    int ij = it;
+    fc_status s = FC_OK;
+    for (int j = 1; j <= o && !s; ++j) {
+      const double dtj = dt / (o + 1 - j);  // stage step dt_j = dt / (o + 1 - j)
+      const int in = (ij == ia) ? ib : ia;
+      s = nonlinear<T>(Xb<T>(ij), st);
+      if (!s) s = z_combine<T>(buf<T>(l.NL), Xb<T>(it), Xb<T>(ij), Xb<T>(in), dtj, 1, l.nf, st);
+      if (!s) s = z_project<T>(Xb<T>(in), dtj, st);
+      ij = in;
+    }
+    if (!s) cur = ij;
+    return s;
+  }
+
+  // ------------------------------------------------------------- dispatch
+  bool f32() const { return p.prec == FC_F32; }
+  fc_status set_fields_any(const void* phys, void* st) {
+    return f32() ? set_fields<float>((const float*)phys, st) : set_fields<double>((const double*)phys, st);
+  }
+  fc_status get_fields_any(void* phys, void* st) {
+    return f32() ? get_fields<float>((float*)phys, st) : get_fields<double>((double*)phys, st);
+  }
+  fc_status rhs_any(const void* in, void* out, void* st) {
+    return f32() ? rhs<float>((const float*)in, (float*)out, st) : rhs<double>((const double*)in, (double*)out, st);
+  }
+  fc_status project_any(double dtj, const void* in, void* out, void* gp, void* st) {
+    return f32() ? project<float>(dtj, (const float*)in, (float*)out, gp, st)
+                 : project<double>(dtj, (const double*)in, (double*)out, gp, st);
+  }
+  fc_status step_any(double dt, void* st) { return f32() ? step<float>(dt, st) : step<double>(dt, st); }
+  size_t state_bytes() const { return 2 * l.es * l.nf * l.Np * l.lines; }
+};
+
+}  // namespace fcns

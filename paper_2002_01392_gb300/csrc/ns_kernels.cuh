@@ -1,0 +1,1003 @@
+// Kernels of the time-splitting FC-Gram Navier-Stokes / Boussinesq step.
+//
+// State representation: every field is kept in the mixed (kx, ky, z') space
+// on the CONTINUED z grid, X[f][s][ky][kx], s = 0..N'-1 (the FC extension of
+// the physical values plus the continuation points).  This is the inverse z
+// DFT of the paper's continued spectral field (Sec. 3, Sec. 4.2): the two
+// representations are related exactly by a length-N' DFT, and every
+// spectral-space operation of the method is applied either as a circular
+// convolution along z' (z derivatives, the z filter) or through explicit
+// Bluestein DFTs (the projection, which mixes the three velocity components
+// with k-dependent weights).
+//
+// Layouts (Kx = Nx/2 + 1, lines = Ny * Kx, line index l = ky * Kx + kx):
+//   X      [nf][N'][lines]   complex   state (extended mixed space)
+//   M*     [nf][Nz][lines]   complex   mixed-space work arrays
+//   rows   [nf][Nz][Ny][Kx]  complex   same memory seen as x-rows
+//   walls  [2][2][lines]     complex double  tangential grad p at z = 0, Lz
+#pragma once
+#include "engine.cuh"
+
+namespace fcns {
+
+// ---------------------------------------------------------------------------
+// tables and geometry shared by the z kernels
+// ---------------------------------------------------------------------------
+template <class T>
+struct ZTab {
+  const double* Mr;     // C x d continuation matrix (float64 path)
+  const float2* Mr2;    // C x d as (hi, lo) float pairs (float32 path)
+  const cx<T>* tw;      // engine twiddles, L entries
+  const cx<T>* H1;      // conv spectrum of d/dz (unit spacing), L entries
+  const cx<T>* H2;      // conv spectrum of d2/dz2 (unit spacing)
+  const cx<T>* Hf;      // conv spectrum of the z filter
+  const cx<T>* chirp;   // Bluestein chirp exp(-i pi n^2 / N'), N' entries
+  const cx<T>* Hbf;     // Bluestein kernel spectrum (forward DFT)
+  const cx<T>* Hbi;     // Bluestein kernel spectrum (inverse DFT)
+  const double* kxo;    // kx with the Nyquist entry zeroed (Kx)
+  const double* kyo;    // ky with the Nyquist entry zeroed (Ny)
+  const double* kzo;    // kz with the Nyquist entry zeroed (N'), FFT order
+  const double* kx;     // kx (Kx)
+  const double* ky;     // ky (Ny)
+  const double* fx;     // x filter / mask factor (Kx)
+  const double* fy;     // y filter / mask factor (Ny)
+};
+
+struct ZGeom {
+  int Nz, Np, d, Cc, Kx, Ny, nf;
+  long long lines;
+  double Lz, dz;
+};
+
+constexpr int DMAX = 10;
+constexpr int MRMAX = 640;
+
+// C continuation value jj (point Nz + jj) of a complex line from its first /
+// last d values (Sec. 3 continuation formula; right matrix M_r, left matrix
+// its row/column reversal).  float32: compensated float-float products.
+template <class T>
+FC_HD cx<T> continuation_value(int jj, const cx<T>* first, const cx<T>* last, int d, int Cc,
+                               const double* Ms, const float2* Ms2) {
+  if constexpr (sizeof(T) == 4) {
+    ff re{0.f, 0.f}, im{0.f, 0.f};
+    for (int i = 0; i < d; ++i) {
+      const float2 m1 = Ms2[jj * d + i];
+      const float2 m2 = Ms2[(Cc - 1 - jj) * d + (d - 1 - i)];
+      ff_fma(re, m1.x, m1.y, last[i].x);
+      ff_fma(im, m1.x, m1.y, last[i].y);
+      ff_fma(re, m2.x, m2.y, first[i].x);
+      ff_fma(im, m2.x, m2.y, first[i].y);
+    }
+    return mk<T>(ff_round(re), ff_round(im));
+  } else {
+    double re = 0, im = 0;
+    for (int i = 0; i < d; ++i) {
+      const double m1 = Ms[jj * d + i];
+      const double m2 = Ms[(Cc - 1 - jj) * d + (d - 1 - i)];
+      re += m1 * last[i].x + m2 * first[i].x;
+      im += m1 * last[i].y + m2 * first[i].y;
+    }
+    return mk<T>((T)re, (T)im);
+  }
+}
+
+template <class T>
+FC_HD void load_mr(unsigned char* sm, const ZTab<T>& t, int n, int tid, int threads) {
+  if constexpr (sizeof(T) == 4) {
+    float2* M2 = reinterpret_cast<float2*>(sm);
+    for (int i = tid; i < n; i += threads) M2[i] = t.Mr2[i];
+  } else {
+    double* M = reinterpret_cast<double*>(sm);
+    for (int i = tid; i < n; i += threads) M[i] = t.Mr[i];
+  }
+}
+
+// ===========================================================================
+// K1  zderiv: dz and dzz of the state at the Nz physical points.
+// Circular convolution of the extended line with the derivative kernels of
+// the N'-periodic grid (= multiplication of the continued spectrum by i kz
+// (Nyquist zeroed) and -kz^2, Sec. 4.2), first Nz outputs.
+// ===========================================================================
+template <class T, int L1, int L2, int LINES>
+struct KZDeriv {
+  using E = Eng<T, L1, L2, LINES>;
+  using C = cx<T>;
+  static constexpr int THREADS = E::THREADS, NPHASE = 3;
+  static constexpr int MINB = (sizeof(T) == 4 && THREADS <= 512) ? 2 : 1;
+  struct Args {
+    ZGeom g;
+    ZTab<T> t;
+    const C* X;
+    C* DZ;
+    C* DZZ;
+    long long tiles;
+    T s1, s2;
+  };
+  struct Regs { C v[L1]; C u[L2]; };
+  static constexpr size_t off_b1 = sizeof(C) * E::BUF;
+  static constexpr size_t smem_bytes = 2 * sizeof(C) * E::BUF;
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
+    C* b0 = reinterpret_cast<C*>(sm);
+    C* b1 = reinterpret_cast<C*>(sm + off_b1);
+    const int r = tid / LINES, li = tid % LINES;
+    const long long f = bid / a.tiles;
+    const long long line = (bid % a.tiles) * LINES + li;
+    const bool valid = line < a.g.lines;
+    if constexpr (P == 0) {
+      if (r < L2) {
+        const C* x = a.X + f * a.g.Np * a.g.lines + line;
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          R.v[j] = (valid && n < a.g.Np) ? x[(long long)n * a.g.lines] : mk<T>(0, 0);
+        }
+        E::template A<-1>(R.v, b0, a.t.tw, r, li);
+      }
+    } else if constexpr (P == 1) {
+      if (r < L1) {
+        E::template B<-1>(R.u, b0, r, li);
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) {
+          b1[E::bidx(r, k2, li)] = R.u[k2];
+          R.u[k2] = cmul(R.u[k2], a.t.H1[r + L1 * k2]);
+        }
+        E::template Bi<1>(R.u, b0, a.t.tw, r, li);
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(b1[E::bidx(r, k2, li)], a.t.H2[r + L1 * k2]);
+        E::template Bi<1>(R.u, b1, a.t.tw, r, li);
+      }
+    } else if constexpr (P == 2) {
+      if (r < L2) {
+        C* dz = a.DZ + f * a.g.Nz * a.g.lines + line;
+        C* dzz = a.DZZ + f * a.g.Nz * a.g.lines + line;
+        E::template Ai<1>(R.v, b0, r, li);
+        if (valid) {
+#pragma unroll
+          for (int j = 0; j < L1; ++j) {
+            const int n = r + L2 * j;
+            if (n < a.g.Nz) dz[(long long)n * a.g.lines] = cscale(R.v[j], a.s1);
+          }
+        }
+        E::template Ai<1>(R.v, b1, r, li);
+        if (valid) {
+#pragma unroll
+          for (int j = 0; j < L1; ++j) {
+            const int n = r + L2 * j;
+            if (n < a.g.Nz) dzz[(long long)n * a.g.lines] = cscale(R.v[j], a.s2);
+          }
+        }
+      }
+    }
+  }
+};
+
+// ===========================================================================
+// K5  zcombine: pressureless stage update in mixed space, BC injection and
+// re-continuation (Sec. 4.4 steps 1-2 with the state in extended mixed
+// space):
+//   v*(z) = v^t(z) + dt_j [ F_xy (f_z * FC(N))(z) + nu (dzz v^{j-1} - kperp^2 v^{j-1}) ]
+//   tangential v* := dt_j grad_par p^{prev} at z = 0, Lz; theta := 0 there;
+//   X_out = [v*; continuation of v*].
+// The z filter acts as a circular convolution of the continued N.
+// ===========================================================================
+template <class T, int L1, int L2, int LINES>
+struct KZCombine {
+  using E = Eng<T, L1, L2, LINES>;
+  using C = cx<T>;
+  static constexpr int THREADS = E::THREADS, NPHASE = 5;
+  static constexpr int MINB = (sizeof(T) == 4 && THREADS <= 512) ? 2 : 1;
+  struct Args {
+    ZGeom g;
+    ZTab<T> t;
+    const C* NL;      // [nf][Nz][lines] nonlinear term (mixed)
+    const C* Xt;      // [nf][N'][lines] state at t
+    const C* Xj;      // [nf][N'][lines] state of the previous stage
+    const C* DZZ;     // [nf][Nz][lines]
+    C* Xout;          // [nf][N'][lines]
+    const double2* gradp;  // [2][2][lines]
+    double dtj;
+    double dif[4];
+    long long tiles;
+    int inject;            // 1: wall injection (RK stage); 0: plain right-hand side
+  };
+  struct Regs { C v[L1]; C u[L2]; };
+  static constexpr size_t off_M = sizeof(C) * E::BUF;
+  static constexpr size_t off_E = off_M + sizeof(double) * MRMAX;
+  static constexpr size_t smem_bytes = off_E + sizeof(C) * LINES * 2 * DMAX;
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
+    C* b0 = reinterpret_cast<C*>(sm);
+    const double* Ms = reinterpret_cast<const double*>(sm + off_M);
+    const float2* Ms2 = reinterpret_cast<const float2*>(sm + off_M);
+    C* Ev = reinterpret_cast<C*>(sm + off_E) + li_of(tid) * 2 * DMAX;
+    const int r = tid / LINES, li = tid % LINES;
+    const int f = (int)(bid / a.tiles);
+    const long long line = (bid % a.tiles) * LINES + li;
+    const bool valid = line < a.g.lines;
+    const int Nz = a.g.Nz, Np = a.g.Np, d = a.g.d;
+    const long long Ls = a.g.lines;
+    if constexpr (P == 0) {
+      load_mr<T>(sm + off_M, a.t, a.g.Cc * d, tid, THREADS);
+      if (r < L2) {
+        const C* x = a.NL + (long long)f * Nz * Ls + line;
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          C val = mk<T>(0, 0);
+          if (valid && n < Nz) val = x[(long long)n * Ls];
+          R.v[j] = val;
+          if (n < d) Ev[n] = val;
+          if (n >= Nz - d && n < Nz) Ev[DMAX + n - (Nz - d)] = val;
+        }
+      }
+    } else if constexpr (P == 1) {
+      if (r < L2) {
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          if (n >= Nz && n < Np) R.v[j] = continuation_value<T>(n - Nz, Ev, Ev + DMAX, d, a.g.Cc, Ms, Ms2);
+        }
+        E::template A<-1>(R.v, b0, a.t.tw, r, li);
+      }
+    } else if constexpr (P == 2) {
+      if (r < L1) {
+        E::template B<-1>(R.u, b0, r, li);
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(R.u[k2], a.t.Hf[r + L1 * k2]);
+        E::template Bi<1>(R.u, b0, a.t.tw, r, li);
+      }
+    } else if constexpr (P == 3) {
+      if (r < L2) {
+        E::template Ai<1>(R.v, b0, r, li);
+        const int kx = (int)(line % a.g.Kx), ky = (int)(line / a.g.Kx);
+        const T fxy = valid ? (T)(a.t.fx[kx] * a.t.fy[ky]) : T(0);
+        const double kp2 = valid ? a.t.kx[kx] * a.t.kx[kx] + a.t.ky[ky] * a.t.ky[ky] : 0.0;
+        const T cdt = (T)a.dtj, cnu = (T)(a.dif[f]), ckp2 = (T)kp2;
+        const long long fo = (long long)f * Np * Ls + line;
+        const C* xt = a.Xt + fo;
+        const C* xj = a.Xj + fo;
+        const C* dzz = a.DZZ + (long long)f * Nz * Ls + line;
+        C* xo = a.Xout + fo;
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          if (n < Nz) {
+            C vs = mk<T>(0, 0);
+            if (valid) {
+              const C vj = xj[(long long)n * Ls];
+              const C zz = dzz[(long long)n * Ls];
+              const C nlf = cscale(R.v[j], fxy);
+              const C visc = csub(zz, cscale(vj, ckp2));
+              const C base = a.Xt ? xt[(long long)n * Ls] : mk<T>(0, 0);
+              vs = cadd(base, cscale(cadd(nlf, cscale(visc, cnu)), cdt));
+              if (a.inject && (n == 0 || n == Nz - 1)) {
+                const int wall = (n == 0) ? 0 : 1;
+                if (f < 2) {
+                  const double2 gp = a.gradp[((long long)wall * 2 + f) * Ls + line];
+                  vs = mk<T>((T)(a.dtj * gp.x), (T)(a.dtj * gp.y));
+                } else if (f == 3) {
+                  vs = mk<T>(0, 0);
+                }
+              }
+              xo[(long long)n * Ls] = vs;
+            }
+            if (n < d) Ev[n] = vs;
+            if (n >= Nz - d) Ev[DMAX + n - (Nz - d)] = vs;
+          }
+        }
+      }
+    } else if constexpr (P == 4) {
+      if (r < L2 && valid) {
+        C* xo = a.Xout + (long long)f * Np * Ls + line;
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          if (n >= Nz && n < Np)
+            xo[(long long)n * Ls] = continuation_value<T>(n - Nz, Ev, Ev + DMAX, d, a.g.Cc, Ms, Ms2);
+        }
+      }
+    }
+  }
+  static FC_HD int li_of(int tid) { return tid % LINES; }
+};
+
+// ===========================================================================
+// K5b  zcontinue: X = [m; continuation of m] for mixed fields m (state from
+// physical fields, Sec. 3), optionally with the wall injection of
+// Sec. 4.1 (bound-v) for the stand-alone projection.
+// ===========================================================================
+template <class T, int LINES>
+struct KZContinue {
+  using C = cx<T>;
+  static constexpr int G = 32;
+  static constexpr int THREADS = G * LINES, NPHASE = 2, MINB = 1;
+  struct Args {
+    ZGeom g;
+    ZTab<T> t;
+    const C* M;     // [nf][Nz][lines]
+    C* X;           // [nf][N'][lines]
+    const double2* gradp;  // injection planes or nullptr
+    double dtj;
+    long long tiles;
+  };
+  struct Regs { int dummy; };
+  static constexpr size_t off_E = sizeof(double) * MRMAX;
+  static constexpr size_t smem_bytes = off_E + sizeof(C) * LINES * 2 * DMAX;
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs&) {
+    const double* Ms = reinterpret_cast<const double*>(sm);
+    const float2* Ms2 = reinterpret_cast<const float2*>(sm);
+    const int r = tid / LINES, li = tid % LINES;
+    C* Ev = reinterpret_cast<C*>(sm + off_E) + li * 2 * DMAX;
+    const int f = (int)(bid / a.tiles);
+    const long long line = (bid % a.tiles) * LINES + li;
+    const bool valid = line < a.g.lines;
+    const int Nz = a.g.Nz, Np = a.g.Np, d = a.g.d;
+    const long long Ls = a.g.lines;
+    const C* m = a.M + (long long)f * Nz * Ls + line;
+    C* x = a.X + (long long)f * Np * Ls + line;
+    if constexpr (P == 0) {
+      load_mr<T>(sm, a.t, a.g.Cc * d, tid, THREADS);
+      if (valid) {
+        for (int n = r; n < Nz; n += G) {
+          C val = m[(long long)n * Ls];
+          if (a.gradp && (n == 0 || n == Nz - 1)) {
+            const int wall = (n == 0) ? 0 : 1;
+            if (f < 2) {
+              const double2 gp = a.gradp[((long long)wall * 2 + f) * Ls + line];
+              val = mk<T>((T)(a.dtj * gp.x), (T)(a.dtj * gp.y));
+            } else if (f == 3) {
+              val = mk<T>(0, 0);
+            }
+          }
+          x[(long long)n * Ls] = val;
+          if (n < d) Ev[n] = val;
+          if (n >= Nz - d) Ev[DMAX + n - (Nz - d)] = val;
+        }
+      }
+    } else {
+      if (valid)
+        for (int n = Nz + r; n < Np; n += G)
+          x[(long long)n * Ls] = continuation_value<T>(n - Nz, Ev, Ev + DMAX, d, a.g.Cc, Ms, Ms2);
+    }
+  }
+};
+
+// ===========================================================================
+// K6  zproject: pressure solve and projection of the three velocity
+// components of the continued v* (Sec. 4.2, Sec. 4.4 steps 3-5), with
+// phi = dt_j p:
+//   s      = (kx v^_x + ky v^_y + kz v^_z) / k^2   (0 where k = 0; odd-order
+//            wavenumbers with the Nyquist entries zeroed)
+//   grad phi^I = (kx sigma, ky sigma, sigma_z),  sigma = IDFT(s), sigma_z = IDFT(kz s)
+//   b, t   = w* - sigma_z at z = 0, Lz
+//   A, B   (Eqs. A, B), gamma = |k_perp| (Nyquist-zeroed wavenumbers);
+//          D = (b + t)/2 where gamma = 0
+//   grad phi^H = (i kx Phi, i ky Phi, Phi'),  Phi = A e^{g(z-Lz)} + B e^{-g z}
+//   X     -= grad phi^I + FC(grad phi^H);  walls <- grad_par phi / dt_j.
+// DFTs of length N' by Bluestein: chirp, circular convolution of length L,
+// chirp.
+// ===========================================================================
+template <class T, int L1, int L2, int LINES>
+struct KZProject {
+  using E = Eng<T, L1, L2, LINES>;
+  using C = cx<T>;
+  static constexpr int THREADS = E::THREADS, NPHASE = 8;
+  static constexpr int MINB = 1;
+  static constexpr int NJ = (L1 + 1) / 2 + 2;  // rows of the compact n-layout stores (N' <= L2 * NJ)
+  struct Args {
+    ZGeom g;
+    ZTab<T> t;
+    C* X;                 // [3][N'][lines] in / out
+    double2* gradp;       // [2][2][lines] out
+    double dtj;
+    long long tiles;
+  };
+  struct Regs { C v[L1]; C u[L2]; };
+  static FC_HD int cidx(int j, int r, int li) { return (j * L2 + r) * LINES + li; }
+  static constexpr size_t CBUF = (size_t)NJ * L2 * LINES;
+  static constexpr size_t off_b1 = sizeof(C) * E::BUF;
+  static constexpr size_t off_s2 = off_b1 + sizeof(C) * E::BUF;
+  static constexpr size_t off_s3 = off_s2 + sizeof(C) * CBUF;
+  static constexpr size_t off_M = off_s3 + sizeof(C) * CBUF;
+  static constexpr size_t off_W = off_M + sizeof(double) * MRMAX;
+  // per line: b, t (complex double), A, B (complex double), D (double)
+  static constexpr size_t smem_bytes = off_W + sizeof(double) * LINES * 12;
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
+    C* b0 = reinterpret_cast<C*>(sm);
+    C* b1 = reinterpret_cast<C*>(sm + off_b1);
+    C* S2 = reinterpret_cast<C*>(sm + off_s2);
+    C* S3 = reinterpret_cast<C*>(sm + off_s3);
+    const double* Ms = reinterpret_cast<const double*>(sm + off_M);
+    const float2* Ms2 = reinterpret_cast<const float2*>(sm + off_M);
+    const int r = tid / LINES, li = tid % LINES;
+    double* W = reinterpret_cast<double*>(sm + off_W) + li * 12;
+    const long long line = bid * LINES + li;
+    const bool valid = line < a.g.lines;
+    const int Nz = a.g.Nz, Np = a.g.Np, d = a.g.d;
+    const long long Ls = a.g.lines;
+    const int kxi = valid ? (int)(line % a.g.Kx) : 0, kyi = valid ? (int)(line / a.g.Kx) : 0;
+    const double kxo = a.t.kxo[kxi], kyo = a.t.kyo[kyi];
+    C* xu = a.X + line;
+    C* xv = a.X + Np * Ls + line;
+    C* xw = a.X + 2LL * Np * Ls + line;
+    const T invNp = T(1.0 / Np);
+
+    if constexpr (P == 0) {
+      load_mr<T>(sm + off_M, a.t, a.g.Cc * d, tid, THREADS);
+      if (r < L2) {
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          C y = mk<T>(0, 0);
+          if (valid && n < Np) {
+            y = cadd(cscale(xu[(long long)n * Ls], (T)kxo), cscale(xv[(long long)n * Ls], (T)kyo));
+            y = cmul(y, a.t.chirp[n]);
+          }
+          R.v[j] = y;
+        }
+        E::template A<-1>(R.v, b0, a.t.tw, r, li);
+      }
+    } else if constexpr (P == 1) {
+      if (r < L1) {
+        E::template B<-1>(R.u, b0, r, li);
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(R.u[k2], a.t.Hbf[r + L1 * k2]);
+        E::template Bi<1>(R.u, b0, a.t.tw, r, li);
+      }
+      if (r < L2) {
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          R.v[j] = (valid && n < Np) ? cmul(xw[(long long)n * Ls], a.t.chirp[n]) : mk<T>(0, 0);
+        }
+        E::template A<-1>(R.v, b1, a.t.tw, r, li);
+      }
+    } else if constexpr (P == 2) {
+      if (r < L2) {  // Y^ = chirp * conv
+        E::template Ai<1>(R.v, b0, r, li);
+#pragma unroll
+        for (int j = 0; j < NJ && j < L1; ++j) {
+          const int n = r + L2 * j;
+          if (n < Np) S2[cidx(j, r, li)] = cmul(R.v[j], a.t.chirp[n]);
+        }
+      }
+      if (r < L1) {
+        E::template B<-1>(R.u, b1, r, li);
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(R.u[k2], a.t.Hbf[r + L1 * k2]);
+        E::template Bi<1>(R.u, b1, a.t.tw, r, li);
+      }
+    } else if constexpr (P == 3) {
+      if (r < L2) {  // W^, s, and the two inverse-DFT inputs
+        E::template Ai<1>(R.v, b1, r, li);
+        const double kp2 = kxo * kxo + kyo * kyo;
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          C s = mk<T>(0, 0);
+          if (n < Np && j < NJ) {
+            const C wh = cmul(R.v[j], a.t.chirp[n]);
+            const double kz = a.t.kzo[n];
+            const double k2 = kp2 + kz * kz;
+            const T inv = k2 > 0 ? (T)(1.0 / k2) : T(0);
+            s = cscale(cadd(S2[cidx(j, r, li)], cscale(wh, (T)kz)), inv);
+            S2[cidx(j, r, li)] = s;
+          }
+          C cc = (n < Np) ? a.t.chirp[n] : mk<T>(1, 0);
+          cc.y = -cc.y;
+          R.v[j] = cmul(s, cc);
+        }
+        E::template A<-1>(R.v, b0, a.t.tw, r, li);
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          C s = mk<T>(0, 0);
+          if (n < Np && j < NJ) {
+            C cc = a.t.chirp[n];
+            cc.y = -cc.y;
+            s = cmul(cscale(S2[cidx(j, r, li)], (T)a.t.kzo[n]), cc);
+          }
+          R.v[j] = s;
+        }
+        E::template A<-1>(R.v, b1, a.t.tw, r, li);
+      }
+    } else if constexpr (P == 4) {
+      if (r < L1) {
+        E::template B<-1>(R.u, b0, r, li);
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(R.u[k2], a.t.Hbi[r + L1 * k2]);
+        E::template Bi<1>(R.u, b0, a.t.tw, r, li);
+        E::template B<-1>(R.u, b1, r, li);
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(R.u[k2], a.t.Hbi[r + L1 * k2]);
+        E::template Bi<1>(R.u, b1, a.t.tw, r, li);
+      }
+    } else if constexpr (P == 5) {
+      if (r < L2) {  // sigma, sigma_z (extended grid); b, t
+        E::template Ai<1>(R.v, b0, r, li);
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          if (n < Np && j < NJ) {
+            C cc = a.t.chirp[n];
+            cc.y = -cc.y;
+            const C sg = cscale(cmul(R.v[j], cc), invNp);
+            S2[cidx(j, r, li)] = sg;
+          }
+        }
+        E::template Ai<1>(R.v, b1, r, li);
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          if (n < Np && j < NJ) {
+            C cc = a.t.chirp[n];
+            cc.y = -cc.y;
+            const C sz = cscale(cmul(R.v[j], cc), invNp);
+            S3[cidx(j, r, li)] = sz;
+            if (valid && (n == 0 || n == Nz - 1)) {
+              const C w = xw[(long long)n * Ls];
+              const int o = (n == 0) ? 0 : 2;
+              W[o] = (double)w.x - (double)sz.x;
+              W[o + 1] = (double)w.y - (double)sz.y;
+            }
+          }
+        }
+      }
+    } else if constexpr (P == 6) {
+      if (r == 0) {  // homogeneous coefficients in float64 (Eqs. A, B, D)
+        const double br = W[0], bi = W[1], tr = W[2], ti = W[3];
+        double Ar = 0, Ai_ = 0, Br = 0, Bi_ = 0, D = 0;
+        // gamma = |k_perp| of the Nyquist-zeroed wavenumbers (the same ones as
+        // the gradient i kx Phi, i ky Phi), so grad phi^H is divergence-free;
+        // where it vanishes, phi^H = D z with D = (b + t)/2.
+        if (kxo == 0.0 && kyo == 0.0) {
+          D = 0.5 * (br + tr);
+        } else {
+          const double gam = sqrt(kxo * kxo + kyo * kyo);
+          const double Ee = exp(-gam * a.g.Lz);
+          const double den = gam * (1.0 - Ee * Ee);
+          Ar = (tr - br * Ee) / den;
+          Ai_ = (ti - bi * Ee) / den;
+          Br = -(br - tr * Ee) / den;
+          Bi_ = -(bi - ti * Ee) / den;
+        }
+        W[4] = Ar; W[5] = Ai_; W[6] = Br; W[7] = Bi_; W[8] = D;
+      }
+    } else if constexpr (P == 7) {
+      if (r < L2 && valid) {
+        const double Ar = W[4], Aim = W[5], Br = W[6], Bim = W[7], D = W[8];
+        const bool mean = (kxo == 0.0 && kyo == 0.0);
+        const double gam = mean ? 0.0 : sqrt(kxo * kxo + kyo * kyo);
+        // Phi and Phi' at physical point s (analytic, float64 coefficients)
+        auto phi_at = [&](int s, C& ph, C& dph) {
+          const double z = s * a.g.dz;
+          if (mean) {
+            ph = mk<T>(0, 0);
+            dph = mk<T>((T)D, 0);
+            return;
+          }
+          T e1, e2;
+          if constexpr (sizeof(T) == 4) {
+            e1 = expf((float)(gam * (z - a.g.Lz)));
+            e2 = expf((float)(-gam * z));
+          } else {
+            e1 = exp(gam * (z - a.g.Lz));
+            e2 = exp(-gam * z);
+          }
+          const T g = (T)gam;
+          ph = mk<T>((T)Ar * e1 + (T)Br * e2, (T)Aim * e1 + (T)Bim * e2);
+          dph = mk<T>(g * ((T)Ar * e1 - (T)Br * e2), g * ((T)Aim * e1 - (T)Bim * e2));
+        };
+        C eph[2 * DMAX], edph[2 * DMAX];
+        bool have_ends = false;
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          if (n < Np && j < NJ) {
+            C ph, dph;
+            if (n < Nz) {
+              phi_at(n, ph, dph);
+            } else {
+              if (!have_ends) {
+                for (int i = 0; i < d; ++i) {
+                  phi_at(i, eph[i], edph[i]);
+                  phi_at(Nz - d + i, eph[DMAX + i], edph[DMAX + i]);
+                }
+                have_ends = true;
+              }
+              ph = continuation_value<T>(n - Nz, eph, eph + DMAX, d, a.g.Cc, Ms, Ms2);
+              dph = continuation_value<T>(n - Nz, edph, edph + DMAX, d, a.g.Cc, Ms, Ms2);
+            }
+            const C sg = S2[cidx(j, r, li)];
+            const C sz = S3[cidx(j, r, li)];
+            // i k Phi = (-k Phi.y, k Phi.x)
+            const C gx = cadd(cscale(sg, (T)kxo), mk<T>(-(T)kxo * ph.y, (T)kxo * ph.x));
+            const C gy = cadd(cscale(sg, (T)kyo), mk<T>(-(T)kyo * ph.y, (T)kyo * ph.x));
+            const C gz = cadd(sz, dph);
+            const long long o = (long long)n * Ls;
+            xu[o] = csub(xu[o], gx);
+            xv[o] = csub(xv[o], gy);
+            xw[o] = csub(xw[o], gz);
+            if (n == 0 || n == Nz - 1) {
+              const int wall = (n == 0) ? 0 : 1;
+              const double s = 1.0 / a.dtj;
+              a.gradp[((long long)wall * 2 + 0) * Ls + line] = make_double2((double)gx.x * s, (double)gx.y * s);
+              a.gradp[((long long)wall * 2 + 1) * Ls + line] = make_double2((double)gy.x * s, (double)gy.y * s);
+            }
+          }
+        }
+      }
+    }
+  }
+};
+
+// ===========================================================================
+// Y transforms (length Ny, 2/3/5-smooth, no padding).  Lines are kx
+// (contiguous), the transform runs over ky with stride Kx, one z plane per
+// grid row.  Arrays are [nf][planes_total][Ny][Kx]; the kernel touches planes
+// 0..Nz-1 of every field.
+// ===========================================================================
+struct YGeom {
+  int Ny, Kx, Nz;
+  long long plane;          // Ny * Kx
+};
+
+// yinv3: V = IFFT_y(A), DY = IFFT_y(i ky A), DZ <- IFFT_y(DZ) (1/Ny included)
+template <class T, int L1, int L2, int LINES>
+struct KYInv3 {
+  using E = Eng<T, L1, L2, LINES>;
+  using C = cx<T>;
+  static constexpr int THREADS = E::THREADS, NPHASE = 4;
+  static constexpr int MINB = (sizeof(T) == 4 && THREADS <= 512) ? 2 : 1;
+  struct Args {
+    YGeom g;
+    const C* tw;
+    const double* kyo;
+    const C* A; long long a_fstride;   // source field stride (planes)
+    C* V; C* DY; C* DZ;                 // [nf][Nz][Ny][Kx]
+    long long tiles;                    // tiles per plane
+    T scale;
+  };
+  struct Regs { C v[L1]; C u[L2]; };
+  static constexpr size_t smem_bytes = 2 * sizeof(C) * E::BUF;
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
+    C* b0 = reinterpret_cast<C*>(sm);
+    C* b1 = b0 + E::BUF;
+    const int r = tid / LINES, li = tid % LINES;
+    const long long tile = bid % a.tiles;
+    const long long pz = bid / a.tiles;          // f * Nz + z
+    const long long f = pz / a.g.Nz, z = pz % a.g.Nz;
+    const int kx = (int)(tile * LINES + li);
+    const bool valid = kx < a.g.Kx;
+    const C* src = a.A + (f * a.a_fstride + z) * a.g.plane + kx;
+    const long long mo = pz * a.g.plane + kx;
+    if constexpr (P == 0) {
+      if (r < L2) {
+#pragma unroll
+        for (int j = 0; j < L1; ++j) R.v[j] = valid ? src[(long long)(r + L2 * j) * a.g.Kx] : mk<T>(0, 0);
+        E::template A<1>(R.v, b0, a.tw, r, li);
+      }
+    } else if constexpr (P == 1) {
+      if (r < L1) {
+        E::template B<1>(R.u, b0, r, li);
+        if (valid)
+#pragma unroll
+          for (int k2 = 0; k2 < L2; ++k2) a.V[mo + (long long)(r + L1 * k2) * a.g.Kx] = cscale(R.u[k2], a.scale);
+      }
+      if (r < L2) {
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int ky = r + L2 * j;
+          const C x = valid ? src[(long long)ky * a.g.Kx] : mk<T>(0, 0);
+          const T k = (T)a.kyo[ky];
+          R.v[j] = mk<T>(-k * x.y, k * x.x);
+        }
+        E::template A<1>(R.v, b1, a.tw, r, li);
+      }
+    } else if constexpr (P == 2) {
+      if (r < L1) {
+        E::template B<1>(R.u, b1, r, li);
+        if (valid)
+#pragma unroll
+          for (int k2 = 0; k2 < L2; ++k2) a.DY[mo + (long long)(r + L1 * k2) * a.g.Kx] = cscale(R.u[k2], a.scale);
+      }
+      if (r < L2) {
+#pragma unroll
+        for (int j = 0; j < L1; ++j) R.v[j] = valid ? a.DZ[mo + (long long)(r + L2 * j) * a.g.Kx] : mk<T>(0, 0);
+        E::template A<1>(R.v, b0, a.tw, r, li);
+      }
+    } else if constexpr (P == 3) {
+      if (r < L1) {
+        E::template B<1>(R.u, b0, r, li);
+        if (valid)
+#pragma unroll
+          for (int k2 = 0; k2 < L2; ++k2) a.DZ[mo + (long long)(r + L1 * k2) * a.g.Kx] = cscale(R.u[k2], a.scale);
+      }
+    }
+  }
+};
+
+// y1: one transform per plane, OUT = scale * FFT_y^{SIGN}(IN) (may alias)
+template <class T, int L1, int L2, int LINES, int SIGN>
+struct KY1 {
+  using E = Eng<T, L1, L2, LINES>;
+  using C = cx<T>;
+  static constexpr int THREADS = E::THREADS, NPHASE = 2;
+  static constexpr int MINB = (sizeof(T) == 4 && THREADS <= 512) ? 2 : 1;
+  struct Args {
+    YGeom g;
+    const C* tw;
+    const C* IN; long long in_fstride;   // planes between fields of IN
+    C* OUT; long long out_fstride;
+    long long tiles;
+    T scale;
+  };
+  struct Regs { C v[L1]; C u[L2]; };
+  static constexpr size_t smem_bytes = sizeof(C) * E::BUF;
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
+    C* b0 = reinterpret_cast<C*>(sm);
+    const int r = tid / LINES, li = tid % LINES;
+    const long long tile = bid % a.tiles;
+    const long long pz = bid / a.tiles;
+    const long long f = pz / a.g.Nz, z = pz % a.g.Nz;
+    const int kx = (int)(tile * LINES + li);
+    const bool valid = kx < a.g.Kx;
+    if constexpr (P == 0) {
+      if (r < L2) {
+        const C* src = a.IN + (f * a.in_fstride + z) * a.g.plane + kx;
+#pragma unroll
+        for (int j = 0; j < L1; ++j) R.v[j] = valid ? src[(long long)(r + L2 * j) * a.g.Kx] : mk<T>(0, 0);
+        E::template A<SIGN>(R.v, b0, a.tw, r, li);
+      }
+    } else {
+      if (r < L1) {
+        E::template B<SIGN>(R.u, b0, r, li);
+        C* dst = a.OUT + (f * a.out_fstride + z) * a.g.plane + kx;
+        if (valid)
+#pragma unroll
+          for (int k2 = 0; k2 < L2; ++k2) dst[(long long)(r + L1 * k2) * a.g.Kx] = cscale(R.u[k2], a.scale);
+      }
+    }
+  }
+};
+
+// ===========================================================================
+// X transforms: one CTA per (y, z) row (all fields), row FFTs of length Nx in
+// shared memory; groups of G threads per transform.
+// ===========================================================================
+template <class T, int L1, int L2>
+struct RowEng {
+  static constexpr int L = L1 * L2;
+  static constexpr int G = L1 > L2 ? L1 : L2;
+  static constexpr int ROW = L2 + 1;     // padded exchange row
+  static constexpr int BUF = L1 * ROW;
+  using C = cx<T>;
+  static FC_HD C twid(const C* tw, int n2, int k1, int sign) {
+    C w = tw[n2 * L1 + k1];
+    if (sign > 0) w.y = -w.y;
+    return w;
+  }
+  template <int SIGN>
+  static FC_HD void A(C (&v)[L1], C* buf, const C* tw, int n2) {
+    dft_reg<L1, SIGN, T>(v);
+#pragma unroll
+    for (int k1 = 0; k1 < L1; ++k1) buf[k1 * ROW + n2] = cmul(v[k1], twid(tw, n2, k1, SIGN));
+  }
+  template <int SIGN>
+  static FC_HD void B(C (&u)[L2], const C* buf, int k1) {
+#pragma unroll
+    for (int n2 = 0; n2 < L2; ++n2) u[n2] = buf[k1 * ROW + n2];
+    dft_reg<L2, SIGN, T>(u);
+  }
+};
+
+// xpass: nonlinear products of one row.  For every field f the real rows
+// v_f, dx v_f, dy v_f, dz v_f are obtained by complex inverse transforms of
+// pairs (v + i dx v), (dy v + i dz v) of Hermitian half spectra; the products
+//   N_f = -(u dx + v dy + w dz) v_f (+ F on u; + gamma theta on w; + gamma w
+//   on theta) are formed in physical space (Sec. 4.2, Sec. 6, Sec. 7) and
+// transformed back in pairs (N_a + i N_b).
+template <class T, int L1, int L2, int NF>
+struct KXPass {
+  using RE = RowEng<T, L1, L2>;
+  using C = cx<T>;
+  static constexpr int Nx = L1 * L2, G = RE::G, NJOB = 2 * NF, NFWD = (NF + 1) / 2;
+  static constexpr int THREADS = NJOB * G, NPHASE = 6, MINB = 1;
+  struct Args {
+    int Kx;
+    long long rows;          // Nz * Ny
+    const C* tw;             // Nx engine twiddles
+    const double* kxo;       // Kx
+    const C* V; const C* DY; const C* DZ;   // [NF][rows][Kx]
+    C* NL;                                  // [NF][rows][Kx]
+    T forcing, gamma, scale;                // scale = 1/Nx
+  };
+  struct Regs { C v[L1]; C u[L2]; };
+  static constexpr size_t off_P = sizeof(C) * RE::BUF * NJOB;
+  static constexpr size_t smem_bytes = off_P + sizeof(T) * 4 * NF * Nx;
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long row, Regs& R) {
+    C* Zb = reinterpret_cast<C*>(sm);
+    T* Pr = reinterpret_cast<T*>(sm + off_P);
+    const int q = tid / G, g = tid % G;
+    const long long Kx = a.Kx;
+    if constexpr (P == 0) {
+      if (g < L2) {
+        const int f = q / 2, type = q % 2;
+        const C* A = (type == 0 ? a.V : a.DY) + ((long long)f * a.rows + row) * Kx;
+        const C* Bq = a.DZ + ((long long)f * a.rows + row) * Kx;
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int k = g + L2 * j;
+          const bool up = k > Nx / 2;
+          const int kk = up ? Nx - k : k;
+          C av = A[kk], bv;
+          if (type == 0) {
+            const T kx = (T)a.kxo[kk];
+            bv = mk<T>(-kx * av.y, kx * av.x);
+          } else {
+            bv = Bq[kk];
+          }
+          if (kk == 0 || kk == Nx / 2) { av.y = T(0); bv.y = T(0); }
+          if (up) { av.y = -av.y; bv.y = -bv.y; }
+          R.v[j] = mk<T>(av.x - bv.y, av.y + bv.x);  // A + i B
+        }
+        RE::template A<1>(R.v, Zb + q * RE::BUF, a.tw, g);
+      }
+    } else if constexpr (P == 1) {
+      if (g < L1) {
+        RE::template B<1>(R.u, Zb + q * RE::BUF, g);
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) {
+          const int n = g + L1 * k2;
+          Pr[(2 * q) * Nx + n] = R.u[k2].x * a.scale;
+          Pr[(2 * q + 1) * Nx + n] = R.u[k2].y * a.scale;
+        }
+      }
+    } else if constexpr (P == 2) {
+      for (int n = tid; n < Nx; n += THREADS) {
+        const T u = Pr[0 * Nx + n], v = Pr[4 * Nx + n], w = Pr[8 * Nx + n];
+        T Nf[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          Nf[f] = -(u * Pr[(4 * f + 1) * Nx + n] + v * Pr[(4 * f + 2) * Nx + n] + w * Pr[(4 * f + 3) * Nx + n]);
+        Nf[0] += a.forcing;
+        if constexpr (NF == 4) {
+          Nf[2] += a.gamma * Pr[12 * Nx + n];
+          Nf[3] += a.gamma * w;
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) Pr[f * Nx + n] = Nf[f];
+      }
+    } else if constexpr (P == 3) {
+      if (q < NFWD && g < L2) {
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = g + L2 * j;
+          const T re = Pr[(2 * q) * Nx + n];
+          const T im = (2 * q + 1 < NF) ? Pr[(2 * q + 1) * Nx + n] : T(0);
+          R.v[j] = mk<T>(re, im);
+        }
+        RE::template A<-1>(R.v, Zb + q * RE::BUF, a.tw, g);
+      }
+    } else if constexpr (P == 4) {
+      if (q < NFWD && g < L1) {
+        RE::template B<-1>(R.u, Zb + q * RE::BUF, g);
+        C* Zn = Zb + (NFWD + q) * RE::BUF;   // natural order spectrum
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) Zn[g + L1 * k2] = R.u[k2];
+      }
+    } else if constexpr (P == 5) {
+      for (int i = tid; i < NFWD * (Nx / 2 + 1); i += THREADS) {
+        const int qq = i / (Nx / 2 + 1), k = i % (Nx / 2 + 1);
+        const C* Zn = Zb + (NFWD + qq) * RE::BUF;
+        const C zk = Zn[k], zm = Zn[(Nx - k) % Nx];
+        // A = (Z_k + conj Z_{N-k}) / 2,  B = (Z_k - conj Z_{N-k}) / (2i)
+        const C Av = mk<T>((zk.x + zm.x) * T(0.5), (zk.y - zm.y) * T(0.5));
+        const C Bv = mk<T>((zk.y + zm.y) * T(0.5), (zm.x - zk.x) * T(0.5));
+        a.NL[((long long)(2 * qq) * a.rows + row) * Kx + k] = Av;
+        if (2 * qq + 1 < NF) a.NL[((long long)(2 * qq + 1) * a.rows + row) * Kx + k] = Bv;
+      }
+    }
+  }
+};
+
+// xfwd: real rows -> Hermitian half spectra, two rows per complex transform.
+// xinv: half spectra -> real rows (scale 1/Nx), two rows per transform.
+template <class T, int L1, int L2, int SIGN, int JOBS>
+struct KXRow {
+  using RE = RowEng<T, L1, L2>;
+  using C = cx<T>;
+  static constexpr int Nx = L1 * L2, G = RE::G;
+  static constexpr int THREADS = JOBS * G, NPHASE = 3, MINB = 1;
+  struct Args {
+    int Kx;
+    long long pairs;        // number of row pairs (rows / 2)
+    const C* tw;
+    const T* R; C* S;       // SIGN = -1: R -> S;  SIGN = +1: S -> R
+    T scale;
+  };
+  struct Regs { C v[L1]; C u[L2]; };
+  static constexpr size_t smem_bytes = sizeof(C) * RE::BUF * JOBS * 2;
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& Rg) {
+    const int q = tid / G, g = tid % G;
+    const long long pair = bid * JOBS + q;
+    const bool valid = pair < a.pairs;
+    C* Zb = reinterpret_cast<C*>(sm) + q * RE::BUF;
+    C* Zn = reinterpret_cast<C*>(sm) + (JOBS + q) * RE::BUF;
+    const long long Kx = a.Kx;
+    if constexpr (SIGN < 0) {
+      const T* r0 = a.R + (2 * pair) * Nx;
+      if constexpr (P == 0) {
+        if (g < L2) {
+#pragma unroll
+          for (int j = 0; j < L1; ++j) {
+            const int n = g + L2 * j;
+            Rg.v[j] = valid ? mk<T>(r0[n], r0[Nx + n]) : mk<T>(0, 0);
+          }
+          RE::template A<-1>(Rg.v, Zb, a.tw, g);
+        }
+      } else if constexpr (P == 1) {
+        if (g < L1) {
+          RE::template B<-1>(Rg.u, Zb, g);
+#pragma unroll
+          for (int k2 = 0; k2 < L2; ++k2) Zn[g + L1 * k2] = Rg.u[k2];
+        }
+      } else {
+        if (valid)
+          for (int k = g; k <= Nx / 2; k += G) {
+            const C zk = Zn[k], zm = Zn[(Nx - k) % Nx];
+            a.S[(2 * pair) * Kx + k] = mk<T>((zk.x + zm.x) * T(0.5), (zk.y - zm.y) * T(0.5));
+            a.S[(2 * pair + 1) * Kx + k] = mk<T>((zk.y + zm.y) * T(0.5), (zm.x - zk.x) * T(0.5));
+          }
+      }
+    } else {
+      if constexpr (P == 0) {
+        if (g < L2) {
+          const C* s0 = a.S + (2 * pair) * Kx;
+#pragma unroll
+          for (int j = 0; j < L1; ++j) {
+            const int k = g + L2 * j;
+            const bool up = k > Nx / 2;
+            const int kk = up ? Nx - k : k;
+            C av = valid ? s0[kk] : mk<T>(0, 0), bv = valid ? s0[Kx + kk] : mk<T>(0, 0);
+            if (kk == 0 || kk == Nx / 2) { av.y = T(0); bv.y = T(0); }
+            if (up) { av.y = -av.y; bv.y = -bv.y; }
+            Rg.v[j] = mk<T>(av.x - bv.y, av.y + bv.x);
+          }
+          RE::template A<1>(Rg.v, Zb, a.tw, g);
+        }
+      } else if constexpr (P == 1) {
+        if (g < L1) {
+          RE::template B<1>(Rg.u, Zb, g);
+#pragma unroll
+          for (int k2 = 0; k2 < L2; ++k2) Zn[g + L1 * k2] = Rg.u[k2];
+        }
+      } else {
+        if (valid) {
+          T* r0 = const_cast<T*>(a.R) + (2 * pair) * Nx;
+          for (int n = g; n < Nx; n += G) {
+            r0[n] = Zn[n].x * a.scale;
+            r0[Nx + n] = Zn[n].y * a.scale;
+          }
+        }
+      }
+    }
+  }
+};
+
+}  // namespace fcns

@@ -18,7 +18,7 @@ namespace fcns {
 
 #ifndef FC_HOSTCHECK
 template <class K>
-__global__ void __launch_bounds__(K::THREADS, 1) phased_kernel(const typename K::Args a) {
+__global__ void __launch_bounds__(K::THREADS, K::MINB) phased_kernel(const typename K::Args a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   typename K::Regs r;
   SFor<0, K::NPHASE>::run([&](auto pc) {

@@ -11,16 +11,22 @@ Seeds: ``numpy.random.Generator(PCG64(BASE_SEED + workload + instance))``.
 Workload recipes (shapes follow the channel and Rayleigh-Benard runs of the
 paper, Sec. 6 table of channel runs and Sec. 7 table of convection runs):
 
-* channel velocity: each component is a sum of horizontal Fourier modes with
-  0 < |k_perp| <= 8, amplitude |k_perp|^-2 and uniform random phase, times a
-  wall-vanishing profile z(Lz - z)(1 + a1 z + a2 z^2), scaled to 0.1 max U,
-  plus the laminar profile U = F z (Lz - z) / (2 nu) in x (Sec. 6, laminar
-  solution; F/nu = 10 as in runs L1-L3).
+* channel velocity: a solenoidal no-slip fluctuation built from a toroidal
+  and a poloidal potential (the construction of App. A, with polynomial
+  instead of Chandrasekhar-Reid profiles),
+      v' = curl(psi z_hat) + curl curl(chi z_hat),
+      psi = X1(x,y) z(Lz - z)(1 + a1 z + a2 z^2),
+      chi = X2(x,y) z^2 (Lz - z)^2 (1 + b1 z),
+  X1, X2 sums of horizontal Fourier modes with 0 < |k_perp| <= 8, random
+  phases and amplitudes |k_perp|^-3 and |k_perp|^-4 (velocity spectrum
+  ~ |k_perp|^-2), scaled to 0.1 max U, plus the laminar profile
+  U = F z (Lz - z) / (2 nu) in x (Sec. 6, laminar solution; F/nu = 10 as in
+  runs L1-L3).  v' vanishes at both walls and is divergence-free.
 * derivative field: f = sum_p X_p(x, y) Z_p(z), X_p a random 2D field with
   |a_k| ~ k^-4/3 up to the 2/3 cutoff, Z_p a Chebyshev series with
   coefficients N(0,1) 2^(-n/2), n <= 16 (exact z-derivatives in closed form).
-* Boussinesq: theta = 1e-3 eta(x,y) sin(pi z / Lz), velocity = 1e-3 times the
-  channel fluctuation (no mean flow).
+* Boussinesq: theta = 1e-3 eta(x,y) sin(pi z / Lz), velocity = 1e-3 times a
+  channel-type solenoidal fluctuation (no mean flow).
 """
 from __future__ import annotations
 
@@ -82,6 +88,48 @@ def kolmogorov_xy_field(g: np.random.Generator, Nx: int, Ny: int,
 # channel flow (incompressible Navier-Stokes, walls at z = 0, Lz)
 # ----------------------------------------------------------------------------
 
+def _xy_derivs(X: np.ndarray, Lx: float, Ly: float):
+    """Exact x, y derivatives of a trigonometric polynomial sampled on the grid."""
+    Ny, Nx = X.shape
+    Xh = np.fft.fft2(X)
+    kx = 2 * np.pi * np.fft.fftfreq(Nx, d=Lx / Nx)
+    ky = 2 * np.pi * np.fft.fftfreq(Ny, d=Ly / Ny)
+    KY, KX = np.meshgrid(ky, kx, indexing="ij")
+    dx = np.real(np.fft.ifft2(1j * KX * Xh))
+    dy = np.real(np.fft.ifft2(1j * KY * Xh))
+    lap = np.real(np.fft.ifft2(-(KX ** 2 + KY ** 2) * Xh))
+    return dx, dy, lap
+
+
+def solenoidal_fluctuation(g: np.random.Generator, Nx: int, Ny: int, Nz: int, Lz: float = 1.0,
+                           Lx: float = 2 * np.pi, Ly: float = 2 * np.pi, dtype=np.float64) -> np.ndarray:
+    """curl(psi z) + curl curl(chi z) with wall-vanishing polynomial profiles,
+    shape [3][Nz][Ny][Nx], scaled to max |v| = 1."""
+    z = z_grid(Nz, Lz)
+    X1 = xy_modes_field(g, Nx, Ny, slope=-3.0, Lx=Lx, Ly=Ly)
+    X2 = xy_modes_field(g, Nx, Ny, slope=-4.0, Lx=Lx, Ly=Ly)
+    a1, a2, b1 = g.uniform(-1.0, 1.0, size=3)
+    poly = np.polynomial.Polynomial
+    P = poly([0.0, Lz, -1.0]) * poly([1.0, a1, a2])          # z (Lz - z)(1 + a1 z + a2 z^2)
+    Q = poly([0.0, Lz, -1.0]) ** 2 * poly([1.0, b1])         # z^2 (Lz - z)^2 (1 + b1 z)
+    Pv, Qv, dQv = P(z), Q(z), Q.deriv()(z)
+    X1x, X1y, _ = _xy_derivs(X1, Lx, Ly)
+    X2x, X2y, X2lap = _xy_derivs(X2, Lx, Ly)
+    # curl(psi z) = (d_y psi, -d_x psi, 0); curl curl(chi z) = (d_x d_z chi, d_y d_z chi, -lap_h chi)
+    terms = [((X1y, Pv), (X2x, dQv)), ((-X1x, Pv), (X2y, dQv)), ((-X2lap, Qv), None)]
+    # scale: max over the grid of each component, evaluated on the profiles' extrema per xy point
+    out = np.empty((3, Nz, Ny, Nx), dtype=dtype)
+    tmp = np.empty((Nz, Ny, Nx), dtype=dtype)
+    for c, (t1, t2) in enumerate(terms):
+        np.multiply(t1[1].astype(dtype)[:, None, None], t1[0].astype(dtype)[None], out=out[c])
+        if t2 is not None:
+            np.multiply(t2[1].astype(dtype)[:, None, None], t2[0].astype(dtype)[None], out=tmp)
+            out[c] += tmp
+    del tmp
+    out *= dtype(1.0) / np.abs(out).max() if dtype is not np.float64 else 1.0 / np.abs(out).max()
+    return out
+
+
 def channel_velocity(Nx: int, Ny: int, Nz: int, nu: float = 1e-2, F_over_nu: float = 10.0,
                      Lz: float = 1.0, seed_offset: int = 0, fluct: float = 0.1,
                      mean_flow: bool = True) -> np.ndarray:
@@ -91,13 +139,7 @@ def channel_velocity(Nx: int, Ny: int, Nz: int, nu: float = 1e-2, F_over_nu: flo
     F = F_over_nu * nu
     U = F * z * (Lz - z) / (2 * nu)
     Umax = F * Lz * Lz / (8 * nu)
-    out = np.empty((3, Nz, Ny, Nx))
-    for c in range(3):
-        X = xy_modes_field(g, Nx, Ny)
-        a1, a2 = g.uniform(-1.0, 1.0, size=2)
-        P = z * (Lz - z) * (1 + a1 * z + a2 * z * z)
-        P = P / np.abs(P).max()
-        out[c] = (fluct * Umax) * P[:, None, None] * X[None, :, :]
+    out = (fluct * Umax) * solenoidal_fluctuation(g, Nx, Ny, Nz, Lz)
     if mean_flow:
         out[0] += U[:, None, None]
     return out
@@ -122,12 +164,8 @@ def boussinesq_fields(Nx: int, Ny: int, Nz: int, Lz: float = 1.0, seed_offset: i
     g = rng(2, seed_offset)
     z = z_grid(Nz, Lz)
     out = np.empty((4, Nz, Ny, Nx), dtype=dtype)
-    for c in range(3):
-        X = xy_modes_field(g, Nx, Ny).astype(dtype)
-        a1, a2 = g.uniform(-1.0, 1.0, size=2)
-        P = z * (Lz - z) * (1 + a1 * z + a2 * z * z)
-        P = (amp * 0.1 * 1.25) * P / np.abs(P).max()
-        np.multiply(P.astype(dtype)[:, None, None], X[None, :, :], out=out[c])
+    out[:3] = solenoidal_fluctuation(g, Nx, Ny, Nz, Lz, dtype=dtype)
+    out[:3] *= dtype(amp * 0.1 * 1.25)
     eta = xy_modes_field(g, Nx, Ny).astype(dtype)
     prof = (amp * np.sin(np.pi * z / Lz)).astype(dtype)
     np.multiply(prof[:, None, None], eta[None, :, :], out=out[3])

@@ -1,0 +1,183 @@
+"""Navier-Stokes / Boussinesq path on the GPU vs the FP64 oracle (through the C ABI)."""
+import numpy as np
+import pytest
+
+from oracle import ns
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2002_01392_gb300 import api as a
+    assert torch.cuda.is_available()
+    return a
+
+
+def _rel(a, b):
+    a = np.asarray(a)
+    a = a.astype(np.complex128 if np.iscomplexobj(a) else np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _cuda(x, dt=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dt)
+
+
+def _oracle_steps(v, P, dt, n):
+    st = ns.to_spectral(v, P)
+    gp = np.zeros((2, 2, P.Ny, P.Kx), complex)
+    for _ in range(n):
+        st, gp = ns.rk_step(st, gp, P, dt)
+    return np.stack([ns.to_physical(c, P) for c in st]), gp, st
+
+
+# ---------------------------------------------------------------------------
+# the plain FP64 channel workload: 32 x 32 x 33, d = 5, C = 25, nu = 1e-2
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cfg0(api):
+    N, Nz, nu = 32, 33, 1e-2
+    p = api.ns_params(Nx=N, Ny=N, Nz=Nz, nu=nu, forcing_x=10 * nu, prec="f64")
+    sim = api.Sim(p)
+    P = ns.Params(N, N, Nz, nu=nu, forcing_x=10 * nu)
+    v = synth.channel_velocity(N, N, Nz, nu=nu)
+    yield sim, P, v
+    sim.close()
+
+
+def test_cfg0_fields_roundtrip(cfg0):
+    sim, P, v = cfg0
+    sim.set_fields(_cuda(v))
+    out = sim.get_fields().cpu().numpy()
+    assert np.abs(out - v).max() < 1e-14
+
+
+def test_cfg0_rhs(cfg0):
+    sim, P, v = cfg0
+    out = sim.rhs(_cuda(v)).cpu().numpy()
+    assert _rel(out, ns.ns_rhs(v, P)) < 1e-11
+
+
+def test_cfg0_projection(cfg0):
+    sim, P, v = cfg0
+    g = np.random.default_rng(2)
+    z = synth.z_grid(P.Nz)
+    vs = v + 0.2 * (z * (1 - z))[None, :, None, None] * g.standard_normal((3, 1, P.Ny, P.Nx))
+    sim.set_fields(_cuda(v))
+    gp = torch.zeros((2, 2, P.Ny, P.Kx), dtype=torch.complex128, device="cuda")
+    out = sim.project(_cuda(vs), 1e-3, gradp_out=gp).cpu().numpy()
+    ref, gref = ns.poisson_project(vs, P, 1e-3)
+    assert _rel(out, ref) < 1e-11
+    assert _rel(gp.cpu().numpy(), gref) < 1e-11
+    # wall-normal velocity after projection is zero to round-off (Sec. 6)
+    assert np.abs(out[2][[0, -1]]).max() < 1e-13
+
+
+def test_cfg0_rk3_steps(cfg0):
+    sim, P, v = cfg0
+    sim.set_fields(_cuda(v))
+    for _ in range(3):
+        sim.step(1e-3)
+    out = sim.get_fields().cpu().numpy()
+    ref, gref, _ = _oracle_steps(v, P, 1e-3, 3)
+    assert _rel(out, ref) < 1e-11
+    assert _rel(sim.wall_gradp().cpu().numpy(), gref) < 1e-10
+
+
+def test_poiseuille_fixed_point(api):
+    N, Nz, nu = 32, 33, 1e-2
+    sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nu=nu, forcing_x=10 * nu, prec="f64"))
+    v = synth.poiseuille(N, N, Nz, F=10 * nu, nu=nu)
+    sim.set_fields(_cuda(v))
+    sim.step(1e-3)
+    assert np.abs(sim.get_fields().cpu().numpy() - v).max() < 1e-10 * 1.25
+    sim.close()
+
+
+def test_checkpoint_restore_bitwise(cfg0):
+    sim, P, v = cfg0
+    sim.set_fields(_cuda(v))
+    sim.step(1e-3)
+    st = sim.get_state().clone()
+    gp = sim.wall_gradp().clone()
+    sim.step(1e-3)
+    a = sim.get_fields().clone()
+    sim.put_state(st)
+    sim.put_wall_gradp(gp)
+    sim.step(1e-3)
+    b = sim.get_fields()
+    assert torch.equal(a, b)
+
+
+def test_caller_workspace_and_determinism(api):
+    N, Nz = 32, 33
+    p = api.ns_params(Nx=N, Ny=N, Nz=Nz, prec="f64")
+    nb = api.ns_workspace_bytes(p)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    s1 = api.Sim(p, workspace=ws)
+    s2 = api.Sim(p)
+    v = _cuda(synth.channel_velocity(N, N, Nz))
+    for s in (s1, s2):
+        s.set_fields(v)
+        s.step(1e-3)
+    assert torch.equal(s1.get_fields(), s2.get_fields())
+    s1.close()
+    s2.close()
+
+
+@pytest.mark.parametrize("N,Nz", [(32, 33), (64, 65)])
+def test_channel_float32(api, N, Nz):
+    nu = 1e-2
+    sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nu=nu, forcing_x=10 * nu, prec="f32"))
+    P = ns.Params(N, N, Nz, nu=nu, forcing_x=10 * nu)
+    v = synth.channel_velocity(N, N, Nz, nu=nu).astype(np.float32).astype(np.float64)
+    sim.set_fields(_cuda(v, torch.float32))
+    for _ in range(2):
+        sim.step(1e-3)
+    out = sim.get_fields().cpu().numpy()
+    ref, _, _ = _oracle_steps(v, P, 1e-3, 2)
+    assert _rel(out, ref) < 1e-5
+    sim.close()
+
+
+@pytest.mark.parametrize("N,Nz", [(32, 65), (128, 129)])
+def test_boussinesq_float32(api, N, Nz):
+    kw = dict(nu=3.162e-3, kappa=3.162e-3, gamma=1.0)
+    sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nfields=4, prec="f32", **kw))
+    P = ns.Params(N, N, Nz, nfields=4, **kw)
+    f = synth.boussinesq_fields(N, N, Nz, amp=1e-1).astype(np.float32).astype(np.float64)
+    sim.set_fields(_cuda(f, torch.float32))
+    sim.step(2e-3)
+    out = sim.get_fields().cpu().numpy()
+    ref, _, _ = _oracle_steps(f, P, 2e-3, 1)
+    for c in range(4):
+        assert _rel(out[c], ref[c]) < 5e-5, c
+    sim.close()
+
+
+def test_full_size_boussinesq_properties(api):
+    """1024 x 1024 x 513, 4 fields, FP32, as bench.py runs it: one RK3 step stays
+    finite, keeps w = 0 at the walls and theta = 0 at the walls, and the
+    conduction state (all zero) is an exact fixed point."""
+    N, Nz = 1024, 513
+    kw = dict(nu=3.162e-4, kappa=3.162e-4, gamma=1.0)
+    sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nfields=4, prec="f32", **kw))
+    z = torch.zeros((4, Nz, N, N), dtype=torch.float32, device="cuda")
+    sim.set_fields(z)
+    sim.step(1e-3)
+    assert torch.count_nonzero(sim.get_fields()) == 0
+    f = torch.from_numpy(synth.boussinesq_fields(N, N, Nz, dtype=np.float32)).cuda()
+    sim.set_fields(f)
+    del f
+    sim.step(1e-3)
+    out = sim.get_fields()
+    assert torch.isfinite(out).all()
+    scale = out[:3].abs().max().item()
+    assert out[2, [0, -1]].abs().max().item() < 1e-5 * scale
+    assert out[3, [0, -1]].abs().max().item() < 1e-5 * out[3].abs().max().item()
+    sim.close()

@@ -71,7 +71,7 @@ def test_conduction_state_is_exactly_fixed(Mr_5_25):
 def test_projection_wall_normal_velocity_is_roundoff(Mr_5_25):
     """After projection w = 0 at the walls to round-off (Sec. 6: <w^2|wall> ~ 1e-35)."""
     p = ns.Params(32, 32, 33, nu=1e-2, Mr=Mr_5_25)
-    v = synth.channel_velocity(32, 32, 33)
+    v = _divergent_field(32, 33)
     vp, gp = ns.poisson_project(v, p, 1e-3)
     assert np.abs(vp[2][[0, -1]]).max() < 1e-14
     st = ns.to_spectral(v, p)
@@ -79,9 +79,20 @@ def test_projection_wall_normal_velocity_is_roundoff(Mr_5_25):
     assert ns.wall_mean_squares(st2, p)[2] < 1e-28
 
 
+def _divergent_field(N, Nz):
+    """Solenoidal channel field plus a seeded non-solenoidal, wall-vanishing part."""
+    v = synth.channel_velocity(N, N, Nz)
+    g = np.random.default_rng(5)
+    z = synth.z_grid(Nz)
+    for c in range(3):
+        X = synth.xy_modes_field(g, N, N)
+        v[c] += 0.2 * (z * (1 - z))[:, None, None] * X[None]
+    return v
+
+
 def test_projection_reduces_divergence(Mr_5_25):
     p = ns.Params(32, 32, 33, nu=1e-2, forcing_x=0.1, Mr=Mr_5_25)
-    v = synth.channel_velocity(32, 32, 33)
+    v = _divergent_field(32, 33)
     st = ns.to_spectral(v, p)
     before = (ns.divergence_phys(st, p) ** 2).mean()
     st2, _ = ns.rk_step(st, _zeros_gp(p), p, 1e-3)
@@ -123,7 +134,7 @@ def test_manufactured_poisson_converges(Mr_5_25):
 
 def test_projection_idempotent_with_consistent_injection(Mr_5_25):
     p = ns.Params(32, 32, 33, Mr=Mr_5_25)
-    v = synth.channel_velocity(32, 32, 33)
+    v = _divergent_field(32, 33)
     vp, g = ns.poisson_project(v, p, 1e-3)
     vp2, _ = ns.poisson_project(vp, p, 1e-3, gradp_prev=-g)
     assert np.abs(vp2 - vp).max() < 1e-6 * np.abs(vp).max()
@@ -174,3 +185,30 @@ def test_filter_factor_values():
     p0 = ns.Params(12, 12, 33, filter=0)
     F0 = ns.filter_factor(p0)
     assert abs(F0[0, 0, 6] - 1e-16) < 1e-28
+
+
+def test_channel_ic_is_solenoidal_no_slip():
+    v = synth.channel_velocity(32, 32, 33)
+    p = ns.Params(32, 32, 33)
+    st = ns.to_spectral(v, p)
+    assert np.abs(v[:, [0, -1]]).max() < 1e-15
+    assert (ns.divergence_phys(st, p) ** 2).mean() < 1e-10
+
+
+@pytest.mark.parametrize("o", [2, 3])
+def test_multistep_stability_at_nyquist_modes(Mr_5_25, o):
+    """Reading K1: with gamma = |k_perp| of the Nyquist-zeroed wavenumbers the
+    projection is divergence-consistent at every (kx, ky); several RK steps stay
+    bounded (with the true Nyquist wavenumber in gamma the x/y Nyquist modes grow
+    by ~1e10 per step from round-off)."""
+    p = ns.Params(32, 32, 33, nu=1e-2, forcing_x=0.1, rk_order=o, Mr=Mr_5_25)
+    v = synth.channel_velocity(32, 32, 33)
+    st = ns.to_spectral(v, p)
+    gp = _zeros_gp(p)
+    for _ in range(5):
+        st, gp = ns.rk_step(st, gp, p, 1e-3)
+    v5 = np.stack([ns.to_physical(c, p) for c in st])
+    assert np.abs(v5).max() < 1.01 * np.abs(v).max()
+    m = ns.z_inverse(st, p)
+    assert np.abs(m[:, :, :, p.Nx // 2]).max() < 1e-12
+    assert np.abs(m[:, :, p.Ny // 2, :]).max() < 1e-12
