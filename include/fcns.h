@@ -19,7 +19,9 @@
  *     CUDA failures surface as FC_ERR_CUDA from the next call that checks.
  *   - Field layouts are row-major with x fastest:
  *       physical  [nf][Nz][Ny][Nx] real (float or double),
- *       spectral  [nf][Nz+C][Ny][Nx/2+1] complex (interleaved re, im).
+ *       state     [nf][Nz+C][Ny][Nx/2+1] complex (interleaved re, im): the
+ *                 fields in (kx, ky, z') on the continued z grid, i.e. the
+ *                 inverse z-DFT of the continued spectral field (Sec. 3).
  *   - Grids include both walls: z_s = s Lz/(Nz-1), s = 0..Nz-1; the
  *     continued (periodic) grid has N' = Nz + C points and period
  *     L'z = N' Lz/(Nz-1).  Forward transforms are unnormalised, inverse
@@ -102,7 +104,8 @@ fc_status fc_destroy(fc_plan_t plan);
  * (Sec. 3: continuation of every z-line from its first and last d samples to
  * N' = Nz + C points; Sec. 4.2: multiplication of the Fourier coefficients by
  * i k (Nyquist entry zeroed) or -k^2; inverse transform truncated to the Nz
- * physical points).  The continuation product is always evaluated in double.
+ * physical points).  The continuation product is evaluated in double (in the
+ * float32 path with compensated float-float arithmetic of double accuracy).
  *   dtype  FC_F32: f, df, d2f are float; FC_F64: double.
  *   batch, Nx, Ny  field count and horizontal sizes (each >= 1); the line
  *          count batch*Nx*Ny must stay below 2^31.
@@ -117,6 +120,31 @@ fc_status fc_destroy(fc_plan_t plan);
  */
 fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
                      const void* f, void* df, void* d2f, fc_stream_t stream);
+
+/*
+ * fc_deriv_z_noalloc -- the same computation and arguments as fc_deriv_z,
+ * for callers that cannot let the library allocate device memory: code that
+ * runs while a CUDA graph is being captured (cudaMalloc cannot be captured),
+ * applications whose device memory belongs to a host framework or a fixed
+ * arena and that forbid allocations by plug-ins, and latency-critical loops
+ * that cannot take cudaMalloc's implicit synchronisation.  The paper has no
+ * counterpart; this is a deployment variant of fc_deriv_z.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.  The plan's
+ *     tables (continuation matrix, kernel spectrum, twiddles) are copied on
+ *     the caller's stream into one fixed 64 KiB static device array that
+ *     every GPU loading the library reserves until the process exits.
+ *   - The first call on each device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture on that device.
+ *   - Every call shares the array and overwrites all of it that it reads;
+ *     calls whose copies and kernels overlap on the GPU (other streams,
+ *     other host threads) race on it and must be serialised by the caller.
+ *   - A plan whose tables would not fit the 64 KiB array returns
+ *     FC_ERR_UNSUPPORTED (the compiled transform lengths, N' + Nz - 1 <= 1080,
+ *     need at most 45 KiB); arguments are checked as in fc_deriv_z.
+ */
+fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
+                             const void* f, void* df, void* d2f, fc_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Navier-Stokes / Boussinesq simulation                                     */
@@ -151,7 +179,7 @@ fc_status ns_params_default(ns_params* p);
 fc_status ns_workspace_bytes(const ns_params* p, size_t* bytes);
 
 /*
- * ns_create -- create a simulation object holding the spectral state of the
+ * ns_create -- create a simulation object holding the state of the
  * nfields fields, the wall pressure-gradient planes (Sec. 4.4 step 2) and the
  * tables.  dev_workspace (device pointer, >= ns_workspace_bytes) is used for
  * every device buffer; if it is NULL the library allocates it itself with
@@ -165,7 +193,7 @@ fc_status ns_destroy(ns_sim_t sim);
 
 /* Set the state from physical fields phys (device pointer,
  * [nf][Nz][Ny][Nx] in the simulation's precision): the state becomes the
- * FC continuation of phys transformed to (kx, ky, kz) (Sec. 3), and the wall
+ * FC continuation of phys in (kx, ky, z') (Sec. 3), and the wall
  * pressure-gradient planes are reset to zero. */
 fc_status ns_set_fields(ns_sim_t sim, const void* phys, fc_stream_t stream);
 
@@ -173,9 +201,10 @@ fc_status ns_set_fields(ns_sim_t sim, const void* phys, fc_stream_t stream);
  * transforms), device pointer [nf][Nz][Ny][Nx]. */
 fc_status ns_get_fields(ns_sim_t sim, void* phys, fc_stream_t stream);
 
-/* Copy the spectral state to / from a device buffer of
- * nf * (Nz+C) * Ny * (Nx/2+1) complex values of the simulation's precision
- * (checkpoint / restore). */
+/* Copy the state to / from a device buffer of nf * (Nz+C) * Ny * (Nx/2+1)
+ * complex values of the simulation's precision (checkpoint / restore).  The
+ * state is kept in (kx, ky, z') on the continued grid; a length-(Nz+C) DFT
+ * along z' turns it into the continued spectral field of the paper. */
 fc_status ns_get_state(ns_sim_t sim, void* spec, fc_stream_t stream);
 fc_status ns_put_state(ns_sim_t sim, const void* spec, fc_stream_t stream);
 
@@ -209,7 +238,7 @@ fc_status ns_rhs(ns_sim_t sim, const void* phys_in, void* rhs_out, fc_stream_t s
  *   vstar_phys, v_phys  device pointers [3][Nz][Ny][Nx] (velocity only).
  *   gradp_wall          device pointer for a copy of the new wall planes
  *                       ([2][2][Ny][Nx/2+1] complex double) or NULL.
- * Leaves the simulation's spectral state unchanged.
+ * Leaves the simulation's state unchanged (its work buffers are overwritten).
  */
 fc_status fc_poisson_project(ns_sim_t sim, double dt_stage, const void* vstar_phys, void* v_phys,
                              void* gradp_wall, fc_stream_t stream);

@@ -18,17 +18,7 @@ fc_status cuda_status(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? FC_ERR_NOMEM : FC_ERR_CUDA;
 }
 
-struct PlanHostTables {
-  int L = 0, L1 = 0, L2 = 0;
-  std::vector<std::complex<double>> H, tw;
-};
-
 }  // namespace fcns
-
-struct fc_plan {
-  fcns::PlanData data;
-  fcns::PlanHostTables deriv;
-};
 
 using namespace fcns;
 
@@ -71,6 +61,19 @@ fc_status fc_setup_ex(int d, int C, int Nz, int M, int n_os, fc_plan_t* out) {
       if (s.L == L) { p->deriv.L = L; p->deriv.L1 = s.L1; p->deriv.L2 = s.L2; }
     deriv_conv_spectrum(Nz, p->data.Np, L, &p->deriv.H);
     engine_twiddles(p->deriv.L1, p->deriv.L2, &p->deriv.tw);
+    auto& t = p->deriv;
+    t.H32.resize(L); t.tw32.resize(L); t.H64.resize(L); t.tw64.resize(L);
+    for (int i = 0; i < L; ++i) {
+      t.H32[i] = make_float2((float)t.H[i].real(), (float)t.H[i].imag());
+      t.tw32[i] = make_float2((float)t.tw[i].real(), (float)t.tw[i].imag());
+      t.H64[i] = make_double2(t.H[i].real(), t.H[i].imag());
+      t.tw64[i] = make_double2(t.tw[i].real(), t.tw[i].imag());
+    }
+  }
+  p->deriv.Mr2.resize(p->data.Mr.size());
+  for (size_t i = 0; i < p->data.Mr.size(); ++i) {
+    const float hi = (float)p->data.Mr[i];
+    p->deriv.Mr2[i] = make_float2(hi, (float)(p->data.Mr[i] - (double)hi));
   }
   *out = p;
   return FC_OK;
@@ -137,16 +140,9 @@ static fc_status deriv_tables_locked(fc_plan* plan, DerivDevTables** out) {
   s = cuda_status(cudaMalloc((void**)&t.Mr, sizeof(double) * plan->data.Mr.size()), "cudaMalloc(Mr)");
   if (!s) s = cuda_status(cudaMemcpy(t.Mr, plan->data.Mr.data(), sizeof(double) * plan->data.Mr.size(),
                                      cudaMemcpyHostToDevice), "cudaMemcpy(Mr)");
-  if (!s) {
-    std::vector<std::complex<double>> split(plan->data.Mr.size());
-    for (size_t i = 0; i < split.size(); ++i) {
-      const float hi = (float)plan->data.Mr[i];
-      split[i] = std::complex<double>(hi, (double)(float)(plan->data.Mr[i] - (double)hi));
-    }
-    void* p2 = nullptr;
-    s = upload<float2>(split, &p2);
-    t.Mr2 = (float2*)p2;
-  }
+  if (!s) s = cuda_status(cudaMalloc((void**)&t.Mr2, sizeof(float2) * plan->deriv.Mr2.size()), "cudaMalloc(Mr2)");
+  if (!s) s = cuda_status(cudaMemcpy(t.Mr2, plan->deriv.Mr2.data(), sizeof(float2) * plan->deriv.Mr2.size(),
+                                     cudaMemcpyHostToDevice), "cudaMemcpy(Mr2)");
   if (!s) s = upload<float2>(plan->deriv.H, &t.H32);
   if (!s) s = upload<double2>(plan->deriv.H, &t.H64);
   if (!s) s = upload<float2>(plan->deriv.tw, &t.tw32);
@@ -162,28 +158,37 @@ static fc_status deriv_tables_locked(fc_plan* plan, DerivDevTables** out) {
 
 }  // namespace fcns
 
-extern "C" fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
-                                const void* f, void* df, void* d2f, fc_stream_t stream) {
-  if (!plan || !f || (!df && !d2f)) { set_error("fc_deriv_z: NULL plan, input or both outputs"); return FC_ERR_ARG; }
-  if (dtype != FC_F32 && dtype != FC_F64) { set_error("fc_deriv_z: bad dtype"); return FC_ERR_ARG; }
-  if (batch < 1 || Nx < 1 || Ny < 1 || !(Lz > 0) || !std::isfinite(Lz)) { set_error("fc_deriv_z: bad sizes"); return FC_ERR_ARG; }
+fc_status fcns::check_deriv_args(const PlanData& pd, const PlanHostTables& t, fc_dtype dtype, int batch, int Nx,
+                                 int Ny, double Lz, const void* f, void* df, void* d2f, const char* who) {
+  std::string w(who);
+  if (!f || (!df && !d2f)) { set_error(w + ": NULL input or both outputs"); return FC_ERR_ARG; }
+  if (dtype != FC_F32 && dtype != FC_F64) { set_error(w + ": bad dtype"); return FC_ERR_ARG; }
+  if (batch < 1 || Nx < 1 || Ny < 1 || !(Lz > 0) || !std::isfinite(Lz)) { set_error(w + ": bad sizes"); return FC_ERR_ARG; }
   const long long lines = (long long)Nx * Ny;
-  if (lines * batch >= (1LL << 31)) { set_error("fc_deriv_z: too many lines"); return FC_ERR_UNSUPPORTED; }
-  if (plan->deriv.L == 0) { set_error("fc_deriv_z: N' + Nz - 1 exceeds the compiled transform lengths"); return FC_ERR_UNSUPPORTED; }
+  if (lines * batch >= (1LL << 31)) { set_error(w + ": too many lines"); return FC_ERR_UNSUPPORTED; }
+  if (t.L == 0) { set_error(w + ": N' + Nz - 1 exceeds the compiled transform lengths"); return FC_ERR_UNSUPPORTED; }
   const size_t es = dtype == FC_F32 ? 4 : 8;
-  const size_t bytes = es * (size_t)lines * plan->data.Nz * batch;
+  const size_t bytes = es * (size_t)lines * pd.Nz * batch;
   auto overlap = [&](const void* a, const void* b) {
     if (!a || !b) return false;
-    const char* x = (const char*)a; const char* y = (const char*)b;
+    const char* x = (const char*)a;
+    const char* y = (const char*)b;
     return x < y + bytes && y < x + bytes;
   };
-  if (overlap(f, df) || overlap(f, d2f) || overlap(df, d2f)) { set_error("fc_deriv_z: overlapping buffers"); return FC_ERR_ARG; }
+  if (overlap(f, df) || overlap(f, d2f) || overlap(df, d2f)) { set_error(w + ": overlapping buffers"); return FC_ERR_ARG; }
+  return FC_OK;
+}
+
+extern "C" fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
+                                const void* f, void* df, void* d2f, fc_stream_t stream) {
+  if (!plan) { set_error("fc_deriv_z: NULL plan"); return FC_ERR_ARG; }
+  fc_status s = check_deriv_args(plan->data, plan->deriv, dtype, batch, Nx, Ny, Lz, f, df, d2f, "fc_deriv_z");
+  if (s) return s;
   DerivDevTables* t = nullptr;
-  fc_status s;
   {
     std::lock_guard<std::mutex> lk(plan->data.mtx);
     s = deriv_tables_locked(plan, &t);
   }
   if (s) return s;
-  return launch_deriv_z(*t, plan->data, dtype, batch, lines, Lz, f, df, d2f, (cudaStream_t)stream);
+  return launch_deriv_z(*t, plan->data, dtype, batch, (long long)Nx * Ny, Lz, f, df, d2f, (cudaStream_t)stream);
 }

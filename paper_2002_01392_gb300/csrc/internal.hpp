@@ -41,6 +41,27 @@ struct PlanData {
 
 fc_status deriv_tables_for_device(PlanData* p, DerivDevTables** out);
 
+// host copies of the derivative tables of one plan, in both precisions
+struct PlanHostTables {
+  int L = 0, L1 = 0, L2 = 0;
+  std::vector<std::complex<double>> H, tw;
+  std::vector<float2> H32, tw32, Mr2;
+  std::vector<double2> H64, tw64;
+};
+
+// argument checks shared by the fc_deriv_z entry points
+fc_status check_deriv_args(const PlanData& p, const PlanHostTables& t, fc_dtype dtype, int batch, int Nx, int Ny,
+                           double Lz, const void* f, void* df, void* d2f, const char* who);
+
+}  // namespace fcns
+
+struct fc_plan {
+  fcns::PlanData data;
+  fcns::PlanHostTables deriv;
+};
+
+namespace fcns {
+
 fc_status launch_deriv_z(const DerivDevTables& t, const PlanData& p, fc_dtype dtype, int batch,
                          long long lines, double Lz, const void* f, void* df, void* d2f,
                          cudaStream_t stream);
