@@ -27,6 +27,30 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = ("RK-stage grid-points/s and fc_deriv_z HBM GB/s (FP32 batched vs FP64 plain); p50/p99")
+DERIV_CONFIG = {"workload": "fc_deriv_z 3x512x512x513 d=5 C=25, d/dz and d2/dz2",
+                "l2": "inputs 1.6 GB (f32) > 129 MB L2, no flush needed"}
+
+
+def _measured_traffic(key):
+    """DRAM bytes per launch from profiles/traffic.txt, if the kernel sources are
+    unchanged since the capture; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, nbytes, srcs = line.split()[:3]
+        if k != key:
+            continue
+        for item in srcs.split(","):
+            fname, h = item.split(":")
+            src = os.path.join(ROOT, "paper_2002_01392_gb300", "csrc", fname)
+            if not os.path.exists(src) or not hashlib.sha1(open(src, "rb").read()).hexdigest().startswith(h):
+                return None
+        return float(nbytes)
+    return None
 
 
 def _peaks():
@@ -229,28 +253,70 @@ def bench_rk(api, torch, steps, warmup, with_e2e=True, shape=None):
     return res
 
 
+class OracleDerivSample:
+    """The FP64 oracle (numpy, one thread) on sampled z-lines of the
+    3 x 512^2 x 513 fc_deriv_z batch: one call = both derivatives of
+    ``lines`` lines."""
+
+    def __init__(self, lines=4096):
+        import synth
+        from oracle import fc, fc_tables
+        self.fc = fc
+        self.Mr = fc_tables.fc_matrix(5, 25, table_dir=os.path.join(ROOT, "tests", "golden"))
+        sf = synth.SeparableField(512, 512, 513, seed_offset=0)
+        self.Z = sf.z_profiles(0)
+        self.X = sf.X.reshape(sf.X.shape[0], -1)
+        self.g = np.random.default_rng(3)
+        self.lines = lines
+
+    def __call__(self):
+        idx = self.g.integers(0, self.X.shape[1], self.lines)
+        f = self.Z.T @ self.X[:, idx]
+        self.fc.fc_deriv_z(f, 1.0, self.Mr, 1, axis=0)
+        self.fc.fc_deriv_z(f, 1.0, self.Mr, 2, axis=0)
+        return self.lines * 513
+
+
+def _threads_used():
+    try:
+        import threadpoolctl
+        return max([i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()] + [1])
+    except Exception:
+        return 1
+
+
 def cpu_baseline_deriv(budget_s=12.0):
     """The FP64 oracle timed on a bounded sample of the same workload: z-lines of
     the 3 x 512^2 x 513 batch, as many as fit in ~budget_s seconds."""
-    import synth
-    from oracle import fc, fc_tables
-    Mr = fc_tables.fc_matrix(5, 25, table_dir=os.path.join(ROOT, "tests", "golden"))
-    sf = synth.SeparableField(512, 512, 513, seed_offset=0)
-    Z = sf.z_profiles(0)                                   # [rank][Nz]
-    g = np.random.default_rng(3)
-    X = sf.X.reshape(sf.X.shape[0], -1)
-    lines_per_chunk = 4096
+    run = OracleDerivSample()
     done = 0
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
-        idx = g.integers(0, X.shape[1], lines_per_chunk)
-        f = Z.T @ X[:, idx]                                 # [Nz][lines]
-        fc.fc_deriv_z(f, 1.0, Mr, 1, axis=0)
-        fc.fc_deriv_z(f, 1.0, Mr, 2, axis=0)
-        done += lines_per_chunk
+        done += run()
     dt = time.perf_counter() - t0
-    return {"value": done * 513 / dt, "unit": "grid-points/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done} z-lines (x 513 points) of the 3x512x512x513 fc_deriv_z batch, FP64 numpy"}
+    return {"value": done / dt, "unit": "grid-points/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done // 513} z-lines (x 513 points) of the 3x512x512x513 fc_deriv_z batch, "
+                      f"FP64 numpy pocketfft, one thread"}
+
+
+def cpu_baseline_rk(budget_s=15.0):
+    """The FP64 oracle RK3 Boussinesq step on a 128 x 128 x 129 grid (a bounded
+    stand-in for the 1024^2 x 513 step; the cost per point grows like log N)."""
+    import synth
+    from oracle import ns
+    N, Nz = 128, 129
+    P = ns.Params(N, N, Nz, nfields=4, nu=3.162e-4, kappa=3.162e-4, gamma=1.0)
+    st = ns.to_spectral(synth.boussinesq_fields(N, N, Nz), P)
+    gp = np.zeros((2, 2, N, N // 2 + 1), complex)
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s or steps == 0:
+        st, gp = ns.rk_step(st, gp, P, 1e-3)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": N * N * Nz * 3 * steps / dt, "unit": "RK-stage grid-points/s", "cores": 1,
+            "kind": "oracle", "sample": f"{steps} RK3 steps of the Boussinesq oracle on 128x128x129 (4 fields, FP64; "
+                                        f"numpy pocketfft on one thread)"}
 
 
 def main():
@@ -262,7 +328,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--rk-steps", type=int, default=5)
     ap.add_argument("--no-rk", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=["deriv32", "deriv64", "rk-small"],
+    ap.add_argument("--profile-case", default=None, choices=["deriv32", "deriv64", "rk-small", "rk-full"],
                     help="small single-kernel case for ncu: fc_deriv_z on 2x256x256x513, no e2e / CPU leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -270,13 +336,24 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = cpu_baseline_deriv(budget_s=max(5.0, min(60.0, 2.0 * args.steps)))
-        print(json.dumps({"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"],
+        # the oracle as it stands, on the host cores: each step = both z-derivatives
+        # of 2048 sampled z-lines of the 3 x 512^2 x 513 batch
+        run = OracleDerivSample(lines=2048)
+        for _ in range(args.warmup):
+            run()
+        t0 = time.perf_counter()
+        pts = sum(run() for _ in range(args.steps))
+        dt = time.perf_counter() - t0
+        val = pts / dt
+        cb = {"value": val, "unit": "grid-points/s", "cores": 1, "kind": "oracle",
+              "sample": f"{args.steps} steps x 2048 z-lines of the 3x512x512x513 fc_deriv_z batch, FP64"}
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": "grid-points/s",
                           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                          "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-                          "config": {"workload": "fc_deriv_z 3x512x512x513 d=5 C=25 (oracle, sampled lines)"},
+                          "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": dict(DERIV_CONFIG, parallelism="single", arm="FP64 CPU oracle on sampled z-lines"),
                           "cpu_baseline": cb,
-                          "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
+                          "e2e": {"value": val, "unit": "grid-points/s", "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0}}))
         return
     import torch
@@ -289,8 +366,9 @@ def main():
     from paper_2002_01392_gb300 import api
     dev_index = torch.cuda.current_device()
     hbm_peak, peak_kind = _peaks()
-    if args.profile_case == "rk-small":
-        r = bench_rk(api, torch, args.steps, args.warmup, with_e2e=False, shape=(256, 256, 257))
+    if args.profile_case in ("rk-small", "rk-full"):
+        shape = (256, 256, 513) if args.profile_case == "rk-small" else None
+        r = bench_rk(api, torch, args.steps, args.warmup, with_e2e=False, shape=shape)
         print(json.dumps({"profile_case": args.profile_case, **r}))
         return
     if args.profile_case:
@@ -315,21 +393,24 @@ def main():
         "metric": METRIC, "value": value, "unit": "grid-points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r32["seconds_per_call_mean"] * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "fc_deriv_z 3x512x512x513 d=5 C=25, d/dz and d2/dz2, FP32 (continuation FP64)",
-                   "l2": "inputs 1.6 GB > L2, no flush", "parallelism": "replicas" if world > 1 else "single"},
+        "config": dict(DERIV_CONFIG, parallelism="replicas" if world > 1 else "single",
+                       arm="FP32 transforms, continuation in float-float (FP64-level)"),
         "p50_ms": r32["p50_ms"], "p99_ms": r32["p99_ms"],
         "fc_deriv_z": {"fp32": {k: v for k, v in r32.items() if k != "e2e"}, "fp64": r64},
         "rk_stage": rk,
         "roofline": {"bound": "hbm", "achieved": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9,
                      "peak": hbm_peak, "unit": "GB/s",
                      "frac": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9 / hbm_peak,
-                     "traffic": None, "peak_kind": peak_kind, "kernel": "fc_deriv_z conv L=1080 FP32"},
+                     "traffic": _measured_traffic("fc_deriv_z_f32"), "peak_kind": peak_kind,
+                     "kernel": "fc_deriv_z conv L=1080 FP32 (phased_kernel<DerivConv<float,30,36,8>>)"},
         "e2e": r32.get("e2e"),
         "gpu_launches": r32["launches"],
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline_deriv()
+        if out.get("rk_stage"):
+            out["rk_stage"]["cpu_baseline"] = cpu_baseline_rk()
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
