@@ -17,11 +17,8 @@
  *     cudaStream_t; NULL means the legacy default stream) and the calls
  *     return without synchronising unless stated otherwise.  Asynchronous
  *     CUDA failures surface as FC_ERR_CUDA from the next call that checks.
- *   - Field layouts are row-major with x fastest:
- *       physical  [nf][Nz][Ny][Nx] real (float or double),
- *       state     [nf][Nz+C][Ny][Nx/2+1] complex (interleaved re, im): the
- *                 fields in (kx, ky, z') on the continued z grid, i.e. the
- *                 inverse z-DFT of the continued spectral field (Sec. 3).
+ *   - Physical fields are row-major [nf][Nz][Ny][Nx] real (float or double),
+ *     x fastest.  The simulation state (see ns_get_state) is internal.
  *   - Grids include both walls: z_s = s Lz/(Nz-1), s = 0..Nz-1; the
  *     continued (periodic) grid has N' = Nz + C points and period
  *     L'z = N' Lz/(Nz-1).  Forward transforms are unnormalised, inverse
@@ -201,10 +198,12 @@ fc_status ns_set_fields(ns_sim_t sim, const void* phys, fc_stream_t stream);
  * transforms), device pointer [nf][Nz][Ny][Nx]. */
 fc_status ns_get_fields(ns_sim_t sim, void* phys, fc_stream_t stream);
 
-/* Copy the state to / from a device buffer of nf * (Nz+C) * Ny * (Nx/2+1)
- * complex values of the simulation's precision (checkpoint / restore).  The
- * state is kept in (kx, ky, z') on the continued grid; a length-(Nz+C) DFT
- * along z' turns it into the continued spectral field of the paper. */
+/* Copy the state to / from a device buffer (checkpoint / restore).  The
+ * buffer holds nf * (Nz+C) * ceil(Ny*(Nx/2+1)/16) * 16 complex values of the
+ * simulation's precision in the library's internal order: the fields in
+ * (kx, ky, z') on the continued grid, lines (ky*(Nx/2+1) + kx) grouped in
+ * tiles of 16, each tile storing its z' rows contiguously.  A length-(Nz+C)
+ * DFT along z' turns it into the continued spectral field of the paper. */
 fc_status ns_get_state(ns_sim_t sim, void* spec, fc_stream_t stream);
 fc_status ns_put_state(ns_sim_t sim, const void* spec, fc_stream_t stream);
 

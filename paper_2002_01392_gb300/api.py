@@ -228,7 +228,9 @@ class Sim:
         return out
 
     def state_shape(self):
-        return (self.p.nfields, self.p.Nz + self.p.C, self.p.Ny, self.Kx)
+        lines = self.p.Ny * self.Kx
+        plines = (lines + 15) // 16 * 16
+        return (self.p.nfields * (self.p.Nz + self.p.C) * plines,)
 
     def get_state(self, out=None, stream=None):
         import torch

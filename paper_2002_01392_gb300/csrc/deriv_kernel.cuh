@@ -16,6 +16,12 @@
 #pragma once
 #include "phases.cuh"
 
+#if defined(__CUDACC__)
+#define DERIV_NOINLINE __host__ __device__ __noinline__
+#else
+#define DERIV_NOINLINE
+#endif
+
 namespace fcns {
 
 template <class T, int L1_, int L2_, int LINES_>
@@ -64,6 +70,30 @@ struct DerivConv {
 
   static FC_HD int bidx(int k1, int n2, int li) { return k1 * ROW + n2 * LINES + li; }
 
+  // continuation value jj of a real line (Sec. 3): M_r f_last + M_l f_first,
+  // float64 (float64 path) or compensated float-float (float32 path); kept out
+  // of line so the unrolled loops stay small
+  static DERIV_NOINLINE T cont_real(int jj, const T* first, const T* last, int d, int Cc, const double* Ms,
+                                    const float2* Ms2) {
+    if constexpr (sizeof(T) == 4) {
+      ff c{0.f, 0.f};
+      for (int i = 0; i < d; ++i) {
+        const float2 m1 = Ms2[jj * d + i];
+        const float2 m2 = Ms2[(Cc - 1 - jj) * d + (d - 1 - i)];
+        ff_fma(c, m1.x, m1.y, (float)last[i]);
+        ff_fma(c, m2.x, m2.y, (float)first[i]);
+      }
+      return (T)ff_round(c);
+    } else {
+      double c = 0.0;
+      for (int i = 0; i < d; ++i) {
+        c += Ms[jj * d + i] * (double)last[i];
+        c += Ms[(Cc - 1 - jj) * d + (d - 1 - i)] * (double)first[i];
+      }
+      return (T)c;
+    }
+  }
+
   template <int P>
   static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
     C* buf = reinterpret_cast<C*>(sm + off_buf);
@@ -102,27 +132,7 @@ struct DerivConv {
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
-          if (n >= a.Nz && n < a.Np) {
-            const int jj = n - a.Nz;
-            if constexpr (sizeof(T) == 4) {
-              // continuation product M_r f_last + M_l f_first in float-float
-              ff c{0.f, 0.f};
-              for (int i = 0; i < a.d; ++i) {
-                const float2 m1 = Ms2[jj * a.d + i];
-                const float2 m2 = Ms2[(a.Cc - 1 - jj) * a.d + (a.d - 1 - i)];
-                ff_fma(c, m1.x, m1.y, (float)last[i]);
-                ff_fma(c, m2.x, m2.y, (float)first[i]);
-              }
-              R.v[j] = mk<T>((T)ff_round(c), T(0));
-            } else {
-              double c = 0.0;
-              for (int i = 0; i < a.d; ++i) {
-                c += Ms[jj * a.d + i] * (double)last[i];
-                c += Ms[(a.Cc - 1 - jj) * a.d + (a.d - 1 - i)] * (double)first[i];
-              }
-              R.v[j] = mk<T>((T)c, T(0));
-            }
-          }
+          if (n >= a.Nz && n < a.Np) R.v[j] = mk<T>(cont_real(n - a.Nz, first, last, a.d, a.Cc, Ms, Ms2), T(0));
         }
         dft_reg<L1, -1, T>(R.v);
 #pragma unroll

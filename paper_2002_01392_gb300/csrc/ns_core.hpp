@@ -18,11 +18,12 @@ namespace fcns {
 
 struct NsLayout {
   int Nx, Ny, Nz, Np, Kx, nf, L, L1, L2, Lx1, Lx2, Ly1, Ly2;
-  long long lines;
+  long long lines, ntiles, plines;   // lines, tiles of TL lines, padded lines
   size_t es;  // bytes per real
   // byte offsets inside the workspace
   size_t X[3], DZ, DZZ, V, DY, NL, gradp;
   size_t kxo, kyo, kzo, kx, ky, fx, fy, Mr, Mr2, twz, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy;
+  size_t tkxo, tkyo, tkzo, tkx, tky, tfx, tfy;   // copies in the simulation's precision
   size_t total;
 };
 
@@ -53,6 +54,8 @@ inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
   NsLayout& l = *o;
   l.Nx = p.Nx; l.Ny = p.Ny; l.Nz = p.Nz; l.Np = p.Nz + p.C; l.Kx = p.Nx / 2 + 1; l.nf = p.nfields;
   l.lines = (long long)p.Ny * l.Kx;
+  l.ntiles = (l.lines + TL - 1) / TL;
+  l.plines = l.ntiles * TL;
   l.es = p.prec == FC_F32 ? 4 : 8;
   const int need = std::max(l.Np + p.Nz - 1, 2 * l.Np - 1);
   if (!z_shape_for(need, &l.L, &l.L1, &l.L2)) return FC_ERR_UNSUPPORTED;
@@ -61,20 +64,24 @@ inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
   const size_t cs = 2 * l.es;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o2 = off; off += (bytes + 255) / 256 * 256; return o2; };
-  for (int i = 0; i < 3; ++i) l.X[i] = take(cs * l.nf * l.Np * l.lines);
-  l.DZ = take(cs * l.nf * l.Nz * l.lines);
-  l.DZZ = take(cs * l.nf * l.Nz * l.lines);
-  l.V = take(cs * l.nf * l.Nz * l.lines);
-  l.DY = take(cs * l.nf * l.Nz * l.lines);
-  l.NL = take(cs * l.nf * l.Nz * l.lines);
+  for (int i = 0; i < 3; ++i) l.X[i] = take(cs * l.nf * l.Np * l.plines);
+  l.DZ = take(cs * l.nf * l.Nz * l.plines);
+  l.DZZ = take(cs * l.nf * l.Nz * l.plines);
+  l.V = take(cs * l.nf * l.Nz * l.plines);
+  l.DY = take(cs * l.nf * l.Nz * l.plines);
+  l.NL = take(cs * l.nf * l.Nz * l.plines);
   l.gradp = take(sizeof(double) * 2 * 4 * l.lines);
   l.kxo = take(8 * l.Kx); l.kyo = take(8 * p.Ny); l.kzo = take(8 * l.Np);
   l.kx = take(8 * l.Kx); l.ky = take(8 * p.Ny); l.fx = take(8 * l.Kx); l.fy = take(8 * p.Ny);
+  l.tkxo = take(l.es * l.Kx); l.tkyo = take(l.es * p.Ny); l.tkzo = take(l.es * l.Np);
+  l.tkx = take(l.es * l.Kx); l.tky = take(l.es * p.Ny); l.tfx = take(l.es * l.Kx); l.tfy = take(l.es * p.Ny);
   l.Mr = take(8 * p.C * p.d); l.Mr2 = take(8 * p.C * p.d);
   l.twz = take(cs * l.L); l.H1 = take(cs * l.L); l.H2 = take(cs * l.L); l.Hf = take(cs * l.L);
   l.chirp = take(cs * l.Np); l.Hbf = take(cs * l.L); l.Hbi = take(cs * l.L);
   l.twx = take(cs * p.Nx); l.twy = take(cs * p.Ny);
   l.total = off;
+  // every array is indexed with 32-bit element offsets
+  if ((double)l.nf * l.Np * l.plines >= 2147483647.0) return FC_ERR_UNSUPPORTED;
   return FC_OK;
 }
 
@@ -143,6 +150,13 @@ struct NsCore {
     if (!s) s = put(l.ky, ky.data(), 8 * ky.size());
     if (!s) s = put(l.fx, fx.data(), 8 * fx.size());
     if (!s) s = put(l.fy, fy.data(), 8 * fy.size());
+    if (!s) s = putr(l.tkxo, kxo);
+    if (!s) s = putr(l.tkyo, kyo);
+    if (!s) s = putr(l.tkzo, kzo);
+    if (!s) s = putr(l.tkx, kx);
+    if (!s) s = putr(l.tky, ky);
+    if (!s) s = putr(l.tfx, fx);
+    if (!s) s = putr(l.tfy, fy);
     if (!s) s = put(l.Mr, T.Mr.data(), 8 * T.Mr.size());
     if (!s) s = put(l.Mr2, mr2.data(), 8 * mr2.size());
     if (!s) s = putc(l.twz, twz);
@@ -155,7 +169,7 @@ struct NsCore {
     if (!s) s = putc(l.twx, twx);
     if (!s) s = putc(l.twy, twy);
     if (!s) s = bk.memset(ws + l.gradp, 0, sizeof(double) * 8 * l.lines, nullptr);
-    if (!s) s = bk.memset(ws + l.X[0], 0, 2 * l.es * l.nf * l.Np * l.lines, nullptr);
+    if (!s) s = bk.memset(ws + l.X[0], 0, l.NL - l.X[0] + 2 * l.es * l.nf * l.Nz * l.plines, nullptr);
     if (!s) s = bk.sync(nullptr);
     return s;
   }
@@ -168,6 +182,11 @@ struct NsCore {
   }
 
   fc_status put(size_t off, const void* src, size_t bytes) { return bk.h2d(ws + off, src, bytes); }
+  fc_status putr(size_t off, const std::vector<double>& v) {
+    if (l.es == 8) return put(off, v.data(), 8 * v.size());
+    std::vector<float> f(v.begin(), v.end());
+    return put(off, f.data(), 4 * f.size());
+  }
   fc_status putc(size_t off, const std::vector<std::complex<double>>& v) {
     if (l.es == 8) return put(off, v.data(), 16 * v.size());
     std::vector<float2> f(v.size());
@@ -181,14 +200,15 @@ struct NsCore {
     t.Mr = at<double>(l.Mr); t.Mr2 = at<float2>(l.Mr2);
     t.tw = at<cx<T>>(l.twz); t.H1 = at<cx<T>>(l.H1); t.H2 = at<cx<T>>(l.H2); t.Hf = at<cx<T>>(l.Hf);
     t.chirp = at<cx<T>>(l.chirp); t.Hbf = at<cx<T>>(l.Hbf); t.Hbi = at<cx<T>>(l.Hbi);
-    t.kxo = at<double>(l.kxo); t.kyo = at<double>(l.kyo); t.kzo = at<double>(l.kzo);
-    t.kx = at<double>(l.kx); t.ky = at<double>(l.ky); t.fx = at<double>(l.fx); t.fy = at<double>(l.fy);
+    t.kxo = at<T>(l.tkxo); t.kyo = at<T>(l.tkyo); t.kzo = at<T>(l.tkzo);
+    t.kx = at<T>(l.tkx); t.ky = at<T>(l.tky); t.fx = at<T>(l.tfx); t.fy = at<T>(l.tfy);
+    t.kxo_d = at<double>(l.kxo); t.kyo_d = at<double>(l.kyo);
     return t;
   }
   ZGeom zgeom(int nf) const {
     ZGeom g;
     g.Nz = p.Nz; g.Np = l.Np; g.d = p.d; g.Cc = p.C; g.Kx = l.Kx; g.Ny = p.Ny; g.nf = nf;
-    g.lines = l.lines; g.Lz = p.Lz; g.dz = p.Lz / (p.Nz - 1);
+    g.lines = l.lines; g.ntiles = l.ntiles; g.Lz = p.Lz; g.dz = p.Lz / (p.Nz - 1);
     return g;
   }
 
@@ -249,7 +269,7 @@ struct NsCore {
     using K = KZProject<T, A, B, zproj_lines<T, LL>()>;                       \
     typename K::Args a;                                                       \
     a.g = zgeom(3); a.t = ztab<T>(); a.X = X; a.gradp = at<double2>(l.gradp); \
-    a.dtj = dtj;                                                              \
+    a.G0 = at<cx<T>>(l.DZ); a.G1 = at<cx<T>>(l.DZZ); a.dtj = dtj;             \
     a.tiles = (l.lines + K::E::LINES - 1) / K::E::LINES;                      \
     s = bk.template run<K>(a, a.tiles, st);                                   \
   }
@@ -260,7 +280,7 @@ struct NsCore {
 
   YGeom ygeom() const {
     YGeom g;
-    g.Ny = p.Ny; g.Kx = l.Kx; g.Nz = p.Nz; g.plane = l.lines;
+    g.Ny = p.Ny; g.Kx = l.Kx; g.Nz = p.Nz; g.plane = l.lines; g.ntiles = l.ntiles;
     return g;
   }
 
@@ -271,7 +291,7 @@ struct NsCore {
   if (p.Ny == NN) {                                                           \
     using K = KYInv3<T, A1, B1, y_lines<T, NN>()>;                            \
     typename K::Args a;                                                       \
-    a.g = ygeom(); a.tw = at<cx<T>>(l.twy); a.kyo = at<double>(l.kyo);        \
+    a.g = ygeom(); a.tw = at<cx<T>>(l.twy); a.kyo = at<T>(l.tkyo);            \
     a.A = A; a.a_fstride = a_fstride;                                         \
     a.V = at<cx<T>>(l.V); a.DY = at<cx<T>>(l.DY); a.DZ = at<cx<T>>(l.DZ);     \
     a.tiles = (l.Kx + K::E::LINES - 1) / K::E::LINES;                         \
@@ -323,7 +343,8 @@ struct NsCore {
   fc_status x_pass_run(long long rows, void* st) {
     if (K::smem_bytes > 227 * 1024) return FC_ERR_UNSUPPORTED;
     typename K::Args a;
-    a.Kx = l.Kx; a.rows = rows; a.tw = at<cx<T>>(l.twx); a.kxo = at<double>(l.kxo);
+    a.Kx = l.Kx; a.Ny = p.Ny; a.Nz = p.Nz; a.rows = rows; a.ntiles = l.ntiles;
+    a.tw = at<cx<T>>(l.twx); a.kxo = at<T>(l.tkxo);
     a.V = at<cx<T>>(l.V); a.DY = at<cx<T>>(l.DY); a.DZ = at<cx<T>>(l.DZ); a.NL = at<cx<T>>(l.NL);
     a.forcing = (T)p.forcing_x; a.gamma = (T)p.gamma; a.scale = (T)(1.0 / p.Nx);
     return bk.template run<K>(a, rows, st);
@@ -337,7 +358,8 @@ struct NsCore {
   if (p.Nx == NN) {                                                           \
     using K = KXRow<T, A1, B1, SIGN, x_jobs<NN>()>;                           \
     typename K::Args a;                                                       \
-    a.Kx = l.Kx; a.pairs = pairs; a.tw = at<cx<T>>(l.twx); a.R = R; a.S = S;  \
+    a.Kx = l.Kx; a.Ny = p.Ny; a.Nz = p.Nz; a.ntiles = l.ntiles;              \
+    a.pairs = pairs; a.tw = at<cx<T>>(l.twx); a.R = R; a.S = S;               \
     a.scale = (T)(SIGN > 0 ? 1.0 / p.Nx : 1.0);                               \
     s = bk.template run<K>(a, (pairs + x_jobs<NN>() - 1) / x_jobs<NN>(), st); \
   }
@@ -442,7 +464,7 @@ struct NsCore {
                  : project<double>(dtj, (const double*)in, (double*)out, gp, st);
   }
   fc_status step_any(double dt, void* st) { return f32() ? step<float>(dt, st) : step<double>(dt, st); }
-  size_t state_bytes() const { return 2 * l.es * l.nf * l.Np * l.lines; }
+  size_t state_bytes() const { return 2 * l.es * l.nf * l.Np * l.plines; }
 };
 
 }  // namespace fcns

@@ -34,20 +34,41 @@ struct ZTab {
   const cx<T>* chirp;   // Bluestein chirp exp(-i pi n^2 / N'), N' entries
   const cx<T>* Hbf;     // Bluestein kernel spectrum (forward DFT)
   const cx<T>* Hbi;     // Bluestein kernel spectrum (inverse DFT)
-  const double* kxo;    // kx with the Nyquist entry zeroed (Kx)
-  const double* kyo;    // ky with the Nyquist entry zeroed (Ny)
-  const double* kzo;    // kz with the Nyquist entry zeroed (N'), FFT order
-  const double* kx;     // kx (Kx)
-  const double* ky;     // ky (Ny)
-  const double* fx;     // x filter / mask factor (Kx)
-  const double* fy;     // y filter / mask factor (Ny)
+  const T* kxo;         // kx with the Nyquist entry zeroed (Kx)
+  const T* kyo;         // ky with the Nyquist entry zeroed (Ny)
+  const T* kzo;         // kz with the Nyquist entry zeroed (N'), FFT order
+  const T* kx;          // kx (Kx)
+  const T* ky;          // ky (Ny)
+  const T* fx;          // x filter / mask factor (Kx)
+  const T* fy;          // y filter / mask factor (Ny)
+  const double* kxo_d;  // float64 copies for the homogeneous-pressure coefficients
+  const double* kyo_d;
 };
 
 struct ZGeom {
   int Nz, Np, d, Cc, Kx, Ny, nf;
   long long lines;
+  long long ntiles;   // ceil(lines / TL)
   double Lz, dz;
 };
+
+// Tiled layout of every [field][z][line] array: lines are grouped in tiles
+// of TL, and a tile stores its z rows contiguously, so the z-line kernels
+// (few lines per CTA) read short runs that are adjacent in memory, and the
+// x / y kernels still read TL contiguous lines per z row.
+constexpr int TL = 16;
+// element index of (field f, row z, line) in an array of Z rows per tile;
+// every array holds fewer than 2^31 elements (checked when the layout is made)
+FC_HD int lay(long long f, long long z, long long line, long long Z, long long ntiles) {
+  const int l = (int)line;
+  return ((((int)f * (int)ntiles + (l >> 4)) * (int)Z + (int)z) << 4) + (l & (TL - 1));
+}
+
+#if defined(__CUDACC__)
+#define FC_NOINLINE __host__ __device__ __noinline__
+#else
+#define FC_NOINLINE
+#endif
 
 constexpr int DMAX = 10;
 constexpr int MRMAX = 640;
@@ -56,8 +77,8 @@ constexpr int MRMAX = 640;
 // last d values (Sec. 3 continuation formula; right matrix M_r, left matrix
 // its row/column reversal).  float32: compensated float-float products.
 template <class T>
-FC_HD cx<T> continuation_value(int jj, const cx<T>* first, const cx<T>* last, int d, int Cc,
-                               const double* Ms, const float2* Ms2) {
+FC_NOINLINE cx<T> continuation_value(int jj, const cx<T>* first, const cx<T>* last, int d, int Cc,
+                                     const double* Ms, const float2* Ms2) {
   if constexpr (sizeof(T) == 4) {
     ff re{0.f, 0.f}, im{0.f, 0.f};
     for (int i = 0; i < d; ++i) {
@@ -103,7 +124,7 @@ struct KZDeriv {
   using E = Eng<T, L1, L2, LINES>;
   using C = cx<T>;
   static constexpr int THREADS = E::THREADS, NPHASE = 3;
-  static constexpr int MINB = (sizeof(T) == 4 && THREADS <= 512) ? 2 : 1;
+  static constexpr int MINB = THREADS <= 160 ? 3 : (THREADS <= 320 ? 2 : 1);
   struct Args {
     ZGeom g;
     ZTab<T> t;
@@ -127,11 +148,11 @@ struct KZDeriv {
     const bool valid = line < a.g.lines;
     if constexpr (P == 0) {
       if (r < L2) {
-        const C* x = a.X + f * a.g.Np * a.g.lines + line;
+        const C* x = a.X + lay(f, 0, line, a.g.Np, a.g.ntiles);
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
-          R.v[j] = (valid && n < a.g.Np) ? x[(long long)n * a.g.lines] : mk<T>(0, 0);
+          R.v[j] = (valid && n < a.g.Np) ? x[n * TL] : mk<T>(0, 0);
         }
         E::template A<-1>(R.v, b0, a.t.tw, r, li);
       }
@@ -150,14 +171,14 @@ struct KZDeriv {
       }
     } else if constexpr (P == 2) {
       if (r < L2) {
-        C* dz = a.DZ + f * a.g.Nz * a.g.lines + line;
-        C* dzz = a.DZZ + f * a.g.Nz * a.g.lines + line;
+        C* dz = a.DZ + lay(f, 0, line, a.g.Nz, a.g.ntiles);
+        C* dzz = a.DZZ + lay(f, 0, line, a.g.Nz, a.g.ntiles);
         E::template Ai<1>(R.v, b0, r, li);
         if (valid) {
 #pragma unroll
           for (int j = 0; j < L1; ++j) {
             const int n = r + L2 * j;
-            if (n < a.g.Nz) dz[(long long)n * a.g.lines] = cscale(R.v[j], a.s1);
+            if (n < a.g.Nz) dz[n * TL] = cscale(R.v[j], a.s1);
           }
         }
         E::template Ai<1>(R.v, b1, r, li);
@@ -165,7 +186,7 @@ struct KZDeriv {
 #pragma unroll
           for (int j = 0; j < L1; ++j) {
             const int n = r + L2 * j;
-            if (n < a.g.Nz) dzz[(long long)n * a.g.lines] = cscale(R.v[j], a.s2);
+            if (n < a.g.Nz) dzz[n * TL] = cscale(R.v[j], a.s2);
           }
         }
       }
@@ -187,7 +208,7 @@ struct KZCombine {
   using E = Eng<T, L1, L2, LINES>;
   using C = cx<T>;
   static constexpr int THREADS = E::THREADS, NPHASE = 5;
-  static constexpr int MINB = (sizeof(T) == 4 && THREADS <= 512) ? 2 : 1;
+  static constexpr int MINB = THREADS <= 160 ? 3 : (THREADS <= 320 ? 2 : 1);
   struct Args {
     ZGeom g;
     ZTab<T> t;
@@ -222,12 +243,12 @@ struct KZCombine {
     if constexpr (P == 0) {
       load_mr<T>(sm + off_M, a.t, a.g.Cc * d, tid, THREADS);
       if (r < L2) {
-        const C* x = a.NL + (long long)f * Nz * Ls + line;
+        const C* x = a.NL + lay(f, 0, line, Nz, a.g.ntiles);
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
           C val = mk<T>(0, 0);
-          if (valid && n < Nz) val = x[(long long)n * Ls];
+          if (valid && n < Nz) val = x[n * TL];
           R.v[j] = val;
           if (n < d) Ev[n] = val;
           if (n >= Nz - d && n < Nz) Ev[DMAX + n - (Nz - d)] = val;
@@ -253,13 +274,13 @@ struct KZCombine {
       if (r < L2) {
         E::template Ai<1>(R.v, b0, r, li);
         const int kx = (int)(line % a.g.Kx), ky = (int)(line / a.g.Kx);
-        const T fxy = valid ? (T)(a.t.fx[kx] * a.t.fy[ky]) : T(0);
-        const double kp2 = valid ? a.t.kx[kx] * a.t.kx[kx] + a.t.ky[ky] * a.t.ky[ky] : 0.0;
-        const T cdt = (T)a.dtj, cnu = (T)(a.dif[f]), ckp2 = (T)kp2;
-        const long long fo = (long long)f * Np * Ls + line;
+        const T fxy = valid ? a.t.fx[kx] * a.t.fy[ky] : T(0);
+        const T ckp2 = valid ? a.t.kx[kx] * a.t.kx[kx] + a.t.ky[ky] * a.t.ky[ky] : T(0);
+        const T cdt = (T)a.dtj, cnu = (T)(a.dif[f]);
+        const long long fo = lay(f, 0, line, Np, a.g.ntiles);
         const C* xt = a.Xt + fo;
         const C* xj = a.Xj + fo;
-        const C* dzz = a.DZZ + (long long)f * Nz * Ls + line;
+        const C* dzz = a.DZZ + lay(f, 0, line, Nz, a.g.ntiles);
         C* xo = a.Xout + fo;
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
@@ -267,11 +288,11 @@ struct KZCombine {
           if (n < Nz) {
             C vs = mk<T>(0, 0);
             if (valid) {
-              const C vj = xj[(long long)n * Ls];
-              const C zz = dzz[(long long)n * Ls];
+              const C vj = xj[n * TL];
+              const C zz = dzz[n * TL];
               const C nlf = cscale(R.v[j], fxy);
               const C visc = csub(zz, cscale(vj, ckp2));
-              const C base = a.Xt ? xt[(long long)n * Ls] : mk<T>(0, 0);
+              const C base = a.Xt ? xt[n * TL] : mk<T>(0, 0);
               vs = cadd(base, cscale(cadd(nlf, cscale(visc, cnu)), cdt));
               if (a.inject && (n == 0 || n == Nz - 1)) {
                 const int wall = (n == 0) ? 0 : 1;
@@ -282,7 +303,7 @@ struct KZCombine {
                   vs = mk<T>(0, 0);
                 }
               }
-              xo[(long long)n * Ls] = vs;
+              xo[n * TL] = vs;
             }
             if (n < d) Ev[n] = vs;
             if (n >= Nz - d) Ev[DMAX + n - (Nz - d)] = vs;
@@ -291,12 +312,12 @@ struct KZCombine {
       }
     } else if constexpr (P == 4) {
       if (r < L2 && valid) {
-        C* xo = a.Xout + (long long)f * Np * Ls + line;
+        C* xo = a.Xout + lay(f, 0, line, Np, a.g.ntiles);
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
           if (n >= Nz && n < Np)
-            xo[(long long)n * Ls] = continuation_value<T>(n - Nz, Ev, Ev + DMAX, d, a.g.Cc, Ms, Ms2);
+            xo[n * TL] = continuation_value<T>(n - Nz, Ev, Ev + DMAX, d, a.g.Cc, Ms, Ms2);
         }
       }
     }
@@ -338,13 +359,13 @@ struct KZContinue {
     const bool valid = line < a.g.lines;
     const int Nz = a.g.Nz, Np = a.g.Np, d = a.g.d;
     const long long Ls = a.g.lines;
-    const C* m = a.M + (long long)f * Nz * Ls + line;
-    C* x = a.X + (long long)f * Np * Ls + line;
+    const C* m = a.M + lay(f, 0, line, Nz, a.g.ntiles);
+    C* x = a.X + lay(f, 0, line, Np, a.g.ntiles);
     if constexpr (P == 0) {
       load_mr<T>(sm, a.t, a.g.Cc * d, tid, THREADS);
       if (valid) {
         for (int n = r; n < Nz; n += G) {
-          C val = m[(long long)n * Ls];
+          C val = m[n * TL];
           if (a.gradp && (n == 0 || n == Nz - 1)) {
             const int wall = (n == 0) ? 0 : 1;
             if (f < 2) {
@@ -354,7 +375,7 @@ struct KZContinue {
               val = mk<T>(0, 0);
             }
           }
-          x[(long long)n * Ls] = val;
+          x[n * TL] = val;
           if (n < d) Ev[n] = val;
           if (n >= Nz - d) Ev[DMAX + n - (Nz - d)] = val;
         }
@@ -362,7 +383,7 @@ struct KZContinue {
     } else {
       if (valid)
         for (int n = Nz + r; n < Np; n += G)
-          x[(long long)n * Ls] = continuation_value<T>(n - Nz, Ev, Ev + DMAX, d, a.g.Cc, Ms, Ms2);
+          x[n * TL] = continuation_value<T>(n - Nz, Ev, Ev + DMAX, d, a.g.Cc, Ms, Ms2);
     }
   }
 };
@@ -379,57 +400,71 @@ struct KZContinue {
 //          D = (b + t)/2 where gamma = 0
 //   grad phi^H = (i kx Phi, i ky Phi, Phi'),  Phi = A e^{g(z-Lz)} + B e^{-g z}
 //   X     -= grad phi^I + FC(grad phi^H);  walls <- grad_par phi / dt_j.
-// DFTs of length N' by Bluestein: chirp, circular convolution of length L,
-// chirp.
+// DFTs of length N' by Bluestein (chirp, circular convolution of length L,
+// chirp), done one after another through a single exchange buffer; the
+// intermediate lines (Y^, s, sigma, sigma_z) go to two global scratch
+// arrays G0, G1 of [N'][lines] (owned element by element by one thread).
 // ===========================================================================
 template <class T, int L1, int L2, int LINES>
 struct KZProject {
   using E = Eng<T, L1, L2, LINES>;
   using C = cx<T>;
-  static constexpr int THREADS = E::THREADS, NPHASE = 8;
-  static constexpr int MINB = 1;
-  static constexpr int NJ = (L1 + 1) / 2 + 2;  // rows of the compact n-layout stores (N' <= L2 * NJ)
+  static constexpr int THREADS = E::THREADS, NPHASE = 12;
+  static constexpr int MINB = LINES <= 4 ? 3 : 1;
   struct Args {
     ZGeom g;
     ZTab<T> t;
     C* X;                 // [3][N'][lines] in / out
+    C* G0;                // scratch [N'][lines]
+    C* G1;                // scratch [N'][lines]
     double2* gradp;       // [2][2][lines] out
     double dtj;
     long long tiles;
   };
   struct Regs { C v[L1]; C u[L2]; };
-  static FC_HD int cidx(int j, int r, int li) { return (j * L2 + r) * LINES + li; }
-  static constexpr size_t CBUF = (size_t)NJ * L2 * LINES;
-  static constexpr size_t off_b1 = sizeof(C) * E::BUF;
-  static constexpr size_t off_s2 = off_b1 + sizeof(C) * E::BUF;
-  static constexpr size_t off_s3 = off_s2 + sizeof(C) * CBUF;
-  static constexpr size_t off_M = off_s3 + sizeof(C) * CBUF;
-  static constexpr size_t off_W = off_M + sizeof(double) * MRMAX;
-  // per line: b, t (complex double), A, B (complex double), D (double)
-  static constexpr size_t smem_bytes = off_W + sizeof(double) * LINES * 12;
+  static constexpr size_t off_M = sizeof(C) * E::BUF;
+  static constexpr size_t off_W = off_M + sizeof(double) * MRMAX;   // per line: b, t, sigma walls (complex double)
+  static constexpr size_t off_E = off_W + sizeof(double) * LINES * 16;
+  // per line: Phi and Phi' at the first / last d points
+  static constexpr size_t smem_bytes = off_E + sizeof(C) * LINES * 4 * DMAX;
+
+  // conj(chirp[n]) (1 outside the line)
+  static FC_HD C cchirp(const ZTab<T>& t, int n, int Np) {
+    C c = n < Np ? t.chirp[n] : mk<T>(1, 0);
+    c.y = -c.y;
+    return c;
+  }
+  static FC_HD void conv(const Args& a, C* b0, const C* H, int r, int li, Regs& R) {
+    if (r < L1) {
+      E::template B<-1>(R.u, b0, r, li);
+#pragma unroll
+      for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(R.u[k2], H[r + L1 * k2]);
+      E::template Bi<1>(R.u, b0, a.t.tw, r, li);
+    }
+  }
 
   template <int P>
   static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
     C* b0 = reinterpret_cast<C*>(sm);
-    C* b1 = reinterpret_cast<C*>(sm + off_b1);
-    C* S2 = reinterpret_cast<C*>(sm + off_s2);
-    C* S3 = reinterpret_cast<C*>(sm + off_s3);
     const double* Ms = reinterpret_cast<const double*>(sm + off_M);
     const float2* Ms2 = reinterpret_cast<const float2*>(sm + off_M);
     const int r = tid / LINES, li = tid % LINES;
-    double* W = reinterpret_cast<double*>(sm + off_W) + li * 12;
+    double* W = reinterpret_cast<double*>(sm + off_W) + li * 16;
+    C* Ev = reinterpret_cast<C*>(sm + off_E) + li * 4 * DMAX;   // Phi first, Phi last, Phi' first, Phi' last
     const long long line = bid * LINES + li;
     const bool valid = line < a.g.lines;
     const int Nz = a.g.Nz, Np = a.g.Np, d = a.g.d;
     const long long Ls = a.g.lines;
     const int kxi = valid ? (int)(line % a.g.Kx) : 0, kyi = valid ? (int)(line / a.g.Kx) : 0;
-    const double kxo = a.t.kxo[kxi], kyo = a.t.kyo[kyi];
-    C* xu = a.X + line;
-    C* xv = a.X + Np * Ls + line;
-    C* xw = a.X + 2LL * Np * Ls + line;
+    const T kxo = a.t.kxo[kxi], kyo = a.t.kyo[kyi];
+    C* xu = a.X + lay(0, 0, line, Np, a.g.ntiles);
+    C* xv = a.X + lay(1, 0, line, Np, a.g.ntiles);
+    C* xw = a.X + lay(2, 0, line, Np, a.g.ntiles);
+    C* g0 = a.G0 + lay(0, 0, line, Np, a.g.ntiles);
+    C* g1 = a.G1 + lay(0, 0, line, Np, a.g.ntiles);
     const T invNp = T(1.0 / Np);
 
-    if constexpr (P == 0) {
+    if constexpr (P == 0) {  // Y = kx u + ky v, Bluestein input
       load_mr<T>(sm + off_M, a.t, a.g.Cc * d, tid, THREADS);
       if (r < L2) {
 #pragma unroll
@@ -437,112 +472,86 @@ struct KZProject {
           const int n = r + L2 * j;
           C y = mk<T>(0, 0);
           if (valid && n < Np) {
-            y = cadd(cscale(xu[(long long)n * Ls], (T)kxo), cscale(xv[(long long)n * Ls], (T)kyo));
+            y = cadd(cscale(xu[n * TL], kxo), cscale(xv[n * TL], kyo));
             y = cmul(y, a.t.chirp[n]);
           }
           R.v[j] = y;
         }
         E::template A<-1>(R.v, b0, a.t.tw, r, li);
       }
-    } else if constexpr (P == 1) {
-      if (r < L1) {
-        E::template B<-1>(R.u, b0, r, li);
-#pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(R.u[k2], a.t.Hbf[r + L1 * k2]);
-        E::template Bi<1>(R.u, b0, a.t.tw, r, li);
-      }
+    } else if constexpr (P == 1 || P == 3 || P == 5 || P == 7) {
+      conv(a, b0, (P <= 3) ? a.t.Hbf : a.t.Hbi, r, li, R);
+    } else if constexpr (P == 2) {  // Y^ -> G0; w Bluestein input
       if (r < L2) {
-#pragma unroll
-        for (int j = 0; j < L1; ++j) {
-          const int n = r + L2 * j;
-          R.v[j] = (valid && n < Np) ? cmul(xw[(long long)n * Ls], a.t.chirp[n]) : mk<T>(0, 0);
-        }
-        E::template A<-1>(R.v, b1, a.t.tw, r, li);
-      }
-    } else if constexpr (P == 2) {
-      if (r < L2) {  // Y^ = chirp * conv
         E::template Ai<1>(R.v, b0, r, li);
 #pragma unroll
-        for (int j = 0; j < NJ && j < L1; ++j) {
+        for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
-          if (n < Np) S2[cidx(j, r, li)] = cmul(R.v[j], a.t.chirp[n]);
+          if (valid && n < Np) g0[n * TL] = cmul(R.v[j], a.t.chirp[n]);
         }
-      }
-      if (r < L1) {
-        E::template B<-1>(R.u, b1, r, li);
-#pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(R.u[k2], a.t.Hbf[r + L1 * k2]);
-        E::template Bi<1>(R.u, b1, a.t.tw, r, li);
-      }
-    } else if constexpr (P == 3) {
-      if (r < L2) {  // W^, s, and the two inverse-DFT inputs
-        E::template Ai<1>(R.v, b1, r, li);
-        const double kp2 = kxo * kxo + kyo * kyo;
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
-          C s = mk<T>(0, 0);
-          if (n < Np && j < NJ) {
-            const C wh = cmul(R.v[j], a.t.chirp[n]);
-            const double kz = a.t.kzo[n];
-            const double k2 = kp2 + kz * kz;
-            const T inv = k2 > 0 ? (T)(1.0 / k2) : T(0);
-            s = cscale(cadd(S2[cidx(j, r, li)], cscale(wh, (T)kz)), inv);
-            S2[cidx(j, r, li)] = s;
-          }
-          C cc = (n < Np) ? a.t.chirp[n] : mk<T>(1, 0);
-          cc.y = -cc.y;
-          R.v[j] = cmul(s, cc);
+          R.v[j] = (valid && n < Np) ? cmul(xw[n * TL], a.t.chirp[n]) : mk<T>(0, 0);
         }
         E::template A<-1>(R.v, b0, a.t.tw, r, li);
+      }
+    } else if constexpr (P == 4) {  // W^, s -> G0; inverse-DFT input for sigma
+      if (r < L2) {
+        E::template Ai<1>(R.v, b0, r, li);
+        const T kp2 = kxo * kxo + kyo * kyo;
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
           C s = mk<T>(0, 0);
-          if (n < Np && j < NJ) {
-            C cc = a.t.chirp[n];
-            cc.y = -cc.y;
-            s = cmul(cscale(S2[cidx(j, r, li)], (T)a.t.kzo[n]), cc);
+          if (valid && n < Np) {
+            const C wh = cmul(R.v[j], a.t.chirp[n]);
+            const T kz = a.t.kzo[n];
+            const T k2 = kp2 + kz * kz;
+            const T inv = k2 > T(0) ? T(1) / k2 : T(0);
+            s = cscale(cadd(g0[n * TL], cscale(wh, kz)), inv);
+            g0[n * TL] = s;
           }
-          R.v[j] = s;
+          R.v[j] = cmul(s, cchirp(a.t, n, Np));
         }
-        E::template A<-1>(R.v, b1, a.t.tw, r, li);
+        E::template A<-1>(R.v, b0, a.t.tw, r, li);
       }
-    } else if constexpr (P == 4) {
-      if (r < L1) {
-        E::template B<-1>(R.u, b0, r, li);
-#pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(R.u[k2], a.t.Hbi[r + L1 * k2]);
-        E::template Bi<1>(R.u, b0, a.t.tw, r, li);
-        E::template B<-1>(R.u, b1, r, li);
-#pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(R.u[k2], a.t.Hbi[r + L1 * k2]);
-        E::template Bi<1>(R.u, b1, a.t.tw, r, li);
-      }
-    } else if constexpr (P == 5) {
-      if (r < L2) {  // sigma, sigma_z (extended grid); b, t
+    } else if constexpr (P == 6) {  // sigma -> G1; inverse-DFT input kz s
+      if (r < L2) {
         E::template Ai<1>(R.v, b0, r, li);
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
-          if (n < Np && j < NJ) {
-            C cc = a.t.chirp[n];
-            cc.y = -cc.y;
-            const C sg = cscale(cmul(R.v[j], cc), invNp);
-            S2[cidx(j, r, li)] = sg;
+          if (valid && n < Np) {
+            const C sg = cscale(cmul(R.v[j], cchirp(a.t, n, Np)), invNp);
+            g1[n * TL] = sg;
+            if (n == 0 || n == Nz - 1) {
+              const int o = (n == 0) ? 4 : 6;
+              W[o] = (double)sg.x;
+              W[o + 1] = (double)sg.y;
+            }
           }
         }
-        E::template Ai<1>(R.v, b1, r, li);
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
-          if (n < Np && j < NJ) {
-            C cc = a.t.chirp[n];
-            cc.y = -cc.y;
-            const C sz = cscale(cmul(R.v[j], cc), invNp);
-            S3[cidx(j, r, li)] = sz;
-            if (valid && (n == 0 || n == Nz - 1)) {
-              const C w = xw[(long long)n * Ls];
+          C s = mk<T>(0, 0);
+          if (valid && n < Np) s = cmul(cscale(g0[n * TL], a.t.kzo[n]), cchirp(a.t, n, Np));
+          R.v[j] = s;
+        }
+        E::template A<-1>(R.v, b0, a.t.tw, r, li);
+      }
+    } else if constexpr (P == 8) {  // sigma_z -> G0; b, t
+      if (r < L2) {
+        E::template Ai<1>(R.v, b0, r, li);
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          if (valid && n < Np) {
+            const C sz = cscale(cmul(R.v[j], cchirp(a.t, n, Np)), invNp);
+            g0[n * TL] = sz;
+            if (n == 0 || n == Nz - 1) {
+              const C w = xw[n * TL];
               const int o = (n == 0) ? 0 : 2;
               W[o] = (double)w.x - (double)sz.x;
               W[o + 1] = (double)w.y - (double)sz.y;
@@ -550,78 +559,58 @@ struct KZProject {
           }
         }
       }
-    } else if constexpr (P == 6) {
-      if (r == 0) {  // homogeneous coefficients in float64 (Eqs. A, B, D)
+    } else if constexpr (P == 9) {  // homogeneous coefficients (float64) -> W[8..12]
+      if (r == 0) {
         const double br = W[0], bi = W[1], tr = W[2], ti = W[3];
-        double Ar = 0, Ai_ = 0, Br = 0, Bi_ = 0, D = 0;
+        double Ar = 0, Aim = 0, Br = 0, Bim = 0, D = 0;
         // gamma = |k_perp| of the Nyquist-zeroed wavenumbers (the same ones as
         // the gradient i kx Phi, i ky Phi), so grad phi^H is divergence-free;
         // where it vanishes, phi^H = D z with D = (b + t)/2.
-        if (kxo == 0.0 && kyo == 0.0) {
+        const double kxd = a.t.kxo_d[kxi], kyd = a.t.kyo_d[kyi];
+        if (kxd == 0.0 && kyd == 0.0) {
           D = 0.5 * (br + tr);
         } else {
-          const double gam = sqrt(kxo * kxo + kyo * kyo);
+          const double gam = sqrt(kxd * kxd + kyd * kyd);
           const double Ee = exp(-gam * a.g.Lz);
           const double den = gam * (1.0 - Ee * Ee);
           Ar = (tr - br * Ee) / den;
-          Ai_ = (ti - bi * Ee) / den;
+          Aim = (ti - bi * Ee) / den;
           Br = -(br - tr * Ee) / den;
-          Bi_ = -(bi - ti * Ee) / den;
+          Bim = -(bi - ti * Ee) / den;
         }
-        W[4] = Ar; W[5] = Ai_; W[6] = Br; W[7] = Bi_; W[8] = D;
+        W[8] = Ar; W[9] = Aim; W[10] = Br; W[11] = Bim; W[12] = D;
       }
-    } else if constexpr (P == 7) {
+    } else if constexpr (P == 10) {  // Phi, Phi' at the 2d end points -> smem
+      if (r < 2 * d) {
+        const int s = r < d ? r : Nz - 2 * d + r;
+        C ph, dph;
+        const T cf[5] = {(T)W[8], (T)W[9], (T)W[10], (T)W[11], (T)W[12]};
+        phi_at(cf, kxo, kyo, (T)a.g.dz, (T)a.g.Lz, s, &ph, &dph);
+        Ev[r < d ? r : DMAX + (r - d)] = ph;
+        Ev[2 * DMAX + (r < d ? r : DMAX + (r - d))] = dph;
+      }
+    } else if constexpr (P == 11) {  // X -= grad phi^I + FC(grad phi^H); wall planes
       if (r < L2 && valid) {
-        const double Ar = W[4], Aim = W[5], Br = W[6], Bim = W[7], D = W[8];
-        const bool mean = (kxo == 0.0 && kyo == 0.0);
-        const double gam = mean ? 0.0 : sqrt(kxo * kxo + kyo * kyo);
-        // Phi and Phi' at physical point s (analytic, float64 coefficients)
-        auto phi_at = [&](int s, C& ph, C& dph) {
-          const double z = s * a.g.dz;
-          if (mean) {
-            ph = mk<T>(0, 0);
-            dph = mk<T>((T)D, 0);
-            return;
-          }
-          T e1, e2;
-          if constexpr (sizeof(T) == 4) {
-            e1 = expf((float)(gam * (z - a.g.Lz)));
-            e2 = expf((float)(-gam * z));
-          } else {
-            e1 = exp(gam * (z - a.g.Lz));
-            e2 = exp(-gam * z);
-          }
-          const T g = (T)gam;
-          ph = mk<T>((T)Ar * e1 + (T)Br * e2, (T)Aim * e1 + (T)Bim * e2);
-          dph = mk<T>(g * ((T)Ar * e1 - (T)Br * e2), g * ((T)Aim * e1 - (T)Bim * e2));
-        };
-        C eph[2 * DMAX], edph[2 * DMAX];
-        bool have_ends = false;
+        const T cf[5] = {(T)W[8], (T)W[9], (T)W[10], (T)W[11], (T)W[12]};
+        const T tdz = (T)a.g.dz, tLz = (T)a.g.Lz;
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
-          if (n < Np && j < NJ) {
+          if (n < Np) {
             C ph, dph;
             if (n < Nz) {
-              phi_at(n, ph, dph);
+              phi_at(cf, kxo, kyo, tdz, tLz, n, &ph, &dph);
             } else {
-              if (!have_ends) {
-                for (int i = 0; i < d; ++i) {
-                  phi_at(i, eph[i], edph[i]);
-                  phi_at(Nz - d + i, eph[DMAX + i], edph[DMAX + i]);
-                }
-                have_ends = true;
-              }
-              ph = continuation_value<T>(n - Nz, eph, eph + DMAX, d, a.g.Cc, Ms, Ms2);
-              dph = continuation_value<T>(n - Nz, edph, edph + DMAX, d, a.g.Cc, Ms, Ms2);
+              ph = continuation_value<T>(n - Nz, Ev, Ev + DMAX, d, a.g.Cc, Ms, Ms2);
+              dph = continuation_value<T>(n - Nz, Ev + 2 * DMAX, Ev + 3 * DMAX, d, a.g.Cc, Ms, Ms2);
             }
-            const C sg = S2[cidx(j, r, li)];
-            const C sz = S3[cidx(j, r, li)];
+            const int o = n * TL;
+            const C sg = g1[o];
+            const C sz = g0[o];
             // i k Phi = (-k Phi.y, k Phi.x)
-            const C gx = cadd(cscale(sg, (T)kxo), mk<T>(-(T)kxo * ph.y, (T)kxo * ph.x));
-            const C gy = cadd(cscale(sg, (T)kyo), mk<T>(-(T)kyo * ph.y, (T)kyo * ph.x));
+            const C gx = cadd(cscale(sg, kxo), mk<T>(-kxo * ph.y, kxo * ph.x));
+            const C gy = cadd(cscale(sg, kyo), mk<T>(-kyo * ph.y, kyo * ph.x));
             const C gz = cadd(sz, dph);
-            const long long o = (long long)n * Ls;
             xu[o] = csub(xu[o], gx);
             xv[o] = csub(xv[o], gy);
             xw[o] = csub(xw[o], gz);
@@ -636,6 +625,30 @@ struct KZProject {
       }
     }
   }
+
+  // Phi and Phi' at physical point s from the float64 coefficients W[8..12]
+  // (evaluated in the path's precision)
+  static FC_NOINLINE void phi_at(const T* cf, T kxo, T kyo, T dz, T Lz, int s, C* ph, C* dph) {
+    if (kxo == T(0) && kyo == T(0)) {
+      *ph = mk<T>(0, 0);
+      *dph = mk<T>(cf[4], 0);
+      return;
+    }
+    const T z = (T)s * dz;
+    T gam, e1, e2;
+    if constexpr (sizeof(T) == 4) {
+      gam = sqrtf(kxo * kxo + kyo * kyo);
+      e1 = expf(gam * (z - Lz));
+      e2 = expf(-gam * z);
+    } else {
+      gam = sqrt(kxo * kxo + kyo * kyo);
+      e1 = exp(gam * (z - Lz));
+      e2 = exp(-gam * z);
+    }
+    const T Ar = cf[0], Aim = cf[1], Br = cf[2], Bim = cf[3];
+    *ph = mk<T>(Ar * e1 + Br * e2, Aim * e1 + Bim * e2);
+    *dph = mk<T>(gam * (Ar * e1 - Br * e2), gam * (Aim * e1 - Bim * e2));
+  }
 };
 
 // ===========================================================================
@@ -646,7 +659,8 @@ struct KZProject {
 // ===========================================================================
 struct YGeom {
   int Ny, Kx, Nz;
-  long long plane;          // Ny * Kx
+  long long plane;          // Ny * Kx (lines)
+  long long ntiles;
 };
 
 // yinv3: V = IFFT_y(A), DY = IFFT_y(i ky A), DZ <- IFFT_y(DZ) (1/Ny included)
@@ -655,12 +669,12 @@ struct KYInv3 {
   using E = Eng<T, L1, L2, LINES>;
   using C = cx<T>;
   static constexpr int THREADS = E::THREADS, NPHASE = 4;
-  static constexpr int MINB = (sizeof(T) == 4 && THREADS <= 512) ? 2 : 1;
+  static constexpr int MINB = THREADS <= 160 ? 3 : (THREADS <= 320 ? 2 : 1);
   struct Args {
     YGeom g;
     const C* tw;
-    const double* kyo;
-    const C* A; long long a_fstride;   // source field stride (planes)
+    const T* kyo;
+    const C* A; long long a_fstride;   // rows per field of the source array
     C* V; C* DY; C* DZ;                 // [nf][Nz][Ny][Kx]
     long long tiles;                    // tiles per plane
     T scale;
@@ -678,12 +692,12 @@ struct KYInv3 {
     const long long f = pz / a.g.Nz, z = pz % a.g.Nz;
     const int kx = (int)(tile * LINES + li);
     const bool valid = kx < a.g.Kx;
-    const C* src = a.A + (f * a.a_fstride + z) * a.g.plane + kx;
-    const long long mo = pz * a.g.plane + kx;
+    auto src = [&](int ky) { return a.A[lay(f, z, (long long)ky * a.g.Kx + kx, a.a_fstride, a.g.ntiles)]; };
+    auto mo = [&](int y) { return lay(f, z, (long long)y * a.g.Kx + kx, a.g.Nz, a.g.ntiles); };
     if constexpr (P == 0) {
       if (r < L2) {
 #pragma unroll
-        for (int j = 0; j < L1; ++j) R.v[j] = valid ? src[(long long)(r + L2 * j) * a.g.Kx] : mk<T>(0, 0);
+        for (int j = 0; j < L1; ++j) R.v[j] = valid ? src(r + L2 * j) : mk<T>(0, 0);
         E::template A<1>(R.v, b0, a.tw, r, li);
       }
     } else if constexpr (P == 1) {
@@ -691,14 +705,14 @@ struct KYInv3 {
         E::template B<1>(R.u, b0, r, li);
         if (valid)
 #pragma unroll
-          for (int k2 = 0; k2 < L2; ++k2) a.V[mo + (long long)(r + L1 * k2) * a.g.Kx] = cscale(R.u[k2], a.scale);
+          for (int k2 = 0; k2 < L2; ++k2) a.V[mo(r + L1 * k2)] = cscale(R.u[k2], a.scale);
       }
       if (r < L2) {
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int ky = r + L2 * j;
-          const C x = valid ? src[(long long)ky * a.g.Kx] : mk<T>(0, 0);
-          const T k = (T)a.kyo[ky];
+          const C x = valid ? src(ky) : mk<T>(0, 0);
+          const T k = a.kyo[ky];
           R.v[j] = mk<T>(-k * x.y, k * x.x);
         }
         E::template A<1>(R.v, b1, a.tw, r, li);
@@ -708,11 +722,11 @@ struct KYInv3 {
         E::template B<1>(R.u, b1, r, li);
         if (valid)
 #pragma unroll
-          for (int k2 = 0; k2 < L2; ++k2) a.DY[mo + (long long)(r + L1 * k2) * a.g.Kx] = cscale(R.u[k2], a.scale);
+          for (int k2 = 0; k2 < L2; ++k2) a.DY[mo(r + L1 * k2)] = cscale(R.u[k2], a.scale);
       }
       if (r < L2) {
 #pragma unroll
-        for (int j = 0; j < L1; ++j) R.v[j] = valid ? a.DZ[mo + (long long)(r + L2 * j) * a.g.Kx] : mk<T>(0, 0);
+        for (int j = 0; j < L1; ++j) R.v[j] = valid ? a.DZ[mo(r + L2 * j)] : mk<T>(0, 0);
         E::template A<1>(R.v, b0, a.tw, r, li);
       }
     } else if constexpr (P == 3) {
@@ -720,7 +734,7 @@ struct KYInv3 {
         E::template B<1>(R.u, b0, r, li);
         if (valid)
 #pragma unroll
-          for (int k2 = 0; k2 < L2; ++k2) a.DZ[mo + (long long)(r + L1 * k2) * a.g.Kx] = cscale(R.u[k2], a.scale);
+          for (int k2 = 0; k2 < L2; ++k2) a.DZ[mo(r + L1 * k2)] = cscale(R.u[k2], a.scale);
       }
     }
   }
@@ -732,7 +746,7 @@ struct KY1 {
   using E = Eng<T, L1, L2, LINES>;
   using C = cx<T>;
   static constexpr int THREADS = E::THREADS, NPHASE = 2;
-  static constexpr int MINB = (sizeof(T) == 4 && THREADS <= 512) ? 2 : 1;
+  static constexpr int MINB = THREADS <= 160 ? 3 : (THREADS <= 320 ? 2 : 1);
   struct Args {
     YGeom g;
     const C* tw;
@@ -755,18 +769,18 @@ struct KY1 {
     const bool valid = kx < a.g.Kx;
     if constexpr (P == 0) {
       if (r < L2) {
-        const C* src = a.IN + (f * a.in_fstride + z) * a.g.plane + kx;
 #pragma unroll
-        for (int j = 0; j < L1; ++j) R.v[j] = valid ? src[(long long)(r + L2 * j) * a.g.Kx] : mk<T>(0, 0);
+        for (int j = 0; j < L1; ++j)
+          R.v[j] = valid ? a.IN[lay(f, z, (long long)(r + L2 * j) * a.g.Kx + kx, a.in_fstride, a.g.ntiles)] : mk<T>(0, 0);
         E::template A<SIGN>(R.v, b0, a.tw, r, li);
       }
     } else {
       if (r < L1) {
         E::template B<SIGN>(R.u, b0, r, li);
-        C* dst = a.OUT + (f * a.out_fstride + z) * a.g.plane + kx;
         if (valid)
 #pragma unroll
-          for (int k2 = 0; k2 < L2; ++k2) dst[(long long)(r + L1 * k2) * a.g.Kx] = cscale(R.u[k2], a.scale);
+          for (int k2 = 0; k2 < L2; ++k2)
+            a.OUT[lay(f, z, (long long)(r + L1 * k2) * a.g.Kx + kx, a.out_fstride, a.g.ntiles)] = cscale(R.u[k2], a.scale);
       }
     }
   }
@@ -813,42 +827,46 @@ struct KXPass {
   using RE = RowEng<T, L1, L2>;
   using C = cx<T>;
   static constexpr int Nx = L1 * L2, G = RE::G, NJOB = 2 * NF, NFWD = (NF + 1) / 2;
-  static constexpr int THREADS = NJOB * G, NPHASE = 6, MINB = 1;
+  static constexpr int THREADS = NJOB * G, NPHASE = 8, MINB = 2;
   struct Args {
-    int Kx;
+    int Kx, Ny, Nz;
     long long rows;          // Nz * Ny
+    long long ntiles;
     const C* tw;             // Nx engine twiddles
-    const double* kxo;       // Kx
+    const T* kxo;            // Kx
     const C* V; const C* DY; const C* DZ;   // [NF][rows][Kx]
     C* NL;                                  // [NF][rows][Kx]
     T forcing, gamma, scale;                // scale = 1/Nx
   };
   struct Regs { C v[L1]; C u[L2]; };
-  static constexpr size_t off_P = sizeof(C) * RE::BUF * NJOB;
-  static constexpr size_t smem_bytes = off_P + sizeof(T) * 4 * NF * Nx;
+  // the real rows Pr alias the exchange buffers (phases separate every reuse)
+  static constexpr size_t zb_bytes = sizeof(C) * RE::BUF * NJOB;
+  static constexpr size_t pr_bytes = sizeof(T) * 4 * NF * Nx;
+  static constexpr size_t smem_bytes = zb_bytes > pr_bytes ? zb_bytes : pr_bytes;
 
   template <int P>
   static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long row, Regs& R) {
     C* Zb = reinterpret_cast<C*>(sm);
-    T* Pr = reinterpret_cast<T*>(sm + off_P);
+    T* Pr = reinterpret_cast<T*>(sm);
     const int q = tid / G, g = tid % G;
     const long long Kx = a.Kx;
-    if constexpr (P == 0) {
+    if constexpr (P == 0) {  // pair spectra (v + i dx v), (dy v + i dz v), inverse first half
       if (g < L2) {
         const int f = q / 2, type = q % 2;
-        const C* A = (type == 0 ? a.V : a.DY) + ((long long)f * a.rows + row) * Kx;
-        const C* Bq = a.DZ + ((long long)f * a.rows + row) * Kx;
+        const C* A = (type == 0 ? a.V : a.DY);
+        const long long z = row / a.Ny, yb = (row % a.Ny) * Kx;
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int k = g + L2 * j;
           const bool up = k > Nx / 2;
           const int kk = up ? Nx - k : k;
-          C av = A[kk], bv;
+          const long long o = lay(f, z, yb + kk, a.Nz, a.ntiles);
+          C av = A[o], bv;
           if (type == 0) {
-            const T kx = (T)a.kxo[kk];
+            const T kx = a.kxo[kk];
             bv = mk<T>(-kx * av.y, kx * av.x);
           } else {
-            bv = Bq[kk];
+            bv = a.DZ[o];
           }
           if (kk == 0 || kk == Nx / 2) { av.y = T(0); bv.y = T(0); }
           if (up) { av.y = -av.y; bv.y = -bv.y; }
@@ -857,8 +875,9 @@ struct KXPass {
         RE::template A<1>(R.v, Zb + q * RE::BUF, a.tw, g);
       }
     } else if constexpr (P == 1) {
+      if (g < L1) RE::template B<1>(R.u, Zb + q * RE::BUF, g);
+    } else if constexpr (P == 2) {  // real rows v_f, dx v_f, dy v_f, dz v_f
       if (g < L1) {
-        RE::template B<1>(R.u, Zb + q * RE::BUF, g);
 #pragma unroll
         for (int k2 = 0; k2 < L2; ++k2) {
           const int n = g + L1 * k2;
@@ -866,7 +885,7 @@ struct KXPass {
           Pr[(2 * q + 1) * Nx + n] = R.u[k2].y * a.scale;
         }
       }
-    } else if constexpr (P == 2) {
+    } else if constexpr (P == 3) {  // products (Sec. 4.2, Sec. 6, Sec. 7)
       for (int n = tid; n < Nx; n += THREADS) {
         const T u = Pr[0 * Nx + n], v = Pr[4 * Nx + n], w = Pr[8 * Nx + n];
         T Nf[NF];
@@ -881,7 +900,7 @@ struct KXPass {
 #pragma unroll
         for (int f = 0; f < NF; ++f) Pr[f * Nx + n] = Nf[f];
       }
-    } else if constexpr (P == 3) {
+    } else if constexpr (P == 4) {
       if (q < NFWD && g < L2) {
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
@@ -890,16 +909,17 @@ struct KXPass {
           const T im = (2 * q + 1 < NF) ? Pr[(2 * q + 1) * Nx + n] : T(0);
           R.v[j] = mk<T>(re, im);
         }
-        RE::template A<-1>(R.v, Zb + q * RE::BUF, a.tw, g);
       }
-    } else if constexpr (P == 4) {
+    } else if constexpr (P == 5) {
+      if (q < NFWD && g < L2) RE::template A<-1>(R.v, Zb + q * RE::BUF, a.tw, g);
+    } else if constexpr (P == 6) {
       if (q < NFWD && g < L1) {
         RE::template B<-1>(R.u, Zb + q * RE::BUF, g);
         C* Zn = Zb + (NFWD + q) * RE::BUF;   // natural order spectrum
 #pragma unroll
         for (int k2 = 0; k2 < L2; ++k2) Zn[g + L1 * k2] = R.u[k2];
       }
-    } else if constexpr (P == 5) {
+    } else if constexpr (P == 7) {
       for (int i = tid; i < NFWD * (Nx / 2 + 1); i += THREADS) {
         const int qq = i / (Nx / 2 + 1), k = i % (Nx / 2 + 1);
         const C* Zn = Zb + (NFWD + qq) * RE::BUF;
@@ -907,8 +927,9 @@ struct KXPass {
         // A = (Z_k + conj Z_{N-k}) / 2,  B = (Z_k - conj Z_{N-k}) / (2i)
         const C Av = mk<T>((zk.x + zm.x) * T(0.5), (zk.y - zm.y) * T(0.5));
         const C Bv = mk<T>((zk.y + zm.y) * T(0.5), (zm.x - zk.x) * T(0.5));
-        a.NL[((long long)(2 * qq) * a.rows + row) * Kx + k] = Av;
-        if (2 * qq + 1 < NF) a.NL[((long long)(2 * qq + 1) * a.rows + row) * Kx + k] = Bv;
+        const long long z = row / a.Ny, yb = (row % a.Ny) * Kx;
+        a.NL[lay(2 * qq, z, yb + k, a.Nz, a.ntiles)] = Av;
+        if (2 * qq + 1 < NF) a.NL[lay(2 * qq + 1, z, yb + k, a.Nz, a.ntiles)] = Bv;
       }
     }
   }
@@ -923,8 +944,9 @@ struct KXRow {
   static constexpr int Nx = L1 * L2, G = RE::G;
   static constexpr int THREADS = JOBS * G, NPHASE = 3, MINB = 1;
   struct Args {
-    int Kx;
+    int Kx, Ny, Nz;
     long long pairs;        // number of row pairs (rows / 2)
+    long long ntiles;
     const C* tw;
     const T* R; C* S;       // SIGN = -1: R -> S;  SIGN = +1: S -> R
     T scale;
@@ -932,6 +954,11 @@ struct KXRow {
   struct Regs { C v[L1]; C u[L2]; };
   static constexpr size_t smem_bytes = sizeof(C) * RE::BUF * JOBS * 2;
 
+  // element k of row R (rows ordered [f][z][y]) in the tiled layout
+  static FC_HD long long sidx(const Args& a, long long R, long long k) {
+    const long long y = R % a.Ny, fz = R / a.Ny;
+    return lay(fz / a.Nz, fz % a.Nz, y * a.Kx + k, a.Nz, a.ntiles);
+  }
   template <int P>
   static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& Rg) {
     const int q = tid / G, g = tid % G;
@@ -961,20 +988,20 @@ struct KXRow {
         if (valid)
           for (int k = g; k <= Nx / 2; k += G) {
             const C zk = Zn[k], zm = Zn[(Nx - k) % Nx];
-            a.S[(2 * pair) * Kx + k] = mk<T>((zk.x + zm.x) * T(0.5), (zk.y - zm.y) * T(0.5));
-            a.S[(2 * pair + 1) * Kx + k] = mk<T>((zk.y + zm.y) * T(0.5), (zm.x - zk.x) * T(0.5));
+            a.S[sidx(a, 2 * pair, k)] = mk<T>((zk.x + zm.x) * T(0.5), (zk.y - zm.y) * T(0.5));
+            a.S[sidx(a, 2 * pair + 1, k)] = mk<T>((zk.y + zm.y) * T(0.5), (zm.x - zk.x) * T(0.5));
           }
       }
     } else {
       if constexpr (P == 0) {
         if (g < L2) {
-          const C* s0 = a.S + (2 * pair) * Kx;
 #pragma unroll
           for (int j = 0; j < L1; ++j) {
             const int k = g + L2 * j;
             const bool up = k > Nx / 2;
             const int kk = up ? Nx - k : k;
-            C av = valid ? s0[kk] : mk<T>(0, 0), bv = valid ? s0[Kx + kk] : mk<T>(0, 0);
+            C av = valid ? a.S[sidx(a, 2 * pair, kk)] : mk<T>(0, 0);
+            C bv = valid ? a.S[sidx(a, 2 * pair + 1, kk)] : mk<T>(0, 0);
             if (kk == 0 || kk == Nx / 2) { av.y = T(0); bv.y = T(0); }
             if (up) { av.y = -av.y; bv.y = -bv.y; }
             Rg.v[j] = mk<T>(av.x - bv.y, av.y + bv.x);

@@ -16,13 +16,13 @@
 namespace fcns {
 // lines per CTA of the z kernels and of the y kernels
 template <class T, int L> constexpr int z_lines() {
-  return sizeof(T) == 4 ? (L >= 576 ? 8 : 16) : (L >= 576 ? 4 : 8);
+  return sizeof(T) == 4 ? (L >= 576 ? 4 : 8) : (L >= 576 ? 2 : 4);
 }
 template <class T, int L> constexpr int zproj_lines() {
   return sizeof(T) == 4 ? (L >= 576 ? 4 : 8) : (L >= 576 ? 2 : 4);
 }
 template <class T, int N> constexpr int y_lines() {
-  return sizeof(T) == 4 ? (N >= 1024 ? 8 : (N >= 512 ? 16 : 32)) : (N >= 1024 ? 4 : (N >= 512 ? 8 : 16));
+  return sizeof(T) == 4 ? (N >= 512 ? 4 : (N >= 128 ? 8 : 16)) : (N >= 512 ? 2 : (N >= 128 ? 4 : 8));
 }
 // row-pair jobs per CTA of the x row transforms
 template <int N> constexpr int x_jobs() { return N >= 512 ? 2 : (N >= 128 ? 4 : 8); }
