@@ -199,11 +199,12 @@ fc_status ns_set_fields(ns_sim_t sim, const void* phys, fc_stream_t stream);
 fc_status ns_get_fields(ns_sim_t sim, void* phys, fc_stream_t stream);
 
 /* Copy the state to / from a device buffer (checkpoint / restore).  The
- * buffer holds nf * (Nz+C) * ceil(Ny*(Nx/2+1)/16) * 16 complex values of the
- * simulation's precision in the library's internal order: the fields in
- * (kx, ky, z') on the continued grid, lines (ky*(Nx/2+1) + kx) grouped in
- * tiles of 16, each tile storing its z' rows contiguously.  A length-(Nz+C)
- * DFT along z' turns it into the continued spectral field of the paper. */
+ * buffer holds nf * (Nz+C) * Ny * Kxp complex values of the simulation's
+ * precision, Kxp = Nx/2+1 rounded up to a multiple of 16, in the library's
+ * internal order: the fields in (kx, ky, z') on the continued grid, lines
+ * (ky * Kxp + kx) grouped in tiles of 16 whose z' rows are contiguous.  A
+ * length-(Nz+C) DFT along z' turns it into the continued spectral field of
+ * the paper. */
 fc_status ns_get_state(ns_sim_t sim, void* spec, fc_stream_t stream);
 fc_status ns_put_state(ns_sim_t sim, const void* spec, fc_stream_t stream);
 

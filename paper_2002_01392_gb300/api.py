@@ -228,8 +228,7 @@ class Sim:
         return out
 
     def state_shape(self):
-        lines = self.p.Ny * self.Kx
-        plines = (lines + 15) // 16 * 16
+        plines = self.p.Ny * ((self.Kx + 15) // 16 * 16)
         return (self.p.nfields * (self.p.Nz + self.p.C) * plines,)
 
     def get_state(self, out=None, stream=None):

@@ -54,19 +54,30 @@ fc_status fc_setup_ex(int d, int C, int Nz, int M, int n_os, fc_plan_t* out) {
   p->data.d = d; p->data.C = C; p->data.Nz = Nz; p->data.Np = Nz + C;
   p->data.M = M; p->data.n_os = n_os; p->data.ls_residual = T.ls_residual;
   p->data.Mr = T.Mr;
-  const int need = p->data.Np + Nz - 1;
-  const int L = pick_engine_length(need);
+  // transform length: N' itself when it is one of the compiled (smooth)
+  // lengths -- the paper's choice of N' (Sec. 6, Sec. 7 tables) -- else the
+  // padded circular-convolution length L >= N' + Nz - 1
+  int L = 0;
+  for (auto& sh : engine_shapes())
+    if (sh.L == p->data.Np) L = sh.L;
+  if (!L) L = pick_engine_length(p->data.Np + Nz - 1);
   if (L > 0) {
     for (auto& s : engine_shapes())
       if (s.L == L) { p->deriv.L = L; p->deriv.L1 = s.L1; p->deriv.L2 = s.L2; }
-    deriv_conv_spectrum(Nz, p->data.Np, L, &p->deriv.H);
     engine_twiddles(p->deriv.L1, p->deriv.L2, &p->deriv.tw);
     auto& t = p->deriv;
-    t.H32.resize(L); t.tw32.resize(L); t.H64.resize(L); t.tw64.resize(L);
+    std::vector<std::complex<double>> H1, H2;
+    deriv_conv_spectra(Nz, p->data.Np, L, &H1, &H2);
+    t.H1_32.resize(L); t.H2_32.resize(L); t.H1_64.resize(L); t.H2_64.resize(L);
     for (int i = 0; i < L; ++i) {
-      t.H32[i] = make_float2((float)t.H[i].real(), (float)t.H[i].imag());
+      t.H1_32[i] = make_float2((float)H1[i].real(), (float)H1[i].imag());
+      t.H2_32[i] = make_float2((float)H2[i].real(), (float)H2[i].imag());
+      t.H1_64[i] = make_double2(H1[i].real(), H1[i].imag());
+      t.H2_64[i] = make_double2(H2[i].real(), H2[i].imag());
+    }
+    t.tw32.resize(L); t.tw64.resize(L);
+    for (int i = 0; i < L; ++i) {
       t.tw32[i] = make_float2((float)t.tw[i].real(), (float)t.tw[i].imag());
-      t.H64[i] = make_double2(t.H[i].real(), t.H[i].imag());
       t.tw64[i] = make_double2(t.tw[i].real(), t.tw[i].imag());
     }
   }
@@ -107,7 +118,8 @@ fc_status fc_destroy(fc_plan_t plan) {
     for (auto& t : plan->data.dev) {
       cudaSetDevice(t.device);
       cudaDeviceSynchronize();
-      cudaFree(t.Mr); cudaFree(t.Mr2); cudaFree(t.H32); cudaFree(t.H64); cudaFree(t.tw32); cudaFree(t.tw64);
+      cudaFree(t.Mr); cudaFree(t.Mr2); cudaFree(t.tw32); cudaFree(t.tw64);
+      cudaFree(t.H1_32); cudaFree(t.H1_64); cudaFree(t.H2_32); cudaFree(t.H2_64);
     }
     cudaSetDevice(cur);
   }
@@ -143,12 +155,21 @@ static fc_status deriv_tables_locked(fc_plan* plan, DerivDevTables** out) {
   if (!s) s = cuda_status(cudaMalloc((void**)&t.Mr2, sizeof(float2) * plan->deriv.Mr2.size()), "cudaMalloc(Mr2)");
   if (!s) s = cuda_status(cudaMemcpy(t.Mr2, plan->deriv.Mr2.data(), sizeof(float2) * plan->deriv.Mr2.size(),
                                      cudaMemcpyHostToDevice), "cudaMemcpy(Mr2)");
-  if (!s) s = upload<float2>(plan->deriv.H, &t.H32);
-  if (!s) s = upload<double2>(plan->deriv.H, &t.H64);
+  auto up = [&](const void* src, size_t bytes, void** dst) {
+    fc_status st = cuda_status(cudaMalloc(dst, bytes), "cudaMalloc(tables)");
+    if (!st) st = cuda_status(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), "cudaMemcpy(tables)");
+    return st;
+  };
+  const size_t L = plan->deriv.L;
+  if (!s) s = up(plan->deriv.H1_32.data(), 8 * L, &t.H1_32);
+  if (!s) s = up(plan->deriv.H2_32.data(), 8 * L, &t.H2_32);
+  if (!s) s = up(plan->deriv.H1_64.data(), 16 * L, &t.H1_64);
+  if (!s) s = up(plan->deriv.H2_64.data(), 16 * L, &t.H2_64);
   if (!s) s = upload<float2>(plan->deriv.tw, &t.tw32);
   if (!s) s = upload<double2>(plan->deriv.tw, &t.tw64);
   if (s) {
-    cudaFree(t.Mr); cudaFree(t.Mr2); cudaFree(t.H32); cudaFree(t.H64); cudaFree(t.tw32); cudaFree(t.tw64);
+    cudaFree(t.Mr); cudaFree(t.Mr2); cudaFree(t.tw32); cudaFree(t.tw64);
+      cudaFree(t.H1_32); cudaFree(t.H1_64); cudaFree(t.H2_32); cudaFree(t.H2_64);
     return s;
   }
   plan->data.dev.push_back(t);

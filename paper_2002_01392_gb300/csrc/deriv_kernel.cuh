@@ -171,3 +171,157 @@ struct DerivConv {
 };
 
 }  // namespace fcns
+
+#include "engine.cuh"
+
+namespace fcns {
+
+// fc_deriv_z with two adjacent real z-lines packed as one complex line
+// x = a + i b.  The derivative kernels d1, d2 of the N'-periodic grid are
+// real, so one forward transform X = FFT_L(x) serves both lines and
+//   IFFT_L(X H1) = d1*a + i d1*b,   IFFT_L(X H2) = d2*a + i d2*b
+// (H1, H2: spectra of d1, d2 placed circularly on L >= N' + Nz - 1, with 1/L):
+// three length-L transforms per two lines instead of four.
+template <class T, int L1_, int L2_, int LINES_>
+struct DerivPair {
+  using E = Eng<T, L1_, L2_, LINES_>;
+  using C = cx<T>;
+  static constexpr int L1 = L1_, L2 = L2_, LINES = LINES_;
+  static constexpr int THREADS = E::THREADS, NPHASE = 4;
+  static constexpr int MINB = THREADS <= 160 ? 3 : (THREADS <= 320 ? 2 : 1);
+  static constexpr int MR_MAX = 640;
+  static constexpr int DMAX = 10;
+
+  struct Args {
+    const T* f;
+    T* df;
+    T* d2f;
+    int Nz, Np, d, Cc;
+    long long lines;      // real lines per field (Nx * Ny)
+    long long pairs;      // ceil(lines / 2)
+    long long tiles;      // tiles of LINES pairs per field
+    long long zstride;    // elements between consecutive z (= lines)
+    long long bstride;    // elements between fields
+    T s1, s2;             // 1/dz, 1/dz^2
+    const double* Mr;
+    const float2* Mr2;
+    const C* H1;          // spectrum of d1 (natural order, length L)
+    const C* H2;          // spectrum of d2
+    const C* tw;          // engine twiddles
+  };
+  struct Regs { C v[L1]; C u[L2]; };
+
+  // (the continuation matrix is read through the data cache: few threads use it)
+  static constexpr size_t off_b1 = sizeof(C) * E::BUF;
+  static constexpr size_t off_E = off_b1 + sizeof(C) * E::BUF;
+  static constexpr size_t smem_bytes = off_E + sizeof(C) * LINES * 2 * DMAX;
+
+  // continuation value jj of a complex line: M_r f_last + M_l f_first
+  static DERIV_NOINLINE C cont_cplx(int jj, const C* first, const C* last, int d, int Cc, const double* Ms,
+                                    const float2* Ms2) {
+    if constexpr (sizeof(T) == 4) {
+      ff re{0.f, 0.f}, im{0.f, 0.f};
+      for (int i = 0; i < d; ++i) {
+        const float2 m1 = Ms2[jj * d + i];
+        const float2 m2 = Ms2[(Cc - 1 - jj) * d + (d - 1 - i)];
+        ff_fma(re, m1.x, m1.y, last[i].x);
+        ff_fma(im, m1.x, m1.y, last[i].y);
+        ff_fma(re, m2.x, m2.y, first[i].x);
+        ff_fma(im, m2.x, m2.y, first[i].y);
+      }
+      return mk<T>(ff_round(re), ff_round(im));
+    } else {
+      double re = 0, im = 0;
+      for (int i = 0; i < d; ++i) {
+        const double m1 = Ms[jj * d + i], m2 = Ms[(Cc - 1 - jj) * d + (d - 1 - i)];
+        re += m1 * last[i].x + m2 * first[i].x;
+        im += m1 * last[i].y + m2 * first[i].y;
+      }
+      return mk<T>((T)re, (T)im);
+    }
+  }
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
+    C* b0 = reinterpret_cast<C*>(sm);
+    C* b1 = reinterpret_cast<C*>(sm + off_b1);
+    const double* Ms = a.Mr;
+    const float2* Ms2 = a.Mr2;
+    const int r = tid / LINES, li = tid % LINES;
+    C* Ev = reinterpret_cast<C*>(sm + off_E) + li * 2 * DMAX;
+    const long long field = bid / a.tiles;
+    const long long pair = (bid % a.tiles) * LINES + li;
+    const long long la = 2 * pair;                 // first line of the pair
+    const bool va = la < a.lines, vb = la + 1 < a.lines;
+    const long long base = field * a.bstride + la;
+
+    if constexpr (P == 0) {
+      if (r < L2) {
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          C x = mk<T>(0, 0);
+          if (n < a.Nz) {
+            const T* p = a.f + base + (long long)n * a.zstride;
+            if (va) x.x = p[0];
+            if (vb) x.y = p[1];
+          }
+          R.v[j] = x;
+          if (n < a.d) Ev[n] = x;
+          if (n >= a.Nz - a.d && n < a.Nz) Ev[DMAX + n - (a.Nz - a.d)] = x;
+        }
+      }
+    } else if constexpr (P == 1) {
+      if (r < L2) {
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int n = r + L2 * j;
+          if (n >= a.Nz && n < a.Np) R.v[j] = cont_cplx(n - a.Nz, Ev, Ev + DMAX, a.d, a.Cc, Ms, Ms2);
+        }
+        E::template A<-1>(R.v, b0, a.tw, r, li);
+      }
+    } else if constexpr (P == 2) {
+      if (r < L1) {
+        E::template B<-1>(R.u, b0, r, li);
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) b1[E::bidx(r, k2, li)] = R.u[k2];
+        E::mulH(R.u, a.H1, r);
+        E::template Bi<1>(R.u, b0, a.tw, r, li);
+        FC_FENCE();
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = b1[E::bidx(r, k2, li)];
+        E::mulH(R.u, a.H2, r);
+        E::template Bi<1>(R.u, b1, a.tw, r, li);
+      }
+    } else if constexpr (P == 3) {
+      if (r < L2 && va) {
+        E::template Ai<1>(R.v, b0, r, li);
+        if (a.df) {
+#pragma unroll
+          for (int j = 0; j < L1; ++j) {
+            const int n = r + L2 * j;
+            if (n < a.Nz) {
+              T* p = a.df + base + (long long)n * a.zstride;
+              p[0] = R.v[j].x * a.s1;
+              if (vb) p[1] = R.v[j].y * a.s1;
+            }
+          }
+        }
+        if (a.d2f) {
+          E::template Ai<1>(R.v, b1, r, li);
+#pragma unroll
+          for (int j = 0; j < L1; ++j) {
+            const int n = r + L2 * j;
+            if (n < a.Nz) {
+              T* p = a.d2f + base + (long long)n * a.zstride;
+              p[0] = R.v[j].x * a.s2;
+              if (vb) p[1] = R.v[j].y * a.s2;
+            }
+          }
+        }
+      }
+    }
+  }
+};
+
+}  // namespace fcns

@@ -9,6 +9,14 @@
 #pragma once
 #include "phases.cuh"
 
+// Scheduling fence: keeps the compiler from hoisting the table loads of the
+// next loop above a register DFT (which would hold both in registers at once).
+#if defined(__CUDA_ARCH__)
+#define FC_FENCE() asm volatile("" ::: "memory")
+#else
+#define FC_FENCE()
+#endif
+
 namespace fcns {
 
 template <class T, int L1_, int L2_, int LINES_>
@@ -36,7 +44,10 @@ struct Eng {
   static FC_HD void A(C (&v)[L1], C* buf, const C* tw, int n2, int li) {
     dft_reg<L1, SIGN, T>(v);
 #pragma unroll
-    for (int k1 = 0; k1 < L1; ++k1) buf[bidx(k1, n2, li)] = cmul(v[k1], twid<SIGN>(tw, n2, k1));
+    for (int k1 = 0; k1 < L1; ++k1) {
+      if (k1 % 6 == 0) FC_FENCE();
+      buf[bidx(k1, n2, li)] = cmul(v[k1], twid<SIGN>(tw, n2, k1));
+    }
   }
   // B: thread k1 -> u[k2] = X[k1 + L1 k2]
   template <int SIGN>
@@ -50,7 +61,18 @@ struct Eng {
   static FC_HD void Bi(C (&u)[L2], C* buf, const C* tw, int k1, int li) {
     dft_reg<L2, SIGN, T>(u);
 #pragma unroll
-    for (int n2 = 0; n2 < L2; ++n2) buf[bidx(k1, n2, li)] = cmul(u[n2], twid<SIGN>(tw, n2, k1));
+    for (int n2 = 0; n2 < L2; ++n2) {
+      if (n2 % 6 == 0) FC_FENCE();
+      buf[bidx(k1, n2, li)] = cmul(u[n2], twid<SIGN>(tw, n2, k1));
+    }
+  }
+  // u[k2] *= H[k1 + L1 k2], in chunks so the table loads are not all live at once
+  static FC_HD void mulH(C (&u)[L2], const C* H, int k1) {
+#pragma unroll
+    for (int k2 = 0; k2 < L2; ++k2) {
+      if (k2 % 6 == 0) FC_FENCE();
+      u[k2] = cmul(u[k2], H[k1 + L1 * k2]);
+    }
   }
   // inverse-direction A: thread n2 -> v[n1] = x[n2 + L2 n1]
   template <int SIGN>

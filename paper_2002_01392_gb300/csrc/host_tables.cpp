@@ -232,44 +232,6 @@ struct Roots {
   }
 };
 
-void deriv_conv_spectrum(int Nz, int Np, int L, std::vector<std::complex<double>>* H) {
-  Roots rn(Np), rl(L);
-  const q twopi = 2 * q_pi();
-  // derivative kernels on the Np-periodic unit grid:
-  // d_o(j) = (1/Np) sum_l fac_o(l) e^{2 pi i l j / Np}
-  // fac_1 = i k (Nyquist zeroed), fac_2 = -k^2, k = 2 pi l_s / Np.
-  const int jlo = -(Np - 1), jhi = Nz - 1;
-  std::vector<q> d1(jhi - jlo + 1), d2(jhi - jlo + 1);
-  for (int j = jlo; j <= jhi; ++j) {
-    q s1 = 0, s2 = 0;
-    for (int l = 0; l < Np; ++l) {
-      int ls = (l <= (Np - 1) / 2) ? l : l - Np;  // signed index, Nyquist -> -Np/2
-      q k = twopi * (q)ls / (q)Np;
-      long long m = ((long long)l * j) % Np;
-      if (m < 0) m += Np;
-      // i k e^{i th} = i k (c + i s) -> real part -k s
-      bool nyq = (Np % 2 == 0) && (l == Np / 2);
-      if (!nyq) s1 += -k * rn.s[m];
-      s2 += -k * k * rn.c[m];
-    }
-    d1[j - jlo] = s1 / (q)Np;
-    d2[j - jlo] = s2 / (q)Np;
-  }
-  H->assign(L, std::complex<double>(0, 0));
-  for (int kk = 0; kk < L; ++kk) {
-    q re = 0, im = 0;
-    for (int j = jlo; j <= jhi; ++j) {
-      long long mm = (((long long)j % L) + L) % L;
-      long long e = (mm * kk) % L;  // e^{-2 pi i mm kk / L}
-      q c = rl.c[e], s = -rl.s[e];
-      q hr = d1[j - jlo], hi = d2[j - jlo];
-      re += hr * c - hi * s;
-      im += hr * s + hi * c;
-    }
-    (*H)[kk] = std::complex<double>((double)(re / (q)L), (double)(im / (q)L));
-  }
-}
-
 // spectrum of a real kernel h(j), j in [-(Np-1), Nz-1], placed circularly on L
 static void kernel_spectrum(const std::vector<q>& h, int jlo, int L, std::vector<std::complex<double>>* H) {
   Roots rl(L);
@@ -289,6 +251,21 @@ static void kernel_spectrum(const std::vector<q>& h, int jlo, int L, std::vector
 
 void deriv_conv_spectra(int Nz, int Np, int L, std::vector<std::complex<double>>* H1,
                         std::vector<std::complex<double>>* H2) {
+  if (L == Np) {
+    // circular convolution of length N' itself: the spectra are the derivative
+    // multipliers i k (Nyquist zeroed) and -k^2 of the N'-periodic unit grid, / N'
+    H1->assign(L, 0);
+    H2->assign(L, 0);
+    const q twopi = 2 * q_pi();
+    for (int l = 0; l < Np; ++l) {
+      const int ls = (l <= (Np - 1) / 2) ? l : l - Np;
+      const q k = twopi * (q)ls / (q)Np;
+      const bool nyq = (Np % 2 == 0) && (l == Np / 2);
+      (*H1)[l] = std::complex<double>(0.0, nyq ? 0.0 : (double)(k / (q)Np));
+      (*H2)[l] = std::complex<double>((double)(-k * k / (q)Np), 0.0);
+    }
+    return;
+  }
   Roots rn(Np);
   const q twopi = 2 * q_pi();
   const int jlo = -(Np - 1), jhi = Nz - 1;

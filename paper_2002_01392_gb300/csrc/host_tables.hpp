@@ -16,15 +16,9 @@ struct FcTables {
 // M_r = A_r Q_r^T.  Returns false on invalid sizes.
 bool build_fc_tables(int d, int C, int M, int n_os, FcTables* out);
 
-// Spectrum (length L, natural frequency order, including the 1/L of the
-// inverse transform) of the length-L circular kernel whose convolution with
-// [f; continuation; 0...] returns, at n < Nz, d1 + i d2 where d1, d2 are the
-// first and second derivatives on the N'-periodic grid with unit spacing.
-// Requires L >= N' + Nz - 1.
-void deriv_conv_spectrum(int Nz, int Np, int L, std::vector<std::complex<double>>* H);
-
 // Spectra (length L, with 1/L) of the circular kernels of d/dz and d2/dz2 on
-// the N'-periodic unit grid, for complex input (first Nz outputs valid).
+// the N'-periodic unit grid (first Nz outputs valid).  L >= N' + Nz - 1
+// (padded circular convolution) or L = N' (the multipliers i k, -k^2 / N').
 void deriv_conv_spectra(int Nz, int Np, int L, std::vector<std::complex<double>>* H1,
                         std::vector<std::complex<double>>* H2);
 

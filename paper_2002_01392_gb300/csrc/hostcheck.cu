@@ -14,26 +14,27 @@ namespace fcns {
 template <class T, int L1, int L2, int LINES>
 static int emu_deriv(const double* Mr, int d, int Cc, int Nz, int batch, long long lines, double Lz,
                      const T* f, T* df, T* d2f) {
-  using K = DerivConv<T, L1, L2, LINES>;
+  using K = DerivPair<T, L1, L2, LINES>;
   const int L = L1 * L2;
-  std::vector<std::complex<double>> H, tw;
-  deriv_conv_spectrum(Nz, Nz + Cc, L, &H);
+  std::vector<std::complex<double>> H1, H2, tw;
+  deriv_conv_spectra(Nz, Nz + Cc, L, &H1, &H2);
   engine_twiddles(L1, L2, &tw);
-  std::vector<cx<T>> Ht(L), twt(L);
+  std::vector<cx<T>> H1t(L), H2t(L), twt(L);
   for (int i = 0; i < L; ++i) {
-    Ht[i] = mk<T>((T)H[i].real(), (T)H[i].imag());
+    H1t[i] = mk<T>((T)H1[i].real(), (T)H1[i].imag());
+    H2t[i] = mk<T>((T)H2[i].real(), (T)H2[i].imag());
     twt[i] = mk<T>((T)tw[i].real(), (T)tw[i].imag());
   }
   typename K::Args a;
   a.f = f; a.df = df; a.d2f = d2f;
   a.Nz = Nz; a.Np = Nz + Cc; a.d = d; a.Cc = Cc;
-  a.lines = lines; a.tiles = (lines + LINES - 1) / LINES;
+  a.lines = lines; a.pairs = (lines + 1) / 2; a.tiles = (a.pairs + LINES - 1) / LINES;
   a.zstride = lines; a.bstride = lines * Nz;
   const double dz = Lz / (Nz - 1);
   a.s1 = T(1.0 / dz); a.s2 = T(1.0 / (dz * dz));
   std::vector<float2> Mr2(Cc * d);
   for (int i = 0; i < Cc * d; ++i) { Mr2[i].x = (float)Mr[i]; Mr2[i].y = (float)(Mr[i] - (double)Mr2[i].x); }
-  a.Mr = Mr; a.Mr2 = Mr2.data(); a.H = Ht.data(); a.tw = twt.data();
+  a.Mr = Mr; a.Mr2 = Mr2.data(); a.H1 = H1t.data(); a.H2 = H2t.data(); a.tw = twt.data();
   phased_emulate<K>(a, a.tiles * batch, K::smem_bytes);
   return 0;
 }
@@ -53,10 +54,11 @@ extern "C" int fchc_deriv_z(int dtype, int L, const double* Mr, int d, int Cc, i
       return emu_deriv<float, A, B, LF>(Mr, d, Cc, Nz, batch, lines, Lz, (const float*)f, (float*)df, (float*)d2f); \
     return emu_deriv<double, A, B, LD>(Mr, d, Cc, Nz, batch, lines, Lz, (const double*)f, (double*)df, (double*)d2f); \
   }
-  HC(96, 8, 12, 32, 16)
-  HC(160, 10, 16, 32, 16)
-  HC(288, 16, 18, 32, 16)
-  HC(1080, 30, 36, 8, 8)
+  HC(64, 8, 8, 16, 8)
+  HC(96, 8, 12, 16, 8)
+  HC(160, 10, 16, 16, 8)
+  HC(288, 16, 18, 16, 8)
+  HC(1080, 30, 36, 4, 2)
 #undef HC
   return -1;
 }
@@ -85,6 +87,10 @@ struct EmuBK {
   fc_status h2d(void* d, const void* s, size_t b) { std::memcpy(d, s, b); return FC_OK; }
   fc_status d2d(void* d, const void* s, size_t b, void*) { std::memmove(d, s, b); return FC_OK; }
   fc_status memset(void* d, int v, size_t b, void*) { std::memset(d, v, b); return FC_OK; }
+  fc_status d2d_2d(void* dst, size_t dp, const void* src, size_t sp, size_t w, size_t rows, void*) {
+    for (size_t r = 0; r < rows; ++r) std::memmove((char*)dst + r * dp, (const char*)src + r * sp, w);
+    return FC_OK;
+  }
   fc_status sync(void*) { return FC_OK; }
 };
 }  // namespace fcns

@@ -25,10 +25,12 @@ struct DerivDevTables {
   int L = 0;
   double* Mr = nullptr;
   float2* Mr2 = nullptr;  // (hi, lo) float split of Mr
-  void* H32 = nullptr;   // float2[L]
-  void* H64 = nullptr;   // double2[L]
   void* tw32 = nullptr;  // float2[L]
   void* tw64 = nullptr;  // double2[L]
+  void* H1_32 = nullptr; // spectra of d1 and d2 separately (paired-line kernel)
+  void* H1_64 = nullptr;
+  void* H2_32 = nullptr;
+  void* H2_64 = nullptr;
 };
 
 struct PlanData {
@@ -44,9 +46,9 @@ fc_status deriv_tables_for_device(PlanData* p, DerivDevTables** out);
 // host copies of the derivative tables of one plan, in both precisions
 struct PlanHostTables {
   int L = 0, L1 = 0, L2 = 0;
-  std::vector<std::complex<double>> H, tw;
-  std::vector<float2> H32, tw32, Mr2;
-  std::vector<double2> H64, tw64;
+  std::vector<std::complex<double>> tw;
+  std::vector<float2> tw32, Mr2, H1_32, H2_32;
+  std::vector<double2> tw64, H1_64, H2_64;
 };
 
 // argument checks shared by the fc_deriv_z entry points

@@ -9,7 +9,7 @@ namespace {
 template <class T, int L1, int L2, int LINES>
 fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long long lines, double Lz,
                     const void* f, void* df, void* d2f, cudaStream_t stream) {
-  using K = DerivConv<T, L1, L2, LINES>;
+  using K = DerivPair<T, L1, L2, LINES>;
   static_assert(K::smem_bytes <= 227 * 1024, "shared memory budget");
   typename K::Args a;
   a.f = static_cast<const T*>(f);
@@ -17,7 +17,8 @@ fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long 
   a.d2f = static_cast<T*>(d2f);
   a.Nz = p.Nz; a.Np = p.Np; a.d = p.d; a.Cc = p.C;
   a.lines = lines;
-  a.tiles = (lines + LINES - 1) / LINES;
+  a.pairs = (lines + 1) / 2;
+  a.tiles = (a.pairs + LINES - 1) / LINES;
   a.zstride = lines;
   a.bstride = lines * p.Nz;
   const double dz = Lz / (p.Nz - 1);
@@ -25,7 +26,8 @@ fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long 
   a.s2 = T(1.0 / (dz * dz));
   a.Mr = t.Mr;
   a.Mr2 = t.Mr2;
-  a.H = static_cast<const cx<T>*>(sizeof(T) == 4 ? t.H32 : t.H64);
+  a.H1 = static_cast<const cx<T>*>(sizeof(T) == 4 ? t.H1_32 : t.H1_64);
+  a.H2 = static_cast<const cx<T>*>(sizeof(T) == 4 ? t.H2_32 : t.H2_64);
   a.tw = static_cast<const cx<T>*>(sizeof(T) == 4 ? t.tw32 : t.tw64);
   auto kern = phased_kernel<K>;
   static bool attr_done = false;  // per instantiation; the attribute is per device but idempotent
@@ -42,7 +44,9 @@ fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long 
 
 const std::vector<EngineShape>& engine_shapes() {
   static const std::vector<EngineShape> s = {
-      {96, 8, 12}, {160, 10, 16}, {192, 12, 16}, {288, 16, 18}, {320, 16, 20}, {576, 24, 24}, {1080, 30, 36}};
+      {64, 8, 8},     {96, 8, 12},    {128, 8, 16},   {160, 10, 16},  {192, 12, 16}, {256, 16, 16},
+      {288, 16, 18},  {320, 16, 20},  {512, 16, 32},  {576, 24, 24},  {768, 24, 32}, {1024, 32, 32},
+      {1080, 30, 36}};
   return s;
 }
 
@@ -60,13 +64,19 @@ fc_status launch_deriv_z(const DerivDevTables& t, const PlanData& p, fc_dtype dt
     return dtype == FC_F32 ? run_deriv<float, A, B, LF>(t, p, batch, lines, Lz, f, df, d2f, stream) \
                            : run_deriv<double, A, B, LD>(t, p, batch, lines, Lz, f, df, d2f, stream);
   switch (t.L) {
-    FC_CASE(96, 8, 12, 32, 16)
-    FC_CASE(160, 10, 16, 32, 16)
-    FC_CASE(192, 12, 16, 32, 16)
-    FC_CASE(288, 16, 18, 32, 16)
-    FC_CASE(320, 16, 20, 32, 16)
-    FC_CASE(576, 24, 24, 16, 8)
-    FC_CASE(1080, 30, 36, 8, 8)
+    FC_CASE(64, 8, 8, 16, 8)
+    FC_CASE(96, 8, 12, 16, 8)
+    FC_CASE(128, 8, 16, 16, 8)
+    FC_CASE(160, 10, 16, 16, 8)
+    FC_CASE(192, 12, 16, 16, 8)
+    FC_CASE(256, 16, 16, 16, 8)
+    FC_CASE(288, 16, 18, 16, 8)
+    FC_CASE(320, 16, 20, 16, 8)
+    FC_CASE(512, 16, 32, 8, 4)
+    FC_CASE(576, 24, 24, 8, 4)
+    FC_CASE(768, 24, 32, 4, 2)
+    FC_CASE(1024, 32, 32, 4, 2)
+    FC_CASE(1080, 30, 36, 4, 2)
     default:
       return FC_ERR_UNSUPPORTED;
   }

@@ -57,8 +57,8 @@ extern "C" fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batc
   const PlanHostTables& h = plan->deriv;
   const size_t cs = dtype == FC_F32 ? sizeof(float2) : sizeof(double2);
   const size_t nMr = plan->data.Mr.size();
-  const size_t oMr = 0, oMr2 = align256(sizeof(double) * nMr), oH = oMr2 + align256(sizeof(float2) * nMr);
-  const size_t oTw = oH + align256(cs * h.L), need = oTw + align256(cs * h.L);
+  const size_t oMr = 0, oMr2 = align256(sizeof(double) * nMr), oH1 = oMr2 + align256(sizeof(float2) * nMr);
+  const size_t oH2 = oH1 + align256(cs * h.L), oTw = oH2 + align256(cs * h.L), need = oTw + align256(cs * h.L);
   if (need > kNoAllocBytes) {
     set_error("fc_deriv_z_noalloc: tables of this plan exceed the 64 KiB static scratch");
     return FC_ERR_UNSUPPORTED;
@@ -70,12 +70,14 @@ extern "C" fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batc
   s = scratch_address(dev, &base);
   if (s) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  const void* Hsrc = dtype == FC_F32 ? (const void*)h.H32.data() : (const void*)h.H64.data();
+  const void* H1src = dtype == FC_F32 ? (const void*)h.H1_32.data() : (const void*)h.H1_64.data();
+  const void* H2src = dtype == FC_F32 ? (const void*)h.H2_32.data() : (const void*)h.H2_64.data();
   const void* Tsrc = dtype == FC_F32 ? (const void*)h.tw32.data() : (const void*)h.tw64.data();
   // every table is overwritten in full, so nothing left by an earlier call is read
   s = cuda_status(cudaMemcpyAsync(base + oMr, plan->data.Mr.data(), sizeof(double) * nMr, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(Mr)");
   if (!s) s = cuda_status(cudaMemcpyAsync(base + oMr2, h.Mr2.data(), sizeof(float2) * nMr, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(Mr2)");
-  if (!s) s = cuda_status(cudaMemcpyAsync(base + oH, Hsrc, cs * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(H)");
+  if (!s) s = cuda_status(cudaMemcpyAsync(base + oH1, H1src, cs * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(H1)");
+  if (!s) s = cuda_status(cudaMemcpyAsync(base + oH2, H2src, cs * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(H2)");
   if (!s) s = cuda_status(cudaMemcpyAsync(base + oTw, Tsrc, cs * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(tw)");
   if (s) return s;
   DerivDevTables t;
@@ -83,7 +85,8 @@ extern "C" fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batc
   t.L = h.L;
   t.Mr = reinterpret_cast<double*>(base + oMr);
   t.Mr2 = reinterpret_cast<float2*>(base + oMr2);
-  t.H32 = t.H64 = base + oH;
+  t.H1_32 = t.H1_64 = base + oH1;
+  t.H2_32 = t.H2_64 = base + oH2;
   t.tw32 = t.tw64 = base + oTw;
   return launch_deriv_z(t, plan->data, dtype, batch, (long long)Nx * Ny, Lz, f, df, d2f, st);
 }

@@ -26,6 +26,10 @@ struct DeviceBK {
   fc_status d2d(void* dst, const void* src, size_t b, void* st) {
     return cuda_status(cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToDevice, (cudaStream_t)st), "cudaMemcpyAsync");
   }
+  fc_status d2d_2d(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t rows, void* st) {
+    return cuda_status(cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyDeviceToDevice,
+                                         (cudaStream_t)st), "cudaMemcpy2DAsync");
+  }
   fc_status memset(void* dst, int v, size_t b, void* st) {
     return cuda_status(cudaMemsetAsync(dst, v, b, (cudaStream_t)st), "cudaMemsetAsync");
   }
@@ -128,14 +132,14 @@ fc_status ns_get_wall_gradp(ns_sim_t s, void* gradp, fc_stream_t stream) {
   fc_status st = check_sim(s, "ns_get_wall_gradp");
   if (st) return st;
   if (!gradp) return FC_ERR_ARG;
-  return s->core.bk.d2d(gradp, s->core.ws + s->core.l.gradp, sizeof(double) * 8 * s->core.l.lines, stream);
+  return s->core.gradp_out(gradp, stream);
 }
 
 fc_status ns_put_wall_gradp(ns_sim_t s, const void* gradp, fc_stream_t stream) {
   fc_status st = check_sim(s, "ns_put_wall_gradp");
   if (st) return st;
   if (!gradp) return FC_ERR_ARG;
-  return s->core.bk.d2d(s->core.ws + s->core.l.gradp, gradp, sizeof(double) * 8 * s->core.l.lines, stream);
+  return s->core.gradp_in(gradp, stream);
 }
 
 fc_status ns_rhs(ns_sim_t s, const void* phys_in, void* rhs_out, fc_stream_t stream) {

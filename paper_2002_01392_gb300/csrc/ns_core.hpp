@@ -17,7 +17,7 @@
 namespace fcns {
 
 struct NsLayout {
-  int Nx, Ny, Nz, Np, Kx, nf, L, L1, L2, Lx1, Lx2, Ly1, Ly2;
+  int Nx, Ny, Nz, Np, Kx, Kxp, nf, L, L1, L2, Lx1, Lx2, Ly1, Ly2;
   long long lines, ntiles, plines;   // lines, tiles of TL lines, padded lines
   size_t es;  // bytes per real
   // byte offsets inside the workspace
@@ -53,7 +53,8 @@ inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
     return FC_ERR_ARG;
   NsLayout& l = *o;
   l.Nx = p.Nx; l.Ny = p.Ny; l.Nz = p.Nz; l.Np = p.Nz + p.C; l.Kx = p.Nx / 2 + 1; l.nf = p.nfields;
-  l.lines = (long long)p.Ny * l.Kx;
+  l.Kxp = (l.Kx + TL - 1) / TL * TL;
+  l.lines = (long long)p.Ny * l.Kxp;
   l.ntiles = (l.lines + TL - 1) / TL;
   l.plines = l.ntiles * TL;
   l.es = p.prec == FC_F32 ? 4 : 8;
@@ -207,7 +208,7 @@ struct NsCore {
   }
   ZGeom zgeom(int nf) const {
     ZGeom g;
-    g.Nz = p.Nz; g.Np = l.Np; g.d = p.d; g.Cc = p.C; g.Kx = l.Kx; g.Ny = p.Ny; g.nf = nf;
+    g.Nz = p.Nz; g.Np = l.Np; g.d = p.d; g.Cc = p.C; g.Kx = l.Kx; g.Kxp = l.Kxp; g.Ny = p.Ny; g.nf = nf;
     g.lines = l.lines; g.ntiles = l.ntiles; g.Lz = p.Lz; g.dz = p.Lz / (p.Nz - 1);
     return g;
   }
@@ -280,7 +281,7 @@ struct NsCore {
 
   YGeom ygeom() const {
     YGeom g;
-    g.Ny = p.Ny; g.Kx = l.Kx; g.Nz = p.Nz; g.plane = l.lines; g.ntiles = l.ntiles;
+    g.Ny = p.Ny; g.Kx = l.Kx; g.Kxp = l.Kxp; g.Nz = p.Nz; g.plane = l.lines; g.ntiles = l.ntiles;
     return g;
   }
 
@@ -343,7 +344,7 @@ struct NsCore {
   fc_status x_pass_run(long long rows, void* st) {
     if (K::smem_bytes > 227 * 1024) return FC_ERR_UNSUPPORTED;
     typename K::Args a;
-    a.Kx = l.Kx; a.Ny = p.Ny; a.Nz = p.Nz; a.rows = rows; a.ntiles = l.ntiles;
+    a.Kx = l.Kx; a.Kxp = l.Kxp; a.Ny = p.Ny; a.Nz = p.Nz; a.rows = rows; a.ntiles = l.ntiles;
     a.tw = at<cx<T>>(l.twx); a.kxo = at<T>(l.tkxo);
     a.V = at<cx<T>>(l.V); a.DY = at<cx<T>>(l.DY); a.DZ = at<cx<T>>(l.DZ); a.NL = at<cx<T>>(l.NL);
     a.forcing = (T)p.forcing_x; a.gamma = (T)p.gamma; a.scale = (T)(1.0 / p.Nx);
@@ -358,7 +359,7 @@ struct NsCore {
   if (p.Nx == NN) {                                                           \
     using K = KXRow<T, A1, B1, SIGN, x_jobs<NN>()>;                           \
     typename K::Args a;                                                       \
-    a.Kx = l.Kx; a.Ny = p.Ny; a.Nz = p.Nz; a.ntiles = l.ntiles;              \
+    a.Kx = l.Kx; a.Kxp = l.Kxp; a.Ny = p.Ny; a.Nz = p.Nz; a.ntiles = l.ntiles; \
     a.pairs = pairs; a.tw = at<cx<T>>(l.twx); a.R = R; a.S = S;               \
     a.scale = (T)(SIGN > 0 ? 1.0 / p.Nx : 1.0);                               \
     s = bk.template run<K>(a, (pairs + x_jobs<NN>() - 1) / x_jobs<NN>(), st); \
@@ -426,7 +427,7 @@ struct NsCore {
     fc_status s = phys_to_state<T>(vin, Xs, 3, at<double2>(l.gradp), dtj, st);
     if (!s) s = z_project<T>(Xs, dtj, st);
     if (!s) s = state_to_phys<T>(Xs, vout, 3, st);
-    if (!s && gp_out) s = bk.d2d(gp_out, ws + l.gradp, sizeof(double) * 8 * l.lines, st);
+    if (!s && gp_out) s = gradp_out(gp_out, st);
     return s;
   }
 
@@ -465,6 +466,13 @@ struct NsCore {
   }
   fc_status step_any(double dt, void* st) { return f32() ? step<float>(dt, st) : step<double>(dt, st); }
   size_t state_bytes() const { return 2 * l.es * l.nf * l.Np * l.plines; }
+  // wall planes: internal [2][2][Ny][Kxp] <-> public [2][2][Ny][Kx] (complex double)
+  fc_status gradp_out(void* dst, void* st) {
+    return bk.d2d_2d(dst, 16 * (size_t)l.Kx, ws + l.gradp, 16 * (size_t)l.Kxp, 16 * (size_t)l.Kx, 4 * (size_t)p.Ny, st);
+  }
+  fc_status gradp_in(const void* src, void* st) {
+    return bk.d2d_2d(ws + l.gradp, 16 * (size_t)l.Kxp, src, 16 * (size_t)l.Kx, 16 * (size_t)l.Kx, 4 * (size_t)p.Ny, st);
+  }
 };
 
 }  // namespace fcns

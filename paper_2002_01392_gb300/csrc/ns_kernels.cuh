@@ -46,9 +46,9 @@ struct ZTab {
 };
 
 struct ZGeom {
-  int Nz, Np, d, Cc, Kx, Ny, nf;
-  long long lines;
-  long long ntiles;   // ceil(lines / TL)
+  int Nz, Np, d, Cc, Kx, Kxp, Ny, nf;   // Kxp: kx row length padded to a multiple of TL
+  long long lines;    // Ny * Kxp (line = ky * Kxp + kx; kx >= Kx are padding)
+  long long ntiles;   // lines / TL
   double Lz, dz;
 };
 
@@ -145,7 +145,7 @@ struct KZDeriv {
     const int r = tid / LINES, li = tid % LINES;
     const long long f = bid / a.tiles;
     const long long line = (bid % a.tiles) * LINES + li;
-    const bool valid = line < a.g.lines;
+    const bool valid = line < a.g.lines && (line % a.g.Kxp) < a.g.Kx;
     if constexpr (P == 0) {
       if (r < L2) {
         const C* x = a.X + lay(f, 0, line, a.g.Np, a.g.ntiles);
@@ -160,13 +160,13 @@ struct KZDeriv {
       if (r < L1) {
         E::template B<-1>(R.u, b0, r, li);
 #pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) {
-          b1[E::bidx(r, k2, li)] = R.u[k2];
-          R.u[k2] = cmul(R.u[k2], a.t.H1[r + L1 * k2]);
-        }
+        for (int k2 = 0; k2 < L2; ++k2) b1[E::bidx(r, k2, li)] = R.u[k2];
+        E::mulH(R.u, a.t.H1, r);
         E::template Bi<1>(R.u, b0, a.t.tw, r, li);
+        FC_FENCE();
 #pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(b1[E::bidx(r, k2, li)], a.t.H2[r + L1 * k2]);
+        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = b1[E::bidx(r, k2, li)];
+        E::mulH(R.u, a.t.H2, r);
         E::template Bi<1>(R.u, b1, a.t.tw, r, li);
       }
     } else if constexpr (P == 2) {
@@ -237,7 +237,7 @@ struct KZCombine {
     const int r = tid / LINES, li = tid % LINES;
     const int f = (int)(bid / a.tiles);
     const long long line = (bid % a.tiles) * LINES + li;
-    const bool valid = line < a.g.lines;
+    const bool valid = line < a.g.lines && (line % a.g.Kxp) < a.g.Kx;
     const int Nz = a.g.Nz, Np = a.g.Np, d = a.g.d;
     const long long Ls = a.g.lines;
     if constexpr (P == 0) {
@@ -266,14 +266,13 @@ struct KZCombine {
     } else if constexpr (P == 2) {
       if (r < L1) {
         E::template B<-1>(R.u, b0, r, li);
-#pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(R.u[k2], a.t.Hf[r + L1 * k2]);
+        E::mulH(R.u, a.t.Hf, r);
         E::template Bi<1>(R.u, b0, a.t.tw, r, li);
       }
     } else if constexpr (P == 3) {
       if (r < L2) {
         E::template Ai<1>(R.v, b0, r, li);
-        const int kx = (int)(line % a.g.Kx), ky = (int)(line / a.g.Kx);
+        const int kx = (int)(line % a.g.Kxp), ky = (int)(line / a.g.Kxp);
         const T fxy = valid ? a.t.fx[kx] * a.t.fy[ky] : T(0);
         const T ckp2 = valid ? a.t.kx[kx] * a.t.kx[kx] + a.t.ky[ky] * a.t.ky[ky] : T(0);
         const T cdt = (T)a.dtj, cnu = (T)(a.dif[f]);
@@ -356,7 +355,7 @@ struct KZContinue {
     C* Ev = reinterpret_cast<C*>(sm + off_E) + li * 2 * DMAX;
     const int f = (int)(bid / a.tiles);
     const long long line = (bid % a.tiles) * LINES + li;
-    const bool valid = line < a.g.lines;
+    const bool valid = line < a.g.lines && (line % a.g.Kxp) < a.g.Kx;
     const int Nz = a.g.Nz, Np = a.g.Np, d = a.g.d;
     const long long Ls = a.g.lines;
     const C* m = a.M + lay(f, 0, line, Nz, a.g.ntiles);
@@ -437,8 +436,7 @@ struct KZProject {
   static FC_HD void conv(const Args& a, C* b0, const C* H, int r, int li, Regs& R) {
     if (r < L1) {
       E::template B<-1>(R.u, b0, r, li);
-#pragma unroll
-      for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = cmul(R.u[k2], H[r + L1 * k2]);
+      E::mulH(R.u, H, r);
       E::template Bi<1>(R.u, b0, a.t.tw, r, li);
     }
   }
@@ -452,10 +450,10 @@ struct KZProject {
     double* W = reinterpret_cast<double*>(sm + off_W) + li * 16;
     C* Ev = reinterpret_cast<C*>(sm + off_E) + li * 4 * DMAX;   // Phi first, Phi last, Phi' first, Phi' last
     const long long line = bid * LINES + li;
-    const bool valid = line < a.g.lines;
+    const bool valid = line < a.g.lines && (line % a.g.Kxp) < a.g.Kx;
     const int Nz = a.g.Nz, Np = a.g.Np, d = a.g.d;
     const long long Ls = a.g.lines;
-    const int kxi = valid ? (int)(line % a.g.Kx) : 0, kyi = valid ? (int)(line / a.g.Kx) : 0;
+    const int kxi = valid ? (int)(line % a.g.Kxp) : 0, kyi = valid ? (int)(line / a.g.Kxp) : 0;
     const T kxo = a.t.kxo[kxi], kyo = a.t.kyo[kyi];
     C* xu = a.X + lay(0, 0, line, Np, a.g.ntiles);
     C* xv = a.X + lay(1, 0, line, Np, a.g.ntiles);
@@ -658,8 +656,8 @@ struct KZProject {
 // 0..Nz-1 of every field.
 // ===========================================================================
 struct YGeom {
-  int Ny, Kx, Nz;
-  long long plane;          // Ny * Kx (lines)
+  int Ny, Kx, Kxp, Nz;
+  long long plane;          // Ny * Kxp (lines)
   long long ntiles;
 };
 
@@ -692,8 +690,11 @@ struct KYInv3 {
     const long long f = pz / a.g.Nz, z = pz % a.g.Nz;
     const int kx = (int)(tile * LINES + li);
     const bool valid = kx < a.g.Kx;
-    auto src = [&](int ky) { return a.A[lay(f, z, (long long)ky * a.g.Kx + kx, a.a_fstride, a.g.ntiles)]; };
-    auto mo = [&](int y) { return lay(f, z, (long long)y * a.g.Kx + kx, a.g.Nz, a.g.ntiles); };
+    // line = ky * Kxp + kx with Kxp a multiple of TL: element offset base + ky * Kxp * Z
+    const int sb = lay(f, z, kx, a.a_fstride, a.g.ntiles), ss = a.g.Kxp * (int)a.a_fstride;
+    const int mb = lay(f, z, kx, a.g.Nz, a.g.ntiles), ms = a.g.Kxp * a.g.Nz;
+    auto src = [&](int ky) { return a.A[sb + ky * ss]; };
+    auto mo = [&](int y) { return mb + y * ms; };
     if constexpr (P == 0) {
       if (r < L2) {
 #pragma unroll
@@ -769,18 +770,18 @@ struct KY1 {
     const bool valid = kx < a.g.Kx;
     if constexpr (P == 0) {
       if (r < L2) {
+        const int ib = lay(f, z, kx, a.in_fstride, a.g.ntiles), is = a.g.Kxp * (int)a.in_fstride;
 #pragma unroll
-        for (int j = 0; j < L1; ++j)
-          R.v[j] = valid ? a.IN[lay(f, z, (long long)(r + L2 * j) * a.g.Kx + kx, a.in_fstride, a.g.ntiles)] : mk<T>(0, 0);
+        for (int j = 0; j < L1; ++j) R.v[j] = valid ? a.IN[ib + (r + L2 * j) * is] : mk<T>(0, 0);
         E::template A<SIGN>(R.v, b0, a.tw, r, li);
       }
     } else {
       if (r < L1) {
         E::template B<SIGN>(R.u, b0, r, li);
+        const int ob = lay(f, z, kx, a.out_fstride, a.g.ntiles), os = a.g.Kxp * (int)a.out_fstride;
         if (valid)
 #pragma unroll
-          for (int k2 = 0; k2 < L2; ++k2)
-            a.OUT[lay(f, z, (long long)(r + L1 * k2) * a.g.Kx + kx, a.out_fstride, a.g.ntiles)] = cscale(R.u[k2], a.scale);
+          for (int k2 = 0; k2 < L2; ++k2) a.OUT[ob + (r + L1 * k2) * os] = cscale(R.u[k2], a.scale);
       }
     }
   }
@@ -829,7 +830,7 @@ struct KXPass {
   static constexpr int Nx = L1 * L2, G = RE::G, NJOB = 2 * NF, NFWD = (NF + 1) / 2;
   static constexpr int THREADS = NJOB * G, NPHASE = 8, MINB = 2;
   struct Args {
-    int Kx, Ny, Nz;
+    int Kx, Kxp, Ny, Nz;
     long long rows;          // Nz * Ny
     long long ntiles;
     const C* tw;             // Nx engine twiddles
@@ -854,7 +855,7 @@ struct KXPass {
       if (g < L2) {
         const int f = q / 2, type = q % 2;
         const C* A = (type == 0 ? a.V : a.DY);
-        const long long z = row / a.Ny, yb = (row % a.Ny) * Kx;
+        const long long z = row / a.Ny, yb = (row % a.Ny) * a.Kxp;
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int k = g + L2 * j;
@@ -927,7 +928,7 @@ struct KXPass {
         // A = (Z_k + conj Z_{N-k}) / 2,  B = (Z_k - conj Z_{N-k}) / (2i)
         const C Av = mk<T>((zk.x + zm.x) * T(0.5), (zk.y - zm.y) * T(0.5));
         const C Bv = mk<T>((zk.y + zm.y) * T(0.5), (zm.x - zk.x) * T(0.5));
-        const long long z = row / a.Ny, yb = (row % a.Ny) * Kx;
+        const long long z = row / a.Ny, yb = (row % a.Ny) * a.Kxp;
         a.NL[lay(2 * qq, z, yb + k, a.Nz, a.ntiles)] = Av;
         if (2 * qq + 1 < NF) a.NL[lay(2 * qq + 1, z, yb + k, a.Nz, a.ntiles)] = Bv;
       }
@@ -944,7 +945,7 @@ struct KXRow {
   static constexpr int Nx = L1 * L2, G = RE::G;
   static constexpr int THREADS = JOBS * G, NPHASE = 3, MINB = 1;
   struct Args {
-    int Kx, Ny, Nz;
+    int Kx, Kxp, Ny, Nz;
     long long pairs;        // number of row pairs (rows / 2)
     long long ntiles;
     const C* tw;
@@ -957,7 +958,7 @@ struct KXRow {
   // element k of row R (rows ordered [f][z][y]) in the tiled layout
   static FC_HD long long sidx(const Args& a, long long R, long long k) {
     const long long y = R % a.Ny, fz = R / a.Ny;
-    return lay(fz / a.Nz, fz % a.Nz, y * a.Kx + k, a.Nz, a.ntiles);
+    return lay(fz / a.Nz, fz % a.Nz, y * a.Kxp + k, a.Nz, a.ntiles);
   }
   template <int P>
   static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& Rg) {
