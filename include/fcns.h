@@ -128,7 +128,7 @@ fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, 
  * counterpart; this is a deployment variant of fc_deriv_z.
  *   - Calls no cudaMalloc, cudaFree or other allocating routine.  The plan's
  *     tables (continuation matrix, kernel spectrum, twiddles) are copied on
- *     the caller's stream into one fixed 64 KiB static device array that
+ *     the caller's stream into one fixed 96 KiB static device array that
  *     every GPU loading the library reserves until the process exits.
  *   - The first call on each device looks up that array's device address
  *     (cudaGetSymbolAddress) with the device current; make that first call
@@ -136,9 +136,9 @@ fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, 
  *   - Every call shares the array and overwrites all of it that it reads;
  *     calls whose copies and kernels overlap on the GPU (other streams,
  *     other host threads) race on it and must be serialised by the caller.
- *   - A plan whose tables would not fit the 64 KiB array returns
- *     FC_ERR_UNSUPPORTED (the compiled transform lengths, N' + Nz - 1 <= 1080,
- *     need at most 45 KiB); arguments are checked as in fc_deriv_z.
+ *   - A plan whose tables would not fit the 96 KiB array returns
+ *     FC_ERR_UNSUPPORTED (the compiled transform lengths, up to 1080, need
+ *     at most 78 KiB); arguments are checked as in fc_deriv_z.
  */
 fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
                              const void* f, void* df, void* d2f, fc_stream_t stream);

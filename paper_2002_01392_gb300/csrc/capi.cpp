@@ -75,8 +75,8 @@ fc_status fc_setup_ex(int d, int C, int Nz, int M, int n_os, fc_plan_t* out) {
       t.H1_64[i] = make_double2(H1[i].real(), H1[i].imag());
       t.H2_64[i] = make_double2(H2[i].real(), H2[i].imag());
     }
-    t.tw32.resize(L); t.tw64.resize(L);
-    for (int i = 0; i < L; ++i) {
+    t.tw32.resize(2 * L); t.tw64.resize(2 * L);
+    for (int i = 0; i < 2 * L; ++i) {
       t.tw32[i] = make_float2((float)t.tw[i].real(), (float)t.tw[i].imag());
       t.tw64[i] = make_double2(t.tw[i].real(), t.tw[i].imag());
     }

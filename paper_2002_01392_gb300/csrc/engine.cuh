@@ -19,6 +19,15 @@
 
 namespace fcns {
 
+// Prefetch the 128-byte line holding p into L2 (no-op on the host).
+FC_HD void prefetch_l2(const void* p) {
+#if defined(__CUDA_ARCH__)
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+#else
+  (void)p;
+#endif
+}
+
 template <class T, int L1_, int L2_, int LINES_>
 struct Eng {
   static constexpr int L1 = L1_, L2 = L2_, L = L1 * L2, LINES = LINES_;
@@ -31,10 +40,17 @@ struct Eng {
 
   static FC_HD int bidx(int k1, int n2, int li) { return k1 * ROW + n2 * LINES + li; }
 
-  // twiddle e^{SIGN 2 pi i n2 k1 / L}; tw holds the SIGN = -1 values
+  // twiddle e^{SIGN 2 pi i n2 k1 / L}; tw holds the SIGN = -1 values twice:
+  // [n2 * L1 + k1] for the k1 threads and [L + k1 * L2 + n2] for the n2 threads
   template <int SIGN>
   static FC_HD C twid(const C* tw, int n2, int k1) {
     C w = tw[n2 * L1 + k1];
+    if (SIGN > 0) w.y = -w.y;
+    return w;
+  }
+  template <int SIGN>
+  static FC_HD C twidA(const C* tw, int n2, int k1) {
+    C w = tw[L + k1 * L2 + n2];
     if (SIGN > 0) w.y = -w.y;
     return w;
   }
@@ -46,7 +62,7 @@ struct Eng {
 #pragma unroll
     for (int k1 = 0; k1 < L1; ++k1) {
       if (k1 % 6 == 0) FC_FENCE();
-      buf[bidx(k1, n2, li)] = cmul(v[k1], twid<SIGN>(tw, n2, k1));
+      buf[bidx(k1, n2, li)] = cmul(v[k1], twidA<SIGN>(tw, n2, k1));
     }
   }
   // B: thread k1 -> u[k2] = X[k1 + L1 k2]

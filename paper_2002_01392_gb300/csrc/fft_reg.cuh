@@ -20,6 +20,14 @@ template <class T> using cx = typename V2<T>::t;
 template <class T> __host__ __device__ __forceinline__ cx<T> mk(T a, T b) { cx<T> r; r.x = a; r.y = b; return r; }
 template <class C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
 template <class C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+// float complex add / subtract / real scaling as one packed 2 x fp32 instruction
+// (sm_100 family), rounded to nearest like the scalar forms
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+#endif
 template <class C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
   C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
 }
@@ -27,6 +35,11 @@ template <class C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {  // a
   C r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
 }
 template <class C, class S> __host__ __device__ __forceinline__ C cscale(C a, S s) { a.x *= s; a.y *= s; return a; }
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+template <> __device__ __forceinline__ float2 cscale<float2, float>(float2 a, float s) {
+  return __fmul2_rn(a, make_float2(s, s));
+}
+#endif
 // multiply by sign * i
 template <int SIGN, class C> __host__ __device__ __forceinline__ C mul_si(C a) {
   C r;

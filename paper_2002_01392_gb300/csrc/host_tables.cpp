@@ -349,12 +349,14 @@ void bluestein_tables(int Np, int L, std::vector<std::complex<double>>* chirp,
 
 void engine_twiddles(int L1, int L2, std::vector<std::complex<double>>* tw) {
   const int L = L1 * L2;
-  tw->resize(L);
+  tw->resize(2 * L);
   for (int n2 = 0; n2 < L2; ++n2)
     for (int k1 = 0; k1 < L1; ++k1) {
       q c, s;
       q_sincos2pi((long long)n2 * k1, L, &c, &s);
-      (*tw)[n2 * L1 + k1] = std::complex<double>((double)c, (double)-s);
+      const std::complex<double> w((double)c, (double)-s);
+      (*tw)[n2 * L1 + k1] = w;          // read by the k1-threads (B side)
+      (*tw)[L + k1 * L2 + n2] = w;      // read by the n2-threads (A side)
     }
 }
 

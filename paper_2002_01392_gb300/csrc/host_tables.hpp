@@ -34,7 +34,8 @@ void filter_conv_spectrum(int Nz, int Np, int L, double beta, double two_p,
 void bluestein_tables(int Np, int L, std::vector<std::complex<double>>* chirp,
                       std::vector<std::complex<double>>* Hfwd, std::vector<std::complex<double>>* Hinv);
 
-// Twiddles tw[n2 * L1 + k1] = exp(-2 pi i n2 k1 / L), L = L1 L2.
+// Twiddles exp(-2 pi i n2 k1 / L), L = L1 L2, stored twice: tw[n2 * L1 + k1]
+// and tw[L + k1 * L2 + n2], so that both thread roles read them contiguously.
 void engine_twiddles(int L1, int L2, std::vector<std::complex<double>>* tw);
 
 // cos / sin of 2 pi num / den, correctly rounded to double from binary128.

@@ -19,12 +19,12 @@ static int emu_deriv(const double* Mr, int d, int Cc, int Nz, int batch, long lo
   std::vector<std::complex<double>> H1, H2, tw;
   deriv_conv_spectra(Nz, Nz + Cc, L, &H1, &H2);
   engine_twiddles(L1, L2, &tw);
-  std::vector<cx<T>> H1t(L), H2t(L), twt(L);
+  std::vector<cx<T>> H1t(L), H2t(L), twt(2 * L);
   for (int i = 0; i < L; ++i) {
     H1t[i] = mk<T>((T)H1[i].real(), (T)H1[i].imag());
     H2t[i] = mk<T>((T)H2[i].real(), (T)H2[i].imag());
-    twt[i] = mk<T>((T)tw[i].real(), (T)tw[i].imag());
   }
+  for (int i = 0; i < 2 * L; ++i) twt[i] = mk<T>((T)tw[i].real(), (T)tw[i].imag());
   typename K::Args a;
   a.f = f; a.df = df; a.d2f = d2f;
   a.Nz = Nz; a.Np = Nz + Cc; a.d = d; a.Cc = Cc;
@@ -35,6 +35,7 @@ static int emu_deriv(const double* Mr, int d, int Cc, int Nz, int batch, long lo
   std::vector<float2> Mr2(Cc * d);
   for (int i = 0; i < Cc * d; ++i) { Mr2[i].x = (float)Mr[i]; Mr2[i].y = (float)(Mr[i] - (double)Mr2[i].x); }
   a.Mr = Mr; a.Mr2 = Mr2.data(); a.H1 = H1t.data(); a.H2 = H2t.data(); a.tw = twt.data();
+  a.nblocks = a.tiles * batch; a.pf_dist = 3;
   phased_emulate<K>(a, a.tiles * batch, K::smem_bytes);
   return 0;
 }

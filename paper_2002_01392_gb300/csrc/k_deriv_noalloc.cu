@@ -8,7 +8,7 @@
 // or a fixed-size arena and that forbid allocations by plug-ins, and
 // latency-critical loops that cannot afford cudaMalloc's implicit device
 // synchronisation.  This entry point instead keeps those tables in one
-// file-scope static device array of fixed size (kNoAllocBytes, reserved by
+// file-scope static device array of fixed size (kNoAllocBytes = 96 KiB, reserved by
 // every GPU that loads the library until the process exits) and copies the
 // plan's tables into it on the caller's stream before every launch.
 #include <mutex>
@@ -18,7 +18,7 @@
 namespace fcns {
 namespace {
 
-constexpr size_t kNoAllocBytes = 64 * 1024;
+constexpr size_t kNoAllocBytes = 96 * 1024;
 constexpr int kMaxDevices = 64;
 
 // Shared by every call on a device; holds the tables of the last call.
@@ -58,9 +58,9 @@ extern "C" fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batc
   const size_t cs = dtype == FC_F32 ? sizeof(float2) : sizeof(double2);
   const size_t nMr = plan->data.Mr.size();
   const size_t oMr = 0, oMr2 = align256(sizeof(double) * nMr), oH1 = oMr2 + align256(sizeof(float2) * nMr);
-  const size_t oH2 = oH1 + align256(cs * h.L), oTw = oH2 + align256(cs * h.L), need = oTw + align256(cs * h.L);
+  const size_t oH2 = oH1 + align256(cs * h.L), oTw = oH2 + align256(cs * h.L), need = oTw + align256(cs * 2 * h.L);
   if (need > kNoAllocBytes) {
-    set_error("fc_deriv_z_noalloc: tables of this plan exceed the 64 KiB static scratch");
+    set_error("fc_deriv_z_noalloc: tables of this plan exceed the 96 KiB static scratch");
     return FC_ERR_UNSUPPORTED;
   }
   int dev = -1;
@@ -78,7 +78,7 @@ extern "C" fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batc
   if (!s) s = cuda_status(cudaMemcpyAsync(base + oMr2, h.Mr2.data(), sizeof(float2) * nMr, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(Mr2)");
   if (!s) s = cuda_status(cudaMemcpyAsync(base + oH1, H1src, cs * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(H1)");
   if (!s) s = cuda_status(cudaMemcpyAsync(base + oH2, H2src, cs * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(H2)");
-  if (!s) s = cuda_status(cudaMemcpyAsync(base + oTw, Tsrc, cs * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(tw)");
+  if (!s) s = cuda_status(cudaMemcpyAsync(base + oTw, Tsrc, cs * 2 * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(tw)");
   if (s) return s;
   DerivDevTables t;
   t.device = dev;

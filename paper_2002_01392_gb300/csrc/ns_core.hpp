@@ -77,9 +77,9 @@ inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
   l.tkxo = take(l.es * l.Kx); l.tkyo = take(l.es * p.Ny); l.tkzo = take(l.es * l.Np);
   l.tkx = take(l.es * l.Kx); l.tky = take(l.es * p.Ny); l.tfx = take(l.es * l.Kx); l.tfy = take(l.es * p.Ny);
   l.Mr = take(8 * p.C * p.d); l.Mr2 = take(8 * p.C * p.d);
-  l.twz = take(cs * l.L); l.H1 = take(cs * l.L); l.H2 = take(cs * l.L); l.Hf = take(cs * l.L);
+  l.twz = take(cs * 2 * l.L); l.H1 = take(cs * l.L); l.H2 = take(cs * l.L); l.Hf = take(cs * l.L);
   l.chirp = take(cs * l.Np); l.Hbf = take(cs * l.L); l.Hbi = take(cs * l.L);
-  l.twx = take(cs * p.Nx); l.twy = take(cs * p.Ny);
+  l.twx = take(cs * 2 * p.Nx); l.twy = take(cs * 2 * p.Ny);
   l.total = off;
   // every array is indexed with 32-bit element offsets
   if ((double)l.nf * l.Np * l.plines >= 2147483647.0) return FC_ERR_UNSUPPORTED;

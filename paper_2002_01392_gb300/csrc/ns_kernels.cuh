@@ -73,6 +73,7 @@ FC_HD int lay(long long f, long long z, long long line, long long Z, long long n
 constexpr int DMAX = 10;
 constexpr int MRMAX = 640;
 
+
 // C continuation value jj (point Nz + jj) of a complex line from its first /
 // last d values (Sec. 3 continuation formula; right matrix M_r, left matrix
 // its row/column reversal).  float32: compensated float-float products.
@@ -698,7 +699,10 @@ struct KYInv3 {
     if constexpr (P == 0) {
       if (r < L2) {
 #pragma unroll
-        for (int j = 0; j < L1; ++j) R.v[j] = valid ? src(r + L2 * j) : mk<T>(0, 0);
+        for (int j = 0; j < L1; ++j) {
+          R.v[j] = valid ? src(r + L2 * j) : mk<T>(0, 0);
+          b1[E::bidx(j, r, li)] = R.v[j];   // raw copy for the dy transform (own slots)
+        }
         E::template A<1>(R.v, b0, a.tw, r, li);
       }
     } else if constexpr (P == 1) {
@@ -712,7 +716,7 @@ struct KYInv3 {
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int ky = r + L2 * j;
-          const C x = valid ? src(ky) : mk<T>(0, 0);
+          const C x = b1[E::bidx(j, r, li)];
           const T k = a.kyo[ky];
           R.v[j] = mk<T>(-k * x.y, k * x.x);
         }
@@ -807,7 +811,12 @@ struct RowEng {
   static FC_HD void A(C (&v)[L1], C* buf, const C* tw, int n2) {
     dft_reg<L1, SIGN, T>(v);
 #pragma unroll
-    for (int k1 = 0; k1 < L1; ++k1) buf[k1 * ROW + n2] = cmul(v[k1], twid(tw, n2, k1, SIGN));
+    for (int k1 = 0; k1 < L1; ++k1) {
+      if (k1 % 6 == 0) FC_FENCE();
+      C w = tw[L + k1 * L2 + n2];   // A-side copy of the twiddles: contiguous across lanes
+      if (SIGN > 0) w.y = -w.y;
+      buf[k1 * ROW + n2] = cmul(v[k1], w);
+    }
   }
   template <int SIGN>
   static FC_HD void B(C (&u)[L2], const C* buf, int k1) {
