@@ -253,11 +253,14 @@ fc_status rk_step(ns_sim_t sim, double dt, fc_stream_t stream);
 /*
  * ns_diagnostics -- scalar diagnostics of the current state, synchronous
  * (host outputs; any pointer may be NULL):
- *   div_ms       mean square of div v over the physical grid (Sec. 6),
- *   wall_u_ms    mean square of u over both walls,  wall_w_ms: of w,
- *   flow_rate    volume mean of u,
+ *   div_ms       mean square of div v over the physical grid points, with the
+ *                FC z-derivative and spectral x, y derivatives (Sec. 6),
+ *   wall_u_ms    mean square of u over the points of both walls,
+ *   wall_w_ms    the same for w (zero to round-off after a projection),
+ *   flow_rate    mean of u over the physical grid points,
  *   nusselt      (Nu at z = 0 + Nu at z = Lz)/2 with Nu = 1 - <d_z theta>/gamma
  *                (Sec. 7; 0 for nfields = 3).
+ * Overwrites the simulation's work buffers (not its state).
  */
 fc_status ns_diagnostics(ns_sim_t sim, double* div_ms, double* wall_u_ms, double* wall_w_ms,
                          double* flow_rate, double* nusselt, fc_stream_t stream);

@@ -281,6 +281,12 @@ class Sim:
     def step(self, dt: float, stream=None):
         _check(_lib.rk_step(self.handle, float(dt), _stream(stream)), "rk_step")
 
+    def diagnostics(self, stream=None):
+        """ns_diagnostics: div_ms, wall_u_ms, wall_w_ms, flow_rate, nusselt (synchronous)."""
+        vals = [_c_double() for _ in range(5)]
+        _check(_lib.ns_diagnostics(self.handle, *[ctypes.byref(v) for v in vals], _stream(stream)), "ns_diagnostics")
+        return dict(zip(["div_ms", "wall_u_ms", "wall_w_ms", "flow_rate", "nusselt"], (v.value for v in vals)))
+
     def close(self):
         if getattr(self, "handle", None):
             _lib.ns_destroy(self.handle)

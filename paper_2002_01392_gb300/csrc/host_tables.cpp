@@ -312,6 +312,33 @@ void filter_conv_spectrum(int Nz, int Np, int L, double beta, double two_p,
   kernel_spectrum(h, jlo, L, Hf);
 }
 
+void z_kernels_real(int Nz, int Np, double beta, double two_p, std::vector<double>* d2, std::vector<double>* hf) {
+  Roots rn(Np);
+  const q twopi = 2 * q_pi();
+  const int jlo = -(Np - 1), jhi = Nz - 1;
+  std::vector<q> fz(Np);
+  for (int l = 0; l < Np; ++l) {
+    int ls = (l <= (Np - 1) / 2) ? l : l - Np;
+    if (Np % 2 == 0 && l == Np / 2) ls = -Np / 2;
+    fz[l] = (q)std::exp(-beta * std::pow(std::fabs((double)ls) / (Np / 2.0), two_p));
+  }
+  d2->assign(jhi - jlo + 1, 0.0);
+  hf->assign(jhi - jlo + 1, 0.0);
+  for (int j = jlo; j <= jhi; ++j) {
+    q s2 = 0, sf = 0;
+    for (int l = 0; l < Np; ++l) {
+      const int ls = (l <= (Np - 1) / 2) ? l : l - Np;
+      const q k = twopi * (q)ls / (q)Np;
+      long long m = ((long long)l * j) % Np;
+      if (m < 0) m += Np;
+      s2 += -k * k * rn.c[m];
+      sf += fz[l] * rn.c[m];
+    }
+    (*d2)[j - jlo] = (double)(s2 / (q)Np);
+    (*hf)[j - jlo] = (double)(sf / (q)Np);
+  }
+}
+
 void bluestein_tables(int Np, int L, std::vector<std::complex<double>>* chirp,
                       std::vector<std::complex<double>>* Hfwd, std::vector<std::complex<double>>* Hinv) {
   Roots rl(L);

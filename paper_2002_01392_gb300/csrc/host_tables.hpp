@@ -27,6 +27,11 @@ void deriv_conv_spectra(int Nz, int Np, int L, std::vector<std::complex<double>>
 void filter_conv_spectrum(int Nz, int Np, int L, double beta, double two_p,
                           std::vector<std::complex<double>>* Hf);
 
+// Real-space kernels on the N'-periodic unit grid, indexed by j + N' - 1 for
+// j in [-(N'-1), Nz-1]: d2 (second derivative) and hf (the z filter), so that
+// (K * x)[n] = sum_m K(n - m) x[m] for n < Nz, m < N'.
+void z_kernels_real(int Nz, int Np, double beta, double two_p, std::vector<double>* d2, std::vector<double>* hf);
+
 // Bluestein tables for a length-Np DFT done with length-L transforms:
 // chirp[n] = exp(-i pi n^2 / Np) (n < Np) and the spectrum (with 1/L) of the
 // circular kernel b[m mod L] = conj(chirp[|m|]), |m| < Np.  For the inverse

@@ -93,6 +93,7 @@ struct EmuBK {
     return FC_OK;
   }
   fc_status sync(void*) { return FC_OK; }
+  fc_status d2h(void* d, const void* s, size_t b, void*) { std::memcpy(d, s, b); return FC_OK; }
 };
 }  // namespace fcns
 
@@ -114,6 +115,7 @@ int fchc_ns_project(void* h, double dt, const void* in, void* out, void* gp) {
   return ((NsCore<EmuBK>*)h)->project_any(dt, in, out, gp, nullptr);
 }
 int fchc_ns_step(void* h, double dt) { return ((NsCore<EmuBK>*)h)->step_any(dt, nullptr); }
+int fchc_ns_diag_raw(void* h, double* acc6) { return ((NsCore<EmuBK>*)h)->diagnostics_any(acc6, nullptr); }
 int fchc_ns_get_state(void* h, void* out) {
   auto* c = (NsCore<EmuBK>*)h;
   std::memcpy(out, c->ws + c->l.X[c->cur], c->state_bytes());

@@ -11,4 +11,7 @@ namespace fcns {
 FC_ZSHAPES(FC_INST_Z)
 #undef FC_INST_Z
 template struct DevRun<KZContinue<double, 8>>;
+template struct DevRun<KDiag<double>>;
+template struct DevRun<KMeanLine<double>>;
+template struct DevRun<KMeanInit<double>>;
 }  // namespace fcns

@@ -11,4 +11,7 @@ namespace fcns {
 FC_ZSHAPES(FC_INST_Z)
 #undef FC_INST_Z
 template struct DevRun<KZContinue<float, 8>>;
+template struct DevRun<KDiag<float>>;
+template struct DevRun<KMeanLine<float>>;
+template struct DevRun<KMeanInit<float>>;
 }  // namespace fcns

@@ -34,6 +34,11 @@ struct DeviceBK {
     return cuda_status(cudaMemsetAsync(dst, v, b, (cudaStream_t)st), "cudaMemsetAsync");
   }
   fc_status sync(void*) { return cuda_status(cudaDeviceSynchronize(), "cudaDeviceSynchronize"); }
+  fc_status d2h(void* dst, const void* src, size_t b, void* st) {
+    fc_status s = cuda_status(cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, (cudaStream_t)st), "cudaMemcpyAsync(D2H)");
+    if (!s) s = cuda_status(cudaStreamSynchronize((cudaStream_t)st), "cudaStreamSynchronize");
+    return s;
+  }
 };
 
 }  // namespace fcns
@@ -125,7 +130,9 @@ fc_status ns_put_state(ns_sim_t s, const void* spec, fc_stream_t stream) {
   fc_status st = check_sim(s, "ns_put_state");
   if (st) return st;
   if (!spec) return FC_ERR_ARG;
-  return s->core.bk.d2d(s->core.ws + s->core.l.X[s->core.cur], spec, s->core.state_bytes(), stream);
+  st = s->core.bk.d2d(s->core.ws + s->core.l.X[s->core.cur], spec, s->core.state_bytes(), stream);
+  if (!st) st = s->core.mean_init_any(stream);
+  return st;
 }
 
 fc_status ns_get_wall_gradp(ns_sim_t s, void* gradp, fc_stream_t stream) {
@@ -164,11 +171,28 @@ fc_status rk_step(ns_sim_t s, double dt, fc_stream_t stream) {
   return s->core.step_any(dt, stream);
 }
 
-fc_status ns_diagnostics(ns_sim_t s, double*, double*, double*, double*, double*, fc_stream_t) {
+fc_status ns_diagnostics(ns_sim_t s, double* div_ms, double* wall_u_ms, double* wall_w_ms, double* flow_rate,
+                         double* nusselt, fc_stream_t stream) {
   fc_status st = check_sim(s, "ns_diagnostics");
   if (st) return st;
-  set_error("ns_diagnostics: not available in this build");
-  return FC_ERR_UNSUPPORTED;
+  double acc[6];
+  st = s->core.diagnostics_any(acc, stream);
+  if (st) return st;
+  const ns_params& p = s->core.p;
+  const double n2 = (double)p.Nx * p.Ny * (double)p.Nx * p.Ny;
+  if (div_ms) *div_ms = acc[0] / n2 / p.Nz;
+  if (wall_u_ms) *wall_u_ms = acc[1] / n2 / 2.0;
+  if (wall_w_ms) *wall_w_ms = acc[2] / n2 / 2.0;
+  if (flow_rate) *flow_rate = acc[3] / ((double)p.Nx * p.Ny) / p.Nz;
+  if (nusselt) {
+    if (p.nfields == 4 && p.gamma != 0.0) {
+      const double m0 = acc[4] / ((double)p.Nx * p.Ny), m1 = acc[5] / ((double)p.Nx * p.Ny);
+      *nusselt = 0.5 * ((1.0 - m0 / p.gamma) + (1.0 - m1 / p.gamma));
+    } else {
+      *nusselt = 0.0;
+    }
+  }
+  return FC_OK;
 }
 
 }  // extern "C"

@@ -21,7 +21,9 @@ struct NsLayout {
   long long lines, ntiles, plines;   // lines, tiles of TL lines, padded lines
   size_t es;  // bytes per real
   // byte offsets inside the workspace
-  size_t X[3], DZ, DZZ, V, DY, NL, gradp;
+  size_t X[3], DZ, DZZ, V, DY, NL, gradp, diag;
+  size_t X64[3], d2r, hfr;   // float64 mean-line shadows and real-space z kernels
+  int nmean;
   size_t kxo, kyo, kzo, kx, ky, fx, fy, Mr, Mr2, twz, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy;
   size_t tkxo, tkyo, tkzo, tkx, tky, tfx, tfy;   // copies in the simulation's precision
   size_t total;
@@ -72,6 +74,11 @@ inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
   l.DY = take(cs * l.nf * l.Nz * l.plines);
   l.NL = take(cs * l.nf * l.Nz * l.plines);
   l.gradp = take(sizeof(double) * 2 * 4 * l.lines);
+  l.diag = take(sizeof(double) * 8);
+  l.nmean = l.nf == 4 ? 3 : 2;
+  for (int i = 0; i < 3; ++i) l.X64[i] = take(16 * (size_t)l.nmean * l.Np);
+  l.d2r = take(8 * (size_t)(l.Np + p.Nz - 1));
+  l.hfr = take(8 * (size_t)(l.Np + p.Nz - 1));
   l.kxo = take(8 * l.Kx); l.kyo = take(8 * p.Ny); l.kzo = take(8 * l.Np);
   l.kx = take(8 * l.Kx); l.ky = take(8 * p.Ny); l.fx = take(8 * l.Kx); l.fy = take(8 * p.Ny);
   l.tkxo = take(l.es * l.Kx); l.tkyo = take(l.es * p.Ny); l.tkzo = take(l.es * l.Np);
@@ -137,6 +144,8 @@ struct NsCore {
     deriv_conv_spectra(p.Nz, l.Np, l.L, &H1, &H2);
     filter_conv_spectrum(p.Nz, l.Np, l.L, p.filter_beta, p.filter_2p, &Hf);
     bluestein_tables(l.Np, l.L, &chirp, &Hbf, &Hbi);
+    std::vector<double> d2r, hfr;
+    z_kernels_real(p.Nz, l.Np, p.filter_beta, p.filter_2p, &d2r, &hfr);
     engine_twiddles(l.Lx1, l.Lx2, &twx);
     engine_twiddles(l.Ly1, l.Ly2, &twy);
     std::vector<float2> mr2(T.Mr.size());
@@ -169,6 +178,9 @@ struct NsCore {
     if (!s) s = putc(l.Hbi, Hbi);
     if (!s) s = putc(l.twx, twx);
     if (!s) s = putc(l.twy, twy);
+    if (!s) s = put(l.d2r, d2r.data(), 8 * d2r.size());
+    if (!s) s = put(l.hfr, hfr.data(), 8 * hfr.size());
+    if (!s) s = bk.memset(ws + l.X64[0], 0, 3 * 16 * (size_t)l.nmean * l.Np, nullptr);
     if (!s) s = bk.memset(ws + l.gradp, 0, sizeof(double) * 8 * l.lines, nullptr);
     if (!s) s = bk.memset(ws + l.X[0], 0, l.NL - l.X[0] + 2 * l.es * l.nf * l.Nz * l.plines, nullptr);
     if (!s) s = bk.sync(nullptr);
@@ -401,10 +413,39 @@ struct NsCore {
     return s;
   }
 
+  // float64 mean-line island (float32 path only)
+  template <class T>
+  void mean_fmap(int* fm) const { fm[0] = 0; fm[1] = 1; fm[2] = 3; }
+  template <class T>
+  fc_status mean_init(int ix, void* st) {
+    if (sizeof(T) != 4) return FC_OK;
+    using K = KMeanInit<T>;
+    typename K::Args a;
+    a.g = zgeom(l.nf); a.X = Xb<T>(ix); a.X64 = at<double2>(l.X64[ix]);
+    mean_fmap<T>(a.fmap);
+    return bk.template run<K>(a, l.nmean, st);
+  }
+  template <class T>
+  fc_status mean_stage(int it, int ij, int in, double dtj, void* st) {
+    if (sizeof(T) != 4) return FC_OK;
+    using K = KMeanLine<T>;
+    typename K::Args a;
+    a.g = zgeom(l.nf); a.Mr = at<double>(l.Mr); a.d2 = at<double>(l.d2r); a.hf = at<double>(l.hfr);
+    a.NL = buf<T>(l.NL); a.Xt = at<double2>(l.X64[it]); a.Xj = at<double2>(l.X64[ij]);
+    a.Xn = at<double2>(l.X64[in]); a.Xo = Xb<T>(in); a.gradp = at<double2>(l.gradp);
+    a.dtj = dtj; a.dif[0] = a.dif[1] = p.nu; a.dif[2] = p.kappa;
+    a.fxy00 = 1.0;   // x, y filter / mask factor of the (0, 0) mode in both filter modes
+    mean_fmap<T>(a.fmap);
+    a.nmean = l.nmean;
+    return bk.template run<K>(a, l.nmean, st);
+  }
+  fc_status mean_init_any(void* st) { return f32() ? mean_init<float>(cur, st) : FC_OK; }
+
   template <class T>
   fc_status set_fields(const T* phys, void* st) {
     fc_status s = phys_to_state<T>(phys, Xb<T>(cur), l.nf, nullptr, 0.0, st);
     if (!s) s = bk.memset(ws + l.gradp, 0, sizeof(double) * 8 * l.lines, st);
+    if (!s) s = mean_init<T>(cur, st);
     return s;
   }
   template <class T>
@@ -442,6 +483,7 @@ struct NsCore {
       const int in = (ij == ia) ? ib : ia;
       s = nonlinear<T>(Xb<T>(ij), st);
       if (!s) s = z_combine<T>(buf<T>(l.NL), Xb<T>(it), Xb<T>(ij), Xb<T>(in), dtj, 1, l.nf, st);
+      if (!s) s = mean_stage<T>(it, ij, in, dtj, st);
       if (!s) s = z_project<T>(Xb<T>(in), dtj, st);
       ij = in;
     }
@@ -465,6 +507,25 @@ struct NsCore {
                  : project<double>(dtj, (const double*)in, (double*)out, gp, st);
   }
   fc_status step_any(double dt, void* st) { return f32() ? step<float>(dt, st) : step<double>(dt, st); }
+
+  // diagnostics of the current state (Sec. 6, Sec. 7); synchronous
+  template <class T>
+  fc_status diagnostics(double out[6], void* st) {
+    fc_status s = bk.memset(ws + l.diag, 0, sizeof(double) * 8, st);
+    if (!s) s = z_deriv<T>(Xb<T>(cur), l.nf, st);
+    if (!s) {
+      using K = KDiag<T>;
+      typename K::Args a;
+      a.g = zgeom(l.nf); a.t = ztab<T>(); a.Nx = p.Nx;
+      a.X = Xb<T>(cur); a.DZ = buf<T>(l.DZ); a.acc = at<double>(l.diag);
+      s = bk.template run<K>(a, l.ntiles, st);
+    }
+    if (!s) s = bk.d2h(out, ws + l.diag, sizeof(double) * 6, st);
+    return s;
+  }
+  fc_status diagnostics_any(double out[6], void* st) {
+    return f32() ? diagnostics<float>(out, st) : diagnostics<double>(out, st);
+  }
   size_t state_bytes() const { return 2 * l.es * l.nf * l.Np * l.plines; }
   // wall planes: internal [2][2][Ny][Kxp] <-> public [2][2][Ny][Kx] (complex double)
   fc_status gradp_out(void* dst, void* st) {

@@ -1038,3 +1038,220 @@ struct KXRow {
 };
 
 }  // namespace fcns
+
+namespace fcns {
+
+// ===========================================================================
+// Diagnostics of the state (Sec. 6: divergence and wall velocities; Sec. 7:
+// Nusselt number; channel flow rate), reduced in float64.  Mean squares over
+// the physical grid follow from the mixed-space values by Parseval over the
+// half spectrum: weight 1 at kx = 0 and kx = Nx/2, 2 elsewhere, / (Nx Ny)^2.
+//   acc[0] += sum over z, lines of w |i kx u + i ky v + dz w|^2
+//   acc[1] += sum over both walls of w |u|^2,   acc[2] += ... of w |w|^2
+//   acc[3] += sum over z of Re u(kx=0, ky=0, z)          (flow rate)
+//   acc[4] += Re dz theta(0, 0, z=0),  acc[5] += Re dz theta(0, 0, z=Lz)
+// ===========================================================================
+template <class T>
+struct KDiag {
+  using C = cx<T>;
+  static constexpr int THREADS = 256, NPHASE = 2, MINB = 1;
+  struct Args {
+    ZGeom g;
+    ZTab<T> t;
+    int Nx;
+    const C* X;     // state (extended), [nf][N'][lines]
+    const C* DZ;    // dz of the state at the Nz points, [nf][Nz][lines]
+    double* acc;    // 6 accumulators
+  };
+  struct Regs { double s[6]; };
+  static constexpr size_t smem_bytes = sizeof(double) * 6 * THREADS;
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
+    double* red = reinterpret_cast<double*>(sm);
+    if constexpr (P == 0) {
+      for (int i = 0; i < 6; ++i) R.s[i] = 0.0;
+      const int li = tid % TL, zr = tid / TL;           // 16 lines x 16 z rows per pass
+      const long long line = bid * TL + li;
+      const int Nz = a.g.Nz, Np = a.g.Np;
+      const int kx = (int)(line % a.g.Kxp), ky = (int)(line / a.g.Kxp);
+      if (line < a.g.lines && kx < a.g.Kx) {
+        const double wgt = (kx == 0 || 2 * kx == a.Nx) ? 1.0 : 2.0;
+        const double kxo = (double)a.t.kxo[kx], kyo = (double)a.t.kyo[ky];
+        const C* u = a.X + lay(0, 0, line, Np, a.g.ntiles);
+        const C* v = a.X + lay(1, 0, line, Np, a.g.ntiles);
+        const C* w = a.X + lay(2, 0, line, Np, a.g.ntiles);
+        const C* dw = a.DZ + lay(2, 0, line, Nz, a.g.ntiles);
+        for (int z = zr; z < Nz; z += THREADS / TL) {
+          const C uu = u[z * TL], vv = v[z * TL], ww = w[z * TL], dd = dw[z * TL];
+          // i kx u + i ky v + dz w
+          const double re = -kxo * (double)uu.y - kyo * (double)vv.y + (double)dd.x;
+          const double im = kxo * (double)uu.x + kyo * (double)vv.x + (double)dd.y;
+          R.s[0] += wgt * (re * re + im * im);
+          if (z == 0 || z == Nz - 1) {
+            R.s[1] += wgt * ((double)uu.x * uu.x + (double)uu.y * uu.y);
+            R.s[2] += wgt * ((double)ww.x * ww.x + (double)ww.y * ww.y);
+          }
+          if (kx == 0 && ky == 0) R.s[3] += (double)uu.x;
+        }
+        if (kx == 0 && ky == 0 && zr == 0 && a.g.nf == 4) {
+          const C* dt = a.DZ + lay(3, 0, line, Nz, a.g.ntiles);
+          R.s[4] = (double)dt[0].x;
+          R.s[5] = (double)dt[(Nz - 1) * TL].x;
+        }
+      }
+      for (int i = 0; i < 6; ++i) red[i * THREADS + tid] = R.s[i];
+    } else {
+      if (tid < 6) {
+        double s = 0.0;
+        for (int t = 0; t < THREADS; ++t) s += red[tid * THREADS + t];
+        if (s != 0.0) {
+#if defined(__CUDA_ARCH__)
+          atomicAdd(a.acc + tid, s);
+#else
+          a.acc[tid] += s;
+#endif
+        }
+      }
+    }
+  }
+};
+
+}  // namespace fcns
+
+namespace fcns {
+
+// ===========================================================================
+// Float64 island of the float32 path: the RK accumulation of the mean-flow
+// line (kx, ky) = (0, 0) of u, v and theta (the fields the projection leaves
+// unchanged on that line) is redone in float64 from a float64 shadow of the
+// line:  v* = v^t + dt_j [ (f_z * FC(N))(z) + nu dzz v^{j-1} ]  (direct sums
+// with the float64 real-space kernels), wall injection, continuation, and
+// both the shadow and the float32 state line are written.  One block per
+// field; runs after the stage combine.
+// ===========================================================================
+template <class T>
+struct KMean {
+  using C = cx<T>;
+  static constexpr int THREADS = 256, NPHASE = 4, MINB = 1, NPMAX = 1200;
+  struct Args {
+    ZGeom g;
+    const double* Mr;       // C x d
+    const double* d2;       // [Np + Nz - 1] real-space kernels (unit spacing)
+    const double* hf;
+    const C* NL;            // nonlinear term (mixed), float32 path
+    const double2* Xt;      // shadows [3][Np] (u, v, theta)
+    const double2* Xj;
+    double2* Xn;
+    C* Xo;                  // float32 state buffer of this stage
+    const double2* gradp;   // wall planes (line 0 entries)
+    double dtj;
+    double dif[3];
+    double fxy00;
+    int fmap[3];            // field index of shadow entry 0, 1, 2
+    int nmean;              // 2 (Navier-Stokes: u, v) or 3 (Boussinesq: u, v, theta)
+  };
+  struct Regs { int dummy; };
+  static constexpr size_t smem_bytes = 2 * sizeof(double2) * NPMAX;
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs&) {
+    double2* nl = reinterpret_cast<double2*>(sm);
+    double2* vs = nl + NPMAX;
+    const int e = (int)bid, f = a.fmap[e];
+    const int Nz = a.g.Nz, Np = a.g.Np, d = a.g.d, Cc = a.g.Cc;
+    const int jlo = -(Np - 1);
+    auto cont = [&](const double2* x, int jj) {
+      double re = 0, im = 0;
+      for (int i = 0; i < d; ++i) {
+        const double m1 = a.Mr[jj * d + i], m2 = a.Mr[(Cc - 1 - jj) * d + (d - 1 - i)];
+        re += m1 * x[Nz - d + i].x + m2 * x[i].x;
+        im += m1 * x[Nz - d + i].y + m2 * x[i].y;
+      }
+      return make_double2(re, im);
+    };
+    if constexpr (P == 0) {
+      const C* src = a.NL + lay(f, 0, 0, Nz, a.g.ntiles);
+      for (int z = tid; z < Nz; z += THREADS) nl[z] = make_double2((double)src[z * TL].x, (double)src[z * TL].y);
+    } else if constexpr (P == 1) {
+      for (int z = Nz + tid; z < Np; z += THREADS) nl[z] = cont(nl, z - Nz);
+    } else if constexpr (P == 2) {
+      const double2* xt = a.Xt + (long long)e * Np;
+      const double2* xj = a.Xj + (long long)e * Np;
+      const double s2 = 1.0 / (a.g.dz * a.g.dz);
+      for (int z = tid; z < Nz; z += THREADS) {
+        double fr = 0, fi = 0, zr = 0, zi = 0;
+        for (int m = 0; m < Np; ++m) {
+          const double hk = a.hf[z - m - jlo], dk = a.d2[z - m - jlo];
+          fr += hk * nl[m].x;
+          fi += hk * nl[m].y;
+          zr += dk * xj[m].x;
+          zi += dk * xj[m].y;
+        }
+        double2 v = make_double2(xt[z].x + a.dtj * (a.fxy00 * fr + a.dif[e] * zr * s2),
+                                 xt[z].y + a.dtj * (a.fxy00 * fi + a.dif[e] * zi * s2));
+        if (z == 0 || z == Nz - 1) {
+          const int wall = (z == 0) ? 0 : 1;
+          if (f < 2) {
+            const double2 gp = a.gradp[((long long)wall * 2 + f) * a.g.lines];
+            v = make_double2(a.dtj * gp.x, a.dtj * gp.y);
+          } else {
+            v = make_double2(0.0, 0.0);
+          }
+        }
+        vs[z] = v;
+      }
+    } else if constexpr (P == 3) {
+      for (int z = Nz + tid; z < Np; z += THREADS) vs[z] = cont(vs, z - Nz);
+    }
+  }
+  // final write (after a barrier): shadow and float32 line
+  static FC_HD void write(const Args& a, unsigned char* sm, int tid, long long bid) {
+    const double2* vs = reinterpret_cast<const double2*>(sm) + NPMAX;
+    const int e = (int)bid, f = a.fmap[e];
+    C* xo = a.Xo + lay(f, 0, 0, a.g.Np, a.g.ntiles);
+    for (int z = tid; z < a.g.Np; z += THREADS) {
+      a.Xn[(long long)e * a.g.Np + z] = vs[z];
+      xo[z * TL] = mk<T>((T)vs[z].x, (T)vs[z].y);
+    }
+  }
+};
+
+// wrapper with the final write as its own phase
+template <class T>
+struct KMeanLine {
+  using Base = KMean<T>;
+  using Args = typename Base::Args;
+  using Regs = typename Base::Regs;
+  static constexpr int THREADS = Base::THREADS, NPHASE = 5, MINB = 1;
+  static constexpr size_t smem_bytes = Base::smem_bytes;
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& r) {
+    if constexpr (P < 4) Base::template phase<P>(a, sm, tid, bid, r);
+    else Base::write(a, sm, tid, bid);
+  }
+};
+
+// shadow <- float32 state line 0 of u, v (, theta)
+template <class T>
+struct KMeanInit {
+  using C = cx<T>;
+  static constexpr int THREADS = 256, NPHASE = 1, MINB = 1;
+  struct Args {
+    ZGeom g;
+    const C* X;
+    double2* X64;
+    int fmap[3];
+  };
+  struct Regs { int dummy; };
+  static constexpr size_t smem_bytes = 16;
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char*, int tid, long long bid, Regs&) {
+    const int e = (int)bid;
+    const C* x = a.X + lay(a.fmap[e], 0, 0, a.g.Np, a.g.ntiles);
+    for (int z = tid; z < a.g.Np; z += THREADS)
+      a.X64[(long long)e * a.g.Np + z] = make_double2((double)x[z * TL].x, (double)x[z * TL].y);
+  }
+};
+
+}  // namespace fcns

@@ -185,3 +185,48 @@ def test_full_size_boussinesq_properties(api):
     assert out[2, [0, -1]].abs().max().item() < 1e-5 * scale
     assert out[3, [0, -1]].abs().max().item() < 1e-5 * out[3].abs().max().item()
     sim.close()
+
+
+def test_diagnostics_boussinesq(api):
+    """ns_diagnostics on the GPU vs the oracle's diagnostics after one RK3 step."""
+    N, Nz = 32, 33
+    kw = dict(nu=3.162e-3, kappa=3.162e-3, gamma=1.0)
+    sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nfields=4, prec="f64", **kw))
+    P = ns.Params(N, N, Nz, nfields=4, **kw)
+    f = synth.boussinesq_fields(N, N, Nz, amp=1e-1)
+    f[0] += 0.3 * (synth.z_grid(Nz) * (1 - synth.z_grid(Nz)))[:, None, None]
+    sim.set_fields(_cuda(f))
+    sim.step(2e-3)
+    _, _, st = _oracle_steps(f, P, 2e-3, 1)
+    d = sim.diagnostics()
+    div = (ns.divergence_phys(st, P) ** 2).mean()
+    wu, wv, ww = ns.wall_mean_squares(st, P)
+    nb, nt = ns.nusselt(st, P)
+    assert abs(d["div_ms"] - div) <= 1e-6 * div
+    assert abs(d["wall_u_ms"] - wu) <= 1e-10 * wu
+    assert d["wall_w_ms"] <= 1e-25
+    assert abs(d["flow_rate"] - ns.flow_rate(st, P)) <= 1e-12
+    assert abs(d["nusselt"] - 0.5 * (nb + nt)) <= 1e-10
+    sim.close()
+
+
+def test_float32_mean_flow_island_long_run(api):
+    """2000 float32 RK3 steps of a decaying mean profile u = 0.5 sin(pi z) with
+    weak fluctuations: the mean-flow line, accumulated in float64, stays within
+    float32 output rounding of the float64 run (float32 accumulation of that
+    line would random-walk by ~1e-6)."""
+    N, Nz = 32, 33
+    z = synth.z_grid(Nz)
+    f = synth.channel_velocity(N, N, Nz, mean_flow=False, fluct=0.01)
+    f[0] += 0.5 * np.sin(np.pi * z)[:, None, None]
+    f = f.astype(np.float32).astype(np.float64)
+    means = []
+    for prec, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nu=1e-2, prec=prec))
+        sim.set_fields(_cuda(f, dt))
+        for _ in range(2000):
+            sim.step(1e-3)
+        means.append(sim.get_fields()[0].double().mean(dim=(1, 2)).cpu().numpy())
+        sim.close()
+    rel = np.abs(means[0] - means[1]).max() / np.abs(means[1]).max()
+    assert rel < 2.4e-7, rel

@@ -76,3 +76,62 @@ def test_boussinesq_float32_steps():
     for c in range(4):
         assert _rel(out[c], ref[c]) < 2e-5, c
     hs.close()
+
+
+def _diag_from_raw(acc, p):
+    n2 = float(p.Nx * p.Ny) ** 2
+    nu_b = 1 - acc[4] / (p.Nx * p.Ny) / p.gamma if p.nfields == 4 else 0.0
+    nu_t = 1 - acc[5] / (p.Nx * p.Ny) / p.gamma if p.nfields == 4 else 0.0
+    return dict(div=acc[0] / n2 / p.Nz, wu=acc[1] / n2 / 2, ww=acc[2] / n2 / 2,
+                flow=acc[3] / (p.Nx * p.Ny) / p.Nz, nu=0.5 * (nu_b + nu_t))
+
+
+def test_diagnostics_match_oracle():
+    import ctypes
+    N, Nz = 16, 33
+    kw = dict(nu=3.162e-3, kappa=3.162e-3, gamma=1.0)
+    hs = HostSim(Nx=N, Ny=N, Nz=Nz, nfields=4, prec="f64", **kw)
+    P = ns.Params(N, N, Nz, nfields=4, **kw)
+    f = synth.boussinesq_fields(N, N, Nz, amp=1e-1)
+    f[0] += 0.3 * (synth.z_grid(Nz) * (1 - synth.z_grid(Nz)))[:, None, None]
+    hs.set_fields(f)
+    hs.step(2e-3)
+    st = ns.to_spectral(f, P)
+    st, _ = ns.rk_step(st, np.zeros((2, 2, N, N // 2 + 1), complex), P, 2e-3)
+    acc = np.zeros(6)
+    assert hs.lib.fchc_ns_diag_raw(ctypes.c_void_p(hs.h), acc.ctypes.data_as(ctypes.c_void_p)) == 0
+    d = _diag_from_raw(acc, hs.p)
+    div = (ns.divergence_phys(st, P) ** 2).mean()
+    wu, wv, ww = ns.wall_mean_squares(st, P)
+    nb, nt = ns.nusselt(st, P)
+    # div v ~ 4e-8 here is a difference of O(1) derivatives: its rounding floor
+    # (~1e-15 absolute) limits the relative agreement of its mean square to ~1e-7
+    assert abs(d["div"] - div) <= 1e-6 * div
+    assert abs(d["wu"] - wu) <= 1e-10 * wu
+    assert abs(d["ww"] - ww) <= 1e-12 * max(wu, 1e-30)
+    assert abs(d["flow"] - ns.flow_rate(st, P)) <= 1e-12
+    assert abs(d["nu"] - 0.5 * (nb + nt)) <= 1e-10
+    hs.close()
+
+
+def test_float32_mean_flow_accumulates_in_float64():
+    """Float64 island of the float32 path: the mean-flow line of a decaying
+    profile u = 0.5 sin(pi z) (plus weak solenoidal fluctuations) follows the
+    float64 run over 100 steps to the float32 rounding of the output fields
+    (2 ulps); the GPU test runs 2000 steps, where float32 accumulation of the
+    line would drift by ~1e-6."""
+    N, Nz = 16, 33
+    z = synth.z_grid(Nz)
+    f = synth.channel_velocity(N, N, Nz, mean_flow=False, fluct=0.01)
+    f[0] += 0.5 * np.sin(np.pi * z)[:, None, None]
+    f = f.astype(np.float32).astype(np.float64)
+    means = []
+    for prec in ("f32", "f64"):
+        hs = HostSim(Nx=N, Ny=N, Nz=Nz, nu=1e-2, prec=prec)
+        hs.set_fields(f)
+        for _ in range(100):
+            hs.step(1e-3)
+        means.append(hs.get_fields()[0].astype(np.float64).mean(axis=(1, 2)))
+        hs.close()
+    rel = np.abs(means[0] - means[1]).max() / np.abs(means[1]).max()
+    assert rel < 2.4e-7, rel
