@@ -148,37 +148,34 @@ struct DerivPair {
         E::template B<-1>(R.u, b0, r, li);
 #pragma unroll
         for (int k2 = 0; k2 < L2; ++k2) b1[E::bidx(r, k2, li)] = R.u[k2];
-        E::mulH(R.u, a.H1, r);
-        E::template Bi<1>(R.u, b0, a.tw, r, li);
-        FC_FENCE();
+        // the two inverse transforms share one copy of the code (instruction cache)
+#pragma unroll 1
+        for (int o = 0; o < 2; ++o) {
+          C* bo = o == 0 ? b0 : b1;
+          if (o == 1) {
+            FC_FENCE();
 #pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = b1[E::bidx(r, k2, li)];
-        E::mulH(R.u, a.H2, r);
-        E::template Bi<1>(R.u, b1, a.tw, r, li);
+            for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = b1[E::bidx(r, k2, li)];
+          }
+          E::mulH(R.u, o == 0 ? a.H1 : a.H2, r);
+          E::template Bi<1>(R.u, bo, a.tw, r, li);
+        }
       }
     } else if constexpr (P == 3) {
       if (r < L2 && va) {
-        E::template Ai<1>(R.v, b0, r, li);
-        if (a.df) {
+#pragma unroll 1
+        for (int o = 0; o < 2; ++o) {
+          T* out = o == 0 ? a.df : a.d2f;
+          if (!out) continue;
+          E::template Ai<1>(R.v, o == 0 ? b0 : b1, r, li);
+          const T sc = o == 0 ? a.s1 : a.s2;
 #pragma unroll
           for (int j = 0; j < L1; ++j) {
             const int n = r + L2 * j;
             if (n < a.Nz) {
-              T* p = a.df + base + (long long)n * a.zstride;
-              p[0] = R.v[j].x * a.s1;
-              if (vb) p[1] = R.v[j].y * a.s1;
-            }
-          }
-        }
-        if (a.d2f) {
-          E::template Ai<1>(R.v, b1, r, li);
-#pragma unroll
-          for (int j = 0; j < L1; ++j) {
-            const int n = r + L2 * j;
-            if (n < a.Nz) {
-              T* p = a.d2f + base + (long long)n * a.zstride;
-              p[0] = R.v[j].x * a.s2;
-              if (vb) p[1] = R.v[j].y * a.s2;
+              T* p = out + base + (long long)n * a.zstride;
+              p[0] = R.v[j].x * sc;
+              if (vb) p[1] = R.v[j].y * sc;
             }
           }
         }

@@ -230,3 +230,31 @@ def test_float32_mean_flow_island_long_run(api):
         sim.close()
     rel = np.abs(means[0] - means[1]).max() / np.abs(means[1]).max()
     assert rel < 2.4e-7, rel
+
+
+@pytest.mark.parametrize("o", [1, 2, 3])
+def test_wall_slip_dt_study(api, o):
+    """Slip study (Sec. 6) on the GPU: <u^2|wall> from ns_diagnostics matches the
+    oracle run by run, falls like dt^4 above the resolution floor for o <= 2, and
+    <w^2|wall> stays at round-off for every dt."""
+    N, Nz, T = 32, 33, 0.032
+    v0 = synth.channel_velocity(N, N, Nz, nu=1e-2, fluct=1.0)
+    P = ns.Params(N, N, Nz, nu=1e-2, forcing_x=0.1, rk_order=o)
+    slips = []
+    for dt in (8e-3, 4e-3):
+        sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nu=1e-2, forcing_x=0.1, rk_order=o, prec="f64"))
+        sim.set_fields(_cuda(v0))
+        for _ in range(int(round(T / dt))):
+            sim.step(dt)
+        d = sim.diagnostics()
+        sim.close()
+        st = ns.to_spectral(v0, P)
+        gp = np.zeros((2, 2, N, N // 2 + 1), complex)
+        for _ in range(int(round(T / dt))):
+            st, gp = ns.rk_step(st, gp, P, dt)
+        wu, _, ww = ns.wall_mean_squares(st, P)
+        assert abs(d["wall_u_ms"] - wu) <= 1e-6 * wu
+        assert d["wall_w_ms"] < 1e-28
+        slips.append(d["wall_u_ms"])
+    if o <= 2:
+        assert np.log2(slips[0] / slips[1]) > 3.5
