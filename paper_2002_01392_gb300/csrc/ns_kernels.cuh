@@ -162,32 +162,31 @@ struct KZDeriv {
         E::template B<-1>(R.u, b0, r, li);
 #pragma unroll
         for (int k2 = 0; k2 < L2; ++k2) b1[E::bidx(r, k2, li)] = R.u[k2];
-        E::mulH(R.u, a.t.H1, r);
-        E::template Bi<1>(R.u, b0, a.t.tw, r, li);
-        FC_FENCE();
+        // the two inverse transforms share one copy of the code (instruction cache)
+#pragma unroll 1
+        for (int o = 0; o < 2; ++o) {
+          if (o == 1) {
+            FC_FENCE();
 #pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = b1[E::bidx(r, k2, li)];
-        E::mulH(R.u, a.t.H2, r);
-        E::template Bi<1>(R.u, b1, a.t.tw, r, li);
+            for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = b1[E::bidx(r, k2, li)];
+          }
+          E::mulH(R.u, o == 0 ? a.t.H1 : a.t.H2, r);
+          E::template Bi<1>(R.u, o == 0 ? b0 : b1, a.t.tw, r, li);
+        }
       }
     } else if constexpr (P == 2) {
       if (r < L2) {
-        C* dz = a.DZ + lay(f, 0, line, a.g.Nz, a.g.ntiles);
-        C* dzz = a.DZZ + lay(f, 0, line, a.g.Nz, a.g.ntiles);
-        E::template Ai<1>(R.v, b0, r, li);
-        if (valid) {
+#pragma unroll 1
+        for (int o = 0; o < 2; ++o) {
+          C* out = (o == 0 ? a.DZ : a.DZZ) + lay(f, 0, line, a.g.Nz, a.g.ntiles);
+          const T sc = o == 0 ? a.s1 : a.s2;
+          E::template Ai<1>(R.v, o == 0 ? b0 : b1, r, li);
+          if (valid) {
 #pragma unroll
-          for (int j = 0; j < L1; ++j) {
-            const int n = r + L2 * j;
-            if (n < a.g.Nz) dz[n * TL] = cscale(R.v[j], a.s1);
-          }
-        }
-        E::template Ai<1>(R.v, b1, r, li);
-        if (valid) {
-#pragma unroll
-          for (int j = 0; j < L1; ++j) {
-            const int n = r + L2 * j;
-            if (n < a.g.Nz) dzz[n * TL] = cscale(R.v[j], a.s2);
+            for (int j = 0; j < L1; ++j) {
+              const int n = r + L2 * j;
+              if (n < a.g.Nz) out[n * TL] = cscale(R.v[j], sc);
+            }
           }
         }
       }
@@ -409,7 +408,9 @@ template <class T, int L1, int L2, int LINES>
 struct KZProject {
   using E = Eng<T, L1, L2, LINES>;
   using C = cx<T>;
-  static constexpr int THREADS = E::THREADS, NPHASE = 12;
+  static constexpr int THREADS = E::THREADS, NPHASE = 7;
+  // phases 1..3 run four times (Y^, W^, sigma, sigma_z) from one copy of code
+  static constexpr int LB = 1, LE = 4, NIT = 4;
   static constexpr int MINB = LINES <= 4 ? 3 : 1;
   struct Args {
     ZGeom g;
@@ -434,16 +435,9 @@ struct KZProject {
     c.y = -c.y;
     return c;
   }
-  static FC_HD void conv(const Args& a, C* b0, const C* H, int r, int li, Regs& R) {
-    if (r < L1) {
-      E::template B<-1>(R.u, b0, r, li);
-      E::mulH(R.u, H, r);
-      E::template Bi<1>(R.u, b0, a.t.tw, r, li);
-    }
-  }
 
   template <int P>
-  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, int it, Regs& R) {
     C* b0 = reinterpret_cast<C*>(sm);
     const double* Ms = reinterpret_cast<const double*>(sm + off_M);
     const float2* Ms2 = reinterpret_cast<const float2*>(sm + off_M);
@@ -463,102 +457,98 @@ struct KZProject {
     C* g1 = a.G1 + lay(0, 0, line, Np, a.g.ntiles);
     const T invNp = T(1.0 / Np);
 
-    if constexpr (P == 0) {  // Y = kx u + ky v, Bluestein input
+    if constexpr (P == 0) {
       load_mr<T>(sm + off_M, a.t, a.g.Cc * d, tid, THREADS);
+    } else if constexpr (P == 1) {  // Bluestein input of transform `it`
       if (r < L2) {
+        if (it == 0) {  // Y = kx u + ky v
 #pragma unroll
-        for (int j = 0; j < L1; ++j) {
-          const int n = r + L2 * j;
-          C y = mk<T>(0, 0);
-          if (valid && n < Np) {
-            y = cadd(cscale(xu[n * TL], kxo), cscale(xv[n * TL], kyo));
-            y = cmul(y, a.t.chirp[n]);
+          for (int j = 0; j < L1; ++j) {
+            const int n = r + L2 * j;
+            C y = mk<T>(0, 0);
+            if (valid && n < Np) {
+              y = cadd(cscale(xu[n * TL], kxo), cscale(xv[n * TL], kyo));
+              y = cmul(y, a.t.chirp[n]);
+            }
+            R.v[j] = y;
           }
-          R.v[j] = y;
-        }
-        E::template A<-1>(R.v, b0, a.t.tw, r, li);
-      }
-    } else if constexpr (P == 1 || P == 3 || P == 5 || P == 7) {
-      conv(a, b0, (P <= 3) ? a.t.Hbf : a.t.Hbi, r, li, R);
-    } else if constexpr (P == 2) {  // Y^ -> G0; w Bluestein input
-      if (r < L2) {
-        E::template Ai<1>(R.v, b0, r, li);
+        } else if (it == 1) {  // w
 #pragma unroll
-        for (int j = 0; j < L1; ++j) {
-          const int n = r + L2 * j;
-          if (valid && n < Np) g0[n * TL] = cmul(R.v[j], a.t.chirp[n]);
-        }
-#pragma unroll
-        for (int j = 0; j < L1; ++j) {
-          const int n = r + L2 * j;
-          R.v[j] = (valid && n < Np) ? cmul(xw[n * TL], a.t.chirp[n]) : mk<T>(0, 0);
-        }
-        E::template A<-1>(R.v, b0, a.t.tw, r, li);
-      }
-    } else if constexpr (P == 4) {  // W^, s -> G0; inverse-DFT input for sigma
-      if (r < L2) {
-        E::template Ai<1>(R.v, b0, r, li);
-        const T kp2 = kxo * kxo + kyo * kyo;
-#pragma unroll
-        for (int j = 0; j < L1; ++j) {
-          const int n = r + L2 * j;
-          C s = mk<T>(0, 0);
-          if (valid && n < Np) {
-            const C wh = cmul(R.v[j], a.t.chirp[n]);
-            const T kz = a.t.kzo[n];
-            const T k2 = kp2 + kz * kz;
-            const T inv = k2 > T(0) ? T(1) / k2 : T(0);
-            s = cscale(cadd(g0[n * TL], cscale(wh, kz)), inv);
-            g0[n * TL] = s;
+          for (int j = 0; j < L1; ++j) {
+            const int n = r + L2 * j;
+            R.v[j] = (valid && n < Np) ? cmul(xw[n * TL], a.t.chirp[n]) : mk<T>(0, 0);
           }
-          R.v[j] = cmul(s, cchirp(a.t, n, Np));
+        } else {  // s (it = 2) or kz s (it = 3), inverse DFT input
+#pragma unroll
+          for (int j = 0; j < L1; ++j) {
+            const int n = r + L2 * j;
+            C x = mk<T>(0, 0);
+            if (valid && n < Np) {
+              x = g0[n * TL];
+              if (it == 3) x = cscale(x, a.t.kzo[n]);
+              x = cmul(x, cchirp(a.t, n, Np));
+            }
+            R.v[j] = x;
+          }
         }
         E::template A<-1>(R.v, b0, a.t.tw, r, li);
       }
-    } else if constexpr (P == 6) {  // sigma -> G1; inverse-DFT input kz s
+    } else if constexpr (P == 2) {
+      if (r < L1) {
+        E::template B<-1>(R.u, b0, r, li);
+        E::mulH(R.u, it < 2 ? a.t.Hbf : a.t.Hbi, r);
+        E::template Bi<1>(R.u, b0, a.t.tw, r, li);
+      }
+    } else if constexpr (P == 3) {  // Bluestein output of transform `it`
       if (r < L2) {
         E::template Ai<1>(R.v, b0, r, li);
+        if (!valid) return;
+        if (it == 0) {  // Y^ -> G0
 #pragma unroll
-        for (int j = 0; j < L1; ++j) {
-          const int n = r + L2 * j;
-          if (valid && n < Np) {
-            const C sg = cscale(cmul(R.v[j], cchirp(a.t, n, Np)), invNp);
-            g1[n * TL] = sg;
-            if (n == 0 || n == Nz - 1) {
-              const int o = (n == 0) ? 4 : 6;
-              W[o] = (double)sg.x;
-              W[o + 1] = (double)sg.y;
+          for (int j = 0; j < L1; ++j) {
+            const int n = r + L2 * j;
+            if (n < Np) g0[n * TL] = cmul(R.v[j], a.t.chirp[n]);
+          }
+        } else if (it == 1) {  // W^, s = (Y^ + kz W^) / k^2 -> G0
+          const T kp2 = kxo * kxo + kyo * kyo;
+#pragma unroll
+          for (int j = 0; j < L1; ++j) {
+            const int n = r + L2 * j;
+            if (n < Np) {
+              const C wh = cmul(R.v[j], a.t.chirp[n]);
+              const T kz = a.t.kzo[n];
+              const T k2 = kp2 + kz * kz;
+              const T inv = k2 > T(0) ? T(1) / k2 : T(0);
+              g0[n * TL] = cscale(cadd(g0[n * TL], cscale(wh, kz)), inv);
             }
           }
-        }
+        } else {  // sigma -> G1 (it = 2), sigma_z -> G0 and b, t (it = 3)
 #pragma unroll
-        for (int j = 0; j < L1; ++j) {
-          const int n = r + L2 * j;
-          C s = mk<T>(0, 0);
-          if (valid && n < Np) s = cmul(cscale(g0[n * TL], a.t.kzo[n]), cchirp(a.t, n, Np));
-          R.v[j] = s;
-        }
-        E::template A<-1>(R.v, b0, a.t.tw, r, li);
-      }
-    } else if constexpr (P == 8) {  // sigma_z -> G0; b, t
-      if (r < L2) {
-        E::template Ai<1>(R.v, b0, r, li);
-#pragma unroll
-        for (int j = 0; j < L1; ++j) {
-          const int n = r + L2 * j;
-          if (valid && n < Np) {
-            const C sz = cscale(cmul(R.v[j], cchirp(a.t, n, Np)), invNp);
-            g0[n * TL] = sz;
-            if (n == 0 || n == Nz - 1) {
-              const C w = xw[n * TL];
-              const int o = (n == 0) ? 0 : 2;
-              W[o] = (double)w.x - (double)sz.x;
-              W[o + 1] = (double)w.y - (double)sz.y;
+          for (int j = 0; j < L1; ++j) {
+            const int n = r + L2 * j;
+            if (n < Np) {
+              const C sg = cscale(cmul(R.v[j], cchirp(a.t, n, Np)), invNp);
+              if (it == 2) {
+                g1[n * TL] = sg;
+                if (n == 0 || n == Nz - 1) {
+                  const int o = (n == 0) ? 4 : 6;
+                  W[o] = (double)sg.x;
+                  W[o + 1] = (double)sg.y;
+                }
+              } else {
+                g0[n * TL] = sg;
+                if (n == 0 || n == Nz - 1) {
+                  const C w = xw[n * TL];
+                  const int o = (n == 0) ? 0 : 2;
+                  W[o] = (double)w.x - (double)sg.x;
+                  W[o + 1] = (double)w.y - (double)sg.y;
+                }
+              }
             }
           }
         }
       }
-    } else if constexpr (P == 9) {  // homogeneous coefficients (float64) -> W[8..12]
+    } else if constexpr (P == 4) {  // homogeneous coefficients (float64) -> W[8..12]
       if (r == 0) {
         const double br = W[0], bi = W[1], tr = W[2], ti = W[3];
         double Ar = 0, Aim = 0, Br = 0, Bim = 0, D = 0;
@@ -579,7 +569,7 @@ struct KZProject {
         }
         W[8] = Ar; W[9] = Aim; W[10] = Br; W[11] = Bim; W[12] = D;
       }
-    } else if constexpr (P == 10) {  // Phi, Phi' at the 2d end points -> smem
+    } else if constexpr (P == 5) {  // Phi, Phi' at the 2d end points -> smem
       if (r < 2 * d) {
         const int s = r < d ? r : Nz - 2 * d + r;
         C ph, dph;
@@ -588,7 +578,7 @@ struct KZProject {
         Ev[r < d ? r : DMAX + (r - d)] = ph;
         Ev[2 * DMAX + (r < d ? r : DMAX + (r - d))] = dph;
       }
-    } else if constexpr (P == 11) {  // X -= grad phi^I + FC(grad phi^H); wall planes
+    } else if constexpr (P == 6) {  // X -= grad phi^I + FC(grad phi^H); wall planes
       if (r < L2 && valid) {
         const T cf[5] = {(T)W[8], (T)W[9], (T)W[10], (T)W[11], (T)W[12]};
         const T tdz = (T)a.g.dz, tLz = (T)a.g.Lz;

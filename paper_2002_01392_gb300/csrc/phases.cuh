@@ -5,6 +5,7 @@
 // index arithmetic be verified against the oracle without a GPU.
 #pragma once
 #include <cuda_runtime.h>
+#include <type_traits>
 #include <vector>
 #include "fft_reg.cuh"
 
@@ -16,16 +17,62 @@
 
 namespace fcns {
 
+// Kernels may declare a loop section: phases [LB, LE) are repeated NIT times
+// with a runtime iteration index (one copy of their code), between the
+// prologue phases [0, LB) and the epilogue phases [LE, NPHASE).  Such kernels
+// define phase<P>(a, smem, tid, bid, it, regs).
+template <class K, class = void>
+struct LoopSpec {
+  static constexpr bool on = false;
+  static constexpr int LB = K::NPHASE, LE = K::NPHASE, NIT = 0;
+};
+template <class K>
+struct LoopSpec<K, std::void_t<decltype(K::NIT)>> {
+  static constexpr bool on = true;
+  static constexpr int LB = K::LB, LE = K::LE, NIT = K::NIT;
+};
+
+template <class K, int P>
+FC_HD void call_phase(const typename K::Args& a, unsigned char* sm, int tid, long long bid, int it,
+                      typename K::Regs& r) {
+  if constexpr (LoopSpec<K>::on) K::template phase<P>(a, sm, tid, bid, it, r);
+  else K::template phase<P>(a, sm, tid, bid, r);
+}
+
 #ifndef FC_HOSTCHECK
 template <class K>
 __global__ void __launch_bounds__(K::THREADS, K::MINB) phased_kernel(const typename K::Args a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   typename K::Regs r;
-  SFor<0, K::NPHASE>::run([&](auto pc) {
-    constexpr int p = decltype(pc)::value;
-    if constexpr (p > 0) __syncthreads();
-    K::template phase<p>(a, smem_raw, (int)threadIdx.x, (long long)blockIdx.x, r);
-  });
+  using LS = LoopSpec<K>;
+  if constexpr (!LS::on) {
+    SFor<0, K::NPHASE>::run([&](auto pc) {
+      constexpr int p = decltype(pc)::value;
+      if constexpr (p > 0) __syncthreads();
+      K::template phase<p>(a, smem_raw, (int)threadIdx.x, (long long)blockIdx.x, r);
+    });
+  } else {
+    const int tid = (int)threadIdx.x;
+    const long long bid = (long long)blockIdx.x;
+    SFor<0, LS::LB>::run([&](auto pc) {
+      constexpr int p = decltype(pc)::value;
+      if constexpr (p > 0) __syncthreads();
+      K::template phase<p>(a, smem_raw, tid, bid, 0, r);
+    });
+#pragma unroll 1
+    for (int it = 0; it < LS::NIT; ++it) {
+      SFor<LS::LB, LS::LE>::run([&](auto pc) {
+        constexpr int p = decltype(pc)::value;
+        __syncthreads();
+        K::template phase<p>(a, smem_raw, tid, bid, it, r);
+      });
+    }
+    SFor<LS::LE, K::NPHASE>::run([&](auto pc) {
+      constexpr int p = decltype(pc)::value;
+      __syncthreads();
+      K::template phase<p>(a, smem_raw, tid, bid, 0, r);
+    });
+  }
 }
 #endif
 
@@ -34,11 +81,23 @@ template <class K>
 void phased_emulate(const typename K::Args& a, long long grid, size_t smem_bytes) {
   std::vector<unsigned char> smem(smem_bytes + 16);
   std::vector<typename K::Regs> regs(K::THREADS);
+  using LS = LoopSpec<K>;
   for (long long b = 0; b < grid; ++b) {
-    SFor<0, K::NPHASE>::run([&](auto pc) {
+    SFor<0, LS::LB>::run([&](auto pc) {
       constexpr int p = decltype(pc)::value;
-      for (int t = 0; t < K::THREADS; ++t) K::template phase<p>(a, smem.data(), t, b, regs[t]);
+      for (int t = 0; t < K::THREADS; ++t) call_phase<K, p>(a, smem.data(), t, b, 0, regs[t]);
     });
+    if constexpr (LS::on) {
+      for (int it = 0; it < LS::NIT; ++it)
+        SFor<LS::LB, LS::LE>::run([&](auto pc) {
+          constexpr int p = decltype(pc)::value;
+          for (int t = 0; t < K::THREADS; ++t) call_phase<K, p>(a, smem.data(), t, b, it, regs[t]);
+        });
+      SFor<LS::LE, K::NPHASE>::run([&](auto pc) {
+        constexpr int p = decltype(pc)::value;
+        for (int t = 0; t < K::THREADS; ++t) call_phase<K, p>(a, smem.data(), t, b, 0, regs[t]);
+      });
+    }
   }
 }
 
