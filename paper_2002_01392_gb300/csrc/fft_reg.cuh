@@ -1,10 +1,13 @@
 // Register-resident small DFTs with compile-time twiddles.
 //
-// A transform of length N = R1 R2 ... Rm is done as m Stockham autosort
-// passes over a register array (all indices compile-time constants after
-// template expansion, so the arrays stay in registers).  Twiddle factors are
-// evaluated at compile time by kcos2pi/ksin2pi (octant reduction + Taylor
-// series written out below), so they become immediates.
+// A length N with coprime factors N = A B (A a power of 2 or 3, B the rest) is
+// split by the prime-factor (Good-Thomas) index maps, which need no twiddle
+// factors at all: the maps are compile-time register renamings.  A prime-power
+// length R1 R2 ... Rm is done as m Stockham autosort passes over a register
+// array (all indices compile-time constants after template expansion, so the
+// arrays stay in registers).  Twiddle factors are evaluated at compile time by
+// kcos2pi/ksin2pi (octant reduction + Taylor series written out below), so
+// they become immediates; powers of i become swaps and sign changes.
 #pragma once
 #include <cuda_runtime.h>
 #include <type_traits>
@@ -169,9 +172,17 @@ __host__ __device__ __forceinline__ void stockham_pass(const cx<T>* in, cx<T>* o
       if constexpr (NS > 1 && r > 0 && ((j % NS) * r) != 0) {
         constexpr long long num = (long long)r * (j % NS);
         constexpr long long den = (long long)NS * R;
-        constexpr T c = T(kcos2pi(num, den));
-        constexpr T s = T(SIGN * ksin2pi(num, den));
-        v[r] = cmul(v[r], mk<T>(c, s));
+        if constexpr ((4 * num) % den == 0) {
+          // e^{SIGN 2 pi i q / 4} = (SIGN i)^q
+          constexpr int q = int(((4 * num) / den) % 4);
+          if constexpr (q == 1) v[r] = mul_si<SIGN>(v[r]);
+          else if constexpr (q == 2) v[r] = mk<T>(-v[r].x, -v[r].y);
+          else if constexpr (q == 3) v[r] = mul_si<-SIGN>(v[r]);
+        } else {
+          constexpr T c = T(kcos2pi(num, den));
+          constexpr T s = T(SIGN * ksin2pi(num, den));
+          v[r] = cmul(v[r], mk<T>(c, s));
+        }
       }
     });
     Radix<R, SIGN, T>::run(v);
@@ -195,12 +206,67 @@ __host__ __device__ __forceinline__ void stockham_all(cx<T>* a) {
   }
 }
 
+// Coprime split for the prime-factor algorithm: A = the 2-part of N, else
+// its 3-part; 0 when N is a prime power (no split).
+constexpr int prime_part(int n, int p) {
+  int r = 1;
+  while (n % p == 0) { n /= p; r *= p; }
+  return r;
+}
+constexpr int pfa_split(int n) {
+  const int a2 = prime_part(n, 2), a3 = prime_part(n, 3), a5 = prime_part(n, 5);
+  const int parts = (a2 > 1) + (a3 > 1) + (a5 > 1);
+  return parts < 2 ? 0 : (a2 > 1 ? a2 : a3);
+}
+// a^{-1} mod m for coprime a, m (m >= 2)
+constexpr int inv_mod(int a, int m) {
+  for (int x = 1; x < m; ++x)
+    if ((a * x) % m == 1) return x;
+  return 0;
+}
+
+template <int N, int SIGN, class T>
+__host__ __device__ __forceinline__ void dft_reg(cx<T> (&a)[N]);
+
+// Good-Thomas: n = (ia B + ib A) mod N, k = the residue pair (k mod A, k mod B),
+// so e^{-2 pi i nk/N} = e^{-2 pi i ia ka/A} e^{-2 pi i ib kb/B} and the
+// transform is a plain A x B two-dimensional DFT.
+template <int N, int A, int SIGN, class T>
+__host__ __device__ __forceinline__ void pfa_reg(cx<T> (&a)[N]) {
+  constexpr int B = N / A;
+  cx<T> t[B][A];
+  SFor<0, B>::run([&](auto bc) {
+    constexpr int ib = decltype(bc)::value;
+    SFor<0, A>::run([&](auto ac) {
+      constexpr int ia = decltype(ac)::value;
+      t[ib][ia] = a[(ia * B + ib * A) % N];
+    });
+    dft_reg<A, SIGN, T>(t[ib]);
+  });
+  constexpr int eA = B * inv_mod(B % A, A), eB = A * inv_mod(A % B, B);  // CRT idempotents
+  SFor<0, A>::run([&](auto ac) {
+    constexpr int ka = decltype(ac)::value;
+    cx<T> u[B];
+    SFor<0, B>::run([&](auto bc) {
+      constexpr int ib = decltype(bc)::value;
+      u[ib] = t[ib][ka];
+    });
+    dft_reg<B, SIGN, T>(u);
+    SFor<0, B>::run([&](auto bc) {
+      constexpr int kb = decltype(bc)::value;
+      a[(ka * eA + kb * eB) % N] = u[kb];
+    });
+  });
+}
+
 // In-place DFT of length N on a register array, natural order in and out.
 // SIGN = -1: X_k = sum x_n e^{-2 pi i nk/N};  SIGN = +1: unnormalised inverse.
 template <int N, int SIGN, class T>
 __host__ __device__ __forceinline__ void dft_reg(cx<T> (&a)[N]) {
   static_assert(smooth235(N), "register DFT needs a 2/3/5-smooth length");
-  stockham_all<N, N, 1, SIGN, T>(a);
+  constexpr int A = pfa_split(N);
+  if constexpr (A > 1) pfa_reg<N, A, SIGN, T>(a);
+  else stockham_all<N, N, 1, SIGN, T>(a);
 }
 
 }  // namespace fcns
