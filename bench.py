@@ -187,6 +187,71 @@ def bench_deriv(api, torch, dtype_np, steps, warmup, with_e2e=True):
     return res
 
 
+class CufftDerivFP64:
+    """The plain comparison path: FC-Gram z-derivatives in float64 through
+    cuFFT (torch.fft) and separate elementwise / einsum kernels, one field
+    after another.  Continuation by the plan's own M_r (Sec. 3), real DFT of
+    length N' along z, multiplication by i kz (Nyquist zeroed) and -kz^2,
+    inverse DFT, first Nz points."""
+
+    def __init__(self, api, torch, Nz, Lz=1.0, d=5, C=25):
+        self.torch = torch
+        plan = api.Plan(d, C, Nz)
+        Mr = torch.from_numpy(plan.matrix()).cuda()                 # C x d
+        self.Mr, self.Ml = Mr, torch.flip(Mr, dims=(0, 1))           # left matrix: row / column reversal
+        self.d, self.C, self.Nz, self.Np = d, C, Nz, Nz + C
+        dz = Lz / (Nz - 1)
+        k = torch.fft.rfftfreq(self.Np, d=dz / (2 * np.pi), device="cuda", dtype=torch.float64)
+        k1 = k.clone()
+        if self.Np % 2 == 0:
+            k1[-1] = 0.0
+        self.ik = (1j * k1).to(torch.complex128).view(-1, 1, 1)
+        self.mk2 = (-(k * k)).to(torch.complex128).view(-1, 1, 1)
+
+    def __call__(self, f, d1, d2):
+        torch, d, Nz, Np = self.torch, self.d, self.Nz, self.Np
+        for b in range(f.shape[0]):
+            x = f[b]
+            cont = torch.einsum("cd,dyx->cyx", self.Mr, x[Nz - d:]) + torch.einsum("cd,dyx->cyx", self.Ml, x[:d])
+            X = torch.fft.rfft(torch.cat([x, cont], dim=0), dim=0)
+            d1[b] = torch.fft.irfft(X * self.ik, n=Np, dim=0)[:Nz]
+            d2[b] = torch.fft.irfft(X * self.mk2, n=Np, dim=0)[:Nz]
+
+
+def bench_cufft64(api, torch, steps, warmup):
+    """Time the plain float64 cuFFT path on the 3 x 512^2 x 513 batch."""
+    fields, shape = deriv_workload(np.float64)
+    f = torch.empty(shape, dtype=torch.float64, device="cuda")
+    for b, sf in enumerate(fields):
+        f[b] = torch.from_numpy(sf.field(0)).cuda()
+    d1, d2 = torch.empty_like(f), torch.empty_like(f)
+    run = CufftDerivFP64(api, torch, shape[1])
+    for _ in range(warmup):
+        run(f, d1, d2)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        ev[i][0].record(stream)
+        run(f, d1, d2)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    times = np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3
+    pts = int(np.prod(shape))
+    res = {"points": pts, "p50_ms": float(np.percentile(times, 50) * 1e3),
+           "p99_ms": float(np.percentile(times, 99) * 1e3), "grid_points_per_s": pts / float(times.mean()),
+           "what": "torch.fft (cuFFT) float64 + separate einsum / elementwise kernels, one field at a time"}
+    # agreement with the library's float64 kernel on the same input (both are the FC derivative)
+    plan = api.Plan(5, 25, shape[1])
+    e1, e2 = torch.empty_like(f), torch.empty_like(f)
+    api.fc_deriv_z(plan, f, e1, e2)
+    res["rel_l2_diff_d1_vs_library_fp64"] = float((e1 - d1).norm() / e1.norm())
+    res["rel_l2_diff_d2_vs_library_fp64"] = float((e2 - d2).norm() / e2.norm())
+    del f, d1, d2, e1, e2
+    torch.cuda.empty_cache()
+    return res
+
+
 RK_SHAPE = (1024, 1024, 513)
 
 
@@ -224,7 +289,7 @@ def bench_rk(api, torch, steps, warmup, with_e2e=True, shape=None):
            "seconds_per_step_mean": float(times.mean()), "p50_ms": float(np.percentile(times, 50) * 1e3),
            "p99_ms": float(np.percentile(times, 99) * 1e3),
            "rk_stage_grid_points_per_s": pts * 3 * steps / total, "workspace_GB": ws_bytes / 1e9,
-           "launches_per_step": 3 * 6}
+           "launches_per_step": 3 * 7}
     out = sim.get_fields()
     res["finite"] = bool(torch.isfinite(out).all().item())
     res["w_wall_rel"] = float(out[2, [0, -1]].abs().max().item() / max(out[:3].abs().max().item(), 1e-300))
@@ -384,6 +449,9 @@ def main():
         r32 = bench_deriv(api, torch, np.float32, args.steps, args.warmup)
         rk = None if args.no_rk else bench_rk(api, torch, args.rk_steps, 3)
     r64 = bench_deriv(api, torch, np.float64, max(3, args.steps // 4), 2, with_e2e=False)
+    rc = bench_cufft64(api, torch, max(3, args.steps // 4), 2)
+    # companion: the paper's kind of smooth N' (512 = 487 + 25): direct length-N' z transforms
+    rks = None if args.no_rk else bench_rk(api, torch, args.rk_steps, 2, with_e2e=False, shape=(1024, 1024, 487))
     # companion: the paper's kind of smooth N' (512 = 487 + 25) at the same horizontal size
     DERIV_SHAPE = (3, 512, 512, 487)
     rs = bench_deriv(api, torch, np.float32, args.steps, 2, with_e2e=False)
@@ -401,8 +469,10 @@ def main():
                        arm="FP32 transforms, continuation in float-float (FP64-level)"),
         "p50_ms": r32["p50_ms"], "p99_ms": r32["p99_ms"],
         "fc_deriv_z": {"fp32": {k: v for k, v in r32.items() if k != "e2e"}, "fp64": r64,
-                       "fp32_smooth_Np512_3x512x512x487": rs},
+                       "fp32_smooth_Np512_3x512x512x487": rs, "cufft_fp64_plain": rc,
+                       "fp32_speedup_vs_cufft_fp64_plain": r32["grid_points_per_s"] / rc["grid_points_per_s"]},
         "rk_stage": rk,
+        "rk_stage_smooth_Np512_1024x1024x487": rks,
         "roofline": {"bound": "hbm", "achieved": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9,
                      "peak": hbm_peak, "unit": "GB/s",
                      "frac": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9 / hbm_peak,

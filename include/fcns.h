@@ -66,7 +66,10 @@ const char* fc_last_error(void);
  * QR of the Vandermonde matrix on the d matching points and oversampled
  * least-squares Fourier continuations of each Gram polynomial with
  * periodicity interval [1 - delta_r, 2b - (1 - delta_r)]).  Host only; the
- * tables are computed in binary128 (_Float128) and rounded to double.
+ * tables are computed in binary128 (_Float128) for d <= 5 and in
+ * double-binary128 (about 67 digits) for d >= 6, whose fits -- e.g. the
+ * paper's d = 7, C = 33 -- are too ill-conditioned for 34 digits, and rounded
+ * to double.
  *   d   number of matching points, 2 <= d <= 10.
  *   C   number of continuation points, d <= C <= 64.
  *   Nz  number of physical z points including both walls, Nz >= 2 d.
@@ -182,6 +185,14 @@ fc_status ns_workspace_bytes(const ns_params* p, size_t* bytes);
  * every device buffer; if it is NULL the library allocates it itself with
  * cudaMalloc and frees it in ns_destroy.  Creation uploads tables with
  * synchronous copies on the current device.
+ * z transforms: when N' = Nz + C is itself a compiled length (64, 128, 256,
+ * 512, 768, 1024 -- the paper's choice of smooth N') the z derivatives and
+ * filter are length-N' spectral multipliers and the projection's DFTs plain
+ * length-N' transforms; otherwise they are circular convolutions and
+ * Bluestein DFTs on a padded length L >= max(N' + Nz - 1, 2 N' - 1) (160,
+ * 288, 320, 576 or 1080).  FC_ERR_UNSUPPORTED when no compiled length fits,
+ * Nx or Ny is not one of 16, 32, 64, 96, 128, 192, 256, 512, 1024, or, in
+ * double precision, L > 576 or Nx > 512.
  */
 fc_status ns_create(const ns_params* p, void* dev_workspace, size_t bytes, ns_sim_t* out);
 

@@ -1,4 +1,5 @@
-// Host-side tables in binary128 arithmetic.
+// Host-side tables in binary128 arithmetic (double-binary128 where the FC
+// fits need more than 34 digits).
 //
 // FC-Gram tables follow App. B of the paper: Gram basis from the QR
 // factorisation of the Vandermonde matrix of the d matching points (the basis
@@ -76,85 +77,212 @@ void sincos2pi(long long num, long long den, double* c, double* s) {
   *s = (double)sq;
 }
 
+// ---------------------------------------------------------------------------
+// Double-binary128 ("qq") arithmetic: a value is hi + lo, |lo| <= ulp(hi)/2,
+// about 226 significant bits (67 digits).  The FC tables need it for d >= 6:
+// the least-squares continuation fits for (d, C) = (7, 33), M = 26 are so
+// ill-conditioned that binary128 (34 digits) leaves ~1e-12 relative error in
+// M_r, while 45 digits reproduce it to double precision.  Built from the
+// error-free transformations of Knuth (two-sum) and Dekker (two-product with
+// the 2^57 + 1 splitter for the 113-bit binary128 significand).
+// ---------------------------------------------------------------------------
+struct qq {
+  q hi = 0, lo = 0;
+  qq() = default;
+  qq(q h) : hi(h) {}
+  qq(q h, q l) : hi(h), lo(l) {}
+  qq(int i) : hi((q)i) {}
+  qq(long long i) : hi((q)i) {}
+  explicit operator double() const { return (double)hi + (double)lo; }
+};
+static inline qq quick_two_sum(q a, q b) {
+  const q s = a + b;
+  return qq(s, b - (s - a));
+}
+static inline qq two_sum(q a, q b) {
+  const q s = a + b, bb = s - a;
+  return qq(s, (a - (s - bb)) + (b - bb));
+}
+static inline void dekker_split(q a, q* h, q* l) {
+  const q t = (q)144115188075855873LL * a;  // (2^57 + 1) a
+  *h = t - (t - a);
+  *l = a - *h;
+}
+static inline qq two_prod(q a, q b) {
+  const q p = a * b;
+  q ah, al, bh, bl;
+  dekker_split(a, &ah, &al);
+  dekker_split(b, &bh, &bl);
+  return qq(p, ((ah * bh - p) + ah * bl + al * bh) + al * bl);
+}
+static inline qq operator+(qq a, qq b) {
+  qq s = two_sum(a.hi, b.hi);
+  const qq t = two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return quick_two_sum(s.hi, s.lo);
+}
+static inline qq operator-(qq a) { return qq(-a.hi, -a.lo); }
+static inline qq operator-(qq a, qq b) { return a + (-b); }
+static inline qq operator*(qq a, qq b) {
+  qq p = two_prod(a.hi, b.hi);
+  p.lo += a.hi * b.lo + a.lo * b.hi;
+  return quick_two_sum(p.hi, p.lo);
+}
+static inline qq operator/(qq a, qq b) {
+  const q q1 = a.hi / b.hi;
+  qq r = a - b * qq(q1);
+  const q q2 = r.hi / b.hi;
+  r = r - b * qq(q2);
+  const q q3 = r.hi / b.hi;
+  return quick_two_sum(q1, q2) + qq(q3);
+}
+static inline qq& operator+=(qq& a, qq b) { return a = a + b; }
+static inline qq& operator-=(qq& a, qq b) { return a = a - b; }
+static inline qq& operator*=(qq& a, qq b) { return a = a * b; }
+static inline qq& operator/=(qq& a, qq b) { return a = a / b; }
+static inline bool operator<(qq a, qq b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+static inline bool operator>(qq a, qq b) { return b < a; }
+static inline bool operator<=(qq a, qq b) { return !(b < a); }
+static inline bool operator==(qq a, qq b) { return a.hi == b.hi && a.lo == b.lo; }
+
+// scalar traits used by the generic table construction below
+template <class S> struct Sc;
+template <> struct Sc<q> {
+  static q sqrt(q x) { return q_sqrt(x); }
+  static q tiny() { return (q)1e-40; }
+};
+template <> struct Sc<qq> {
+  static qq sqrt(qq x) {
+    if (x.hi <= 0) return qq(0);
+    const qq y(q_sqrt(x.hi));
+    return y + (x - y * y) / (qq(2) * y);  // one Newton step doubles the 113 bits
+  }
+  static qq tiny() { return qq((q)1e-75); }
+};
+
+// atan(1/x) by its alternating series, pi by Machin's formula
+template <class S>
+static S g_atan_inv(int x) {
+  const S x2 = S(x) * S(x);
+  S term = S(1) / S(x), sum = term;
+  for (int k = 1; k < 800; ++k) {
+    term /= x2;
+    const S t = term / S(2 * k + 1);
+    sum += (k & 1) ? -t : t;
+    if (t < Sc<S>::tiny()) break;
+  }
+  return sum;
+}
+template <class S>
+static S g_pi() {
+  static const S pi = S(16) * g_atan_inv<S>(5) - S(4) * g_atan_inv<S>(239);
+  return pi;
+}
+template <class S>
+static void g_sincos2pi(long long num, long long den, S* c, S* s) {
+  long long r = ((num % den) + den) % den;
+  long long m4 = (8 * r + den) / (2 * den);
+  long long resid = 4 * r - m4 * den;
+  int m = int(m4 & 3);
+  const S psi = S(2) * g_pi<S>() * (S(resid) / S(4 * den));
+  // Taylor series, |psi| <= pi/4: 40 terms reach 1e-100
+  const S x2 = psi * psi;
+  S ts = psi, tc = S(1), sn = psi, cs = S(1);
+  for (int n = 1; n < 40; ++n) {
+    ts *= -x2 / S((2 * n) * (2 * n + 1));
+    tc *= -x2 / S((2 * n - 1) * (2 * n));
+    sn += ts;
+    cs += tc;
+  }
+  switch (m) {
+    case 0: *c = cs; *s = sn; break;
+    case 1: *c = -sn; *s = cs; break;
+    case 2: *c = -cs; *s = -sn; break;
+    default: *c = sn; *s = -cs; break;
+  }
+}
+
 // Householder QR least squares: minimise |A x - b| for A (m x n, m >= n),
 // several right-hand sides.  A is overwritten.
-static void lsq_solve(std::vector<q>& A, int m, int n, std::vector<std::vector<q>>& rhs,
-                      std::vector<std::vector<q>>* sol) {
-  std::vector<q> v(m);
+template <class S>
+static void lsq_solve(std::vector<S>& A, int m, int n, std::vector<std::vector<S>>& rhs,
+                      std::vector<std::vector<S>>* sol) {
+  std::vector<S> v(m);
   for (int k = 0; k < n; ++k) {
-    q norm = 0;
+    S norm = 0;
     for (int i = k; i < m; ++i) norm += A[i * n + k] * A[i * n + k];
-    norm = q_sqrt(norm);
-    q alpha = A[k * n + k] > 0 ? -norm : norm;
+    norm = Sc<S>::sqrt(norm);
+    S alpha = A[k * n + k] > S(0) ? -norm : norm;
     for (int i = 0; i < m; ++i) v[i] = 0;
     v[k] = A[k * n + k] - alpha;
     for (int i = k + 1; i < m; ++i) v[i] = A[i * n + k];
-    q vnorm2 = 0;
+    S vnorm2 = 0;
     for (int i = k; i < m; ++i) vnorm2 += v[i] * v[i];
-    if (vnorm2 == 0) continue;
+    if (vnorm2 == S(0)) continue;
     for (int j = k; j < n; ++j) {
-      q dot = 0;
+      S dot = 0;
       for (int i = k; i < m; ++i) dot += v[i] * A[i * n + j];
-      q f = 2 * dot / vnorm2;
+      S f = S(2) * dot / vnorm2;
       for (int i = k; i < m; ++i) A[i * n + j] -= f * v[i];
     }
     for (auto& b : rhs) {
-      q dot = 0;
+      S dot = 0;
       for (int i = k; i < m; ++i) dot += v[i] * b[i];
-      q f = 2 * dot / vnorm2;
+      S f = S(2) * dot / vnorm2;
       for (int i = k; i < m; ++i) b[i] -= f * v[i];
     }
   }
-  sol->assign(rhs.size(), std::vector<q>(n));
+  sol->assign(rhs.size(), std::vector<S>(n));
   for (size_t r = 0; r < rhs.size(); ++r) {
     auto& x = (*sol)[r];
     for (int k = n - 1; k >= 0; --k) {
-      q s = rhs[r][k];
+      S s = rhs[r][k];
       for (int j = k + 1; j < n; ++j) s -= A[k * n + j] * x[j];
       x[k] = s / A[k * n + k];
     }
   }
 }
 
-bool build_fc_tables(int d, int C, int M, int n_os, FcTables* out) {
-  if (d < 2 || d > 10 || C < d || C > 64 || M < 1 || n_os < 1) return false;
+template <class S>
+static bool build_fc_tables_in(int d, int C, int M, int n_os, FcTables* out) {
   const int P = 2 * (d + C);  // Fourier period in grid units
-  // --- Gram basis: Householder QR of the Vandermonde V[i][p] = t_i^p, t_i = i
-  std::vector<q> V(d * d);
+  // --- Gram basis: orthonormalise the Vandermonde columns V[i][p] = t_i^p, t_i = i
+  std::vector<S> V(d * d);
   for (int i = 0; i < d; ++i) {
-    q tp = 1;
-    for (int p = 0; p < d; ++p) { V[i * d + p] = tp; tp *= (q)i; }
+    S tp = 1;
+    for (int p = 0; p < d; ++p) { V[i * d + p] = tp; tp *= S(i); }
   }
-  // modified Gram-Schmidt in binary128 on the columns gives Q (d x d) and R
-  std::vector<q> Qm(d * d), R(d * d, 0);
+  // modified Gram-Schmidt on the columns gives Q (d x d) and R
+  std::vector<S> Qm(d * d), R(d * d, S(0));
   for (int k = 0; k < d; ++k) {
-    std::vector<q> col(d);
+    std::vector<S> col(d);
     for (int i = 0; i < d; ++i) col[i] = V[i * d + k];
     for (int pass = 0; pass < 2; ++pass)  // re-orthogonalise once
       for (int j = 0; j < k; ++j) {
-        q dot = 0;
+        S dot = 0;
         for (int i = 0; i < d; ++i) dot += Qm[i * d + j] * col[i];
         R[j * d + k] += dot;
         for (int i = 0; i < d; ++i) col[i] -= dot * Qm[i * d + j];
       }
-    q nrm = 0;
+    S nrm = 0;
     for (int i = 0; i < d; ++i) nrm += col[i] * col[i];
-    nrm = q_sqrt(nrm);
+    nrm = Sc<S>::sqrt(nrm);
     R[k * d + k] = nrm;
     for (int i = 0; i < d; ++i) Qm[i * d + k] = col[i] / nrm;
   }
   // polynomial coefficients of Gram polynomial k: Q = V R^{-1}, so c_k = column k of R^{-1}
-  std::vector<q> Rinv(d * d, 0);
+  std::vector<S> Rinv(d * d, S(0));
   for (int k = 0; k < d; ++k) {
-    // solve R x = e_k
-    for (int i = d - 1; i >= 0; --i) {
-      q s = (i == k) ? 1 : 0;
+    for (int i = d - 1; i >= 0; --i) {  // solve R x = e_k
+      S s = (i == k) ? S(1) : S(0);
       for (int j = i + 1; j < d; ++j) s -= R[i * d + j] * Rinv[j * d + k];
       Rinv[i * d + k] = s / R[i * d + i];
     }
   }
-  auto gram_val = [&](int k, q t) {
-    q s = 0, tp = 1;
+  auto gram_val = [&](int k, S t) {
+    S s = 0, tp = 1;
     for (int p = 0; p < d; ++p) { s += Rinv[p * d + k] * tp; tp *= t; }
     return s;
   };
@@ -162,51 +290,51 @@ bool build_fc_tables(int d, int C, int M, int n_os, FcTables* out) {
   const int npt = (d - 1) * n_os + 1;
   const int m = 2 * npt, n = 2 * M + 1;
   if (m < n) return false;
-  std::vector<q> A(m * n);
+  std::vector<S> A(m * n);
   std::vector<long long> tnum(m);  // t = tnum / n_os
   for (int i = 0; i < npt; ++i) { tnum[i] = i; tnum[npt + i] = (long long)(d + C) * n_os + i; }
   for (int r = 0; r < m; ++r) {
     A[r * n] = 1;
     for (int mm = 1; mm <= M; ++mm) {
-      q c, s;
-      q_sincos2pi((long long)mm * tnum[r], (long long)P * n_os, &c, &s);
+      S c, s;
+      g_sincos2pi<S>((long long)mm * tnum[r], (long long)P * n_os, &c, &s);
       A[r * n + 2 * mm - 1] = c;
       A[r * n + 2 * mm] = s;
     }
   }
-  std::vector<q> Acopy = A;
-  std::vector<std::vector<q>> rhs(d, std::vector<q>(m, 0));
+  std::vector<S> Acopy = A;
+  std::vector<std::vector<S>> rhs(d, std::vector<S>(m, S(0)));
   for (int k = 0; k < d; ++k)
-    for (int i = 0; i < npt; ++i) rhs[k][i] = gram_val(k, (q)tnum[i] / (q)n_os);
-  std::vector<std::vector<q>> rhs0 = rhs, sol;
-  lsq_solve(A, m, n, rhs, &sol);
+    for (int i = 0; i < npt; ++i) rhs[k][i] = gram_val(k, S(tnum[i]) / S(n_os));
+  std::vector<std::vector<S>> rhs0 = rhs, sol;
+  lsq_solve<S>(A, m, n, rhs, &sol);
   // residuals
   double worst = 0;
   for (int k = 0; k < d; ++k) {
-    q rr = 0, bb = 0;
+    S rr = 0, bb = 0;
     for (int r = 0; r < m; ++r) {
-      q s = 0;
+      S s = 0;
       for (int j = 0; j < n; ++j) s += Acopy[r * n + j] * sol[k][j];
-      q e = s - rhs0[k][r];
+      S e = s - rhs0[k][r];
       rr += e * e;
       bb += rhs0[k][r] * rhs0[k][r];
     }
-    double rel = (double)q_sqrt(rr / bb);
+    const double rel = (double)Sc<S>::sqrt(rr / bb);
     if (rel > worst) worst = rel;
   }
   // --- evaluate the continuations at t = d + j and form M_r = A_r Q^T
-  std::vector<q> Ar(C * d);
+  std::vector<S> Ar(C * d);
   for (int j = 0; j < C; ++j) {
-    std::vector<q> row(n);
+    std::vector<S> row(n);
     row[0] = 1;
     for (int mm = 1; mm <= M; ++mm) {
-      q c, s;
-      q_sincos2pi((long long)mm * (d + j), P, &c, &s);
+      S c, s;
+      g_sincos2pi<S>((long long)mm * (d + j), P, &c, &s);
       row[2 * mm - 1] = c;
       row[2 * mm] = s;
     }
     for (int k = 0; k < d; ++k) {
-      q s = 0;
+      S s = 0;
       for (int jj = 0; jj < n; ++jj) s += row[jj] * sol[k][jj];
       Ar[j * d + k] = s;
     }
@@ -216,11 +344,18 @@ bool build_fc_tables(int d, int C, int M, int n_os, FcTables* out) {
   out->Mr.assign(C * d, 0.0);
   for (int j = 0; j < C; ++j)
     for (int i = 0; i < d; ++i) {
-      q s = 0;
+      S s = 0;
       for (int k = 0; k < d; ++k) s += Ar[j * d + k] * Qm[i * d + k];
       out->Mr[j * d + i] = (double)s;
     }
   return true;
+}
+
+bool build_fc_tables(int d, int C, int M, int n_os, FcTables* out) {
+  if (d < 2 || d > 10 || C < d || C > 64 || M < 1 || n_os < 1) return false;
+  // binary128 reproduces the d = 5 tables to double precision; larger d needs
+  // the double-binary128 arithmetic
+  return d <= 5 ? build_fc_tables_in<q>(d, C, M, n_os, out) : build_fc_tables_in<qq>(d, C, M, n_os, out);
 }
 
 // direct DFT helpers on binary128 with a root table
@@ -297,6 +432,11 @@ void filter_conv_spectrum(int Nz, int Np, int L, double beta, double two_p,
     if (Np % 2 == 0 && l == Np / 2) ls = -Np / 2;
     const double x = std::fabs((double)ls) / (Np / 2.0);
     fz[l] = (q)std::exp(-beta * std::pow(x, two_p));
+  }
+  if (L == Np) {  // circular convolution of length N' itself: the filter factors, / N'
+    Hf->assign(L, 0);
+    for (int l = 0; l < Np; ++l) (*Hf)[l] = std::complex<double>((double)(fz[l] / (q)Np), 0.0);
+    return;
   }
   const int jlo = -(Np - 1), jhi = Nz - 1;
   std::vector<q> h(jhi - jlo + 1);

@@ -1,14 +1,14 @@
-// Instantiation of the z-line kernels of the Navier-Stokes step (double).
+// Instantiation of the z-line kernels of the Navier-Stokes step (double), padded lengths.
 #include "dev_run.cuh"
 #include "ns_kernels.cuh"
 #include "shapes.hpp"
 
 namespace fcns {
-#define FC_INST_Z(LL, A, B)                                            \
+#define FC_INST_Z(LL, A, B, D)                                            \
   template struct DevRun<KZDeriv<double, A, B, z_lines<double, LL>()>>;    \
   template struct DevRun<KZCombine<double, A, B, z_lines<double, LL>()>>;  \
-  template struct DevRun<KZProject<double, A, B, zproj_lines<double, LL>()>>;
-FC_ZSHAPES(FC_INST_Z)
+  template struct DevRun<KZProject<double, A, B, zproj_lines<double, LL>(), D>>;
+FC_ZSHAPES_PADDED(FC_INST_Z)
 #undef FC_INST_Z
 template struct DevRun<KZContinue<double, 8>>;
 template struct DevRun<KDiag<double>>;

@@ -1,14 +1,14 @@
-// Instantiation of the z-line kernels of the Navier-Stokes step (float).
+// Instantiation of the z-line kernels of the Navier-Stokes step (float), padded lengths.
 #include "dev_run.cuh"
 #include "ns_kernels.cuh"
 #include "shapes.hpp"
 
 namespace fcns {
-#define FC_INST_Z(LL, A, B)                                            \
+#define FC_INST_Z(LL, A, B, D)                                            \
   template struct DevRun<KZDeriv<float, A, B, z_lines<float, LL>()>>;    \
   template struct DevRun<KZCombine<float, A, B, z_lines<float, LL>()>>;  \
-  template struct DevRun<KZProject<float, A, B, zproj_lines<float, LL>()>>;
-FC_ZSHAPES(FC_INST_Z)
+  template struct DevRun<KZProject<float, A, B, zproj_lines<float, LL>(), D>>;
+FC_ZSHAPES_PADDED(FC_INST_Z)
 #undef FC_INST_Z
 template struct DevRun<KZContinue<float, 8>>;
 template struct DevRun<KDiag<float>>;

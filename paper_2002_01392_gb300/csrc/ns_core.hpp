@@ -18,6 +18,7 @@ namespace fcns {
 
 struct NsLayout {
   int Nx, Ny, Nz, Np, Kx, Kxp, nf, L, L1, L2, Lx1, Lx2, Ly1, Ly2;
+  bool zdirect;   // L = N' (plain length-N' z transforms)
   long long lines, ntiles, plines;   // lines, tiles of TL lines, padded lines
   size_t es;  // bytes per real
   // byte offsets inside the workspace
@@ -29,10 +30,17 @@ struct NsLayout {
   size_t total;
 };
 
-inline bool z_shape_for(int need, int* L, int* L1, int* L2) {
+// z transform for continued length Np: Np itself when it is a compiled direct
+// length, else the smallest padded length >= max(Np + Nz - 1, 2 Np - 1)
+inline bool z_shape_for(int Np, int Nz, int* L, int* L1, int* L2, bool* direct) {
   int best = 0;
-#define FC_ZPICK(LL, A, B) \
-  if (!best && LL >= need) { best = LL; *L1 = A; *L2 = B; }
+#define FC_ZDIRECT(LL, A, B, D) \
+  if (D && !best && LL == Np) { best = LL; *L1 = A; *L2 = B; *direct = true; }
+  FC_ZSHAPES(FC_ZDIRECT)
+#undef FC_ZDIRECT
+  const int need = std::max(Np + Nz - 1, 2 * Np - 1);
+#define FC_ZPICK(LL, A, B, D) \
+  if (!D && !best && LL >= need) { best = LL; *L1 = A; *L2 = B; *direct = false; }
   FC_ZSHAPES(FC_ZPICK)
 #undef FC_ZPICK
   *L = best;
@@ -60,8 +68,7 @@ inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
   l.ntiles = (l.lines + TL - 1) / TL;
   l.plines = l.ntiles * TL;
   l.es = p.prec == FC_F32 ? 4 : 8;
-  const int need = std::max(l.Np + p.Nz - 1, 2 * l.Np - 1);
-  if (!z_shape_for(need, &l.L, &l.L1, &l.L2)) return FC_ERR_UNSUPPORTED;
+  if (!z_shape_for(l.Np, p.Nz, &l.L, &l.L1, &l.L2, &l.zdirect)) return FC_ERR_UNSUPPORTED;
   if (!xy_shape_for(p.Nx, &l.Lx1, &l.Lx2) || !xy_shape_for(p.Ny, &l.Ly1, &l.Ly2)) return FC_ERR_UNSUPPORTED;
   if (p.prec == FC_F64 && (l.L > 576 || p.Nx > 512)) return FC_ERR_UNSUPPORTED;
   const size_t cs = 2 * l.es;
@@ -143,7 +150,13 @@ struct NsCore {
     engine_twiddles(l.L1, l.L2, &twz);
     deriv_conv_spectra(p.Nz, l.Np, l.L, &H1, &H2);
     filter_conv_spectrum(p.Nz, l.Np, l.L, p.filter_beta, p.filter_2p, &Hf);
-    bluestein_tables(l.Np, l.L, &chirp, &Hbf, &Hbi);
+    if (l.zdirect) {  // no Bluestein DFTs
+      chirp.assign(l.Np, 0);
+      Hbf.assign(l.L, 0);
+      Hbi.assign(l.L, 0);
+    } else {
+      bluestein_tables(l.Np, l.L, &chirp, &Hbf, &Hbi);
+    }
     std::vector<double> d2r, hfr;
     z_kernels_real(p.Nz, l.Np, p.filter_beta, p.filter_2p, &d2r, &hfr);
     engine_twiddles(l.Lx1, l.Lx2, &twx);
@@ -229,7 +242,7 @@ struct NsCore {
   template <class T>
   fc_status z_deriv(const cx<T>* X, int nf, void* st) {
     fc_status s = FC_ERR_UNSUPPORTED;
-#define FC_ZD(LL, A, B)                                                        \
+#define FC_ZD(LL, A, B, D)                                                        \
   if (l.L == LL) {                                                            \
     using K = KZDeriv<T, A, B, z_lines<T, LL>()>;                             \
     typename K::Args a;                                                       \
@@ -249,7 +262,7 @@ struct NsCore {
   fc_status z_combine(const cx<T>* NL, const cx<T>* Xt, const cx<T>* Xj, cx<T>* Xo, double dtj, int inject,
                       int nf, void* st) {
     fc_status s = FC_ERR_UNSUPPORTED;
-#define FC_ZC(LL, A, B)                                                        \
+#define FC_ZC(LL, A, B, D)                                                        \
   if (l.L == LL) {                                                            \
     using K = KZCombine<T, A, B, z_lines<T, LL>()>;                           \
     typename K::Args a;                                                       \
@@ -277,9 +290,9 @@ struct NsCore {
   template <class T>
   fc_status z_project(cx<T>* X, double dtj, void* st) {
     fc_status s = FC_ERR_UNSUPPORTED;
-#define FC_ZP(LL, A, B)                                                        \
+#define FC_ZP(LL, A, B, D)                                                        \
   if (l.L == LL) {                                                            \
-    using K = KZProject<T, A, B, zproj_lines<T, LL>()>;                       \
+    using K = KZProject<T, A, B, zproj_lines<T, LL>(), D>;                       \
     typename K::Args a;                                                       \
     a.g = zgeom(3); a.t = ztab<T>(); a.X = X; a.gradp = at<double2>(l.gradp); \
     a.G0 = at<cx<T>>(l.DZ); a.G1 = at<cx<T>>(l.DZZ); a.dtj = dtj;             \

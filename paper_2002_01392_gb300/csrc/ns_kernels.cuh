@@ -400,11 +400,13 @@ struct KZContinue {
 //   grad phi^H = (i kx Phi, i ky Phi, Phi'),  Phi = A e^{g(z-Lz)} + B e^{-g z}
 //   X     -= grad phi^I + FC(grad phi^H);  walls <- grad_par phi / dt_j.
 // DFTs of length N' by Bluestein (chirp, circular convolution of length L,
-// chirp), done one after another through a single exchange buffer; the
+// chirp), or, when N' itself is a compiled length (DIRECT, L = N'), by one
+// length-N' transform each; done one after another through a single exchange
+// buffer; the
 // intermediate lines (Y^, s, sigma, sigma_z) go to two global scratch
 // arrays G0, G1 of [N'][lines] (owned element by element by one thread).
 // ===========================================================================
-template <class T, int L1, int L2, int LINES>
+template <class T, int L1, int L2, int LINES, bool DIRECT>
 struct KZProject {
   using E = Eng<T, L1, L2, LINES>;
   using C = cx<T>;
@@ -436,6 +438,55 @@ struct KZProject {
     return c;
   }
 
+  // Output value n of DFT `it` from the raw transform result `val`, and what
+  // the projection does with it (K = min(it, 2)):
+  //   it 0: Y^ -> G0;  it 1: W^, s = (Y^ + kz W^) / k^2 -> G0;
+  //   it 2: sigma -> G1 and its wall values;  it 3: sigma_z -> G0, b and t.
+  template <int K>
+  static FC_HD void post(const Args& a, int it, int n, C val, T kxo, T kyo, T invNp, C* g0, C* g1,
+                         const C* xw, double* W) {
+    const int Nz = a.g.Nz, Np = a.g.Np;
+    if constexpr (K < 2) {
+      if constexpr (!DIRECT) val = cmul(val, a.t.chirp[n]);
+      if constexpr (K == 0) {
+        g0[n * TL] = val;
+      } else {
+        const T kz = a.t.kzo[n];
+        const T k2 = kxo * kxo + kyo * kyo + kz * kz;
+        const T inv = k2 > T(0) ? T(1) / k2 : T(0);
+        g0[n * TL] = cscale(cadd(g0[n * TL], cscale(val, kz)), inv);
+      }
+    } else {
+      // direct: the inverse DFT is conj(DFT(conj(.)))
+      if constexpr (DIRECT) val = mk<T>(val.x, -val.y);
+      else val = cmul(val, cchirp(a.t, n, Np));
+      const C sg = cscale(val, invNp);
+      if (it == 2) {
+        g1[n * TL] = sg;
+        if (n == 0 || n == Nz - 1) {
+          const int o = (n == 0) ? 4 : 6;
+          W[o] = (double)sg.x;
+          W[o + 1] = (double)sg.y;
+        }
+      } else {
+        g0[n * TL] = sg;
+        if (n == 0 || n == Nz - 1) {
+          const C w = xw[n * TL];
+          const int o = (n == 0) ? 0 : 2;
+          W[o] = (double)w.x - (double)sg.x;
+          W[o + 1] = (double)w.y - (double)sg.y;
+        }
+      }
+    }
+  }
+  // f(integral_constant<K>) with K = min(it, 2), the branch taken outside the element loops
+  template <class F>
+  static FC_HD void by_kind(int it, F&& f) {
+    if (it == 0) f(std::integral_constant<int, 0>{});
+    else if (it == 1) f(std::integral_constant<int, 1>{});
+    else f(std::integral_constant<int, 2>{});
+  }
+
   template <int P>
   static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, int it, Regs& R) {
     C* b0 = reinterpret_cast<C*>(sm);
@@ -459,7 +510,7 @@ struct KZProject {
 
     if constexpr (P == 0) {
       load_mr<T>(sm + off_M, a.t, a.g.Cc * d, tid, THREADS);
-    } else if constexpr (P == 1) {  // Bluestein input of transform `it`
+    } else if constexpr (P == 1) {  // input of transform `it`
       if (r < L2) {
         if (it == 0) {  // Y = kx u + ky v
 #pragma unroll
@@ -468,7 +519,7 @@ struct KZProject {
             C y = mk<T>(0, 0);
             if (valid && n < Np) {
               y = cadd(cscale(xu[n * TL], kxo), cscale(xv[n * TL], kyo));
-              y = cmul(y, a.t.chirp[n]);
+              if constexpr (!DIRECT) y = cmul(y, a.t.chirp[n]);
             }
             R.v[j] = y;
           }
@@ -476,7 +527,12 @@ struct KZProject {
 #pragma unroll
           for (int j = 0; j < L1; ++j) {
             const int n = r + L2 * j;
-            R.v[j] = (valid && n < Np) ? cmul(xw[n * TL], a.t.chirp[n]) : mk<T>(0, 0);
+            C y = mk<T>(0, 0);
+            if (valid && n < Np) {
+              y = xw[n * TL];
+              if constexpr (!DIRECT) y = cmul(y, a.t.chirp[n]);
+            }
+            R.v[j] = y;
           }
         } else {  // s (it = 2) or kz s (it = 3), inverse DFT input
 #pragma unroll
@@ -486,7 +542,8 @@ struct KZProject {
             if (valid && n < Np) {
               x = g0[n * TL];
               if (it == 3) x = cscale(x, a.t.kzo[n]);
-              x = cmul(x, cchirp(a.t, n, Np));
+              if constexpr (DIRECT) x.y = -x.y;
+              else x = cmul(x, cchirp(a.t, n, Np));
             }
             R.v[j] = x;
           }
@@ -496,56 +553,33 @@ struct KZProject {
     } else if constexpr (P == 2) {
       if (r < L1) {
         E::template B<-1>(R.u, b0, r, li);
-        E::mulH(R.u, it < 2 ? a.t.Hbf : a.t.Hbi, r);
-        E::template Bi<1>(R.u, b0, a.t.tw, r, li);
+        if constexpr (DIRECT) {
+          // L = N': thread k1 holds DFT values k1 + L1 k2, final
+          if (valid) {
+            by_kind(it, [&](auto kc) {
+              constexpr int K = decltype(kc)::value;
+#pragma unroll
+              for (int k2 = 0; k2 < L2; ++k2) post<K>(a, it, r + L1 * k2, R.u[k2], kxo, kyo, invNp, g0, g1, xw, W);
+            });
+          }
+        } else {
+          E::mulH(R.u, it < 2 ? a.t.Hbf : a.t.Hbi, r);
+          E::template Bi<1>(R.u, b0, a.t.tw, r, li);
+        }
       }
     } else if constexpr (P == 3) {  // Bluestein output of transform `it`
-      if (r < L2) {
-        E::template Ai<1>(R.v, b0, r, li);
-        if (!valid) return;
-        if (it == 0) {  // Y^ -> G0
+      if constexpr (!DIRECT) {
+        if (r < L2) {
+          E::template Ai<1>(R.v, b0, r, li);
+          if (!valid) return;
+          by_kind(it, [&](auto kc) {
+            constexpr int K = decltype(kc)::value;
 #pragma unroll
-          for (int j = 0; j < L1; ++j) {
-            const int n = r + L2 * j;
-            if (n < Np) g0[n * TL] = cmul(R.v[j], a.t.chirp[n]);
-          }
-        } else if (it == 1) {  // W^, s = (Y^ + kz W^) / k^2 -> G0
-          const T kp2 = kxo * kxo + kyo * kyo;
-#pragma unroll
-          for (int j = 0; j < L1; ++j) {
-            const int n = r + L2 * j;
-            if (n < Np) {
-              const C wh = cmul(R.v[j], a.t.chirp[n]);
-              const T kz = a.t.kzo[n];
-              const T k2 = kp2 + kz * kz;
-              const T inv = k2 > T(0) ? T(1) / k2 : T(0);
-              g0[n * TL] = cscale(cadd(g0[n * TL], cscale(wh, kz)), inv);
+            for (int j = 0; j < L1; ++j) {
+              const int n = r + L2 * j;
+              if (n < Np) post<K>(a, it, n, R.v[j], kxo, kyo, invNp, g0, g1, xw, W);
             }
-          }
-        } else {  // sigma -> G1 (it = 2), sigma_z -> G0 and b, t (it = 3)
-#pragma unroll
-          for (int j = 0; j < L1; ++j) {
-            const int n = r + L2 * j;
-            if (n < Np) {
-              const C sg = cscale(cmul(R.v[j], cchirp(a.t, n, Np)), invNp);
-              if (it == 2) {
-                g1[n * TL] = sg;
-                if (n == 0 || n == Nz - 1) {
-                  const int o = (n == 0) ? 4 : 6;
-                  W[o] = (double)sg.x;
-                  W[o + 1] = (double)sg.y;
-                }
-              } else {
-                g0[n * TL] = sg;
-                if (n == 0 || n == Nz - 1) {
-                  const C w = xw[n * TL];
-                  const int o = (n == 0) ? 0 : 2;
-                  W[o] = (double)w.x - (double)sg.x;
-                  W[o + 1] = (double)w.y - (double)sg.y;
-                }
-              }
-            }
-          }
+          });
         }
       }
     } else if constexpr (P == 4) {  // homogeneous coefficients (float64) -> W[8..12]
@@ -570,13 +604,13 @@ struct KZProject {
         W[8] = Ar; W[9] = Aim; W[10] = Br; W[11] = Bim; W[12] = D;
       }
     } else if constexpr (P == 5) {  // Phi, Phi' at the 2d end points -> smem
-      if (r < 2 * d) {
-        const int s = r < d ? r : Nz - 2 * d + r;
+      for (int q = r; q < 2 * d; q += E::G) {
+        const int s = q < d ? q : Nz - 2 * d + q;
         C ph, dph;
         const T cf[5] = {(T)W[8], (T)W[9], (T)W[10], (T)W[11], (T)W[12]};
         phi_at(cf, kxo, kyo, (T)a.g.dz, (T)a.g.Lz, s, &ph, &dph);
-        Ev[r < d ? r : DMAX + (r - d)] = ph;
-        Ev[2 * DMAX + (r < d ? r : DMAX + (r - d))] = dph;
+        Ev[q < d ? q : DMAX + (q - d)] = ph;
+        Ev[2 * DMAX + (q < d ? q : DMAX + (q - d))] = dph;
       }
     } else if constexpr (P == 6) {  // X -= grad phi^I + FC(grad phi^H); wall planes
       if (r < L2 && valid) {

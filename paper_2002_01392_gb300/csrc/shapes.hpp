@@ -1,17 +1,26 @@
 // Transform shapes compiled into the library.
-//   Z shapes: padded length L = L1 * L2 of the z-line circular convolutions
-//             and Bluestein DFTs (L >= N' + Nz - 1 and L >= 2 N' - 1).
+//   Z shapes: length L = L1 * L2 of the z-line transforms and whether it is a
+//             DIRECT length (used only when N' = L: z derivatives and filter
+//             are spectral multipliers, the projection's DFTs are plain
+//             length-N' transforms -- the paper's smooth N') or a padded one
+//             (any N' with L >= N' + Nz - 1 and L >= 2 N' - 1: circular
+//             convolutions and Bluestein DFTs).
 //   XY shapes: x and y lengths Nx, Ny (2/3/5-smooth).
 #pragma once
 
 #ifdef FC_HOSTCHECK
-#define FC_ZSHAPES(M) M(160, 10, 16) M(288, 16, 18)
+#define FC_ZSHAPES_DIRECT(M) M(64, 8, 8, true)
+#define FC_ZSHAPES_PADDED(M) M(160, 10, 16, false) M(288, 16, 18, false)
 #define FC_XYSHAPES(M) M(16, 4, 4) M(32, 4, 8)
 #else
-#define FC_ZSHAPES(M) M(160, 10, 16) M(288, 16, 18) M(320, 16, 20) M(576, 24, 24) M(1080, 30, 36)
+#define FC_ZSHAPES_DIRECT(M) \
+  M(64, 8, 8, true) M(128, 8, 16, true) M(256, 16, 16, true) M(512, 16, 32, true) M(768, 24, 32, true) M(1024, 32, 32, true)
+#define FC_ZSHAPES_PADDED(M) \
+  M(160, 10, 16, false) M(288, 16, 18, false) M(320, 16, 20, false) M(576, 24, 24, false) M(1080, 30, 36, false)
 #define FC_XYSHAPES(M) \
   M(16, 4, 4) M(32, 4, 8) M(64, 8, 8) M(96, 8, 12) M(128, 8, 16) M(192, 12, 16) M(256, 16, 16) M(512, 16, 32) M(1024, 32, 32)
 #endif
+#define FC_ZSHAPES(M) FC_ZSHAPES_DIRECT(M) FC_ZSHAPES_PADDED(M)
 
 namespace fcns {
 // lines per CTA of the z kernels and of the y kernels

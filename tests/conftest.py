@@ -24,3 +24,9 @@ def golden_dir():
 def Mr_5_25():
     from oracle.fc_tables import fc_matrix
     return fc_matrix(5, 25, table_dir=GOLDEN)
+
+
+@pytest.fixture(scope="session")
+def Mr_7_33():
+    from oracle.fc_tables import fc_matrix
+    return fc_matrix(7, 33, table_dir=GOLDEN)

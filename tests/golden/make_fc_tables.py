@@ -15,5 +15,5 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 from oracle import fc_tables  # noqa: E402
 
 if __name__ == "__main__":
-    for d, C in [(5, 25), (5, 15)]:
+    for d, C in [(5, 25), (5, 15), (7, 33)]:
         print(fc_tables.write_table(d, C, HERE))

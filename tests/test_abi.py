@@ -49,6 +49,17 @@ def test_fc_setup_tables_match_oracle(api, Mr_5_25):
     assert info["M"] == 20 and info["n_os"] == 20 and info["ls_residual"] < 1e-15
 
 
+def test_fc_setup_d7_tables_match_oracle(api, Mr_7_33):
+    """(d, C) = (7, 33), M = 26: the fits need more than binary128, so the
+    library builds them in double-binary128 arithmetic; the oracle's are mpmath
+    at 60 digits in another basis."""
+    plan = api.Plan(7, 33, 65)
+    Mr = plan.matrix()
+    assert np.abs(Mr - Mr_7_33).max() / np.abs(Mr_7_33).max() < 1e-15
+    info = plan.info()
+    assert info["M"] == 26 and info["ls_residual"] < 1e-17
+
+
 def test_fc_setup_demo_tables(api, golden_dir):
     from oracle import fc_tables
     ref = fc_tables.fc_matrix(5, 15, table_dir=golden_dir)

@@ -164,6 +164,70 @@ def test_boussinesq_float32(api, N, Nz):
     sim.close()
 
 
+@pytest.mark.parametrize("N,Nz", [(32, 39), (32, 103), (16, 231)])
+def test_direct_length_channel_matches_oracle(api, N, Nz):
+    """N' = Nz + 25 = 64, 128, 256: compiled transform lengths, so the z
+    derivatives and filter are length-N' spectral multipliers and the
+    projection uses plain length-N' DFTs (the paper's smooth N')."""
+    nu = 1e-2
+    p = api.ns_params(Nx=N, Ny=N, Nz=Nz, nu=nu, forcing_x=10 * nu, prec="f64")
+    sim = api.Sim(p)
+    P = ns.Params(N, N, Nz, nu=nu, forcing_x=10 * nu)
+    v = synth.channel_velocity(N, N, Nz, nu=nu)
+    vc = _cuda(v)
+    assert _rel(sim.rhs(vc).cpu().numpy(), ns.ns_rhs(v, P)) < 1e-11
+    sim.set_fields(vc)
+    for _ in range(3):
+        sim.step(1e-3)
+    ref, gref, _ = _oracle_steps(v, P, 1e-3, 3)
+    assert _rel(sim.get_fields().cpu().numpy(), ref) < 1e-11
+    assert _rel(sim.wall_gradp().cpu().numpy(), gref) < 1e-9
+    sim.close()
+
+
+def test_d7_channel_matches_oracle(api, Mr_7_33):
+    """d = 7, C = 33 (N' = 66) on the 32 x 32 x 33 channel: right-hand side and
+    three RK3 steps vs the oracle with the same tables; float64 floor scaled by
+    the continuation's amplification (cancellation in M_r f)."""
+    from numerics import fc_amplification
+    N, Nz, nu = 32, 33, 1e-2
+    sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, d=7, C=33, nu=nu, forcing_x=10 * nu, prec="f64"))
+    P = ns.Params(N, N, Nz, d=7, C=33, nu=nu, forcing_x=10 * nu, Mr=Mr_7_33)
+    v = synth.channel_velocity(N, N, Nz, nu=nu)
+    tol = 1e-11 * fc_amplification(Mr_7_33)
+    assert _rel(sim.rhs(_cuda(v)).cpu().numpy(), ns.ns_rhs(v, P)) < tol
+    sim.set_fields(_cuda(v))
+    for _ in range(3):
+        sim.step(1e-3)
+    ref, _, _ = _oracle_steps(v, P, 1e-3, 3)
+    assert _rel(sim.get_fields().cpu().numpy(), ref) < tol
+    sim.close()
+
+
+def test_full_size_smooth_boussinesq_float32(api):
+    """1024 x 1024 x 487 (N' = 512, direct), 4 fields, FP32: the conduction
+    state (all zero) is an exact fixed point, and one RK3 step of the seeded
+    fields stays finite with w = 0 and theta = 0 at the walls."""
+    N, Nz = 1024, 487
+    kw = dict(nu=3.162e-4, kappa=3.162e-4, gamma=1.0)
+    sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nfields=4, prec="f32", **kw))
+    z = torch.zeros((4, Nz, N, N), dtype=torch.float32, device="cuda")
+    sim.set_fields(z)
+    sim.step(1e-3)
+    assert torch.count_nonzero(sim.get_fields()) == 0
+    del z
+    f = torch.from_numpy(synth.boussinesq_fields(N, N, Nz, dtype=np.float32)).cuda()
+    sim.set_fields(f)
+    del f
+    sim.step(1e-3)
+    out = sim.get_fields()
+    assert torch.isfinite(out).all()
+    scale = out[:3].abs().max().item()
+    assert out[2, [0, -1]].abs().max().item() < 1e-5 * scale
+    assert out[3, [0, -1]].abs().max().item() < 1e-5 * out[3].abs().max().item()
+    sim.close()
+
+
 def test_full_size_boussinesq_properties(api):
     """1024 x 1024 x 513, 4 fields, FP32, as bench.py runs it: one RK3 step stays
     finite, keeps w = 0 at the walls and theta = 0 at the walls, and the

@@ -9,7 +9,7 @@ import pytest
 
 from conftest import ROOT
 from oracle import fc
-from numerics import norm_bound
+from numerics import fc_amplification, norm_bound, rel_bound_f64
 import synth
 
 HC = os.path.join(ROOT, "paper_2002_01392_gb300", "libfcns_hostcheck.so")
@@ -24,6 +24,22 @@ def hc():
 
 def _vp(a):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@pytest.mark.parametrize("Nz,L,Nx,Ny,B", [(33, 160, 6, 5, 2), (513, 1080, 9, 2, 1)])
+def test_deriv_kernel_d7_matches_oracle(hc, Mr_7_33, Nz, L, Nx, Ny, B):
+    """d = 7, C = 33 tables (entries up to 4.5e5) through the same kernel, float64."""
+    sf = synth.SeparableField(Nx, Ny, Nz, rank=3, seed_offset=Nz + 7)
+    f = np.ascontiguousarray(np.stack([sf.field(0)] * B))
+    d1, d2 = np.zeros_like(f), np.zeros_like(f)
+    assert hc.fchc_deriv_z(1, L, _vp(Mr_7_33), 7, 33, Nz, B, Nx, Ny, ctypes.c_double(1.0),
+                           _vp(f), _vp(d1), _vp(d2)) == 0
+    Np = Nz + 33
+    amp = fc_amplification(Mr_7_33)
+    for order, out in ((1, d1), (2, d2)):
+        ref = fc.fc_deriv_z(f, 1.0, Mr_7_33, order, axis=1)
+        rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+        assert rel < amp * rel_bound_f64(order, Np), (order, rel)
 
 
 @pytest.mark.parametrize("Nz,L,Nx,Ny,B", [(33, 96, 5, 7, 2), (10, 96, 33, 1, 1), (65, 160, 40, 3, 1),

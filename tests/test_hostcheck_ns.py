@@ -59,6 +59,58 @@ def test_rk3_steps_match_oracle(chan):
     assert _rel(hs.get_fields(), ref) < 1e-13
 
 
+@pytest.mark.parametrize("prec,tol,tol_rhs", [("f64", 1e-12, 1e-12), ("f32", 2e-5, 5e-4)])
+def test_direct_length_steps_match_oracle(prec, tol, tol_rhs):
+    """N' = Nz + C = 64 is itself a compiled transform length: z derivatives and
+    the filter become spectral multipliers of length N' and the projection's
+    DFTs plain length-N' transforms (no padding, no Bluestein).  The float32
+    right-hand side carries nu d2/dz2, whose rounding floor is eps (k_max/k)^2
+    ~ 1e-4 here."""
+    N, Nz = 16, 39
+    hs = HostSim(Nx=N, Ny=N, Nz=Nz, nu=1e-2, forcing_x=0.1, prec=prec)
+    P = ns.Params(N, N, Nz, nu=1e-2, forcing_x=0.1)
+    v = synth.channel_velocity(N, N, Nz)
+    assert _rel(hs.rhs(v), ns.ns_rhs(v, P)) < tol_rhs
+    g = np.random.default_rng(3)
+    z = synth.z_grid(Nz)
+    vs = v + 0.2 * (z * (1 - z))[None, :, None, None] * g.standard_normal((3, 1, N, N))
+    hs.set_fields(v)
+    out, gp = hs.project(vs, 1e-3)
+    ref, gref = ns.poisson_project(vs, P, 1e-3)
+    assert _rel(out, ref) < tol
+    assert _rel(gp, gref) < 10 * tol
+    hs.set_fields(v)
+    st = ns.to_spectral(v, P)
+    gp = np.zeros((2, 2, N, P.Kx), complex)
+    for _ in range(2):
+        hs.step(1e-3)
+        st, gp = ns.rk_step(st, gp, P, 1e-3)
+    ref = np.stack([ns.to_physical(c, P) for c in st])
+    assert _rel(hs.get_fields(), ref) < tol
+    hs.close()
+
+
+def test_d7_tables_channel_matches_oracle(Mr_7_33):
+    """d = 7, C = 33 (N' = 58 + 8 = 66): the library's double-binary128 tables
+    through the whole kernel sequence, float64, tolerance scaled by the
+    continuation's amplification."""
+    from numerics import fc_amplification
+    N, Nz = 16, 33
+    hs = HostSim(Nx=N, Ny=N, Nz=Nz, d=7, C=33, nu=1e-2, forcing_x=0.1, prec="f64")
+    P = ns.Params(N, N, Nz, d=7, C=33, nu=1e-2, forcing_x=0.1, Mr=Mr_7_33)
+    v = synth.channel_velocity(N, N, Nz)
+    tol = 1e-12 * fc_amplification(Mr_7_33)
+    assert _rel(hs.rhs(v), ns.ns_rhs(v, P)) < tol
+    hs.set_fields(v)
+    st = ns.to_spectral(v, P)
+    gp = np.zeros((2, 2, N, P.Kx), complex)
+    hs.step(1e-3)
+    st, gp = ns.rk_step(st, gp, P, 1e-3)
+    ref = np.stack([ns.to_physical(c, P) for c in st])
+    assert _rel(hs.get_fields(), ref) < tol
+    hs.close()
+
+
 def test_boussinesq_float32_steps():
     N, Nz = 16, 65
     kw = dict(Nx=N, Ny=N, Nz=Nz, nfields=4, nu=3.162e-3, kappa=3.162e-3, gamma=1.0, prec="f32")

@@ -10,7 +10,7 @@ import synth
 
 def test_stored_tables_match_fresh_build(golden_dir):
     pytest.importorskip("mpmath")
-    for d, C in [(5, 25), (5, 15)]:
+    for d, C in [(5, 25), (5, 15), (7, 33)]:
         fresh = fc_tables._to_f64(fc_tables.build_mr_mp(d, C)[0])
         stored = fc_tables.read_table(fc_tables.table_path(d, C, fc_tables.default_bandwidth(d, C),
                                                            fc_tables.N_OS, golden_dir))
@@ -44,6 +44,42 @@ def test_first_row_is_polynomial_extrapolation(Mr_5_25):
     # blend to zero next to the left matching set
     assert np.abs(Mr_5_25[-1]).max() < 1e-7
     assert Mr_5_25.shape == (25, 5)
+
+
+def test_d7_first_and_last_rows(Mr_7_33):
+    """(d, C) = (7, 33), the paper's larger setting (App. B: 231 numbers): the
+    first continuation point follows the degree-6 matching polynomial
+    (alternating binomials of order 7) and the last blends to zero."""
+    assert Mr_7_33.shape == (33, 7)
+    np.testing.assert_allclose(Mr_7_33[0], [1, -7, 21, -35, 35, -21, 7], atol=1e-6)
+    assert np.abs(Mr_7_33[-1]).max() < 1e-9
+
+
+def test_d7_boundary_order_of_convergence(Mr_7_33):
+    """Observed boundary order for sin(5z) with d = 7: d - 1 for d/dz and d - 2
+    for d2/dz2, as d = 5 gives 4 and 3."""
+    Ns = [33, 49, 65, 97]
+    e1, e2 = [], []
+    for Nz in Ns:
+        z = synth.z_grid(Nz)
+        f = np.sin(5 * z)
+        e1.append(np.abs(fc.fc_deriv_z(f, 1.0, Mr_7_33, 1) - 5 * np.cos(5 * z)).max())
+        e2.append(np.abs(fc.fc_deriv_z(f, 1.0, Mr_7_33, 2) + 25 * np.sin(5 * z)).max())
+    ratio = [math.log((Ns[i + 1] - 1) / (Ns[i] - 1)) for i in range(3)]
+    o1 = [math.log(e1[i] / e1[i + 1]) / ratio[i] for i in range(3)]
+    o2 = [math.log(e2[i] / e2[i + 1]) / ratio[i] for i in range(3)]
+    assert min(o1) > 5.7 and min(o2) > 4.7, (o1, o2)
+
+
+@pytest.mark.parametrize("Nz", [33, 129, 513])
+def test_d7_polynomials_below_degree_d(Mr_7_33, Nz):
+    z = synth.z_grid(Nz)
+    for p in range(7):
+        f = z ** p
+        d1 = p * z ** max(p - 1, 0) if p > 0 else 0 * z
+        d2 = p * (p - 1) * z ** max(p - 2, 0) if p > 1 else 0 * z
+        assert np.abs(fc.fc_deriv_z(f, 1.0, Mr_7_33, 1) - d1).max() < 3e-8
+        assert np.abs(fc.fc_deriv_z(f, 1.0, Mr_7_33, 2) - d2).max() < 2e-6
 
 
 def test_mirror_symmetry(Mr_5_25):
