@@ -394,8 +394,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--rk-steps", type=int, default=5)
     ap.add_argument("--no-rk", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=["deriv32", "deriv64", "rk-small", "rk-full"],
-                    help="small single-kernel case for ncu: fc_deriv_z on 2x256x256x513, no e2e / CPU leg")
+    ap.add_argument("--profile-case", default=None,
+                    choices=["deriv32", "deriv64", "rk-small", "rk-mid", "rk-full", "rk-smooth"],
+                    help="small single-kernel case for ncu (deriv: fc_deriv_z on 2x256x256x513; rk-*: one RK3 grid), no e2e / CPU leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -432,8 +433,9 @@ def main():
     from paper_2002_01392_gb300 import api
     dev_index = torch.cuda.current_device()
     hbm_peak, peak_kind = _peaks()
-    if args.profile_case in ("rk-small", "rk-full"):
-        shape = (256, 256, 513) if args.profile_case == "rk-small" else None
+    if args.profile_case and args.profile_case.startswith("rk"):
+        shape = {"rk-small": (256, 256, 513), "rk-mid": (1024, 1024, 33), "rk-full": None,
+                 "rk-smooth": (1024, 1024, 487)}[args.profile_case]
         r = bench_rk(api, torch, args.steps, args.warmup, with_e2e=False, shape=shape)
         print(json.dumps({"profile_case": args.profile_case, **r}))
         return
