@@ -318,6 +318,103 @@ def bench_rk(api, torch, steps, warmup, with_e2e=True, shape=None):
     return res
 
 
+def bench_ensemble(api, torch, steps=5, warmup=3, n=64):
+    """Batched ensemble: n independent channel instances of uneven sizes
+    (64^2 x 65, 96^2 x 97, 128^2 x 129, 192^2 x 129; nu log-uniform in
+    [1e-3, 1e-2]), FP32 with the float64 mean-flow line, one RK3 step of all
+    members = one CUDA graph launch.  Beside it: the plain path, the same
+    instances in float64 stepped one after another with rk_step."""
+    import synth
+    specs = synth.ensemble_specs(n)
+    pts = sum(s["Nx"] * s["Ny"] * s["Nz"] for s in specs)
+    stream = torch.cuda.current_stream()
+
+    def make(prec):
+        sims = []
+        for sp in specs:
+            p = api.ns_params(Nx=sp["Nx"], Ny=sp["Ny"], Nz=sp["Nz"], nu=sp["nu"], forcing_x=10 * sp["nu"], prec=prec)
+            sim = api.Sim(p)
+            v = synth.channel_velocity(sp["Nx"], sp["Ny"], sp["Nz"], nu=sp["nu"], seed_offset=sp["seed_offset"])
+            sim.set_fields(torch.from_numpy(v).to("cuda", sim.dtype))
+            sims.append(sim)
+        return sims
+
+    def timed(fn, k):
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for i in range(k):
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3
+
+    dt = 2e-4
+    sims = make("f32")
+    batch = api.Batch(sims)
+    for _ in range(warmup):
+        batch.step(dt)
+    t = timed(lambda: batch.step(dt), steps)
+    info = batch.info()
+    finite = all(bool(torch.isfinite(s.get_fields()).all().item()) for s in sims)
+    batch.close()
+    for s in sims:
+        s.close()
+    sims64 = make("f64")
+
+    def plain():
+        for s in sims64:
+            s.step(dt)
+    for _ in range(2):
+        plain()
+    t64 = timed(plain, max(2, steps // 2))
+    for s in sims64:
+        s.close()
+    torch.cuda.empty_cache()
+    res = {"instances": n, "grids": [list(g) for g in synth.ENSEMBLE_GRIDS], "points": pts,
+           "p50_ms": float(np.percentile(t, 50) * 1e3), "p99_ms": float(np.percentile(t, 99) * 1e3),
+           "rk_stage_grid_points_per_s": pts * 3 / float(t.mean()), "graph_nodes": info["graph_nodes"],
+           "graph_launches_per_step": 1, "finite": finite,
+           "plain_fp64_sequential": {"p50_ms": float(np.percentile(t64, 50) * 1e3),
+                                     "rk_stage_grid_points_per_s": pts * 3 / float(t64.mean())}}
+    res["speedup_vs_plain_fp64"] = res["rk_stage_grid_points_per_s"] / res["plain_fp64_sequential"]["rk_stage_grid_points_per_s"]
+    return res
+
+
+def bench_serving(api, torch, rate=2000.0, duration=2.0, resident=48, slots=8):
+    """Serving: Poisson arrivals (mean ``rate`` per second, ``duration``
+    seconds) of fc_poisson_project and rk_step requests, 50/50, on ``resident``
+    FP32 simulations drawn uniformly from 64^2 x 65, 128^2 x 129, 256^2 x 257,
+    admitted by HBM footprint; requests overlap on ``slots`` CUDA streams."""
+    import synth
+    from paper_2002_01392_gb300 import serve
+    grids = ((64, 64, 65), (128, 128, 129), (256, 256, 257))
+    g = np.random.default_rng(2002013924)
+    free, total = torch.cuda.mem_get_info()
+    srv = serve.Server(int(0.5 * free), slots=slots)
+    sims, shapes = [], []
+    for i in range(resident):
+        Nx, Ny, Nz = grids[int(g.integers(0, 3))]
+        p = api.ns_params(Nx=Nx, Ny=Ny, Nz=Nz, nu=5e-3, forcing_x=5e-2, prec="f32")
+        v = synth.channel_velocity(Nx, Ny, Nz, nu=5e-3, seed_offset=2000 + i)
+        sid = srv.admit(p, torch.from_numpy(v.astype(np.float32)).cuda())
+        if sid is not None:
+            sims.append(sid)
+            shapes.append((Nx, Ny, Nz))
+    inputs = {sid: torch.from_numpy(synth.channel_velocity(*shapes[k], nu=5e-3, seed_offset=3000 + k)
+                                    .astype(np.float32)).cuda() for k, sid in enumerate(sims)}
+    reqs = serve.poisson_requests(rate, duration, sims, g, kinds=("project", "step"), dt=2e-4)
+    for r in reqs:
+        if r.kind == "project":
+            r.inp = inputs[r.sim]
+    stats = srv.run(reqs)
+    stats.update({"arrival_rate_per_s": rate, "duration_s": duration, "slots": slots,
+                  "grids": [list(x) for x in grids], "mix": "50/50 fc_poisson_project / rk_step"})
+    srv.close()
+    torch.cuda.empty_cache()
+    return stats
+
+
 class OracleDerivSample:
     """The FP64 oracle (numpy, one thread) on sampled z-lines of the
     3 x 512^2 x 513 fc_deriv_z batch: one call = both derivatives of
@@ -454,6 +551,8 @@ def main():
     rc = bench_cufft64(api, torch, max(3, args.steps // 4), 2)
     # companion: the paper's kind of smooth N' (512 = 487 + 25): direct length-N' z transforms
     rks = None if args.no_rk else bench_rk(api, torch, args.rk_steps, 2, with_e2e=False, shape=(1024, 1024, 487))
+    ens = None if args.no_rk else bench_ensemble(api, torch)
+    srv = None if args.no_rk else bench_serving(api, torch)
     # companion: the paper's kind of smooth N' (512 = 487 + 25) at the same horizontal size
     DERIV_SHAPE = (3, 512, 512, 487)
     rs = bench_deriv(api, torch, np.float32, args.steps, 2, with_e2e=False)
@@ -475,6 +574,8 @@ def main():
                        "fp32_speedup_vs_cufft_fp64_plain": r32["grid_points_per_s"] / rc["grid_points_per_s"]},
         "rk_stage": rk,
         "rk_stage_smooth_Np512_1024x1024x487": rks,
+        "ensemble_64_uneven_fp32_graph": ens,
+        "serving_poisson_2000_per_s": srv,
         "roofline": {"bound": "hbm", "achieved": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9,
                      "peak": hbm_peak, "unit": "GB/s",
                      "frac": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9 / hbm_peak,

@@ -276,6 +276,55 @@ fc_status rk_step(ns_sim_t sim, double dt, fc_stream_t stream);
 fc_status ns_diagnostics(ns_sim_t sim, double* div_ms, double* wall_u_ms, double* wall_w_ms,
                          double* flow_rate, double* nusselt, fc_stream_t stream);
 
+/*
+ * ns_interpolate -- restart on another grid (Sec. 6: "spectral interpolation,
+ * by zero padding the transformed fields in the wavenumber domain"): the state
+ * of dst becomes the interpolant of src's state, re-continued on dst's grid;
+ * dst's wall planes are reset to zero.  x, y: zero padding (dst Nx >= src Nx,
+ * dst Ny >= src Ny), coefficients scaled by (Nx2 Ny2)/(Nx1 Ny1), a coarse
+ * Nyquist coefficient split in half between +N/2 and -N/2.  z: the
+ * N'-periodic series of each source line (Nyquist term as a cosine) evaluated
+ * at dst's Nz physical points (any Nz; the continuation period changes with
+ * the grid, so z coefficients are not padded directly).  Both simulations on
+ * the current device, same box, nfields and precision (else FC_ERR_ARG);
+ * FC_ERR_UNSUPPORTED if dst's work buffers cannot hold the Nz x N'(src)
+ * weight table.  Uploads the weights with a synchronous copy.
+ */
+fc_status ns_interpolate(ns_sim_t dst, ns_sim_t src, fc_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched ensemble: many independent simulations, one graph launch per step */
+/* ------------------------------------------------------------------------ */
+
+typedef struct ns_batch* ns_batch_t;
+
+/*
+ * ns_batch_create -- group n simulations (created on the current device,
+ * each at most once; any sizes, precisions and parameters) so that one RK
+ * step of all of them (Sec. 4.4, as rk_step) runs as a single CUDA graph
+ * launch.  The members stay owned by the caller and must outlive the batch;
+ * the batch copies the array of handles.  FC_ERR_ARG for NULL / repeated
+ * members, FC_ERR_STATE for members of another device.
+ */
+fc_status ns_batch_create(ns_sim_t* sims, int n, ns_batch_t* out);
+
+/*
+ * ns_batch_step -- advance member i by one RK step of size dt[i] (host array
+ * of n positive values).  The first call for a given set of step sizes and
+ * buffer rotation captures the members' kernels into a graph (members spread
+ * over 8 concurrent branches) on private streams; later calls replay it with
+ * one cudaGraphLaunch on `stream`.  Results are bitwise those of rk_step on
+ * each member.  Up to 6 graphs are cached; members must not be stepped
+ * through other calls concurrently.
+ */
+fc_status ns_batch_step(ns_batch_t batch, const double* dt, fc_stream_t stream);
+
+/* Members, nodes of the last captured graph, graphs cached (NULL to skip). */
+fc_status ns_batch_info(ns_batch_t batch, int* members, int* graph_nodes, int* graphs_cached);
+
+/* Release the graphs and streams (not the members). */
+fc_status ns_batch_destroy(ns_batch_t batch);
+
 #ifdef __cplusplus
 }
 #endif

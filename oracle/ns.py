@@ -371,3 +371,51 @@ def nusselt(state: np.ndarray, p: Params):
 
 def flow_rate(state: np.ndarray, p: Params) -> float:
     return to_physical(state[0], p).mean()
+
+
+# ----------------------------------------------------------------------------
+# restarts on another grid (Sec. 6: spectral interpolation by zero padding)
+# ----------------------------------------------------------------------------
+
+def spectral_interpolate(state: np.ndarray, p1: Params, p2: Params) -> np.ndarray:
+    """State of grid p1 -> state of grid p2 (Nx2 >= Nx1, Ny2 >= Ny1, same box,
+    fields and (d, C)), following the restart procedure of Sec. 6.
+
+    x, y: the transformed field is zero-padded in the wavenumber domain; the
+    coefficients scale with (Nx2 Ny2)/(Nx1 Ny1) (unnormalised forward
+    transforms) and a Nyquist coefficient of the coarse grid, which stands for
+    a cosine, is split in half between +N/2 and -N/2 (reading I1).
+    z: the continued field is N'1-periodic with period L'1 = N'1 dz1; its
+    Fourier series (the Nyquist term as a cosine, reading I2) is evaluated at
+    the Nz2 physical points of the new grid, and those values are FC-continued
+    on the new grid (the continuation period changes with the grid, so the z
+    coefficients cannot be zero-padded directly; reading I3)."""
+    assert p2.Nx >= p1.Nx and p2.Ny >= p1.Ny and p1.Lz == p2.Lz
+    nf = state.shape[0]
+    Np1 = p1.Np
+    # z: evaluate the series at the new points, per (kx, ky) line
+    dz1 = p1.Lz / (p1.Nz - 1)
+    z2 = np.arange(p2.Nz) * (p2.Lz / (p2.Nz - 1))
+    L1 = Np1 * dz1
+    l = np.fft.fftfreq(Np1, 1.0 / Np1)                     # signed integer frequencies
+    E = np.exp(2j * np.pi * np.outer(z2, l) / L1)          # [Nz2][N'1]
+    if Np1 % 2 == 0:
+        E[:, Np1 // 2] = np.cos(np.pi * Np1 * z2 / L1)     # Nyquist as a cosine
+    mixed1 = np.einsum("sl,flyx->fsyx", E, state) / Np1    # [nf][Nz2][Ny1][Kx1]
+    # x, y: zero padding
+    Kx1, Kx2 = p1.Kx, p2.Kx
+    mixed2 = np.zeros((nf, p2.Nz, p2.Ny, Kx2), complex)
+    scale = (p2.Nx * p2.Ny) / (p1.Nx * p1.Ny)
+    ny1 = p1.Ny
+    for j1 in range(ny1):
+        m = j1 if j1 < ny1 // 2 else j1 - ny1                # signed ky index
+        rows = [(m % p2.Ny, 1.0)]
+        if ny1 % 2 == 0 and j1 == ny1 // 2 and p2.Ny > ny1:  # coarse Nyquist -> +-N/2, half each
+            rows = [((ny1 // 2) % p2.Ny, 0.5), ((-ny1 // 2) % p2.Ny, 0.5)]
+        for j2, w in rows:
+            blk = mixed1[:, :, j1, :Kx1] * (scale * w)
+            if p1.Nx % 2 == 0 and p2.Nx > p1.Nx:
+                blk = blk.copy()
+                blk[..., Kx1 - 1] *= 0.5                     # coarse x Nyquist (r2c: one side stored)
+            mixed2[:, :, j2, :Kx1] += blk
+    return z_forward(mixed2, p2)

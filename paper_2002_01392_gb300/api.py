@@ -58,13 +58,18 @@ _sig("fc_setup_ex", [_c_int, _c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_vp)
 _sig("fc_plan_matrix", [_vp, ctypes.POINTER(_c_double)])
 _sig("fc_plan_info", [_vp] + [ctypes.POINTER(_c_int)] * 5 + [ctypes.POINTER(_c_double)])
 _sig("fc_destroy", [_vp])
+_sig("ns_batch_create", [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(_vp)])
+_sig("ns_batch_step", [_vp, ctypes.POINTER(_c_double), _vp])
+_sig("ns_batch_info", [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)])
+_sig("ns_batch_destroy", [_vp])
 _sig("fc_deriv_z", [_vp, _c_int, _c_int, _c_int, _c_int, _c_double, _vp, _vp, _vp, _vp])
 _sig("fc_deriv_z_noalloc", [_vp, _c_int, _c_int, _c_int, _c_int, _c_double, _vp, _vp, _vp, _vp])
 
 EXPORTED = ["fc_status_str", "fc_last_error", "fc_setup", "fc_setup_ex", "fc_plan_matrix", "fc_plan_info",
             "fc_destroy", "fc_deriv_z", "fc_deriv_z_noalloc", "ns_params_default", "ns_workspace_bytes", "ns_create", "ns_destroy",
             "ns_set_fields", "ns_get_fields", "ns_get_state", "ns_put_state", "ns_get_wall_gradp",
-            "ns_put_wall_gradp", "ns_rhs", "fc_poisson_project", "rk_step", "ns_diagnostics"]
+            "ns_put_wall_gradp", "ns_rhs", "fc_poisson_project", "rk_step", "ns_diagnostics",
+            "ns_batch_create", "ns_batch_step", "ns_batch_info", "ns_batch_destroy", "ns_interpolate"]
 
 
 def _check(status: int, where: str):
@@ -281,6 +286,10 @@ class Sim:
     def step(self, dt: float, stream=None):
         _check(_lib.rk_step(self.handle, float(dt), _stream(stream)), "rk_step")
 
+    def interpolate_from(self, src: "Sim", stream=None):
+        """ns_interpolate: this state := spectral interpolation of src's state."""
+        _check(_lib.ns_interpolate(self.handle, src.handle, _stream(stream)), "ns_interpolate")
+
     def diagnostics(self, stream=None):
         """ns_diagnostics: div_ms, wall_u_ms, wall_w_ms, flow_rate, nusselt (synchronous)."""
         vals = [_c_double() for _ in range(5)]
@@ -290,6 +299,42 @@ class Sim:
     def close(self):
         if getattr(self, "handle", None):
             _lib.ns_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """ns_batch: independent simulations advanced together, one CUDA graph
+    launch per step (the members stay owned by the caller)."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        arr = (_vp * len(self.sims))(*[x.handle for x in self.sims])
+        h = _vp()
+        _check(_lib.ns_batch_create(arr, len(self.sims), ctypes.byref(h)), "ns_batch_create")
+        self.handle = h
+
+    def step(self, dt, stream=None):
+        """dt: one step size for all members or a sequence of per-member sizes."""
+        n = len(self.sims)
+        vals = [float(dt)] * n if not hasattr(dt, "__len__") else [float(x) for x in dt]
+        if len(vals) != n:
+            raise ValueError("one dt per member")
+        _check(_lib.ns_batch_step(self.handle, (_c_double * n)(*vals), _stream(stream)), "ns_batch_step")
+
+    def info(self):
+        m, g, c = _c_int(), _c_int(), _c_int()
+        _check(_lib.ns_batch_info(self.handle, ctypes.byref(m), ctypes.byref(g), ctypes.byref(c)), "ns_batch_info")
+        return dict(members=m.value, graph_nodes=g.value, graphs_cached=c.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.ns_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

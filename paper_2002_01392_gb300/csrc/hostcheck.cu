@@ -115,6 +115,9 @@ int fchc_ns_project(void* h, double dt, const void* in, void* out, void* gp) {
   return ((NsCore<EmuBK>*)h)->project_any(dt, in, out, gp, nullptr);
 }
 int fchc_ns_step(void* h, double dt) { return ((NsCore<EmuBK>*)h)->step_any(dt, nullptr); }
+int fchc_ns_interpolate(void* dst, void* src) {
+  return ((NsCore<EmuBK>*)dst)->interpolate_from_any(*(NsCore<EmuBK>*)src, nullptr);
+}
 int fchc_ns_diag_raw(void* h, double* acc6) { return ((NsCore<EmuBK>*)h)->diagnostics_any(acc6, nullptr); }
 int fchc_ns_get_state(void* h, void* out) {
   auto* c = (NsCore<EmuBK>*)h;

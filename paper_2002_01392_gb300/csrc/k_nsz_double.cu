@@ -14,4 +14,5 @@ template struct DevRun<KZContinue<double, 8>>;
 template struct DevRun<KDiag<double>>;
 template struct DevRun<KMeanLine<double>>;
 template struct DevRun<KMeanInit<double>>;
+template struct DevRun<KInterp<double>>;
 }  // namespace fcns

@@ -14,4 +14,5 @@ template struct DevRun<KZContinue<float, 8>>;
 template struct DevRun<KDiag<float>>;
 template struct DevRun<KMeanLine<float>>;
 template struct DevRun<KMeanInit<float>>;
+template struct DevRun<KInterp<float>>;
 }  // namespace fcns

@@ -1,6 +1,7 @@
 // Navier-Stokes entry points of the C ABI (GPU backend of NsCore).
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "internal.hpp"
 #include "ns_core.hpp"
@@ -48,6 +49,27 @@ using namespace fcns;
 struct ns_sim {
   NsCore<DeviceBK> core;
   int device = -1;
+};
+
+// A set of simulations whose RK steps are replayed from captured CUDA graphs.
+// Members are spread over NB capture branches (fork / join on events), so
+// independent instances run concurrently inside one graph launch.  A graph
+// depends on the members' buffer rotation (NsCore::cur) and on the step
+// sizes, which form the cache key.
+struct ns_batch {
+  static constexpr int NB = 8;
+  std::vector<ns_sim_t> sims;
+  int device = -1;
+  cudaStream_t cap = nullptr;
+  cudaStream_t br[NB] = {};
+  cudaEvent_t fork = nullptr, join[NB] = {};
+  struct Entry {
+    std::vector<int> cur_in, cur_out;
+    std::vector<double> dt;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::vector<Entry> cache;
+  int launches_per_graph = 0;
 };
 
 static fc_status check_sim(ns_sim_t s, const char* what) {
@@ -169,6 +191,134 @@ fc_status rk_step(ns_sim_t s, double dt, fc_stream_t stream) {
   if (st) return st;
   if (!(dt > 0)) { set_error("rk_step: dt must be positive"); return FC_ERR_ARG; }
   return s->core.step_any(dt, stream);
+}
+
+fc_status ns_interpolate(ns_sim_t dst, ns_sim_t src, fc_stream_t stream) {
+  fc_status st = check_sim(dst, "ns_interpolate");
+  if (!st) st = check_sim(src, "ns_interpolate");
+  if (st) return st;
+  if (dst == src) { set_error("ns_interpolate: source and destination are the same"); return FC_ERR_ARG; }
+  st = dst->core.interpolate_from_any(src->core, stream);
+  if (st == FC_ERR_ARG) set_error("ns_interpolate: grids not compatible (finer Nx, Ny; same box, fields, precision)");
+  return st;
+}
+
+fc_status ns_batch_create(ns_sim_t* sims, int n, ns_batch_t* out) {
+  if (!sims || !out || n < 1) { set_error("ns_batch_create: bad arguments"); return FC_ERR_ARG; }
+  *out = nullptr;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < n; ++i) {
+    if (!sims[i]) { set_error("ns_batch_create: NULL member"); return FC_ERR_ARG; }
+    if (sims[i]->device != dev) { set_error("ns_batch_create: members on another device"); return FC_ERR_STATE; }
+    for (int j = 0; j < i; ++j)
+      if (sims[j] == sims[i]) { set_error("ns_batch_create: a simulation appears twice"); return FC_ERR_ARG; }
+  }
+  ns_batch* b = new (std::nothrow) ns_batch;
+  if (!b) return FC_ERR_NOMEM;
+  b->sims.assign(sims, sims + n);
+  b->device = dev;
+  fc_status st = cuda_status(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+  for (int i = 0; i < ns_batch::NB && !st; ++i) {
+    st = cuda_status(cudaStreamCreateWithFlags(&b->br[i], cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!st) st = cuda_status(cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming), "cudaEventCreate");
+  }
+  if (!st) st = cuda_status(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "cudaEventCreate");
+  if (st) { ns_batch_destroy(b); return st; }
+  *out = b;
+  return FC_OK;
+}
+
+fc_status ns_batch_destroy(ns_batch_t b) {
+  if (!b) return FC_ERR_ARG;
+  for (auto& e : b->cache)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+  for (int i = 0; i < ns_batch::NB; ++i) {
+    if (b->br[i]) cudaStreamDestroy(b->br[i]);
+    if (b->join[i]) cudaEventDestroy(b->join[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+  return FC_OK;
+}
+
+// Capture one RK step of every member (step sizes dt) into a graph.
+static fc_status batch_capture(ns_batch_t b, const double* dt, ns_batch::Entry* e) {
+  const int n = (int)b->sims.size();
+  e->cur_in.resize(n);
+  e->dt.assign(dt, dt + n);
+  for (int i = 0; i < n; ++i) e->cur_in[i] = b->sims[i]->core.cur;
+  fc_status st = cuda_status(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  if (st) return st;
+  st = cuda_status(cudaEventRecord(b->fork, b->cap), "cudaEventRecord");
+  const int nb = n < ns_batch::NB ? n : ns_batch::NB;
+  for (int k = 0; k < nb && !st; ++k) st = cuda_status(cudaStreamWaitEvent(b->br[k], b->fork, 0), "cudaStreamWaitEvent");
+  for (int i = 0; i < n && !st; ++i) st = b->sims[i]->core.step_any(dt[i], b->br[i % nb]);
+  for (int k = 0; k < nb && !st; ++k) {
+    st = cuda_status(cudaEventRecord(b->join[k], b->br[k]), "cudaEventRecord");
+    if (!st) st = cuda_status(cudaStreamWaitEvent(b->cap, b->join[k], 0), "cudaStreamWaitEvent");
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(b->cap, &g);
+  if (!st) st = cuda_status(ec, "cudaStreamEndCapture");
+  e->cur_out.resize(n);
+  for (int i = 0; i < n; ++i) {  // capture ran the host side of step(): keep its rotation, undo it for now
+    e->cur_out[i] = b->sims[i]->core.cur;
+    b->sims[i]->core.cur = e->cur_in[i];
+  }
+  if (!st) {
+    size_t nodes = 0;
+    cudaGraphGetNodes(g, nullptr, &nodes);
+    b->launches_per_graph = (int)nodes;
+    st = cuda_status(cudaGraphInstantiate(&e->exec, g, 0), "cudaGraphInstantiate");
+  }
+  if (g) cudaGraphDestroy(g);
+  return st;
+}
+
+fc_status ns_batch_step(ns_batch_t b, const double* dt, fc_stream_t stream) {
+  if (!b || !dt) { set_error("ns_batch_step: NULL argument"); return FC_ERR_ARG; }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) {
+    set_error("ns_batch_step: called with a different current device than ns_batch_create");
+    return FC_ERR_STATE;
+  }
+  const int n = (int)b->sims.size();
+  for (int i = 0; i < n; ++i)
+    if (!(dt[i] > 0)) { set_error("ns_batch_step: dt must be positive"); return FC_ERR_ARG; }
+  ns_batch::Entry* hit = nullptr;
+  for (auto& e : b->cache) {
+    bool same = true;
+    for (int i = 0; i < n && same; ++i) same = e.cur_in[i] == b->sims[i]->core.cur && e.dt[i] == dt[i];
+    if (same) { hit = &e; break; }
+  }
+  if (!hit) {
+    if (b->cache.size() >= 6) {  // a new set of step sizes: drop the old graphs
+      for (auto& e : b->cache) cudaGraphExecDestroy(e.exec);
+      b->cache.clear();
+    }
+    ns_batch::Entry e;
+    fc_status st = batch_capture(b, dt, &e);
+    if (st) {
+      if (e.exec) cudaGraphExecDestroy(e.exec);
+      return st;
+    }
+    b->cache.push_back(e);
+    hit = &b->cache.back();
+  }
+  fc_status st = cuda_status(cudaGraphLaunch(hit->exec, (cudaStream_t)stream), "cudaGraphLaunch");
+  if (st) return st;
+  for (int i = 0; i < n; ++i) b->sims[i]->core.cur = hit->cur_out[i];
+  return FC_OK;
+}
+
+fc_status ns_batch_info(ns_batch_t b, int* members, int* graph_nodes, int* graphs_cached) {
+  if (!b) return FC_ERR_ARG;
+  if (members) *members = (int)b->sims.size();
+  if (graph_nodes) *graph_nodes = b->launches_per_graph;
+  if (graphs_cached) *graphs_cached = (int)b->cache.size();
+  return FC_OK;
 }
 
 fc_status ns_diagnostics(ns_sim_t s, double* div_ms, double* wall_u_ms, double* wall_w_ms, double* flow_rate,

@@ -464,6 +464,63 @@ struct NsCore {
   template <class T>
   fc_status get_fields(T* phys, void* st) { return state_to_phys<T>(Xb<T>(cur), phys, l.nf, st); }
 
+  // state := spectral interpolation of src's state onto this grid (Sec. 6
+  // restarts; see KInterp), re-continued here; wall planes reset to zero.
+  // The evaluation weights go to this simulation's DZZ work buffer.
+  template <class T>
+  fc_status interpolate_from(const NsCore& src, void* st) {
+    const NsLayout& l1 = src.l;
+    const size_t need = sizeof(cx<T>) * (size_t)p.Nz * l1.Np;
+    if (need > 2 * l.es * l.nf * (size_t)p.Nz * l.plines) return FC_ERR_UNSUPPORTED;
+    std::vector<cx<T>> W((size_t)p.Nz * l1.Np);
+    const int Np1 = l1.Np;
+    const double dz1 = src.p.Lz / (src.p.Nz - 1), L1 = Np1 * dz1, dz2 = p.Lz / (p.Nz - 1);
+    // W[s][n] = (1/N'1) sum_l A_l(z_s) e^{-2 pi i l n / N'1}, A_l = e^{i k_l z}
+    // (k_l = 2 pi l / L'1, signed l) and a cosine for the Nyquist term
+    std::vector<std::complex<double>> Bt((size_t)Np1 * Np1), A(Np1);
+    for (int ll = 0; ll < Np1; ++ll)
+      for (int n = 0; n < Np1; ++n) {
+        double c, sn;
+        sincos2pi(-(long long)ll * n, Np1, &c, &sn);
+        Bt[(size_t)ll * Np1 + n] = std::complex<double>(c, sn);
+      }
+    for (int s2 = 0; s2 < p.Nz; ++s2) {
+      const double z = s2 * dz2;
+      for (int ll = 0; ll < Np1; ++ll) {
+        const int ls = (ll <= (Np1 - 1) / 2) ? ll : ll - Np1;
+        if (Np1 % 2 == 0 && ll == Np1 / 2) A[ll] = std::cos(M_PI * Np1 * z / L1);
+        else A[ll] = std::polar(1.0, 2 * M_PI * ls * z / L1);
+      }
+      for (int n = 0; n < Np1; ++n) {
+        std::complex<double> acc = 0;
+        for (int ll = 0; ll < Np1; ++ll) acc += A[ll] * Bt[(size_t)ll * Np1 + n];
+        acc /= (double)Np1;
+        W[(size_t)s2 * Np1 + n] = mk<T>((T)acc.real(), (T)acc.imag());
+      }
+    }
+    fc_status s = bk.h2d(ws + l.DZZ, W.data(), sizeof(cx<T>) * W.size());
+    if (s) return s;
+    using K = KInterp<T>;
+    typename K::Args a;
+    a.X1 = reinterpret_cast<const cx<T>*>(src.ws + l1.X[src.cur]);
+    a.Np1 = l1.Np; a.Kx1 = l1.Kx; a.Kxp1 = l1.Kxp; a.Ny1 = src.p.Ny; a.Nx1 = src.p.Nx; a.ntiles1 = l1.ntiles;
+    a.M2 = buf<T>(l.V); a.Nz2 = p.Nz; a.Kx2 = l.Kx; a.Kxp2 = l.Kxp; a.Ny2 = p.Ny; a.Nx2 = p.Nx; a.ntiles2 = l.ntiles;
+    a.W = buf<T>(l.DZZ);
+    a.scale = (T)((double)p.Nx * p.Ny / ((double)src.p.Nx * src.p.Ny));
+    a.sblocks = (p.Nz + 15) / 16;
+    s = bk.template run<K>(a, (long long)a.sblocks * l.ntiles * l.nf, st);
+    if (!s) s = z_continue<T>(buf<T>(l.V), Xb<T>(cur), l.nf, nullptr, 0.0, st);
+    if (!s) s = bk.memset(ws + l.gradp, 0, sizeof(double) * 8 * l.lines, st);
+    if (!s) s = mean_init<T>(cur, st);
+    return s;
+  }
+  fc_status interpolate_from_any(const NsCore& src, void* st) {
+    if (src.p.prec != p.prec || src.p.nfields != p.nfields || p.Nx < src.p.Nx || p.Ny < src.p.Ny ||
+        src.p.Lx != p.Lx || src.p.Ly != p.Ly || src.p.Lz != p.Lz)
+      return FC_ERR_ARG;
+    return f32() ? interpolate_from<float>(src, st) : interpolate_from<double>(src, st);
+  }
+
   template <class T>
   fc_status rhs(const T* in, T* out, void* st) {
     cx<T>* Xs = Xb<T>((cur + 1) % 3);

@@ -413,7 +413,7 @@ struct KZProject {
   static constexpr int THREADS = E::THREADS, NPHASE = 7;
   // phases 1..3 run four times (Y^, W^, sigma, sigma_z) from one copy of code
   static constexpr int LB = 1, LE = 4, NIT = 4;
-  static constexpr int MINB = LINES <= 4 ? 3 : 1;
+  static constexpr int MINB = THREADS <= 160 ? 3 : (THREADS <= 320 ? 2 : 1);
   struct Args {
     ZGeom g;
     ZTab<T> t;
@@ -1253,6 +1253,70 @@ struct KMeanLine {
   static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& r) {
     if constexpr (P < 4) Base::template phase<P>(a, sm, tid, bid, r);
     else Base::write(a, sm, tid, bid);
+  }
+};
+
+// ===========================================================================
+// KInterp  restart on a finer grid (Sec. 6, spectral interpolation): for every
+// (kx, ky) line of the destination grid, the source line with the same
+// wavenumbers (zero padding in x, y; a coarse Nyquist coefficient, which
+// stands for a cosine, split in half between +N/2 and -N/2) has its
+// N'-periodic z series evaluated at the destination's Nz physical points:
+//   M[f][s][line2] = scale * w * sum_n W[s][n] X1[f][n][line1].
+// Block: 16 destination lines (one tile) x 16 rows s; thread (s % 16, line).
+// ===========================================================================
+template <class T>
+struct KInterp {
+  using C = cx<T>;
+  static constexpr int THREADS = 256, NPHASE = 1, MINB = 2;
+  struct Args {
+    const C* X1;        // source state, tiled [nf][N'1][lines1]
+    int Np1, Kx1, Kxp1, Ny1, Nx1;
+    long long ntiles1;
+    C* M2;              // destination mixed rows, tiled [nf][Nz2][lines2]
+    int Nz2, Kx2, Kxp2, Ny2, Nx2;
+    long long ntiles2;
+    const C* W;         // [Nz2][N'1] evaluation weights (1/N'1 included)
+    T scale;            // (Nx2 Ny2) / (Nx1 Ny1)
+    int sblocks;        // ceil(Nz2 / 16)
+  };
+  struct Regs { int dummy; };
+  static constexpr size_t smem_bytes = 16;
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char*, int tid, long long bid, Regs&) {
+    const int li = tid & 15, sl = tid >> 4;
+    const long long tile = (bid / a.sblocks) % a.ntiles2;
+    const int f = (int)(bid / a.sblocks / a.ntiles2);
+    const int s = (int)(bid % a.sblocks) * 16 + sl;
+    if (s >= a.Nz2) return;
+    const long long line2 = tile * TL + li;
+    const int kx2 = (int)(line2 % a.Kxp2), ky2 = (int)(line2 / a.Kxp2);
+    C acc = mk<T>(0, 0);
+    // source line and weight of this destination mode (none: zero)
+    int kx1 = -1, ky1 = -1;
+    T w = a.scale;
+    if (kx2 < a.Kx2 && ky2 < a.Ny2) {
+      if (a.Nx2 == a.Nx1) kx1 = kx2;
+      else if (kx2 < a.Nx1 / 2) kx1 = kx2;
+      else if (kx2 == a.Nx1 / 2) { kx1 = kx2; w *= T(0.5); }
+      const int m = ky2 < a.Ny2 / 2 ? ky2 : ky2 - a.Ny2;   // signed ky (sizes are even)
+      if (a.Ny2 == a.Ny1) ky1 = ky2;
+      else if (2 * (m < 0 ? -m : m) < a.Ny1) ky1 = m < 0 ? m + a.Ny1 : m;
+      else if (2 * (m < 0 ? -m : m) == a.Ny1) { ky1 = a.Ny1 / 2; w *= T(0.5); }
+    }
+    if (kx1 >= 0 && ky1 >= 0) {
+      const long long line1 = (long long)ky1 * a.Kxp1 + kx1;
+      const C* x = a.X1 + lay(f, 0, line1, a.Np1, a.ntiles1);
+      const C* wr = a.W + (long long)s * a.Np1;
+      for (int n = 0; n < a.Np1; ++n) {
+        const C xv = x[n * TL], wv = wr[n];
+        acc.x += wv.x * xv.x - wv.y * xv.y;
+        acc.y += wv.x * xv.y + wv.y * xv.x;
+      }
+      acc = cscale(acc, w);
+    }
+    if (line2 < (long long)a.Ny2 * a.Kxp2) a.M2[lay(f, s, line2, a.Nz2, a.ntiles2)] = acc;
   }
 };
 

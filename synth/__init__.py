@@ -241,6 +241,27 @@ def chandrasekhar_reid_noise(Nx: int, Ny: int, Nz: int, Lx: float = 2 * np.pi, L
 
 
 # ----------------------------------------------------------------------------
+# ensembles of independent channel instances of uneven sizes
+# ----------------------------------------------------------------------------
+
+ENSEMBLE_GRIDS = ((64, 64, 65), (96, 96, 97), (128, 128, 129), (192, 192, 129))
+
+
+def ensemble_specs(n: int = 64, seed_offset: int = 0, grids=ENSEMBLE_GRIDS, nu_range=(1e-3, 1e-2)):
+    """n channel instances: grid drawn uniformly from ``grids``, viscosity
+    log-uniform in ``nu_range`` (the batched-ensemble workload).  Returns a list
+    of dicts (Nx, Ny, Nz, nu, seed_offset); each instance's fields come from
+    ``channel_velocity(..., seed_offset=...)``."""
+    g = rng(4, seed_offset)
+    out = []
+    for i in range(n):
+        Nx, Ny, Nz = grids[int(g.integers(0, len(grids)))]
+        nu = float(np.exp(g.uniform(np.log(nu_range[0]), np.log(nu_range[1]))))
+        out.append(dict(Nx=Nx, Ny=Ny, Nz=Nz, nu=nu, seed_offset=1000 + i))
+    return out
+
+
+# ----------------------------------------------------------------------------
 # Rayleigh-Benard (Boussinesq): fields u, v, w, theta
 # ----------------------------------------------------------------------------
 

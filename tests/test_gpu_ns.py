@@ -322,3 +322,26 @@ def test_wall_slip_dt_study(api, o):
         slips.append(d["wall_u_ms"])
     if o <= 2:
         assert np.log2(slips[0] / slips[1]) > 3.5
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_restart_interpolation(api, prec, tol):
+    """ns_interpolate (Sec. 6 restarts): 64^2 x 65 after one RK3 step onto
+    128^2 x 129, against the oracle's spectral interpolation."""
+    nu = 1e-2
+    src = api.Sim(api.ns_params(Nx=64, Ny=64, Nz=65, nu=nu, forcing_x=10 * nu, prec=prec))
+    dst = api.Sim(api.ns_params(Nx=128, Ny=128, Nz=129, nu=nu, forcing_x=10 * nu, prec=prec))
+    v = synth.channel_velocity(64, 64, 65, nu=nu)
+    src.set_fields(_cuda(v, src.dtype))
+    src.step(1e-3)
+    dst.interpolate_from(src)
+    P1, P2 = ns.Params(64, 64, 65, nu=nu, forcing_x=10 * nu), ns.Params(128, 128, 129, nu=nu, forcing_x=10 * nu)
+    st = ns.to_spectral(v, P1)
+    st, _ = ns.rk_step(st, np.zeros((2, 2, 64, P1.Kx), complex), P1, 1e-3)
+    ref = ns.to_physical(ns.spectral_interpolate(st, P1, P2), P2)
+    assert _rel(dst.get_fields().cpu().numpy(), ref) < tol
+    assert torch.count_nonzero(dst.wall_gradp()) == 0
+    dst.step(5e-4)                                    # the restarted run advances
+    assert torch.isfinite(dst.get_fields()).all()
+    src.close()
+    dst.close()

@@ -187,3 +187,23 @@ def test_float32_mean_flow_accumulates_in_float64():
         hs.close()
     rel = np.abs(means[0] - means[1]).max() / np.abs(means[1]).max()
     assert rel < 2.4e-7, rel
+
+
+@pytest.mark.parametrize("src,dst", [((16, 16, 33), (32, 32, 65)), ((16, 16, 33), (16, 16, 49)),
+                                     ((32, 32, 33), (32, 32, 33))])
+def test_interpolation_matches_oracle(src, dst):
+    """Restart on another grid (Sec. 6): KInterp + re-continuation vs the
+    oracle's zero padding / series evaluation (float64)."""
+    hs1 = HostSim(Nx=src[0], Ny=src[1], Nz=src[2], nu=1e-2, prec="f64")
+    hs2 = HostSim(Nx=dst[0], Ny=dst[1], Nz=dst[2], nu=1e-2, prec="f64")
+    P1, P2 = ns.Params(*src), ns.Params(*dst)
+    v = synth.channel_velocity(*src)
+    hs1.set_fields(v)
+    hs1.step(1e-3)                     # a state that is not a plain continuation
+    st = ns.to_spectral(v, P1)
+    st, _ = ns.rk_step(st, np.zeros((2, 2, src[1], P1.Kx), complex), P1, 1e-3)
+    assert hs2.interpolate_from(hs1) == 0
+    ref = ns.to_physical(ns.spectral_interpolate(st, P1, P2), P2)
+    assert _rel(hs2.get_fields(), ref) < 1e-12
+    hs1.close()
+    hs2.close()

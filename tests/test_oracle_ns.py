@@ -234,3 +234,45 @@ def test_wall_slip_converges_with_dt(Mr_5_25, o):
     order = math.log2(res[0][0] / res[1][0])
     assert order > 3.5, order
     assert max(r[2] for r in res) < 1e-28
+
+
+
+def _bandlimited(Nx, Ny, Nz):
+    """Band-limited in x, y (including both Nyquist cosines of a 16-point grid),
+    smooth in z."""
+    x = np.arange(Nx) * 2 * np.pi / Nx
+    y = np.arange(Ny) * 2 * np.pi / Ny
+    z = synth.z_grid(Nz)
+    X, Y = np.meshgrid(x, y)
+    a = (np.cos(2 * X + Y)[None] * np.sin(2 * z)[:, None, None]
+         + np.cos(3 * X - 2 * Y)[None] * (z ** 2)[:, None, None]
+         + np.cos(8 * X)[None] * np.exp(z)[:, None, None] + np.cos(8 * Y)[None] * np.cos(z)[:, None, None])
+    return np.stack([a, 0.5 * a, -a])
+
+
+def test_interpolation_identity():
+    """Interpolating onto the same grid returns the same fields."""
+    P = ns.Params(16, 16, 33)
+    v = synth.channel_velocity(16, 16, 33)
+    out = ns.to_physical(ns.spectral_interpolate(ns.to_spectral(v, P), P, P), P)
+    assert np.abs(out - v).max() < 1e-13 * np.abs(v).max()
+
+
+def test_interpolation_horizontal_refinement_is_exact():
+    """Same Nz, finer x, y: a band-limited field (Nyquist cosines included) is
+    reproduced to round-off on the finer grid."""
+    P1, P2 = ns.Params(16, 16, 33), ns.Params(32, 48, 33, Ly=2 * np.pi)
+    f1, f2 = _bandlimited(16, 16, 33), _bandlimited(32, 48, 33)
+    out = ns.to_physical(ns.spectral_interpolate(ns.to_spectral(f1, P1), P1, P2), P2)
+    assert np.abs(out - f2).max() < 1e-12
+
+
+def test_interpolation_vertical_refinement_converges():
+    """Finer Nz: the continued series is evaluated between the old points; the
+    error is the FC error of the source grid and falls with its Nz."""
+    errs = []
+    for nz1, nz2 in ((33, 65), (65, 129)):
+        P1, P2 = ns.Params(16, 16, nz1), ns.Params(32, 32, nz2)
+        out = ns.to_physical(ns.spectral_interpolate(ns.to_spectral(_bandlimited(16, 16, nz1), P1), P1, P2), P2)
+        errs.append(np.abs(out - _bandlimited(32, 32, nz2)).max())
+    assert errs[0] < 1e-7 and errs[1] < 3e-9 and errs[1] < errs[0] / 10
