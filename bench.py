@@ -553,6 +553,7 @@ def main():
     rks = None if args.no_rk else bench_rk(api, torch, args.rk_steps, 2, with_e2e=False, shape=(1024, 1024, 487))
     ens = None if args.no_rk else bench_ensemble(api, torch)
     srv = None if args.no_rk else bench_serving(api, torch)
+    srv_low = None if args.no_rk else bench_serving(api, torch, rate=300.0)
     # companion: the paper's kind of smooth N' (512 = 487 + 25) at the same horizontal size
     DERIV_SHAPE = (3, 512, 512, 487)
     rs = bench_deriv(api, torch, np.float32, args.steps, 2, with_e2e=False)
@@ -576,6 +577,7 @@ def main():
         "rk_stage_smooth_Np512_1024x1024x487": rks,
         "ensemble_64_uneven_fp32_graph": ens,
         "serving_poisson_2000_per_s": srv,
+        "serving_poisson_300_per_s": srv_low,
         "roofline": {"bound": "hbm", "achieved": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9,
                      "peak": hbm_peak, "unit": "GB/s",
                      "frac": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9 / hbm_peak,

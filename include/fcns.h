@@ -277,6 +277,24 @@ fc_status ns_diagnostics(ns_sim_t sim, double* div_ms, double* wall_u_ms, double
                          double* flow_rate, double* nusselt, fc_stream_t stream);
 
 /*
+ * ns_profiles -- horizontal statistics of the current state (Sec. 6 r.m.s.
+ * velocity profiles and spectra; Sec. 7 temperature profiles), synchronous,
+ * host outputs (each may be NULL), by Parseval from the state's physical rows:
+ *   mean[f*Nz + s]       <q_f>_{x,y} at z_s,
+ *   rms[f*Nz + s]        sqrt(<(q_f - <q_f>_{x,y})^2>_{x,y}) at z_s,
+ *   spectrum[f*ns + j]   (1/Lz) int dz of the horizontal power of q_f in shell j
+ *                        (modes with j - 1/2 <= |k_perp|/dk < j + 1/2, the mean
+ *                        mode excluded; trapezoid rule over the Nz levels), so
+ *                        sum_j spectrum = <rms^2>_z;
+ * ns and dk from ns_spectrum_shells (dk = min(2 pi/Lx, 2 pi/Ly)).  Uses the
+ * simulation's work buffers (not its state).
+ */
+fc_status ns_profiles(ns_sim_t sim, double* mean, double* rms, double* spectrum, fc_stream_t stream);
+
+/* Number of spectrum shells and their width (either pointer may be NULL). */
+fc_status ns_spectrum_shells(ns_sim_t sim, int* nshell, double* dk);
+
+/*
  * ns_interpolate -- restart on another grid (Sec. 6: "spectral interpolation,
  * by zero padding the transformed fields in the wavenumber domain"): the state
  * of dst becomes the interpolant of src's state, re-continued on dst's grid;

@@ -419,3 +419,41 @@ def spectral_interpolate(state: np.ndarray, p1: Params, p2: Params) -> np.ndarra
                 blk[..., Kx1 - 1] *= 0.5                     # coarse x Nyquist (r2c: one side stored)
             mixed2[:, :, j2, :Kx1] += blk
     return z_forward(mixed2, p2)
+
+
+# ----------------------------------------------------------------------------
+# horizontal statistics (Sec. 6 r.m.s. profiles and spectra)
+# ----------------------------------------------------------------------------
+
+def profiles(state: np.ndarray, p: Params):
+    """Horizontal mean and r.m.s. fluctuation of every field at the Nz
+    physical levels, computed in physical space: [nf][Nz] each."""
+    phys = to_physical(state, p)
+    mean = phys.mean(axis=(-2, -1))
+    rms = np.sqrt(((phys - mean[..., None, None]) ** 2).mean(axis=(-2, -1)))
+    return mean, rms
+
+
+def shell_spectrum(state: np.ndarray, p: Params):
+    """Horizontal power of every field in shells of |k_perp| (width
+    dk = min(2 pi/Lx, 2 pi/Ly), shell j holds j - 1/2 <= |k_perp|/dk < j + 1/2,
+    mean mode excluded), averaged over z with the trapezoid rule: sums to the
+    z-average of rms^2.  From the physical fields' 2D FFTs (full spectrum)."""
+    phys = to_physical(state, p)
+    nf = phys.shape[0]
+    F = np.fft.fft2(phys, axes=(-2, -1)) / (p.Nx * p.Ny)          # [nf][Nz][Ny][Nx]
+    P = np.abs(F) ** 2
+    P[..., 0, 0] = 0.0
+    kx = 2 * np.pi * np.fft.fftfreq(p.Nx, 1.0 / p.Nx) / p.Lx
+    ky = 2 * np.pi * np.fft.fftfreq(p.Ny, 1.0 / p.Ny) / p.Ly
+    dk = min(2 * np.pi / p.Lx, 2 * np.pi / p.Ly)
+    kmax = math.hypot(math.pi * p.Nx / p.Lx, math.pi * p.Ny / p.Ly)
+    ns = int(math.floor(kmax / dk + 0.5)) + 1
+    j = np.floor(np.hypot(kx[None, :], ky[:, None]) / dk + 0.5).astype(int)
+    wz = np.full(p.Nz, 1.0 / (p.Nz - 1))
+    wz[[0, -1]] *= 0.5
+    out = np.zeros((nf, ns))
+    Pz = np.einsum("fzyx,z->fyx", P, wz)
+    for f in range(nf):
+        np.add.at(out[f], np.minimum(j, ns - 1).ravel(), Pz[f].ravel())
+    return out, dk

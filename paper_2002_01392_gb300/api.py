@@ -58,6 +58,9 @@ _sig("fc_setup_ex", [_c_int, _c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_vp)
 _sig("fc_plan_matrix", [_vp, ctypes.POINTER(_c_double)])
 _sig("fc_plan_info", [_vp] + [ctypes.POINTER(_c_int)] * 5 + [ctypes.POINTER(_c_double)])
 _sig("fc_destroy", [_vp])
+_sig("ns_interpolate", [_vp, _vp, _vp])
+_sig("ns_profiles", [_vp] + [ctypes.POINTER(_c_double)] * 3 + [_vp])
+_sig("ns_spectrum_shells", [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_double)])
 _sig("ns_batch_create", [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(_vp)])
 _sig("ns_batch_step", [_vp, ctypes.POINTER(_c_double), _vp])
 _sig("ns_batch_info", [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)])
@@ -69,7 +72,8 @@ EXPORTED = ["fc_status_str", "fc_last_error", "fc_setup", "fc_setup_ex", "fc_pla
             "fc_destroy", "fc_deriv_z", "fc_deriv_z_noalloc", "ns_params_default", "ns_workspace_bytes", "ns_create", "ns_destroy",
             "ns_set_fields", "ns_get_fields", "ns_get_state", "ns_put_state", "ns_get_wall_gradp",
             "ns_put_wall_gradp", "ns_rhs", "fc_poisson_project", "rk_step", "ns_diagnostics",
-            "ns_batch_create", "ns_batch_step", "ns_batch_info", "ns_batch_destroy", "ns_interpolate"]
+            "ns_batch_create", "ns_batch_step", "ns_batch_info", "ns_batch_destroy", "ns_interpolate",
+            "ns_profiles", "ns_spectrum_shells"]
 
 
 def _check(status: int, where: str):
@@ -285,6 +289,20 @@ class Sim:
 
     def step(self, dt: float, stream=None):
         _check(_lib.rk_step(self.handle, float(dt), _stream(stream)), "rk_step")
+
+    def profiles(self, stream=None):
+        """ns_profiles: dict of numpy arrays mean [nf][Nz], rms [nf][Nz],
+        spectrum [nf][nshell] and the shell width dk (synchronous)."""
+        import numpy as np
+        ns_, dk = _c_int(), _c_double()
+        _check(_lib.ns_spectrum_shells(self.handle, ctypes.byref(ns_), ctypes.byref(dk)), "ns_spectrum_shells")
+        nf, Nz = self.p.nfields, self.p.Nz
+        mean, rms = np.empty((nf, Nz)), np.empty((nf, Nz))
+        spec = np.empty((nf, ns_.value))
+        P = ctypes.POINTER(_c_double)
+        _check(_lib.ns_profiles(self.handle, mean.ctypes.data_as(P), rms.ctypes.data_as(P), spec.ctypes.data_as(P),
+                                _stream(stream)), "ns_profiles")
+        return dict(mean=mean, rms=rms, spectrum=spec, dk=dk.value)
 
     def interpolate_from(self, src: "Sim", stream=None):
         """ns_interpolate: this state := spectral interpolation of src's state."""

@@ -35,7 +35,7 @@ static int emu_deriv(const double* Mr, int d, int Cc, int Nz, int batch, long lo
   std::vector<float2> Mr2(Cc * d);
   for (int i = 0; i < Cc * d; ++i) { Mr2[i].x = (float)Mr[i]; Mr2[i].y = (float)(Mr[i] - (double)Mr2[i].x); }
   a.Mr = Mr; a.Mr2 = Mr2.data(); a.H1 = H1t.data(); a.H2 = H2t.data(); a.tw = twt.data();
-  a.nblocks = a.tiles * batch; a.pf_dist = 3;
+
   phased_emulate<K>(a, a.tiles * batch, K::smem_bytes);
   return 0;
 }
@@ -115,6 +115,7 @@ int fchc_ns_project(void* h, double dt, const void* in, void* out, void* gp) {
   return ((NsCore<EmuBK>*)h)->project_any(dt, in, out, gp, nullptr);
 }
 int fchc_ns_step(void* h, double dt) { return ((NsCore<EmuBK>*)h)->step_any(dt, nullptr); }
+int fchc_ns_profiles_raw(void* h, double* out) { return ((NsCore<EmuBK>*)h)->profiles_any(out, nullptr); }
 int fchc_ns_interpolate(void* dst, void* src) {
   return ((NsCore<EmuBK>*)dst)->interpolate_from_any(*(NsCore<EmuBK>*)src, nullptr);
 }

@@ -36,15 +36,6 @@ fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long 
   if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(fc_deriv_z)");
   const long long grid = a.tiles * batch;
   if (grid > 0x7fffffffLL) return FC_ERR_UNSUPPORTED;
-  // resident blocks on the device: the prefetch distance of the L2 prefetch
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 0;
-  }
-  a.nblocks = grid;
-  a.pf_dist = (long long)sms * K::MINB;
   kern<<<(unsigned)grid, K::THREADS, K::smem_bytes, stream>>>(a);
   return cuda_status(cudaGetLastError(), "fc_deriv_z launch");
 }

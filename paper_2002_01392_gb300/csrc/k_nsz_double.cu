@@ -15,4 +15,5 @@ template struct DevRun<KDiag<double>>;
 template struct DevRun<KMeanLine<double>>;
 template struct DevRun<KMeanInit<double>>;
 template struct DevRun<KInterp<double>>;
+template struct DevRun<KProf<double>>;
 }  // namespace fcns

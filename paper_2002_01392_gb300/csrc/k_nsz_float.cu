@@ -15,4 +15,5 @@ template struct DevRun<KDiag<float>>;
 template struct DevRun<KMeanLine<float>>;
 template struct DevRun<KMeanInit<float>>;
 template struct DevRun<KInterp<float>>;
+template struct DevRun<KProf<float>>;
 }  // namespace fcns

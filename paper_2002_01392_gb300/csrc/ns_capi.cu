@@ -193,6 +193,37 @@ fc_status rk_step(ns_sim_t s, double dt, fc_stream_t stream) {
   return s->core.step_any(dt, stream);
 }
 
+fc_status ns_spectrum_shells(ns_sim_t s, int* nshell, double* dk) {
+  fc_status st = check_sim(s, "ns_spectrum_shells");
+  if (st) return st;
+  if (nshell) *nshell = s->core.nshell();
+  if (dk) *dk = s->core.shell_width();
+  return FC_OK;
+}
+
+fc_status ns_profiles(ns_sim_t s, double* mean, double* rms, double* spectrum, fc_stream_t stream) {
+  fc_status st = check_sim(s, "ns_profiles");
+  if (st) return st;
+  const ns_params& p = s->core.p;
+  const int nf = p.nfields, Nz = p.Nz, ns = s->core.nshell();
+  std::vector<double> raw((size_t)nf * Nz * (2 + ns));
+  st = s->core.profiles_any(raw.data(), stream);
+  if (st) return st;
+  const double n1 = (double)p.Nx * p.Ny, n2 = n1 * n1;
+  if (spectrum) std::memset(spectrum, 0, sizeof(double) * nf * ns);
+  for (int f = 0; f < nf; ++f)
+    for (int z = 0; z < Nz; ++z) {
+      const double* r = raw.data() + ((size_t)f * Nz + z) * (2 + ns);
+      if (mean) mean[(size_t)f * Nz + z] = r[1] / n1;
+      if (rms) rms[(size_t)f * Nz + z] = std::sqrt(r[0] / n2);
+      if (spectrum) {
+        const double wz = (z == 0 || z == Nz - 1) ? 0.5 / (Nz - 1) : 1.0 / (Nz - 1);  // trapezoid, / Lz
+        for (int j = 0; j < ns; ++j) spectrum[(size_t)f * ns + j] += wz * r[2 + j] / n2;
+      }
+    }
+  return FC_OK;
+}
+
 fc_status ns_interpolate(ns_sim_t dst, ns_sim_t src, fc_stream_t stream) {
   fc_status st = check_sim(dst, "ns_interpolate");
   if (!st) st = check_sim(src, "ns_interpolate");

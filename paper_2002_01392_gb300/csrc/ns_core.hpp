@@ -514,6 +514,31 @@ struct NsCore {
     if (!s) s = mean_init<T>(cur, st);
     return s;
   }
+  // horizontal statistics of the current state per field and physical level
+  // (KProf); out: host [nf][Nz][2 + nshell] (unnormalised sums, see KProf)
+  int nshell() const {
+    const double kxm = M_PI * p.Nx / p.Lx, kym = M_PI * p.Ny / p.Ly;
+    return (int)std::floor(std::sqrt(kxm * kxm + kym * kym) / shell_width() + 0.5) + 1;
+  }
+  double shell_width() const { return std::min(2 * M_PI / p.Lx, 2 * M_PI / p.Ly); }
+  template <class T>
+  fc_status profiles(double* out, void* st) {
+    using K = KProf<T>;
+    typename K::Args a;
+    a.g = zgeom(l.nf); a.Nx = p.Nx; a.X = Xb<T>(cur);
+    a.kx_unit = 2 * M_PI / p.Lx; a.ky_unit = 2 * M_PI / p.Ly; a.dk = shell_width();
+    a.nshell = nshell();
+    if (a.nshell > K::NSMAX) return FC_ERR_UNSUPPORTED;
+    const size_t bytes = sizeof(double) * (size_t)l.nf * p.Nz * (2 + a.nshell);
+    if (bytes > 2 * l.es * (size_t)l.nf * p.Nz * l.plines) return FC_ERR_UNSUPPORTED;
+    a.out = reinterpret_cast<double*>(ws + l.NL);
+    fc_status s = bk.memset(ws + l.NL, 0, bytes, st);
+    if (!s) s = bk.template run<K>(a, (long long)l.nf * p.Nz, st);
+    if (!s) s = bk.d2h(out, ws + l.NL, bytes, st);
+    return s;
+  }
+  fc_status profiles_any(double* out, void* st) { return f32() ? profiles<float>(out, st) : profiles<double>(out, st); }
+
   fc_status interpolate_from_any(const NsCore& src, void* st) {
     if (src.p.prec != p.prec || src.p.nfields != p.nfields || p.Nx < src.p.Nx || p.Ny < src.p.Ny ||
         src.p.Lx != p.Lx || src.p.Ly != p.Ly || src.p.Lz != p.Lz)

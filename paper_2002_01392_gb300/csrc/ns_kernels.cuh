@@ -1320,6 +1320,75 @@ struct KInterp {
   }
 };
 
+// ===========================================================================
+// KProf  horizontal statistics per field and physical level z_s (Sec. 6
+// r.m.s. profiles and spectra), by Parseval from the state rows n < Nz (the
+// state is in (kx, ky, z') space and z' = z at the physical points):
+//   sum[f][s]      = sum over (kx, ky) != (0, 0) of w |X|^2   (w = 2 for the
+//                    kx stored once for +-kx, else 1)
+//   mean[f][s]     = Re X(0, 0)
+//   bins[f][s][j]  = sum of w |X|^2 over the modes of shell j = round(|k_perp| / dk)
+// (all unnormalised; the host divides by (Nx Ny)^2).  One block per (f, s).
+// ===========================================================================
+template <class T>
+struct KProf {
+  using C = cx<T>;
+  static constexpr int THREADS = 256, NPHASE = 3, MINB = 2;
+  struct Args {
+    ZGeom g;
+    int Nx;
+    const C* X;          // state [nf][N'][lines]
+    double kx_unit, ky_unit, dk;   // 2 pi / Lx, 2 pi / Ly, shell width
+    int nshell;
+    double* out;         // [nf][Nz][2 + nshell]: sum, mean, bins
+  };
+  struct Regs { double s; };
+  static constexpr int NSMAX = 2048;
+  static constexpr size_t smem_bytes = sizeof(double) * (THREADS + NSMAX);
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
+    double* red = reinterpret_cast<double*>(sm);
+    double* bins = red + THREADS;
+    const int f = (int)(bid / a.g.Nz), s = (int)(bid % a.g.Nz);
+    double* o = a.out + ((long long)f * a.g.Nz + s) * (2 + a.nshell);
+    if constexpr (P == 0) {
+      for (int j = tid; j < a.nshell; j += THREADS) bins[j] = 0.0;
+    } else if constexpr (P == 1) {
+      R.s = 0.0;
+      for (long long l = tid; l < a.g.lines; l += THREADS) {
+        const int kx = (int)(l % a.g.Kxp), ky = (int)(l / a.g.Kxp);
+        if (kx >= a.g.Kx) continue;
+        const C v = a.X[lay(f, s, l, a.g.Np, a.g.ntiles)];
+        if (kx == 0 && ky == 0) {
+          o[1] = (double)v.x;
+          continue;
+        }
+        const double w = (kx == 0 || 2 * kx == a.Nx) ? 1.0 : 2.0;
+        const double p = w * ((double)v.x * v.x + (double)v.y * v.y);
+        R.s += p;
+        const int m = ky <= (a.g.Ny - 1) / 2 ? ky : ky - a.g.Ny;
+        const double kxp = a.kx_unit * kx, kyp = a.ky_unit * m;
+        int j = (int)floor(sqrt(kxp * kxp + kyp * kyp) / a.dk + 0.5);
+        if (j >= a.nshell) j = a.nshell - 1;
+#if defined(__CUDA_ARCH__)
+        atomicAdd(bins + j, p);
+#else
+        bins[j] += p;
+#endif
+      }
+      red[tid] = R.s;
+    } else {
+      if (tid == 0) {
+        double t = 0.0;
+        for (int i = 0; i < THREADS; ++i) t += red[i];
+        o[0] = t;
+      }
+      for (int j = tid; j < a.nshell; j += THREADS) o[2 + j] = bins[j];
+    }
+  }
+};
+
 // shadow <- float32 state line 0 of u, v (, theta)
 template <class T>
 struct KMeanInit {

@@ -18,7 +18,8 @@ class HostSim:
         self.lib.fchc_ns_create.restype = ctypes.c_void_p
         self.lib.fchc_ns_create.argtypes = [ctypes.c_void_p]
         for n in ("fchc_ns_set_fields", "fchc_ns_get_fields", "fchc_ns_rhs", "fchc_ns_step", "fchc_ns_project",
-                  "fchc_ns_destroy", "fchc_ns_get_state", "fchc_ns_diag_raw", "fchc_ns_interpolate"):
+                  "fchc_ns_destroy", "fchc_ns_get_state", "fchc_ns_diag_raw", "fchc_ns_interpolate",
+                  "fchc_ns_profiles_raw"):
             getattr(self.lib, n).argtypes = None
         self.p = ns_params(**kw)
         self.h = self.lib.fchc_ns_create(ctypes.addressof(self.p))
@@ -52,6 +53,11 @@ class HostSim:
         assert self.lib.fchc_ns_project(ctypes.c_void_p(self.h), ctypes.c_double(dt), self._vp(a), self._vp(out),
                                         self._vp(gp)) == 0
         return out, gp
+
+    def profiles_raw(self, nshell):
+        out = np.zeros((self.p.nfields, self.p.Nz, 2 + nshell))
+        assert self.lib.fchc_ns_profiles_raw(ctypes.c_void_p(self.h), self._vp(out)) == 0
+        return out
 
     def interpolate_from(self, src):
         return self.lib.fchc_ns_interpolate(ctypes.c_void_p(self.h), ctypes.c_void_p(src.h))

@@ -345,3 +345,23 @@ def test_restart_interpolation(api, prec, tol):
     assert torch.isfinite(dst.get_fields()).all()
     src.close()
     dst.close()
+
+
+
+def test_profiles_and_spectrum(api):
+    """ns_profiles on the GPU vs the oracle after one RK3 step (float64)."""
+    N, Nz, nu = 64, 65, 1e-2
+    sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nu=nu, forcing_x=10 * nu, prec="f64"))
+    P = ns.Params(N, N, Nz, nu=nu, forcing_x=10 * nu)
+    v = synth.channel_velocity(N, N, Nz, nu=nu)
+    sim.set_fields(_cuda(v))
+    sim.step(1e-3)
+    _, _, st = _oracle_steps(v, P, 1e-3, 1)
+    mean, rms = ns.profiles(st, P)
+    E, dk = ns.shell_spectrum(st, P)
+    d = sim.profiles()
+    assert d["dk"] == dk and d["spectrum"].shape == E.shape
+    assert np.abs(d["mean"] - mean).max() < 1e-12 * np.abs(mean).max()
+    assert np.abs(d["rms"] - rms).max() < 1e-11 * rms.max()
+    assert np.abs(d["spectrum"] - E).max() < 1e-11 * E.max()
+    sim.close()

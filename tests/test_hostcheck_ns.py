@@ -207,3 +207,26 @@ def test_interpolation_matches_oracle(src, dst):
     assert _rel(hs2.get_fields(), ref) < 1e-12
     hs1.close()
     hs2.close()
+
+
+
+def test_profiles_kernel_matches_oracle():
+    """KProf sums (Parseval from the state rows) vs the oracle's physical-space
+    statistics: means, r.m.s. profiles and the z-averaged shell spectrum."""
+    N, Nz = 32, 33
+    hs = HostSim(Nx=N, Ny=N, Nz=Nz, nu=1e-2, prec="f64")
+    P = ns.Params(N, N, Nz)
+    v = synth.channel_velocity(N, N, Nz)
+    hs.set_fields(v)
+    st = ns.to_spectral(v, P)
+    mean, rms = ns.profiles(st, P)
+    E, dk = ns.shell_spectrum(st, P)
+    raw = hs.profiles_raw(E.shape[1])
+    n2 = float(N * N) ** 2
+    np.testing.assert_allclose(raw[..., 1] / (N * N), mean, atol=1e-13 * np.abs(mean).max())
+    np.testing.assert_allclose(np.sqrt(raw[..., 0] / n2), rms, rtol=1e-12, atol=1e-15)
+    wz = np.full(Nz, 1.0 / (Nz - 1))
+    wz[[0, -1]] *= 0.5
+    spec = np.einsum("fzj,z->fj", raw[..., 2:], wz) / n2
+    np.testing.assert_allclose(spec, E, rtol=1e-12, atol=1e-14 * E.max())
+    hs.close()

@@ -276,3 +276,32 @@ def test_interpolation_vertical_refinement_converges():
         out = ns.to_physical(ns.spectral_interpolate(ns.to_spectral(_bandlimited(16, 16, nz1), P1), P1, P2), P2)
         errs.append(np.abs(out - _bandlimited(32, 32, nz2)).max())
     assert errs[0] < 1e-7 and errs[1] < 3e-9 and errs[1] < errs[0] / 10
+
+
+
+def test_profiles_and_spectrum_closed_forms():
+    """cos(3x + 4y) g(z) + U(z): mean U, rms |g|/sqrt(2), and all its power in
+    shell 5 (|k| = 5) with the trapezoid mean of g^2/2; Parseval sum rule."""
+    P = ns.Params(32, 32, 33)
+    z = synth.z_grid(33)
+    x = np.arange(32) * 2 * np.pi / 32
+    X, Y = np.meshgrid(x, x)
+    g = np.sin(np.pi * z) * (1 + z)
+    U = z * (1 - z)
+    f = np.cos(3 * X + 4 * Y)[None] * g[:, None, None] + U[:, None, None]
+    phys = np.stack([f, 2 * f, 0 * f])
+    st = ns.to_spectral(phys, P)
+    mean, rms = ns.profiles(st, P)
+    np.testing.assert_allclose(mean[0], U, atol=1e-13)
+    np.testing.assert_allclose(rms[1], 2 * np.abs(g) / np.sqrt(2), atol=1e-13)
+    E, dk = ns.shell_spectrum(st, P)
+    wz = np.full(33, 1 / 32.0)
+    wz[[0, -1]] *= 0.5
+    assert dk == 1.0 and abs(E[0, 5] - (wz * g ** 2 / 2).sum()) < 1e-14
+    assert abs(E[0].sum() - E[0, 5]) < 1e-14
+    # sum rule on a general field
+    v = synth.channel_velocity(32, 32, 33)
+    st = ns.to_spectral(v, P)
+    E, _ = ns.shell_spectrum(st, P)
+    _, rms = ns.profiles(st, P)
+    np.testing.assert_allclose(E.sum(axis=1), (wz * rms ** 2).sum(axis=1), rtol=1e-12)
