@@ -35,11 +35,14 @@ namespace fcns {
 //   IFFT_L(X H1) = d1*a + i d1*b,   IFFT_L(X H2) = d2*a + i d2*b
 // (H1, H2: spectra of d1, d2 placed circularly on L >= N' + Nz - 1, with 1/L):
 // three length-L transforms per two lines instead of four.
-template <class T, int L1_, int L2_, int LINES_>
+// JN: registers j >= JN of the input (indices r + L2 j) are known to be zero
+// (N' <= L2 JN, the padded case) and no output lies there, so their loads,
+// continuation checks and stores are left out at compile time.
+template <class T, int L1_, int L2_, int LINES_, int JN_ = L1_>
 struct DerivPair {
   using E = Eng<T, L1_, L2_, LINES_>;
   using C = cx<T>;
-  static constexpr int L1 = L1_, L2 = L2_, LINES = LINES_;
+  static constexpr int L1 = L1_, L2 = L2_, LINES = LINES_, JN = JN_;
   static constexpr int THREADS = E::THREADS, NPHASE = 4;
   static constexpr int MINB = THREADS <= 160 ? 3 : (THREADS <= 320 ? 2 : 1);
   static constexpr int MR_MAX = 640;
@@ -112,6 +115,10 @@ struct DerivPair {
       if (r < L2) {
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
+          if (j >= JN) {
+            R.v[j] = mk<T>(0, 0);
+            continue;
+          }
           const int n = r + L2 * j;
           C x = mk<T>(0, 0);
           if (n < a.Nz) {
@@ -127,7 +134,7 @@ struct DerivPair {
     } else if constexpr (P == 1) {
       if (r < L2) {
 #pragma unroll
-        for (int j = 0; j < L1; ++j) {
+        for (int j = 0; j < JN; ++j) {
           const int n = r + L2 * j;
           if (n >= a.Nz && n < a.Np) R.v[j] = cont_cplx(n - a.Nz, Ev, Ev + DMAX, a.d, a.Cc, Ms, Ms2);
         }
@@ -160,7 +167,7 @@ struct DerivPair {
           E::template Ai<1>(R.v, o == 0 ? b0 : b1, r, li);
           const T sc = o == 0 ? a.s1 : a.s2;
 #pragma unroll
-          for (int j = 0; j < L1; ++j) {
+          for (int j = 0; j < JN; ++j) {
             const int n = r + L2 * j;
             if (n < a.Nz) {
               T* p = out + base + (long long)n * a.zstride;

@@ -11,10 +11,10 @@
 
 namespace fcns {
 
-template <class T, int L1, int L2, int LINES>
+template <class T, int L1, int L2, int LINES, int JN>
 static int emu_deriv(const double* Mr, int d, int Cc, int Nz, int batch, long long lines, double Lz,
                      const T* f, T* df, T* d2f) {
-  using K = DerivPair<T, L1, L2, LINES>;
+  using K = DerivPair<T, L1, L2, LINES, JN>;
   const int L = L1 * L2;
   std::vector<std::complex<double>> H1, H2, tw;
   deriv_conv_spectra(Nz, Nz + Cc, L, &H1, &H2);
@@ -51,9 +51,14 @@ extern "C" int fchc_deriv_z(int dtype, int L, const double* Mr, int d, int Cc, i
   const long long lines = (long long)Nx * Ny;
 #define HC(LL, A, B, LF, LD)                                                                                 \
   if (L == LL) {                                                                                            \
+    if (Nz + Cc <= B * (A / 2 + 1)) {                                                                       \
+      if (dtype == 0)                                                                                       \
+        return emu_deriv<float, A, B, LF, A / 2 + 1>(Mr, d, Cc, Nz, batch, lines, Lz, (const float*)f, (float*)df, (float*)d2f); \
+      return emu_deriv<double, A, B, LD, A / 2 + 1>(Mr, d, Cc, Nz, batch, lines, Lz, (const double*)f, (double*)df, (double*)d2f); \
+    }                                                                                                       \
     if (dtype == 0)                                                                                         \
-      return emu_deriv<float, A, B, LF>(Mr, d, Cc, Nz, batch, lines, Lz, (const float*)f, (float*)df, (float*)d2f); \
-    return emu_deriv<double, A, B, LD>(Mr, d, Cc, Nz, batch, lines, Lz, (const double*)f, (double*)df, (double*)d2f); \
+      return emu_deriv<float, A, B, LF, A>(Mr, d, Cc, Nz, batch, lines, Lz, (const float*)f, (float*)df, (float*)d2f); \
+    return emu_deriv<double, A, B, LD, A>(Mr, d, Cc, Nz, batch, lines, Lz, (const double*)f, (double*)df, (double*)d2f); \
   }
   HC(64, 8, 8, 16, 8)
   HC(96, 8, 12, 16, 8)

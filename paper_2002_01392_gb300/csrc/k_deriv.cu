@@ -1,46 +1,11 @@
-// Launchers of the fc_deriv_z kernels (float and double, every compiled L).
-#include "deriv_kernel.cuh"
+// fc_deriv_z: compiled transform shapes and the dispatch by precision.
 #include "internal.hpp"
 
 namespace fcns {
 
-namespace {
-
-template <class T, int L1, int L2, int LINES>
-fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long long lines, double Lz,
-                    const void* f, void* df, void* d2f, cudaStream_t stream) {
-  using K = DerivPair<T, L1, L2, LINES>;
-  static_assert(K::smem_bytes <= 227 * 1024, "shared memory budget");
-  typename K::Args a;
-  a.f = static_cast<const T*>(f);
-  a.df = static_cast<T*>(df);
-  a.d2f = static_cast<T*>(d2f);
-  a.Nz = p.Nz; a.Np = p.Np; a.d = p.d; a.Cc = p.C;
-  a.lines = lines;
-  a.pairs = (lines + 1) / 2;
-  a.tiles = (a.pairs + LINES - 1) / LINES;
-  a.zstride = lines;
-  a.bstride = lines * p.Nz;
-  const double dz = Lz / (p.Nz - 1);
-  a.s1 = T(1.0 / dz);
-  a.s2 = T(1.0 / (dz * dz));
-  a.Mr = t.Mr;
-  a.Mr2 = t.Mr2;
-  a.H1 = static_cast<const cx<T>*>(sizeof(T) == 4 ? t.H1_32 : t.H1_64);
-  a.H2 = static_cast<const cx<T>*>(sizeof(T) == 4 ? t.H2_32 : t.H2_64);
-  a.tw = static_cast<const cx<T>*>(sizeof(T) == 4 ? t.tw32 : t.tw64);
-  auto kern = phased_kernel<K>;
-  static bool attr_done = false;  // per instantiation; the attribute is per device but idempotent
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem_bytes);
-  (void)attr_done;
-  if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(fc_deriv_z)");
-  const long long grid = a.tiles * batch;
-  if (grid > 0x7fffffffLL) return FC_ERR_UNSUPPORTED;
-  kern<<<(unsigned)grid, K::THREADS, K::smem_bytes, stream>>>(a);
-  return cuda_status(cudaGetLastError(), "fc_deriv_z launch");
-}
-
-}  // namespace
+template <class T>
+fc_status launch_deriv_typed(const DerivDevTables& t, const PlanData& p, int batch, long long lines, double Lz,
+                             const void* f, void* df, void* d2f, cudaStream_t stream);
 
 const std::vector<EngineShape>& engine_shapes() {
   static const std::vector<EngineShape> s = {
@@ -59,28 +24,8 @@ int pick_engine_length(int need) {
 fc_status launch_deriv_z(const DerivDevTables& t, const PlanData& p, fc_dtype dtype, int batch,
                          long long lines, double Lz, const void* f, void* df, void* d2f,
                          cudaStream_t stream) {
-#define FC_CASE(LL, A, B, LF, LD)                                                                 \
-  case LL:                                                                                        \
-    return dtype == FC_F32 ? run_deriv<float, A, B, LF>(t, p, batch, lines, Lz, f, df, d2f, stream) \
-                           : run_deriv<double, A, B, LD>(t, p, batch, lines, Lz, f, df, d2f, stream);
-  switch (t.L) {
-    FC_CASE(64, 8, 8, 16, 8)
-    FC_CASE(96, 8, 12, 16, 8)
-    FC_CASE(128, 8, 16, 16, 8)
-    FC_CASE(160, 10, 16, 16, 8)
-    FC_CASE(192, 12, 16, 16, 8)
-    FC_CASE(256, 16, 16, 16, 8)
-    FC_CASE(288, 16, 18, 16, 8)
-    FC_CASE(320, 16, 20, 16, 8)
-    FC_CASE(512, 16, 32, 8, 4)
-    FC_CASE(576, 24, 24, 8, 4)
-    FC_CASE(768, 24, 32, 4, 2)
-    FC_CASE(1024, 32, 32, 4, 2)
-    FC_CASE(1080, 30, 36, 4, 2)
-    default:
-      return FC_ERR_UNSUPPORTED;
-  }
-#undef FC_CASE
+  return dtype == FC_F32 ? launch_deriv_typed<float>(t, p, batch, lines, Lz, f, df, d2f, stream)
+                         : launch_deriv_typed<double>(t, p, batch, lines, Lz, f, df, d2f, stream);
 }
 
 }  // namespace fcns

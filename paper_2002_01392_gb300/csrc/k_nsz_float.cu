@@ -5,8 +5,8 @@
 
 namespace fcns {
 #define FC_INST_Z(LL, A, B, D)                                            \
-  template struct DevRun<KZDeriv<float, A, B, z_lines<float, LL>()>>;    \
-  template struct DevRun<KZCombine<float, A, B, z_lines<float, LL>()>>;  \
+  template struct DevRun<KZDeriv<float, A, B, z_lines<float, LL>(), D ? A : A / 2>>; \
+  template struct DevRun<KZCombine<float, A, B, z_lines<float, LL>(), D ? A : A / 2>>; \
   template struct DevRun<KZProject<float, A, B, zproj_lines<float, LL>(), D>>;
 FC_ZSHAPES_PADDED(FC_INST_Z)
 #undef FC_INST_Z

@@ -244,7 +244,7 @@ struct NsCore {
     fc_status s = FC_ERR_UNSUPPORTED;
 #define FC_ZD(LL, A, B, D)                                                        \
   if (l.L == LL) {                                                            \
-    using K = KZDeriv<T, A, B, z_lines<T, LL>()>;                             \
+    using K = KZDeriv<T, A, B, z_lines<T, LL>(), D ? A : A / 2>;                             \
     typename K::Args a;                                                       \
     a.g = zgeom(nf); a.t = ztab<T>(); a.X = X;                                \
     a.DZ = at<cx<T>>(l.DZ); a.DZZ = at<cx<T>>(l.DZZ);                         \
@@ -264,7 +264,7 @@ struct NsCore {
     fc_status s = FC_ERR_UNSUPPORTED;
 #define FC_ZC(LL, A, B, D)                                                        \
   if (l.L == LL) {                                                            \
-    using K = KZCombine<T, A, B, z_lines<T, LL>()>;                           \
+    using K = KZCombine<T, A, B, z_lines<T, LL>(), D ? A : A / 2>;                           \
     typename K::Args a;                                                       \
     a.g = zgeom(nf); a.t = ztab<T>(); a.NL = NL; a.Xt = Xt; a.Xj = Xj;        \
     a.DZZ = at<cx<T>>(l.DZZ); a.Xout = Xo; a.gradp = at<double2>(l.gradp);    \

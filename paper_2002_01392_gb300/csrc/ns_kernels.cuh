@@ -120,7 +120,10 @@ FC_HD void load_mr(unsigned char* sm, const ZTab<T>& t, int n, int tid, int thre
 // the N'-periodic grid (= multiplication of the continued spectrum by i kz
 // (Nyquist zeroed) and -kz^2, Sec. 4.2), first Nz outputs.
 // ===========================================================================
-template <class T, int L1, int L2, int LINES>
+// JN: input registers j >= JN (indices r + L2 j >= L2 JN) are known to be
+// zero and hold no output: L2 JN >= N' (padded lengths, L >= 2 N' - 1, give
+// JN = L1 / 2; direct lengths JN = L1).
+template <class T, int L1, int L2, int LINES, int JN = L1>
 struct KZDeriv {
   using E = Eng<T, L1, L2, LINES>;
   using C = cx<T>;
@@ -153,7 +156,7 @@ struct KZDeriv {
 #pragma unroll
         for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
-          R.v[j] = (valid && n < a.g.Np) ? x[n * TL] : mk<T>(0, 0);
+          R.v[j] = (j < JN && valid && n < a.g.Np) ? x[n * TL] : mk<T>(0, 0);
         }
         E::template A<-1>(R.v, b0, a.t.tw, r, li);
       }
@@ -183,7 +186,7 @@ struct KZDeriv {
           E::template Ai<1>(R.v, o == 0 ? b0 : b1, r, li);
           if (valid) {
 #pragma unroll
-            for (int j = 0; j < L1; ++j) {
+            for (int j = 0; j < JN; ++j) {
               const int n = r + L2 * j;
               if (n < a.g.Nz) out[n * TL] = cscale(R.v[j], sc);
             }
@@ -203,7 +206,7 @@ struct KZDeriv {
 //   X_out = [v*; continuation of v*].
 // The z filter acts as a circular convolution of the continued N.
 // ===========================================================================
-template <class T, int L1, int L2, int LINES>
+template <class T, int L1, int L2, int LINES, int JN = L1>
 struct KZCombine {
   using E = Eng<T, L1, L2, LINES>;
   using C = cx<T>;
@@ -248,6 +251,10 @@ struct KZCombine {
         for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
           C val = mk<T>(0, 0);
+          if (j >= JN) {
+            R.v[j] = val;
+            continue;
+          }
           if (valid && n < Nz) val = x[n * TL];
           R.v[j] = val;
           if (n < d) Ev[n] = val;
@@ -257,7 +264,7 @@ struct KZCombine {
     } else if constexpr (P == 1) {
       if (r < L2) {
 #pragma unroll
-        for (int j = 0; j < L1; ++j) {
+        for (int j = 0; j < JN; ++j) {
           const int n = r + L2 * j;
           if (n >= Nz && n < Np) R.v[j] = continuation_value<T>(n - Nz, Ev, Ev + DMAX, d, a.g.Cc, Ms, Ms2);
         }
@@ -282,7 +289,7 @@ struct KZCombine {
         const C* dzz = a.DZZ + lay(f, 0, line, Nz, a.g.ntiles);
         C* xo = a.Xout + fo;
 #pragma unroll
-        for (int j = 0; j < L1; ++j) {
+        for (int j = 0; j < JN; ++j) {
           const int n = r + L2 * j;
           if (n < Nz) {
             C vs = mk<T>(0, 0);
@@ -313,7 +320,7 @@ struct KZCombine {
       if (r < L2 && valid) {
         C* xo = a.Xout + lay(f, 0, line, Np, a.g.ntiles);
 #pragma unroll
-        for (int j = 0; j < L1; ++j) {
+        for (int j = 0; j < JN; ++j) {
           const int n = r + L2 * j;
           if (n >= Nz && n < Np)
             xo[n * TL] = continuation_value<T>(n - Nz, Ev, Ev + DMAX, d, a.g.Cc, Ms, Ms2);
@@ -409,6 +416,7 @@ struct KZContinue {
 template <class T, int L1, int L2, int LINES, bool DIRECT>
 struct KZProject {
   using E = Eng<T, L1, L2, LINES>;
+  static constexpr int JN = DIRECT ? L1 : L1 / 2;
   using C = cx<T>;
   static constexpr int THREADS = E::THREADS, NPHASE = 7;
   // phases 1..3 run four times (Y^, W^, sigma, sigma_z) from one copy of code
@@ -517,7 +525,7 @@ struct KZProject {
           for (int j = 0; j < L1; ++j) {
             const int n = r + L2 * j;
             C y = mk<T>(0, 0);
-            if (valid && n < Np) {
+            if (j < JN && valid && n < Np) {
               y = cadd(cscale(xu[n * TL], kxo), cscale(xv[n * TL], kyo));
               if constexpr (!DIRECT) y = cmul(y, a.t.chirp[n]);
             }
@@ -528,7 +536,7 @@ struct KZProject {
           for (int j = 0; j < L1; ++j) {
             const int n = r + L2 * j;
             C y = mk<T>(0, 0);
-            if (valid && n < Np) {
+            if (j < JN && valid && n < Np) {
               y = xw[n * TL];
               if constexpr (!DIRECT) y = cmul(y, a.t.chirp[n]);
             }
@@ -539,7 +547,7 @@ struct KZProject {
           for (int j = 0; j < L1; ++j) {
             const int n = r + L2 * j;
             C x = mk<T>(0, 0);
-            if (valid && n < Np) {
+            if (j < JN && valid && n < Np) {
               x = g0[n * TL];
               if (it == 3) x = cscale(x, a.t.kzo[n]);
               if constexpr (DIRECT) x.y = -x.y;
@@ -575,7 +583,7 @@ struct KZProject {
           by_kind(it, [&](auto kc) {
             constexpr int K = decltype(kc)::value;
 #pragma unroll
-            for (int j = 0; j < L1; ++j) {
+            for (int j = 0; j < JN; ++j) {
               const int n = r + L2 * j;
               if (n < Np) post<K>(a, it, n, R.v[j], kxo, kyo, invNp, g0, g1, xw, W);
             }
@@ -617,7 +625,7 @@ struct KZProject {
         const T cf[5] = {(T)W[8], (T)W[9], (T)W[10], (T)W[11], (T)W[12]};
         const T tdz = (T)a.g.dz, tLz = (T)a.g.Lz;
 #pragma unroll
-        for (int j = 0; j < L1; ++j) {
+        for (int j = 0; j < JN; ++j) {
           const int n = r + L2 * j;
           if (n < Np) {
             C ph, dph;
