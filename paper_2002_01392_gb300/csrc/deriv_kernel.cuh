@@ -64,6 +64,8 @@ struct DerivPair {
     const C* H1;          // spectrum of d1 (natural order, length L)
     const C* H2;          // spectrum of d2
     const C* tw;          // engine twiddles
+    long long pf_dist;    // prefetch into L2 the input of block bid + pf_dist (0: off)
+    long long nblocks;    // grid size
   };
   struct Regs { C v[L1]; C u[L2]; };
 
@@ -132,6 +134,14 @@ struct DerivPair {
         }
       }
     } else if constexpr (P == 1) {
+      // the block that will run on this SM about one block-lifetime from now:
+      // bring its input rows into L2 while this block computes
+      if (a.pf_dist > 0 && bid + a.pf_dist < a.nblocks) {
+        const long long b2 = bid + a.pf_dist;
+        const long long f2 = b2 / a.tiles, p2 = (b2 % a.tiles) * LINES;
+        const T* src = a.f + f2 * a.bstride + 2 * p2;
+        for (int n = tid; n < a.Nz; n += THREADS) prefetch_l2(src + (long long)n * a.zstride);
+      }
       if (r < L2) {
 #pragma unroll
         for (int j = 0; j < JN; ++j) {

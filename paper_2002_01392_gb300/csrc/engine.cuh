@@ -19,6 +19,15 @@
 
 namespace fcns {
 
+// Prefetch the 128-byte line holding p into L2 (no-op on the host).
+FC_HD void prefetch_l2(const void* p) {
+#if defined(__CUDA_ARCH__)
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+#else
+  (void)p;
+#endif
+}
+
 template <class T, int L1_, int L2_, int LINES_>
 struct Eng {
   static constexpr int L1 = L1_, L2 = L2_, L = L1 * L2, LINES = LINES_;

@@ -36,6 +36,8 @@ static int emu_deriv(const double* Mr, int d, int Cc, int Nz, int batch, long lo
   for (int i = 0; i < Cc * d; ++i) { Mr2[i].x = (float)Mr[i]; Mr2[i].y = (float)(Mr[i] - (double)Mr2[i].x); }
   a.Mr = Mr; a.Mr2 = Mr2.data(); a.H1 = H1t.data(); a.H2 = H2t.data(); a.tw = twt.data();
 
+  a.nblocks = a.tiles * batch;
+  a.pf_dist = 3;
   phased_emulate<K>(a, a.tiles * batch, K::smem_bytes);
   return 0;
 }
