@@ -45,7 +45,7 @@ fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long 
   const long long grid = a.tiles * batch;
   if (grid > 0x7fffffffLL) return FC_ERR_UNSUPPORTED;
   // L2 prefetch of the block one residency ahead: measured +27 % for the
-  // length-512 transforms and -1.7 % for 1080 on GB300, so only below 1000
+  // length-512 transforms and -7 % for 1080 on GB300, so only below 1000
   static int sms = 0;
   if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 0;
   a.nblocks = grid;
