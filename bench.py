@@ -582,7 +582,7 @@ def main():
                      "peak": hbm_peak, "unit": "GB/s",
                      "frac": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9 / hbm_peak,
                      "traffic": _measured_traffic("fc_deriv_z_f32"), "peak_kind": peak_kind,
-                     "kernel": "fc_deriv_z conv L=1080 FP32, paired lines (phased_kernel<DerivPair<float,30,36,4>>)"},
+                     "kernel": "fc_deriv_z conv L=1080 FP32, paired lines, registers j >= 16 known zero (phased_kernel<DerivPair<float,30,36,4,16>>)"},
         "e2e": r32.get("e2e"),
         "gpu_launches": r32["launches"],
         "clocks": clk.summary(),
