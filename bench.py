@@ -290,6 +290,12 @@ def bench_rk(api, torch, steps, warmup, with_e2e=True, shape=None):
            "p99_ms": float(np.percentile(times, 99) * 1e3),
            "rk_stage_grid_points_per_s": pts * 3 * steps / total, "workspace_GB": ws_bytes / 1e9,
            "launches_per_step": 3 * 7}
+    # stage roofline of the fused-pass traffic model: 288 B per grid point per
+    # stage for the 4-field Boussinesq step in float32 (72 B per field)
+    hbm_peak, _ = _peaks()
+    stage_s = float(times.mean()) / 3
+    res["roofline_stage"] = {"bound": "hbm", "model_bytes_per_point": 288, "achieved": 288 * pts / stage_s / 1e9,
+                             "peak": hbm_peak, "unit": "GB/s", "frac": 288 * pts / stage_s / 1e9 / hbm_peak}
     out = sim.get_fields()
     res["finite"] = bool(torch.isfinite(out).all().item())
     res["w_wall_rel"] = float(out[2, [0, -1]].abs().max().item() / max(out[:3].abs().max().item(), 1e-300))

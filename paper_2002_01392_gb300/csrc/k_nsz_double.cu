@@ -5,7 +5,7 @@
 
 namespace fcns {
 #define FC_INST_Z(LL, A, B, D)                                            \
-  template struct DevRun<KZDeriv<double, A, B, z_lines<double, LL>(), D ? A : A / 2>>; \
+  template struct DevRun<KZDeriv<double, A, B, zderiv_lines<double, LL>(), D ? A : A / 2>>; \
   template struct DevRun<KZCombine<double, A, B, z_lines<double, LL>(), D ? A : A / 2>>; \
   template struct DevRun<KZProject<double, A, B, zproj_lines<double, LL>(), D>>;
 FC_ZSHAPES_PADDED(FC_INST_Z)

@@ -5,7 +5,7 @@
 
 namespace fcns {
 #define FC_INST_Z(LL, A, B, D)                                            \
-  template struct DevRun<KZDeriv<float, A, B, z_lines<float, LL>(), D ? A : A / 2>>; \
+  template struct DevRun<KZDeriv<float, A, B, zderiv_lines<float, LL>(), D ? A : A / 2>>; \
   template struct DevRun<KZCombine<float, A, B, z_lines<float, LL>(), D ? A : A / 2>>; \
   template struct DevRun<KZProject<float, A, B, zproj_lines<float, LL>(), D>>;
 FC_ZSHAPES_DIRECT(FC_INST_Z)

@@ -244,7 +244,7 @@ struct NsCore {
     fc_status s = FC_ERR_UNSUPPORTED;
 #define FC_ZD(LL, A, B, D)                                                        \
   if (l.L == LL) {                                                            \
-    using K = KZDeriv<T, A, B, z_lines<T, LL>(), D ? A : A / 2>;                             \
+    using K = KZDeriv<T, A, B, zderiv_lines<T, LL>(), D ? A : A / 2>;                             \
     typename K::Args a;                                                       \
     a.g = zgeom(nf); a.t = ztab<T>(); a.X = X;                                \
     a.DZ = at<cx<T>>(l.DZ); a.DZZ = at<cx<T>>(l.DZZ);                         \

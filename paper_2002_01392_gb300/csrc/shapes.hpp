@@ -23,15 +23,23 @@
 #define FC_ZSHAPES(M) FC_ZSHAPES_DIRECT(M) FC_ZSHAPES_PADDED(M)
 
 namespace fcns {
-// lines per CTA of the z kernels and of the y kernels
+// lines per CTA of the z kernels and of the y kernels.  float: 8 lines (64
+// contiguous bytes of every z / ky row per CTA); measured on the 1024^2 x 513
+// Boussinesq step, 8 instead of 4 lines for the z kernels and the y transforms
+// of length 1024 took the step from 314 to 256 ms (2 lines: 350-363 ms).
 template <class T, int L> constexpr int z_lines() {
+  return sizeof(T) == 4 ? 8 : (L >= 576 ? 2 : 4);
+}
+// the z-derivative kernel (two exchange buffers) keeps 4 lines at L >= 576:
+// 14.7 ms against 17.8 ms per launch with 8 on the same step
+template <class T, int L> constexpr int zderiv_lines() {
   return sizeof(T) == 4 ? (L >= 576 ? 4 : 8) : (L >= 576 ? 2 : 4);
 }
 template <class T, int L> constexpr int zproj_lines() {
-  return sizeof(T) == 4 ? (L >= 576 ? 4 : 8) : (L >= 576 ? 2 : 4);
+  return sizeof(T) == 4 ? 8 : (L >= 576 ? 2 : 4);
 }
 template <class T, int N> constexpr int y_lines() {
-  return sizeof(T) == 4 ? (N >= 512 ? 4 : (N >= 128 ? 8 : 16)) : (N >= 512 ? 2 : (N >= 128 ? 4 : 8));
+  return sizeof(T) == 4 ? (N >= 128 ? 8 : 16) : (N >= 512 ? 2 : (N >= 128 ? 4 : 8));
 }
 // row-pair jobs per CTA of the x row transforms
 template <int N> constexpr int x_jobs() { return N >= 512 ? 2 : (N >= 128 ? 4 : 8); }
