@@ -21,10 +21,6 @@
 #define DERIV_NOINLINE
 #endif
 
-namespace fcns {
-
-}  // namespace fcns
-
 #include "engine.cuh"
 
 namespace fcns {
