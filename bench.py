@@ -265,6 +265,7 @@ def bench_rk(api, torch, steps, warmup, with_e2e=True, shape=None):
     p = api.ns_params(Nx=Nx, Ny=Ny, Nz=Nz, nfields=4, prec="f32", rk_order=3, **kw)
     ws_bytes = api.ns_workspace_bytes(p)
     sim = api.Sim(p)
+    tiles = sim.tune(1)                    # autotuned lines per CTA (ns_tune)
     host = synth.boussinesq_fields(Nx, Ny, Nz, dtype=np.float32)
     f = torch.from_numpy(host).cuda()
     sim.set_fields(f)
@@ -289,7 +290,7 @@ def bench_rk(api, torch, steps, warmup, with_e2e=True, shape=None):
            "seconds_per_step_mean": float(times.mean()), "p50_ms": float(np.percentile(times, 50) * 1e3),
            "p99_ms": float(np.percentile(times, 99) * 1e3),
            "rk_stage_grid_points_per_s": pts * 3 * steps / total, "workspace_GB": ws_bytes / 1e9,
-           "launches_per_step": 3 * 7}
+           "launches_per_step": 3 * 7, "tiles_autotuned": tiles}
     # stage roofline of the fused-pass traffic model: 288 B per grid point per
     # stage for the 4-field Boussinesq step in float32 (72 B per field)
     hbm_peak, _ = _peaks()

@@ -310,6 +310,19 @@ fc_status ns_spectrum_shells(ns_sim_t sim, int* nshell, double* dk);
  */
 fc_status ns_interpolate(ns_sim_t dst, ns_sim_t src, fc_stream_t stream);
 
+/*
+ * ns_tune -- lines per CTA (tile) of the five kernel kinds of the RK step
+ * (z derivatives, stage combine, projection, y inverse, y forward); two tile
+ * sizes of each are compiled.  mode 0: the built-in defaults; 1: autotune --
+ * time both sizes of each kernel on this simulation's buffers and keep the
+ * faster (synchronous; cached per process and size; the state and the wall
+ * planes are preserved); 2: set from tiles.  tiles: 5 ints (0 = default,
+ * 1 = alternative), read for mode 2, written with the choice if non-NULL.
+ * The choice does not change any result (every line is computed the same
+ * way whatever the tile).
+ */
+fc_status ns_tune(ns_sim_t sim, int mode, int* tiles, fc_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batched ensemble: many independent simulations, one graph launch per step */
 /* ------------------------------------------------------------------------ */
@@ -320,7 +333,7 @@ typedef struct ns_batch* ns_batch_t;
  * ns_batch_create -- group n simulations (created on the current device,
  * each at most once; any sizes, precisions and parameters) so that one RK
  * step of all of them (Sec. 4.4, as rk_step) runs as a single CUDA graph
- * launch.  The members stay owned by the caller and must outlive the batch;
+ * launch.  Autotunes the tiles of every member first (ns_tune mode 1).  The members stay owned by the caller and must outlive the batch;
  * the batch copies the array of handles.  FC_ERR_ARG for NULL / repeated
  * members, FC_ERR_STATE for members of another device.
  */

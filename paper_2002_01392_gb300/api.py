@@ -59,6 +59,7 @@ _sig("fc_plan_matrix", [_vp, ctypes.POINTER(_c_double)])
 _sig("fc_plan_info", [_vp] + [ctypes.POINTER(_c_int)] * 5 + [ctypes.POINTER(_c_double)])
 _sig("fc_destroy", [_vp])
 _sig("ns_interpolate", [_vp, _vp, _vp])
+_sig("ns_tune", [_vp, _c_int, ctypes.POINTER(_c_int), _vp])
 _sig("ns_profiles", [_vp] + [ctypes.POINTER(_c_double)] * 3 + [_vp])
 _sig("ns_spectrum_shells", [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_double)])
 _sig("ns_batch_create", [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(_vp)])
@@ -73,7 +74,7 @@ EXPORTED = ["fc_status_str", "fc_last_error", "fc_setup", "fc_setup_ex", "fc_pla
             "ns_set_fields", "ns_get_fields", "ns_get_state", "ns_put_state", "ns_get_wall_gradp",
             "ns_put_wall_gradp", "ns_rhs", "fc_poisson_project", "rk_step", "ns_diagnostics",
             "ns_batch_create", "ns_batch_step", "ns_batch_info", "ns_batch_destroy", "ns_interpolate",
-            "ns_profiles", "ns_spectrum_shells"]
+            "ns_profiles", "ns_spectrum_shells", "ns_tune"]
 
 
 def _check(status: int, where: str):
@@ -303,6 +304,12 @@ class Sim:
         _check(_lib.ns_profiles(self.handle, mean.ctypes.data_as(P), rms.ctypes.data_as(P), spec.ctypes.data_as(P),
                                 _stream(stream)), "ns_profiles")
         return dict(mean=mean, rms=rms, spectrum=spec, dk=dk.value)
+
+    def tune(self, mode: int = 1, tiles=None, stream=None):
+        """ns_tune: 0 defaults, 1 autotune, 2 set ``tiles`` (5 ints); returns the choice."""
+        arr = (_c_int * 5)(*(tiles or [0] * 5))
+        _check(_lib.ns_tune(self.handle, int(mode), arr, _stream(stream)), "ns_tune")
+        return list(arr)
 
     def interpolate_from(self, src: "Sim", stream=None):
         """ns_interpolate: this state := spectral interpolation of src's state."""

@@ -101,6 +101,8 @@ struct EmuBK {
   }
   fc_status sync(void*) { return FC_OK; }
   fc_status d2h(void* d, const void* s, size_t b, void*) { std::memcpy(d, s, b); return FC_OK; }
+  template <class F>
+  fc_status time_ms(F&&, void*, float*) { return FC_ERR_UNSUPPORTED; }  // no timing on the host
 };
 }  // namespace fcns
 
@@ -122,6 +124,11 @@ int fchc_ns_project(void* h, double dt, const void* in, void* out, void* gp) {
   return ((NsCore<EmuBK>*)h)->project_any(dt, in, out, gp, nullptr);
 }
 int fchc_ns_step(void* h, double dt) { return ((NsCore<EmuBK>*)h)->step_any(dt, nullptr); }
+int fchc_ns_set_tiles(void* h, const int* tiles) {
+  auto* c = (NsCore<EmuBK>*)h;
+  for (int k = 0; k < NsCore<EmuBK>::TK_N; ++k) c->tile[k] = tiles[k] ? 1 : 0;
+  return 0;
+}
 int fchc_ns_profiles_raw(void* h, double* out) { return ((NsCore<EmuBK>*)h)->profiles_any(out, nullptr); }
 int fchc_ns_interpolate(void* dst, void* src) {
   return ((NsCore<EmuBK>*)dst)->interpolate_from_any(*(NsCore<EmuBK>*)src, nullptr);

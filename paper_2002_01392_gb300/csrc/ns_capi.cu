@@ -35,6 +35,21 @@ struct DeviceBK {
     return cuda_status(cudaMemsetAsync(dst, v, b, (cudaStream_t)st), "cudaMemsetAsync");
   }
   fc_status sync(void*) { return cuda_status(cudaDeviceSynchronize(), "cudaDeviceSynchronize"); }
+  // duration of the launches made by f on stream st (synchronous)
+  template <class F>
+  fc_status time_ms(F&& f, void* st, float* ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    fc_status s = cuda_status(cudaEventCreate(&e0), "cudaEventCreate");
+    if (!s) s = cuda_status(cudaEventCreate(&e1), "cudaEventCreate");
+    if (!s) s = cuda_status(cudaEventRecord(e0, (cudaStream_t)st), "cudaEventRecord");
+    if (!s) s = f();
+    if (!s) s = cuda_status(cudaEventRecord(e1, (cudaStream_t)st), "cudaEventRecord");
+    if (!s) s = cuda_status(cudaEventSynchronize(e1), "cudaEventSynchronize");
+    if (!s) s = cuda_status(cudaEventElapsedTime(ms, e0, e1), "cudaEventElapsedTime");
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return s;
+  }
   fc_status d2h(void* dst, const void* src, size_t b, void* st) {
     fc_status s = cuda_status(cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, (cudaStream_t)st), "cudaMemcpyAsync(D2H)");
     if (!s) s = cuda_status(cudaStreamSynchronize((cudaStream_t)st), "cudaStreamSynchronize");
@@ -234,6 +249,26 @@ fc_status ns_interpolate(ns_sim_t dst, ns_sim_t src, fc_stream_t stream) {
   return st;
 }
 
+fc_status ns_tune(ns_sim_t s, int mode, int* tiles, fc_stream_t stream) {
+  fc_status st = check_sim(s, "ns_tune");
+  if (st) return st;
+  auto& c = s->core;
+  if (mode == 0) {
+    for (int k = 0; k < c.TK_N; ++k) c.tile[k] = 0;
+  } else if (mode == 1) {
+    st = c.autotune_any(stream);
+  } else if (mode == 2) {
+    if (!tiles) { set_error("ns_tune: NULL tiles"); return FC_ERR_ARG; }
+    for (int k = 0; k < c.TK_N; ++k) c.tile[k] = tiles[k] ? 1 : 0;
+  } else {
+    set_error("ns_tune: mode must be 0, 1 or 2");
+    return FC_ERR_ARG;
+  }
+  if (!st && tiles)
+    for (int k = 0; k < c.TK_N; ++k) tiles[k] = c.tile[k];
+  return st;
+}
+
 fc_status ns_batch_create(ns_sim_t* sims, int n, ns_batch_t* out) {
   if (!sims || !out || n < 1) { set_error("ns_batch_create: bad arguments"); return FC_ERR_ARG; }
   *out = nullptr;
@@ -244,6 +279,10 @@ fc_status ns_batch_create(ns_sim_t* sims, int n, ns_batch_t* out) {
     if (sims[i]->device != dev) { set_error("ns_batch_create: members on another device"); return FC_ERR_STATE; }
     for (int j = 0; j < i; ++j)
       if (sims[j] == sims[i]) { set_error("ns_batch_create: a simulation appears twice"); return FC_ERR_ARG; }
+  }
+  for (int i = 0; i < n; ++i) {  // tile sizes of every member picked by measurement (cached per size)
+    fc_status t = sims[i]->core.autotune_any(nullptr);
+    if (t) return t;
   }
   ns_batch* b = new (std::nothrow) ns_batch;
   if (!b) return FC_ERR_NOMEM;

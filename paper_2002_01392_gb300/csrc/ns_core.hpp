@@ -4,9 +4,12 @@
 // kernel (on the GPU for libfcns, on the CPU for the host-check library) and
 // moves memory, so that the same sequence is what the CPU tests check.
 #pragma once
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "../../include/fcns.h"
@@ -239,39 +242,57 @@ struct NsCore {
   }
 
   // ------------------------------------------------------------ launchers
+  // Tile choice per kernel kind (lines per CTA): 0 = the built-in default of
+  // shapes.hpp, 1 = its alternative tile_alt (both compiled); see ns_tune.
+  enum { TK_ZD, TK_ZC, TK_ZP, TK_YI, TK_Y1, TK_N };
+  int tile[TK_N] = {0, 0, 0, 0, 0};
+
+  template <class T, int A, int B, int LN, int JN>
+  fc_status z_deriv_run(const cx<T>* X, int nf, void* st) {
+    using K = KZDeriv<T, A, B, LN, JN>;
+    typename K::Args a;
+    a.g = zgeom(nf); a.t = ztab<T>(); a.X = X;
+    a.DZ = at<cx<T>>(l.DZ); a.DZZ = at<cx<T>>(l.DZZ);
+    a.tiles = (l.lines + LN - 1) / LN;
+    const double dz = p.Lz / (p.Nz - 1);
+    a.s1 = (T)(1.0 / dz); a.s2 = (T)(1.0 / (dz * dz));
+    return bk.template run<K>(a, a.tiles * nf, st);
+  }
   template <class T>
   fc_status z_deriv(const cx<T>* X, int nf, void* st) {
     fc_status s = FC_ERR_UNSUPPORTED;
-#define FC_ZD(LL, A, B, D)                                                        \
-  if (l.L == LL) {                                                            \
-    using K = KZDeriv<T, A, B, zderiv_lines<T, LL>(), D ? A : A / 2>;                             \
-    typename K::Args a;                                                       \
-    a.g = zgeom(nf); a.t = ztab<T>(); a.X = X;                                \
-    a.DZ = at<cx<T>>(l.DZ); a.DZZ = at<cx<T>>(l.DZZ);                         \
-    a.tiles = (l.lines + K::E::LINES - 1) / K::E::LINES;                      \
-    const double dz = p.Lz / (p.Nz - 1);                                      \
-    a.s1 = (T)(1.0 / dz); a.s2 = (T)(1.0 / (dz * dz));                        \
-    s = bk.template run<K>(a, a.tiles * nf, st);                              \
+#define FC_ZD(LL, A, B, D)                                                                   \
+  if (l.L == LL) {                                                                           \
+    constexpr int LN = zderiv_lines<T, LL>();                                                \
+    s = tile[TK_ZD] ? z_deriv_run<T, A, B, tile_alt<LN>(), D ? A : A / 2>(X, nf, st)         \
+                    : z_deriv_run<T, A, B, LN, D ? A : A / 2>(X, nf, st);                    \
   }
     FC_ZSHAPES(FC_ZD)
 #undef FC_ZD
     return s;
   }
 
+  template <class T, int A, int B, int LN, int JN>
+  fc_status z_combine_run(const cx<T>* NL, const cx<T>* Xt, const cx<T>* Xj, cx<T>* Xo, double dtj, int inject,
+                          int nf, void* st) {
+    using K = KZCombine<T, A, B, LN, JN>;
+    typename K::Args a;
+    a.g = zgeom(nf); a.t = ztab<T>(); a.NL = NL; a.Xt = Xt; a.Xj = Xj;
+    a.DZZ = at<cx<T>>(l.DZZ); a.Xout = Xo; a.gradp = at<double2>(l.gradp);
+    a.dtj = dtj; a.dif[0] = a.dif[1] = a.dif[2] = p.nu; a.dif[3] = p.kappa;
+    a.inject = inject;
+    a.tiles = (l.lines + LN - 1) / LN;
+    return bk.template run<K>(a, a.tiles * nf, st);
+  }
   template <class T>
   fc_status z_combine(const cx<T>* NL, const cx<T>* Xt, const cx<T>* Xj, cx<T>* Xo, double dtj, int inject,
                       int nf, void* st) {
     fc_status s = FC_ERR_UNSUPPORTED;
-#define FC_ZC(LL, A, B, D)                                                        \
-  if (l.L == LL) {                                                            \
-    using K = KZCombine<T, A, B, z_lines<T, LL>(), D ? A : A / 2>;                           \
-    typename K::Args a;                                                       \
-    a.g = zgeom(nf); a.t = ztab<T>(); a.NL = NL; a.Xt = Xt; a.Xj = Xj;        \
-    a.DZZ = at<cx<T>>(l.DZZ); a.Xout = Xo; a.gradp = at<double2>(l.gradp);    \
-    a.dtj = dtj; a.dif[0] = a.dif[1] = a.dif[2] = p.nu; a.dif[3] = p.kappa;   \
-    a.inject = inject;                                                        \
-    a.tiles = (l.lines + K::E::LINES - 1) / K::E::LINES;                      \
-    s = bk.template run<K>(a, a.tiles * nf, st);                              \
+#define FC_ZC(LL, A, B, D)                                                                             \
+  if (l.L == LL) {                                                                                     \
+    constexpr int LN = z_lines<T, LL>();                                                               \
+    s = tile[TK_ZC] ? z_combine_run<T, A, B, tile_alt<LN>(), D ? A : A / 2>(NL, Xt, Xj, Xo, dtj, inject, nf, st) \
+                    : z_combine_run<T, A, B, LN, D ? A : A / 2>(NL, Xt, Xj, Xo, dtj, inject, nf, st);  \
   }
     FC_ZSHAPES(FC_ZC)
 #undef FC_ZC
@@ -287,17 +308,23 @@ struct NsCore {
     return bk.template run<K>(a, a.tiles * nf, st);
   }
 
+  template <class T, int A, int B, int LN, bool D>
+  fc_status z_project_run(cx<T>* X, double dtj, void* st) {
+    using K = KZProject<T, A, B, LN, D>;
+    typename K::Args a;
+    a.g = zgeom(3); a.t = ztab<T>(); a.X = X; a.gradp = at<double2>(l.gradp);
+    a.G0 = at<cx<T>>(l.DZ); a.G1 = at<cx<T>>(l.DZZ); a.dtj = dtj;
+    a.tiles = (l.lines + LN - 1) / LN;
+    return bk.template run<K>(a, a.tiles, st);
+  }
   template <class T>
   fc_status z_project(cx<T>* X, double dtj, void* st) {
     fc_status s = FC_ERR_UNSUPPORTED;
-#define FC_ZP(LL, A, B, D)                                                        \
-  if (l.L == LL) {                                                            \
-    using K = KZProject<T, A, B, zproj_lines<T, LL>(), D>;                       \
-    typename K::Args a;                                                       \
-    a.g = zgeom(3); a.t = ztab<T>(); a.X = X; a.gradp = at<double2>(l.gradp); \
-    a.G0 = at<cx<T>>(l.DZ); a.G1 = at<cx<T>>(l.DZZ); a.dtj = dtj;             \
-    a.tiles = (l.lines + K::E::LINES - 1) / K::E::LINES;                      \
-    s = bk.template run<K>(a, a.tiles, st);                                   \
+#define FC_ZP(LL, A, B, D)                                                               \
+  if (l.L == LL) {                                                                       \
+    constexpr int LN = zproj_lines<T, LL>();                                             \
+    s = tile[TK_ZP] ? z_project_run<T, A, B, tile_alt<LN>(), D>(X, dtj, st)              \
+                    : z_project_run<T, A, B, LN, D>(X, dtj, st);                         \
   }
     FC_ZSHAPES(FC_ZP)
 #undef FC_ZP
@@ -310,37 +337,49 @@ struct NsCore {
     return g;
   }
 
+  template <class T, int A1, int B1, int LN>
+  fc_status y_inv3_run(const cx<T>* A, long long a_fstride, int nf, void* st) {
+    using K = KYInv3<T, A1, B1, LN>;
+    typename K::Args a;
+    a.g = ygeom(); a.tw = at<cx<T>>(l.twy); a.kyo = at<T>(l.tkyo);
+    a.A = A; a.a_fstride = a_fstride;
+    a.V = at<cx<T>>(l.V); a.DY = at<cx<T>>(l.DY); a.DZ = at<cx<T>>(l.DZ);
+    a.tiles = (l.Kx + LN - 1) / LN;
+    a.scale = (T)(1.0 / p.Ny);
+    return bk.template run<K>(a, a.tiles * nf * p.Nz, st);
+  }
   template <class T>
   fc_status y_inv3(const cx<T>* A, long long a_fstride, int nf, void* st) {
     fc_status s = FC_ERR_UNSUPPORTED;
-#define FC_YI(NN, A1, B1)                                                      \
-  if (p.Ny == NN) {                                                           \
-    using K = KYInv3<T, A1, B1, y_lines<T, NN>()>;                            \
-    typename K::Args a;                                                       \
-    a.g = ygeom(); a.tw = at<cx<T>>(l.twy); a.kyo = at<T>(l.tkyo);            \
-    a.A = A; a.a_fstride = a_fstride;                                         \
-    a.V = at<cx<T>>(l.V); a.DY = at<cx<T>>(l.DY); a.DZ = at<cx<T>>(l.DZ);     \
-    a.tiles = (l.Kx + K::E::LINES - 1) / K::E::LINES;                         \
-    a.scale = (T)(1.0 / p.Ny);                                                \
-    s = bk.template run<K>(a, a.tiles * nf * p.Nz, st);                       \
+#define FC_YI(NN, A1, B1)                                                           \
+  if (p.Ny == NN) {                                                                \
+    constexpr int LN = y_lines<T, NN>();                                           \
+    s = tile[TK_YI] ? y_inv3_run<T, A1, B1, tile_alt<LN>()>(A, a_fstride, nf, st)  \
+                    : y_inv3_run<T, A1, B1, LN>(A, a_fstride, nf, st);             \
   }
     FC_XYSHAPES(FC_YI)
 #undef FC_YI
     return s;
   }
 
+  template <class T, int SIGN, int A1, int B1, int LN>
+  fc_status y_one_run(const cx<T>* IN, long long in_fs, cx<T>* OUT, long long out_fs, int nf, double scale, void* st) {
+    using K = KY1<T, A1, B1, LN, SIGN>;
+    typename K::Args a;
+    a.g = ygeom(); a.tw = at<cx<T>>(l.twy);
+    a.IN = IN; a.in_fstride = in_fs; a.OUT = OUT; a.out_fstride = out_fs;
+    a.tiles = (l.Kx + LN - 1) / LN;
+    a.scale = (T)scale;
+    return bk.template run<K>(a, a.tiles * nf * p.Nz, st);
+  }
   template <class T, int SIGN>
   fc_status y_one(const cx<T>* IN, long long in_fs, cx<T>* OUT, long long out_fs, int nf, double scale, void* st) {
     fc_status s = FC_ERR_UNSUPPORTED;
-#define FC_Y1(NN, A1, B1)                                                      \
-  if (p.Ny == NN) {                                                           \
-    using K = KY1<T, A1, B1, y_lines<T, NN>(), SIGN>;                         \
-    typename K::Args a;                                                       \
-    a.g = ygeom(); a.tw = at<cx<T>>(l.twy);                                   \
-    a.IN = IN; a.in_fstride = in_fs; a.OUT = OUT; a.out_fstride = out_fs;     \
-    a.tiles = (l.Kx + K::E::LINES - 1) / K::E::LINES;                         \
-    a.scale = (T)scale;                                                       \
-    s = bk.template run<K>(a, a.tiles * nf * p.Nz, st);                       \
+#define FC_Y1(NN, A1, B1)                                                                              \
+  if (p.Ny == NN) {                                                                                   \
+    constexpr int LN = y_lines<T, NN>();                                                              \
+    s = tile[TK_Y1] ? y_one_run<T, SIGN, A1, B1, tile_alt<LN>()>(IN, in_fs, OUT, out_fs, nf, scale, st) \
+                    : y_one_run<T, SIGN, A1, B1, LN>(IN, in_fs, OUT, out_fs, nf, scale, st);          \
   }
     FC_XYSHAPES(FC_Y1)
 #undef FC_Y1
@@ -538,6 +577,66 @@ struct NsCore {
     return s;
   }
   fc_status profiles_any(double* out, void* st) { return f32() ? profiles<float>(out, st) : profiles<double>(out, st); }
+
+  // Autotuner of the lines per CTA: each kernel kind of the RK step is timed
+  // with both compiled tile sizes on this simulation's buffers (two timed
+  // launches each after a warm-up) and the faster kept.  The state and the
+  // wall planes are preserved (the projection runs on a spare buffer; the
+  // planes it writes are restored).  Results are cached per process by size,
+  // so instances of equal sizes are tuned once.
+  template <class T>
+  fc_status autotune(void* st) {
+    static std::mutex mu;
+    static std::map<std::vector<long long>, std::array<int, TK_N>> cache;
+    const std::vector<long long> key = {(long long)p.prec, p.Nx, p.Ny, p.Nz, p.C, l.nf, l.L};
+    {
+      std::lock_guard<std::mutex> g(mu);
+      auto it = cache.find(key);
+      if (it != cache.end()) {
+        for (int k = 0; k < TK_N; ++k) tile[k] = it->second[k];
+        return FC_OK;
+      }
+    }
+    std::vector<double> gp(8 * (size_t)l.lines);
+    fc_status s = bk.d2h(gp.data(), ws + l.gradp, sizeof(double) * gp.size(), st);
+    cx<T>* Xs = Xb<T>((cur + 1) % 3);
+    cx<T>* Xo = Xb<T>((cur + 2) % 3);
+    auto launch = [&](int k) -> fc_status {
+      switch (k) {
+        case TK_ZD: return z_deriv<T>(Xb<T>(cur), l.nf, st);
+        case TK_ZC: return z_combine<T>(buf<T>(l.NL), Xb<T>(cur), Xb<T>(cur), Xo, 0.0, 0, l.nf, st);
+        case TK_ZP: return z_project<T>(Xs, 1.0, st);
+        case TK_YI: return y_inv3<T>(Xb<T>(cur), l.Np, l.nf, st);
+        default: return y_one<T, -1>(buf<T>(l.NL), p.Nz, buf<T>(l.NL), p.Nz, l.nf, 1.0, st);
+      }
+    };
+    std::array<int, TK_N> pick{};
+    for (int k = 0; k < TK_N && !s; ++k) {
+      float best[2] = {3e38f, 3e38f};
+      for (int c = 0; c < 2 && !s; ++c) {
+        tile[k] = c;
+        fc_status w = launch(k);  // warm-up
+        if (w == FC_ERR_UNSUPPORTED) continue;  // this tile does not fit the shared memory
+        s = w;
+        for (int r = 0; r < 2 && !s; ++r) {
+          float ms = 0;
+          s = bk.time_ms([&] { return launch(k); }, st, &ms);
+          if (!s && ms < best[c]) best[c] = ms;
+        }
+      }
+      pick[k] = best[1] < best[0] ? 1 : 0;
+      tile[k] = pick[k];
+    }
+    if (!s) s = bk.h2d(ws + l.gradp, gp.data(), sizeof(double) * gp.size());
+    if (s) {
+      for (int k = 0; k < TK_N; ++k) tile[k] = 0;
+      return s;
+    }
+    std::lock_guard<std::mutex> g(mu);
+    cache[key] = pick;
+    return FC_OK;
+  }
+  fc_status autotune_any(void* st) { return f32() ? autotune<float>(st) : autotune<double>(st); }
 
   fc_status interpolate_from_any(const NsCore& src, void* st) {
     if (src.p.prec != p.prec || src.p.nfields != p.nfields || p.Nx < src.p.Nx || p.Ny < src.p.Ny ||

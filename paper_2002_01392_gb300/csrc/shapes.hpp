@@ -41,6 +41,9 @@ template <class T, int L> constexpr int zproj_lines() {
 template <class T, int N> constexpr int y_lines() {
   return sizeof(T) == 4 ? (N >= 128 ? 8 : 16) : (N >= 512 ? 2 : (N >= 128 ? 4 : 8));
 }
+// the alternative lines per CTA compiled beside each default (the autotuner
+// of ns_tune times both)
+template <int D> constexpr int tile_alt() { return D >= 8 ? D / 2 : 2 * D; }
 // row-pair jobs per CTA of the x row transforms
 template <int N> constexpr int x_jobs() { return N >= 512 ? 2 : (N >= 128 ? 4 : 8); }
 }  // namespace fcns

@@ -19,7 +19,7 @@ class HostSim:
         self.lib.fchc_ns_create.argtypes = [ctypes.c_void_p]
         for n in ("fchc_ns_set_fields", "fchc_ns_get_fields", "fchc_ns_rhs", "fchc_ns_step", "fchc_ns_project",
                   "fchc_ns_destroy", "fchc_ns_get_state", "fchc_ns_diag_raw", "fchc_ns_interpolate",
-                  "fchc_ns_profiles_raw"):
+                  "fchc_ns_profiles_raw", "fchc_ns_set_tiles"):
             getattr(self.lib, n).argtypes = None
         self.p = ns_params(**kw)
         self.h = self.lib.fchc_ns_create(ctypes.addressof(self.p))
@@ -53,6 +53,10 @@ class HostSim:
         assert self.lib.fchc_ns_project(ctypes.c_void_p(self.h), ctypes.c_double(dt), self._vp(a), self._vp(out),
                                         self._vp(gp)) == 0
         return out, gp
+
+    def set_tiles(self, tiles):
+        arr = np.ascontiguousarray(tiles, dtype=np.int32)
+        assert self.lib.fchc_ns_set_tiles(ctypes.c_void_p(self.h), self._vp(arr)) == 0
 
     def profiles_raw(self, nshell):
         out = np.zeros((self.p.nfields, self.p.Nz, 2 + nshell))

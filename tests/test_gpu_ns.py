@@ -365,3 +365,25 @@ def test_profiles_and_spectrum(api):
     assert np.abs(d["rms"] - rms).max() < 1e-11 * rms.max()
     assert np.abs(d["spectrum"] - E).max() < 1e-11 * E.max()
     sim.close()
+
+
+
+def test_tiles_do_not_change_results(api):
+    """ns_tune: the alternative tiles and the autotuned choice give bitwise the
+    same step as the defaults (float32 Boussinesq, 64^2 x 65)."""
+    N, Nz = 64, 65
+    kw = dict(nu=3.162e-3, kappa=3.162e-3, gamma=1.0)
+    f = torch.from_numpy(synth.boussinesq_fields(N, N, Nz, amp=1e-1, dtype=np.float32)).cuda()
+    outs = []
+    for mode, tiles in ((0, None), (2, [1, 1, 1, 1, 1]), (1, None)):
+        sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nfields=4, prec="f32", **kw))
+        choice = sim.tune(mode, tiles)
+        assert all(c in (0, 1) for c in choice)
+        if mode == 2:
+            assert choice == [1, 1, 1, 1, 1]
+        sim.set_fields(f)
+        for _ in range(2):
+            sim.step(1e-3)
+        outs.append(sim.get_fields())
+        sim.close()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])

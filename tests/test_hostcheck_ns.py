@@ -230,3 +230,24 @@ def test_profiles_kernel_matches_oracle():
     spec = np.einsum("fzj,z->fj", raw[..., 2:], wz) / n2
     np.testing.assert_allclose(spec, E, rtol=1e-12, atol=1e-14 * E.max())
     hs.close()
+
+
+
+@pytest.mark.parametrize("Nz", [33, 39])
+def test_alternative_tiles_match_oracle(Nz):
+    """Every kernel kind of the step with its alternative (autotuner) tile size:
+    padded (Nz = 33) and direct (Nz = 39, N' = 64) z lengths."""
+    N = 16 if Nz == 39 else 32
+    hs = HostSim(Nx=N, Ny=N, Nz=Nz, nu=1e-2, forcing_x=0.1, prec="f64")
+    hs.set_tiles([1, 1, 1, 1, 1])
+    P = ns.Params(N, N, Nz, nu=1e-2, forcing_x=0.1)
+    v = synth.channel_velocity(N, N, Nz)
+    hs.set_fields(v)
+    st = ns.to_spectral(v, P)
+    gp = np.zeros((2, 2, N, P.Kx), complex)
+    for _ in range(2):
+        hs.step(1e-3)
+        st, gp = ns.rk_step(st, gp, P, 1e-3)
+    ref = np.stack([ns.to_physical(c, P) for c in st])
+    assert _rel(hs.get_fields(), ref) < 1e-12
+    hs.close()
