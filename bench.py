@@ -148,9 +148,20 @@ def bench_deriv(api, torch, dtype_np, steps, warmup, with_e2e=True):
     pts = int(np.prod(shape))
     es = np.dtype(dtype_np).itemsize
     alg_bytes = 3 * es * pts
+    # latency distribution: 200 more timed calls after 20 warm-ups (the timed
+    # K calls above give the headline value)
+    for _ in range(20):
+        api.fc_deriv_z(plan, f, d1, d2)
+    dist = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(200)]
+    for a0, a1 in dist:
+        a0.record(stream)
+        api.fc_deriv_z(plan, f, d1, d2)
+        a1.record(stream)
+    torch.cuda.synchronize()
+    lat = np.array([a.elapsed_time(b) for a, b in dist])
     res = {
-        "points": pts, "seconds_per_call_mean": float(times.mean()), "p50_ms": float(np.percentile(times, 50) * 1e3),
-        "p99_ms": float(np.percentile(times, 99) * 1e3), "grid_points_per_s": pts * steps / total,
+        "points": pts, "seconds_per_call_mean": float(times.mean()), "p50_ms": float(np.percentile(lat, 50)),
+        "p99_ms": float(np.percentile(lat, 99)), "latency_reps": 200, "grid_points_per_s": pts * steps / total,
         "alg_bytes_per_call": alg_bytes, "alg_GBps": alg_bytes * steps / total / 1e9, "launches": steps,
     }
     # accuracy vs the FP64 oracle on 64 sampled lines (reported beside the number)
