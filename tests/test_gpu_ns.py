@@ -387,3 +387,19 @@ def test_tiles_do_not_change_results(api):
         outs.append(sim.get_fields())
         sim.close()
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("Nz,prec,tol", [(129, "f64", 1e-11), (257, "f64", 1e-11), (257, "f32", 3e-5),
+                                         (743, "f32", 3e-5), (999, "f32", 3e-5)])
+def test_every_z_length_one_step(api, Nz, prec, tol):
+    """One RK3 step on a 16 x 16 horizontal grid for the remaining compiled z
+    lengths: padded 320 (N' = 154) and 576 (N' = 282), direct 768 and 1024."""
+    N, nu = 16, 1e-2
+    sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nu=nu, forcing_x=10 * nu, prec=prec))
+    P = ns.Params(N, N, Nz, nu=nu, forcing_x=10 * nu)
+    v = synth.channel_velocity(N, N, Nz, nu=nu)
+    sim.set_fields(_cuda(v, sim.dtype))
+    sim.step(1e-4)
+    ref, _, _ = _oracle_steps(v, P, 1e-4, 1)
+    assert _rel(sim.get_fields().cpu().numpy(), ref) < tol
+    sim.close()
