@@ -296,7 +296,7 @@ def bench_cufft64(api, torch, steps, warmup):
 RK_SHAPE = (1024, 1024, 513)
 
 
-def bench_rk(api, torch, steps, warmup, with_e2e=True, shape=None):
+def bench_rk(api, torch, steps, warmup, with_e2e=True, shape=None, tune=True):
     """Boussinesq Rayleigh-Benard RK3 step (4 fields, FP32 transforms) on
     1024 x 1024 x 513, Ra = 1e7, Pr = 1 (nu = kappa = sqrt(Pr/Ra) = 3.162e-4,
     gamma = 1, Lz = 1).  Returns RK-stage grid-points/s = Nx Ny Nz o / t_step."""
@@ -306,7 +306,7 @@ def bench_rk(api, torch, steps, warmup, with_e2e=True, shape=None):
     p = api.ns_params(Nx=Nx, Ny=Ny, Nz=Nz, nfields=4, prec="f32", rk_order=3, **kw)
     ws_bytes = api.ns_workspace_bytes(p)
     sim = api.Sim(p)
-    tiles = sim.tune(1)                    # autotuned lines per CTA (ns_tune)
+    tiles = sim.tune(1 if tune else 0)     # autotuned lines per CTA (ns_tune), or the defaults
     host = synth.boussinesq_fields(Nx, Ny, Nz, dtype=np.float32)
     f = torch.from_numpy(host).cuda()
     sim.set_fields(f)
@@ -539,6 +539,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--rk-steps", type=int, default=5)
     ap.add_argument("--no-rk", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="profile cases: default tiles, no autotuning launches")
     ap.add_argument("--profile-case", default=None,
                     choices=["deriv32", "deriv64", "rk-small", "rk-mid", "rk-full", "rk-smooth"],
                     help="small single-kernel case for ncu (deriv: fc_deriv_z on 2x256x256x513; rk-*: one RK3 grid), no e2e / CPU leg")
@@ -581,7 +582,7 @@ def main():
     if args.profile_case and args.profile_case.startswith("rk"):
         shape = {"rk-small": (256, 256, 513), "rk-mid": (1024, 1024, 33), "rk-full": None,
                  "rk-smooth": (1024, 1024, 487)}[args.profile_case]
-        r = bench_rk(api, torch, args.steps, args.warmup, with_e2e=False, shape=shape)
+        r = bench_rk(api, torch, args.steps, args.warmup, with_e2e=False, shape=shape, tune=not args.no_tune)
         print(json.dumps({"profile_case": args.profile_case, **r}))
         return
     if args.profile_case:
