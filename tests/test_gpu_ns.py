@@ -389,11 +389,12 @@ def test_tiles_do_not_change_results(api):
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
 
 
-@pytest.mark.parametrize("Nz,prec,tol", [(129, "f64", 1e-11), (257, "f64", 1e-11), (257, "f32", 3e-5),
-                                         (743, "f32", 3e-5), (999, "f32", 3e-5)])
+@pytest.mark.parametrize("Nz,prec,tol", [(10, "f64", 1e-11), (129, "f64", 1e-11), (257, "f64", 1e-11),
+                                         (257, "f32", 3e-5), (743, "f32", 3e-5), (999, "f32", 3e-5)])
 def test_every_z_length_one_step(api, Nz, prec, tol):
     """One RK3 step on a 16 x 16 horizontal grid for the remaining compiled z
-    lengths: padded 320 (N' = 154) and 576 (N' = 282), direct 768 and 1024."""
+    lengths: the smallest grid (Nz = 2d = 10, padded 160), padded 320
+    (N' = 154) and 576 (N' = 282), direct 768 and 1024."""
     N, nu = 16, 1e-2
     sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nu=nu, forcing_x=10 * nu, prec=prec))
     P = ns.Params(N, N, Nz, nu=nu, forcing_x=10 * nu)
@@ -402,4 +403,22 @@ def test_every_z_length_one_step(api, Nz, prec, tol):
     sim.step(1e-4)
     ref, _, _ = _oracle_steps(v, P, 1e-4, 1)
     assert _rel(sim.get_fields().cpu().numpy(), ref) < tol
+    sim.close()
+
+
+def test_general_parameters_match_oracle(api):
+    """Exponential filter in x, y, z (mode 0), a 4 x 3 x 2 box with Nx != Ny,
+    kappa != nu, gamma = 2.5, fourth-order time splitting, float64."""
+    kw = dict(nfields=4, nu=1e-3, kappa=2e-3, gamma=2.5, rk_order=4, filter=0, Lx=4.0, Ly=3.0, Lz=2.0)
+    Nx, Ny, Nz = 64, 32, 65
+    sim = api.Sim(api.ns_params(Nx=Nx, Ny=Ny, Nz=Nz, prec="f64", **kw))
+    P = ns.Params(Nx, Ny, Nz, **kw)
+    f = synth.boussinesq_fields(Nx, Ny, Nz, Lz=2.0, amp=1e-1)
+    assert _rel(sim.rhs(_cuda(f)).cpu().numpy(), ns.ns_rhs(f, P)) < 1e-11
+    sim.set_fields(_cuda(f))
+    for _ in range(2):
+        sim.step(2e-3)
+    ref, gref, _ = _oracle_steps(f, P, 2e-3, 2)
+    assert _rel(sim.get_fields().cpu().numpy(), ref) < 1e-11
+    assert _rel(sim.wall_gradp().cpu().numpy(), gref) < 1e-9
     sim.close()

@@ -251,3 +251,24 @@ def test_alternative_tiles_match_oracle(Nz):
     ref = np.stack([ns.to_physical(c, P) for c in st])
     assert _rel(hs.get_fields(), ref) < 1e-12
     hs.close()
+
+
+def test_general_parameters_match_oracle():
+    """Everything away from the defaults at once: exponential filter in x, y
+    and z (mode 0), a 4 x 3 x 2 box with Nx != Ny, kappa != nu, gamma = 2.5,
+    fourth-order time splitting, float64."""
+    kw = dict(nfields=4, nu=1e-3, kappa=2e-3, gamma=2.5, rk_order=4, filter=0, Lx=4.0, Ly=3.0, Lz=2.0)
+    Nx, Ny, Nz = 32, 16, 33
+    hs = HostSim(Nx=Nx, Ny=Ny, Nz=Nz, prec="f64", **kw)
+    P = ns.Params(Nx, Ny, Nz, **kw)
+    f = synth.boussinesq_fields(Nx, Ny, Nz, Lz=2.0, amp=1e-1)
+    assert _rel(hs.rhs(f), ns.ns_rhs(f, P)) < 1e-12
+    hs.set_fields(f)
+    st = ns.to_spectral(f, P)
+    gp = np.zeros((2, 2, Ny, P.Kx), complex)
+    for _ in range(2):
+        hs.step(2e-3)
+        st, gp = ns.rk_step(st, gp, P, 2e-3)
+    ref = np.stack([ns.to_physical(c, P) for c in st])
+    assert _rel(hs.get_fields(), ref) < 1e-12
+    hs.close()
