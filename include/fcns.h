@@ -356,6 +356,60 @@ fc_status ns_batch_info(ns_batch_t batch, int* members, int* graph_nodes, int* g
 /* Release the graphs and streams (not the members). */
 fc_status ns_batch_destroy(ns_batch_t batch);
 
+/* ------------------------------------------------------------------------ */
+/* Failure detection and injection                                            */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * fc_count_nonfinite -- number of Inf / NaN values among n reals of type
+ * dtype at the device pointer data (for example an fc_deriv_z output),
+ * counted by a kernel on `stream`; synchronous (waits for the stream).
+ * *count (host) receives the number; returns FC_ERR_NONFINITE when it is
+ * positive, FC_OK otherwise.  n = 0 is allowed (count 0, nothing launched).
+ */
+fc_status fc_count_nonfinite(fc_dtype dtype, const void* data, long long n, long long* count,
+                             fc_stream_t stream);
+
+/*
+ * ns_check_finite -- number of Inf / NaN values (real and imaginary parts
+ * counted separately) in the simulation's state: every field on the N'
+ * continued rows of every physical (kx, ky) line.  Synchronous; *count (host)
+ * receives the number; FC_ERR_NONFINITE when it is positive.  Also resets
+ * the flag of ns_set_finite_check to this count.
+ */
+fc_status ns_check_finite(ns_sim_t sim, long long* count, fc_stream_t stream);
+
+/*
+ * ns_set_finite_check -- check the state for non-finite values after every
+ * `every`-th rk_step (and after every ns_batch_step of a batch holding the
+ * simulation); 0 (the default) turns the check off.  The check is a kernel
+ * that adds the count to a device-side flag, followed by an asynchronous
+ * copy of the flag into pinned host memory, so no call waits for it: once
+ * the copy of a failed check has landed, rk_step and ns_batch_step return
+ * FC_ERR_NONFINITE without enqueuing work, until ns_check_finite finds the
+ * state clean again (after ns_set_fields or ns_put_state).  Costs one read
+ * of the state per checked step.
+ */
+fc_status ns_set_finite_check(ns_sim_t sim, int every);
+
+/*
+ * fc_inject_failure -- testing aid for callers' error handling, host only:
+ * after `skip` further calls of the entry point named `entry` (its C name;
+ * "fc_setup" covers fc_setup_ex too; "*" matches every entry point that
+ * checks), the next `count` calls (count < 0: all later calls) return
+ * `status` at once, enqueue nothing, write nothing and set fc_last_error to
+ * "<entry>: injected failure".  entry = NULL removes every rule.  Rules can
+ * also come from the environment variable FCNS_INJECT, a comma-separated
+ * list of "entry:status:skip:count" (status by name, e.g. FC_ERR_CUDA, or
+ * number), read on the first check.  The entry points that check are
+ * fc_setup, fc_deriv_z, fc_deriv_z_noalloc, fc_count_nonfinite, ns_create,
+ * ns_set_fields, ns_get_fields, ns_get_state, ns_put_state, ns_rhs,
+ * fc_poisson_project, rk_step, ns_diagnostics, ns_profiles, ns_interpolate,
+ * ns_tune, ns_check_finite, ns_batch_create and ns_batch_step.
+ * FC_ERR_ARG for a NULL-free rule with status FC_OK, skip < 0 or count = 0.
+ */
+fc_status fc_inject_failure(const char* entry, fc_status status, long long skip, long long count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,18 +68,50 @@ _sig("ns_batch_info", [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctyp
 _sig("ns_batch_destroy", [_vp])
 _sig("fc_deriv_z", [_vp, _c_int, _c_int, _c_int, _c_int, _c_double, _vp, _vp, _vp, _vp])
 _sig("fc_deriv_z_noalloc", [_vp, _c_int, _c_int, _c_int, _c_int, _c_double, _vp, _vp, _vp, _vp])
+_sig("fc_count_nonfinite", [_c_int, _vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong), _vp])
+_sig("ns_check_finite", [_vp, ctypes.POINTER(ctypes.c_longlong), _vp])
+_sig("ns_set_finite_check", [_vp, _c_int])
+_sig("fc_inject_failure", [ctypes.c_char_p, _c_int, ctypes.c_longlong, ctypes.c_longlong])
 
 EXPORTED = ["fc_status_str", "fc_last_error", "fc_setup", "fc_setup_ex", "fc_plan_matrix", "fc_plan_info",
             "fc_destroy", "fc_deriv_z", "fc_deriv_z_noalloc", "ns_params_default", "ns_workspace_bytes", "ns_create", "ns_destroy",
             "ns_set_fields", "ns_get_fields", "ns_get_state", "ns_put_state", "ns_get_wall_gradp",
             "ns_put_wall_gradp", "ns_rhs", "fc_poisson_project", "rk_step", "ns_diagnostics",
             "ns_batch_create", "ns_batch_step", "ns_batch_info", "ns_batch_destroy", "ns_interpolate",
-            "ns_profiles", "ns_spectrum_shells", "ns_tune"]
+            "ns_profiles", "ns_spectrum_shells", "ns_tune", "fc_count_nonfinite", "ns_check_finite",
+            "ns_set_finite_check", "fc_inject_failure"]
 
 
 def _check(status: int, where: str):
     if status != 0:
         raise FcError(status, where)
+
+
+STATUS = {"FC_OK": 0, "FC_ERR_ARG": 1, "FC_ERR_UNSUPPORTED": 2, "FC_ERR_CUDA": 3, "FC_ERR_NOMEM": 4,
+          "FC_ERR_TIMEOUT": 5, "FC_ERR_NONFINITE": 6, "FC_ERR_STATE": 7}
+
+
+def inject_failure(entry: str, status="FC_ERR_CUDA", skip: int = 0, count: int = 1):
+    """fc_inject_failure: after ``skip`` calls of ``entry`` the next ``count``
+    calls (all later ones if negative) return ``status`` without doing anything."""
+    code = STATUS[status] if isinstance(status, str) else int(status)
+    _check(_lib.fc_inject_failure(entry.encode(), code, int(skip), int(count)), "fc_inject_failure")
+
+
+def clear_injected():
+    _check(_lib.fc_inject_failure(None, 0, 0, 0), "fc_inject_failure")
+
+
+def count_nonfinite(t, stream=None) -> int:
+    """fc_count_nonfinite: number of Inf / NaN values of a float32 / float64
+    CUDA tensor (synchronous; no exception for a positive count)."""
+    if not t.is_cuda:
+        raise ValueError("t must be a CUDA tensor")
+    n = ctypes.c_longlong()
+    st = _lib.fc_count_nonfinite(_dtype_code(t), _ptr(t), t.numel(), ctypes.byref(n), _stream(stream))
+    if st not in (0, STATUS["FC_ERR_NONFINITE"]):
+        _check(st, "fc_count_nonfinite")
+    return n.value
 
 
 def _stream(stream=None) -> int:
@@ -290,6 +322,19 @@ class Sim:
 
     def step(self, dt: float, stream=None):
         _check(_lib.rk_step(self.handle, float(dt), _stream(stream)), "rk_step")
+
+    def check_finite(self, stream=None) -> int:
+        """ns_check_finite: number of non-finite state values (synchronous;
+        no exception for a positive count)."""
+        n = ctypes.c_longlong()
+        st = _lib.ns_check_finite(self.handle, ctypes.byref(n), _stream(stream))
+        if st not in (0, STATUS["FC_ERR_NONFINITE"]):
+            _check(st, "ns_check_finite")
+        return n.value
+
+    def set_finite_check(self, every: int):
+        """ns_set_finite_check: check the state after every ``every``-th step (0: off)."""
+        _check(_lib.ns_set_finite_check(self.handle, int(every)), "ns_set_finite_check")
 
     def profiles(self, stream=None):
         """ns_profiles: dict of numpy arrays mean [nf][Nz], rms [nf][Nz],

@@ -90,5 +90,29 @@ def build(verbose: bool = False, hostcheck: bool = True) -> str:
     return LIB
 
 
+def build_hostcheck_asan() -> str:
+    """The host-check library built with AddressSanitizer and guard bands
+    between the simulation's workspace arrays (for the CPU memory-safety
+    test; load it into a process that preloads libasan).  Returns its path."""
+    os.makedirs(BUILD, exist_ok=True)
+    cuda = _cuda_home()
+    out = os.path.join(BUILD, "libfcns_hostcheck_asan.so")
+    if _newer(out, _deps()):
+        return out
+    san = ["-fsanitize=address", "-fno-omit-frame-pointer"]
+    hc_obj = os.path.join(BUILD, "hostcheck_asan.o")
+    ht_obj = os.path.join(BUILD, "host_tables_asan.o")
+    jobs = [[os.path.join(cuda, "bin", "nvcc"), "-std=c++17", "-O1", "--expt-relaxed-constexpr", "-DFC_LAYOUT_GUARD=256",
+             "-Xcompiler", ",".join(["-fPIC"] + san), "-diag-suppress", "20013", "-x", "cu", "-c",
+             os.path.join(CSRC, "hostcheck.cu"), "-o", hc_obj],
+            ["g++", "-std=gnu++17", "-O1", "-fPIC", *san, "-I", os.path.join(ROOT, "include"), "-I",
+             os.path.join(cuda, "include"), "-c", os.path.join(CSRC, "host_tables.cpp"), "-o", ht_obj]]
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        list(ex.map(_run, jobs))
+    _run(["g++", "-shared", *san, "-o", out, hc_obj, ht_obj, "-L", os.path.join(cuda, "lib64"),
+          "-Wl,-rpath," + os.path.join(cuda, "lib64"), "-lcudart"])
+    return out
+
+
 if __name__ == "__main__":
     print(build(verbose=True))

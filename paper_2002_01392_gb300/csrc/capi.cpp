@@ -1,7 +1,11 @@
 // C ABI of libfcns: argument validation, plan objects, dispatch to launchers.
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "host_tables.hpp"
 #include "internal.hpp"
@@ -16,6 +20,78 @@ fc_status cuda_status(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return FC_OK;
   set_error(std::string(what) + ": " + cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? FC_ERR_NOMEM : FC_ERR_CUDA;
+}
+
+// Failure injection (tests of callers' error handling; nothing reaches the
+// GPU): rules "entry:status:skip:count" from fc_inject_failure or from the
+// FCNS_INJECT environment variable (comma-separated rules, read on the first
+// check).  A rule lets `skip` calls of its entry point through, then fails
+// the next `count` calls (count < 0: every later call); entry "*" matches
+// every entry point that checks.
+namespace {
+struct InjectRule {
+  std::string entry;
+  fc_status status;
+  long long skip, count;
+};
+std::mutex g_inj_mtx;
+std::vector<InjectRule> g_inj;
+std::atomic<int> g_inj_state{-1};  // -1: environment not read; 0: no rules; 1: rules armed
+
+bool parse_status(const std::string& t, fc_status* out) {
+  static const char* names[] = {"FC_OK", "FC_ERR_ARG", "FC_ERR_UNSUPPORTED", "FC_ERR_CUDA",
+                                "FC_ERR_NOMEM", "FC_ERR_TIMEOUT", "FC_ERR_NONFINITE", "FC_ERR_STATE"};
+  for (int i = 1; i < 8; ++i)
+    if (t == names[i] || t == std::to_string(i)) { *out = (fc_status)i; return true; }
+  return false;
+}
+
+// caller holds g_inj_mtx
+void read_env_rules() {
+  const char* env = std::getenv("FCNS_INJECT");
+  std::string all = env ? env : "";
+  size_t pos = 0;
+  while (pos < all.size()) {
+    size_t end = all.find(',', pos);
+    if (end == std::string::npos) end = all.size();
+    std::string rule = all.substr(pos, end - pos), f[4];
+    pos = end + 1;
+    int k = 0;
+    size_t q = 0;
+    while (k < 4) {
+      size_t c = rule.find(':', q);
+      f[k++] = rule.substr(q, c == std::string::npos ? std::string::npos : c - q);
+      if (c == std::string::npos) break;
+      q = c + 1;
+    }
+    fc_status st;
+    if (f[0].empty() || !parse_status(f[1], &st)) continue;
+    g_inj.push_back({f[0], st, f[2].empty() ? 0 : std::atoll(f[2].c_str()), f[3].empty() ? 1 : std::atoll(f[3].c_str())});
+  }
+  g_inj_state.store(g_inj.empty() ? 0 : 1);
+}
+}  // namespace
+
+fc_status injected(const char* entry) {
+  if (g_inj_state.load(std::memory_order_acquire) == 0) return FC_OK;
+  std::lock_guard<std::mutex> lk(g_inj_mtx);
+  if (g_inj_state.load() < 0) read_env_rules();
+  fc_status out = FC_OK;
+  for (auto& r : g_inj) {
+    if (r.entry != "*" && r.entry != entry) continue;
+    if (r.skip > 0) { --r.skip; continue; }
+    if (r.count == 0) continue;
+    if (r.count > 0) --r.count;
+    out = r.status;
+    break;
+  }
+  std::vector<InjectRule> live;
+  for (auto& r : g_inj)
+    if (r.count != 0) live.push_back(r);
+  g_inj.swap(live);
+  g_inj_state.store(g_inj.empty() ? 0 : 1);
+  if (out) set_error(std::string(entry) + ": injected failure");
+  return out;
 }
 
 }  // namespace fcns
@@ -40,7 +116,25 @@ const char* fc_status_str(fc_status s) {
 
 const char* fc_last_error(void) { return g_last_error.c_str(); }
 
+fc_status fc_inject_failure(const char* entry, fc_status status, long long skip, long long count) {
+  std::lock_guard<std::mutex> lk(g_inj_mtx);
+  if (g_inj_state.load() < 0) read_env_rules();
+  if (!entry) {
+    g_inj.clear();
+    g_inj_state.store(0);
+    return FC_OK;
+  }
+  if (status == FC_OK || (int)status < 0 || (int)status > 7 || skip < 0 || count == 0) {
+    set_error("fc_inject_failure: status must be an error code, skip >= 0 and count != 0");
+    return FC_ERR_ARG;
+  }
+  g_inj.push_back({entry, status, skip, count});
+  g_inj_state.store(1);
+  return FC_OK;
+}
+
 fc_status fc_setup_ex(int d, int C, int Nz, int M, int n_os, fc_plan_t* out) {
+  if (fc_status inj = injected("fc_setup")) return inj;
   if (!out) { set_error("fc_setup: out is NULL"); return FC_ERR_ARG; }
   *out = nullptr;
   if (d < 2 || d > 10 || C < d || C > 64 || Nz < 2 * d || M < 1 || n_os < 1 || 2 * M + 1 > 2 * ((d - 1) * n_os + 1)) {
@@ -202,6 +296,7 @@ fc_status fcns::check_deriv_args(const PlanData& pd, const PlanHostTables& t, fc
 
 extern "C" fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
                                 const void* f, void* df, void* d2f, fc_stream_t stream) {
+  if (fc_status inj = injected("fc_deriv_z")) return inj;
   if (!plan) { set_error("fc_deriv_z: NULL plan"); return FC_ERR_ARG; }
   fc_status s = check_deriv_args(plan->data, plan->deriv, dtype, batch, Nx, Ny, Lz, f, df, d2f, "fc_deriv_z");
   if (s) return s;

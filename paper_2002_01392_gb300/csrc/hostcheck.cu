@@ -77,6 +77,9 @@ extern "C" int fchc_deriv_z(int dtype, int L, const double* Mr, int d, int Cc, i
 // ---------------------------------------------------------------------------
 #include <cstdlib>
 #include <cstring>
+#if defined(__SANITIZE_ADDRESS__)
+#include <sanitizer/asan_interface.h>
+#endif
 
 #include "ns_core.hpp"
 
@@ -110,10 +113,21 @@ extern "C" {
 void* fchc_ns_create(const ns_params* p) {
   auto* c = new NsCore<EmuBK>();
   if (c->create(*p, nullptr, 0)) { c->destroy(); delete c; return nullptr; }
+#if FC_LAYOUT_GUARD && defined(__SANITIZE_ADDRESS__)
+  // the guard bands between the workspace arrays become unaddressable: a
+  // kernel or copy that strays out of its array is reported by the sanitizer
+  for (auto& g : c->l.guards) {
+    const size_t b = (g.first + 7) / 8 * 8;
+    if (g.second > b) ASAN_POISON_MEMORY_REGION(c->ws + b, g.second - b);
+  }
+#endif
   return c;
 }
 void fchc_ns_destroy(void* h) {
   auto* c = (NsCore<EmuBK>*)h;
+#if FC_LAYOUT_GUARD && defined(__SANITIZE_ADDRESS__)
+  ASAN_UNPOISON_MEMORY_REGION(c->ws, c->l.total);
+#endif
   c->destroy();
   delete c;
 }
@@ -138,5 +152,24 @@ int fchc_ns_get_state(void* h, void* out) {
   auto* c = (NsCore<EmuBK>*)h;
   std::memcpy(out, c->ws + c->l.X[c->cur], c->state_bytes());
   return 0;
+}
+int fchc_ns_put_state(void* h, const void* in) {
+  auto* c = (NsCore<EmuBK>*)h;
+  std::memcpy(c->ws + c->l.X[c->cur], in, c->state_bytes());
+  return c->mean_init_any(nullptr);
+}
+int fchc_ns_count_nonfinite(void* h, long long* count) {
+  auto* c = (NsCore<EmuBK>*)h;
+  fc_status s = c->count_nonfinite_any(true, nullptr);
+  unsigned long long n = 0;
+  if (!s) s = c->bk.d2h(&n, c->ws + c->l.nfin, sizeof(n), nullptr);
+  *count = (long long)n;
+  return s;
+}
+// thread order inside a phase (0 ascending, 1 descending) and shared-memory
+// poisoning of the emulation (see phased_emulate)
+void fchc_set_emulation(int order, int poison) {
+  emu_order() = order;
+  emu_poison() = poison;
 }
 }

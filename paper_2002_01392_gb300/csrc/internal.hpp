@@ -12,6 +12,9 @@ namespace fcns {
 
 void set_error(const std::string& msg);
 fc_status cuda_status(cudaError_t e, const char* what);
+// host-side failure injection: the status an armed entry point must return
+// now (FC_OK when it is not armed); checked first thing by the entry points
+fc_status injected(const char* entry);
 
 // lengths of the two-pass line engine that are compiled: L = L1 * L2
 struct EngineShape { int L, L1, L2; };

@@ -51,6 +51,7 @@ using namespace fcns;
 
 extern "C" fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
                                         const void* f, void* df, void* d2f, fc_stream_t stream) {
+  if (fc_status inj = injected("fc_deriv_z_noalloc")) return inj;
   if (!plan) { set_error("fc_deriv_z_noalloc: NULL plan"); return FC_ERR_ARG; }
   fc_status s = check_deriv_args(plan->data, plan->deriv, dtype, batch, Nx, Ny, Lz, f, df, d2f, "fc_deriv_z_noalloc");
   if (s) return s;

@@ -19,4 +19,6 @@ template struct DevRun<KMeanLine<double>>;
 template struct DevRun<KMeanInit<double>>;
 template struct DevRun<KInterp<double>>;
 template struct DevRun<KProf<double>>;
+template struct DevRun<KFinite<double>>;
+template struct DevRun<KCount<double>>;
 }  // namespace fcns

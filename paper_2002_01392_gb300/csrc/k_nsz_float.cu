@@ -19,4 +19,6 @@ template struct DevRun<KMeanLine<float>>;
 template struct DevRun<KMeanInit<float>>;
 template struct DevRun<KInterp<float>>;
 template struct DevRun<KProf<float>>;
+template struct DevRun<KFinite<float>>;
+template struct DevRun<KCount<float>>;
 }  // namespace fcns

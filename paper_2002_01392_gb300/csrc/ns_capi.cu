@@ -64,7 +64,28 @@ using namespace fcns;
 struct ns_sim {
   NsCore<DeviceBK> core;
   int device = -1;
+  // non-finite check after every check_every-th step: the device counter
+  // (workspace) is copied into the pinned host word hflag after the count,
+  // and later calls read hflag without synchronising
+  int check_every = 0;
+  long long nsteps = 0;
+  unsigned long long* hflag = nullptr;
 };
+
+static fc_status check_enqueue(ns_sim* s, cudaStream_t st) {
+  fc_status r = s->core.count_nonfinite_any(false, st);
+  if (!r) r = cuda_status(cudaMemcpyAsync(s->hflag, s->core.ws + s->core.l.nfin, sizeof(unsigned long long),
+                                          cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync(non-finite flag)");
+  return r;
+}
+
+static fc_status check_flag(ns_sim* s, const char* what) {
+  if (s->check_every <= 0 || !s->hflag) return FC_OK;
+  const unsigned long long n = *static_cast<volatile unsigned long long*>(s->hflag);
+  if (!n) return FC_OK;
+  set_error(std::string(what) + ": a checked step left " + std::to_string(n) + " non-finite state values");
+  return FC_ERR_NONFINITE;
+}
 
 // A set of simulations whose RK steps are replayed from captured CUDA graphs.
 // Members are spread over NB capture branches (fork / join on events), so
@@ -81,6 +102,7 @@ struct ns_batch {
   struct Entry {
     std::vector<int> cur_in, cur_out;
     std::vector<double> dt;
+    std::vector<char> chk;   // members checked for non-finite values after the step
     cudaGraphExec_t exec = nullptr;
   };
   std::vector<Entry> cache;
@@ -118,6 +140,7 @@ fc_status ns_workspace_bytes(const ns_params* p, size_t* bytes) {
 }
 
 fc_status ns_create(const ns_params* p, void* dev_workspace, size_t bytes, ns_sim_t* out) {
+  if (fc_status inj = injected("ns_create")) return inj;
   if (!p || !out) { set_error("ns_create: NULL argument"); return FC_ERR_ARG; }
   *out = nullptr;
   ns_sim* s = new (std::nothrow) ns_sim;
@@ -138,11 +161,13 @@ fc_status ns_create(const ns_params* p, void* dev_workspace, size_t bytes, ns_si
 fc_status ns_destroy(ns_sim_t s) {
   if (!s) return FC_ERR_ARG;
   fc_status st = s->core.destroy();
+  if (s->hflag) cudaFreeHost(s->hflag);
   delete s;
   return st;
 }
 
 fc_status ns_set_fields(ns_sim_t s, const void* phys, fc_stream_t stream) {
+  if (fc_status inj = injected("ns_set_fields")) return inj;
   fc_status st = check_sim(s, "ns_set_fields");
   if (st) return st;
   if (!phys) { set_error("ns_set_fields: NULL fields"); return FC_ERR_ARG; }
@@ -150,6 +175,7 @@ fc_status ns_set_fields(ns_sim_t s, const void* phys, fc_stream_t stream) {
 }
 
 fc_status ns_get_fields(ns_sim_t s, void* phys, fc_stream_t stream) {
+  if (fc_status inj = injected("ns_get_fields")) return inj;
   fc_status st = check_sim(s, "ns_get_fields");
   if (st) return st;
   if (!phys) { set_error("ns_get_fields: NULL fields"); return FC_ERR_ARG; }
@@ -157,6 +183,7 @@ fc_status ns_get_fields(ns_sim_t s, void* phys, fc_stream_t stream) {
 }
 
 fc_status ns_get_state(ns_sim_t s, void* spec, fc_stream_t stream) {
+  if (fc_status inj = injected("ns_get_state")) return inj;
   fc_status st = check_sim(s, "ns_get_state");
   if (st) return st;
   if (!spec) return FC_ERR_ARG;
@@ -164,6 +191,7 @@ fc_status ns_get_state(ns_sim_t s, void* spec, fc_stream_t stream) {
 }
 
 fc_status ns_put_state(ns_sim_t s, const void* spec, fc_stream_t stream) {
+  if (fc_status inj = injected("ns_put_state")) return inj;
   fc_status st = check_sim(s, "ns_put_state");
   if (st) return st;
   if (!spec) return FC_ERR_ARG;
@@ -187,6 +215,7 @@ fc_status ns_put_wall_gradp(ns_sim_t s, const void* gradp, fc_stream_t stream) {
 }
 
 fc_status ns_rhs(ns_sim_t s, const void* phys_in, void* rhs_out, fc_stream_t stream) {
+  if (fc_status inj = injected("ns_rhs")) return inj;
   fc_status st = check_sim(s, "ns_rhs");
   if (st) return st;
   if (!phys_in || !rhs_out || phys_in == rhs_out) { set_error("ns_rhs: bad buffers"); return FC_ERR_ARG; }
@@ -195,6 +224,7 @@ fc_status ns_rhs(ns_sim_t s, const void* phys_in, void* rhs_out, fc_stream_t str
 
 fc_status fc_poisson_project(ns_sim_t s, double dt_stage, const void* vstar_phys, void* v_phys, void* gradp_wall,
                              fc_stream_t stream) {
+  if (fc_status inj = injected("fc_poisson_project")) return inj;
   fc_status st = check_sim(s, "fc_poisson_project");
   if (st) return st;
   if (!vstar_phys || !v_phys || !(dt_stage > 0)) { set_error("fc_poisson_project: bad arguments"); return FC_ERR_ARG; }
@@ -202,10 +232,86 @@ fc_status fc_poisson_project(ns_sim_t s, double dt_stage, const void* vstar_phys
 }
 
 fc_status rk_step(ns_sim_t s, double dt, fc_stream_t stream) {
-  fc_status st = check_sim(s, "rk_step");
+  fc_status st = injected("rk_step");
+  if (!st) st = check_sim(s, "rk_step");
   if (st) return st;
   if (!(dt > 0)) { set_error("rk_step: dt must be positive"); return FC_ERR_ARG; }
-  return s->core.step_any(dt, stream);
+  st = check_flag(s, "rk_step");
+  if (!st) st = s->core.step_any(dt, stream);
+  if (!st && s->check_every > 0 && ++s->nsteps % s->check_every == 0) st = check_enqueue(s, (cudaStream_t)stream);
+  return st;
+}
+
+fc_status ns_set_finite_check(ns_sim_t s, int every) {
+  fc_status st = check_sim(s, "ns_set_finite_check");
+  if (st) return st;
+  if (every < 0) { set_error("ns_set_finite_check: every must be >= 0"); return FC_ERR_ARG; }
+  if (every > 0 && !s->hflag) {
+    void* h = nullptr;
+    st = cuda_status(cudaHostAlloc(&h, sizeof(unsigned long long), cudaHostAllocDefault), "cudaHostAlloc");
+    if (st) return st;
+    s->hflag = static_cast<unsigned long long*>(h);
+    *s->hflag = 0;
+  }
+  s->check_every = every;
+  s->nsteps = 0;
+  return FC_OK;
+}
+
+fc_status ns_check_finite(ns_sim_t s, long long* count, fc_stream_t stream) {
+  fc_status st = injected("ns_check_finite");
+  if (!st) st = check_sim(s, "ns_check_finite");
+  if (st) return st;
+  if (!count) { set_error("ns_check_finite: NULL count"); return FC_ERR_ARG; }
+  unsigned long long n = 0;
+  st = s->core.count_nonfinite_any(true, stream);
+  if (!st) st = s->core.bk.d2h(&n, s->core.ws + s->core.l.nfin, sizeof(n), stream);
+  if (st) return st;
+  if (s->hflag) *static_cast<volatile unsigned long long*>(s->hflag) = n;
+  *count = (long long)n;
+  if (n) {
+    set_error("ns_check_finite: " + std::to_string(n) + " non-finite state values");
+    return FC_ERR_NONFINITE;
+  }
+  return FC_OK;
+}
+
+fc_status fc_count_nonfinite(fc_dtype dtype, const void* data, long long n, long long* count, fc_stream_t stream) {
+  fc_status st = injected("fc_count_nonfinite");
+  if (st) return st;
+  if (!count || n < 0 || (n > 0 && !data) || (dtype != FC_F32 && dtype != FC_F64)) {
+    set_error("fc_count_nonfinite: bad arguments");
+    return FC_ERR_ARG;
+  }
+  *count = 0;
+  if (n == 0) return FC_OK;
+  cudaStream_t cs = (cudaStream_t)stream;
+  unsigned long long* dc = nullptr;
+  st = cuda_status(cudaMallocAsync((void**)&dc, sizeof(unsigned long long), cs), "cudaMallocAsync");
+  if (st) return st;
+  st = cuda_status(cudaMemsetAsync(dc, 0, sizeof(unsigned long long), cs), "cudaMemsetAsync");
+  const long long per = 256 * 64;
+  const long long grid = (n + per - 1) / per;
+  if (!st) {
+    if (dtype == FC_F32) {
+      KCount<float>::Args a{static_cast<const float*>(data), n, per, dc};
+      st = DevRun<KCount<float>>::run(a, grid, cs);
+    } else {
+      KCount<double>::Args a{static_cast<const double*>(data), n, per, dc};
+      st = DevRun<KCount<double>>::run(a, grid, cs);
+    }
+  }
+  unsigned long long h = 0;
+  if (!st) st = cuda_status(cudaMemcpyAsync(&h, dc, sizeof(h), cudaMemcpyDeviceToHost, cs), "cudaMemcpyAsync(D2H)");
+  cudaFreeAsync(dc, cs);
+  if (!st) st = cuda_status(cudaStreamSynchronize(cs), "cudaStreamSynchronize");
+  if (st) return st;
+  *count = (long long)h;
+  if (h) {
+    set_error("fc_count_nonfinite: " + std::to_string(h) + " non-finite values");
+    return FC_ERR_NONFINITE;
+  }
+  return FC_OK;
 }
 
 fc_status ns_spectrum_shells(ns_sim_t s, int* nshell, double* dk) {
@@ -217,6 +323,7 @@ fc_status ns_spectrum_shells(ns_sim_t s, int* nshell, double* dk) {
 }
 
 fc_status ns_profiles(ns_sim_t s, double* mean, double* rms, double* spectrum, fc_stream_t stream) {
+  if (fc_status inj = injected("ns_profiles")) return inj;
   fc_status st = check_sim(s, "ns_profiles");
   if (st) return st;
   const ns_params& p = s->core.p;
@@ -240,6 +347,7 @@ fc_status ns_profiles(ns_sim_t s, double* mean, double* rms, double* spectrum, f
 }
 
 fc_status ns_interpolate(ns_sim_t dst, ns_sim_t src, fc_stream_t stream) {
+  if (fc_status inj = injected("ns_interpolate")) return inj;
   fc_status st = check_sim(dst, "ns_interpolate");
   if (!st) st = check_sim(src, "ns_interpolate");
   if (st) return st;
@@ -250,6 +358,7 @@ fc_status ns_interpolate(ns_sim_t dst, ns_sim_t src, fc_stream_t stream) {
 }
 
 fc_status ns_tune(ns_sim_t s, int mode, int* tiles, fc_stream_t stream) {
+  if (fc_status inj = injected("ns_tune")) return inj;
   fc_status st = check_sim(s, "ns_tune");
   if (st) return st;
   auto& c = s->core;
@@ -270,6 +379,7 @@ fc_status ns_tune(ns_sim_t s, int mode, int* tiles, fc_stream_t stream) {
 }
 
 fc_status ns_batch_create(ns_sim_t* sims, int n, ns_batch_t* out) {
+  if (fc_status inj = injected("ns_batch_create")) return inj;
   if (!sims || !out || n < 1) { set_error("ns_batch_create: bad arguments"); return FC_ERR_ARG; }
   *out = nullptr;
   int dev = -1;
@@ -324,7 +434,13 @@ static fc_status batch_capture(ns_batch_t b, const double* dt, ns_batch::Entry* 
   st = cuda_status(cudaEventRecord(b->fork, b->cap), "cudaEventRecord");
   const int nb = n < ns_batch::NB ? n : ns_batch::NB;
   for (int k = 0; k < nb && !st; ++k) st = cuda_status(cudaStreamWaitEvent(b->br[k], b->fork, 0), "cudaStreamWaitEvent");
-  for (int i = 0; i < n && !st; ++i) st = b->sims[i]->core.step_any(dt[i], b->br[i % nb]);
+  e->chk.resize(n);
+  for (int i = 0; i < n && !st; ++i) {
+    ns_sim* m = b->sims[i];
+    e->chk[i] = m->check_every > 0;
+    st = m->core.step_any(dt[i], b->br[i % nb]);
+    if (!st && e->chk[i]) st = check_enqueue(m, b->br[i % nb]);
+  }
   for (int k = 0; k < nb && !st; ++k) {
     st = cuda_status(cudaEventRecord(b->join[k], b->br[k]), "cudaEventRecord");
     if (!st) st = cuda_status(cudaStreamWaitEvent(b->cap, b->join[k], 0), "cudaStreamWaitEvent");
@@ -348,6 +464,7 @@ static fc_status batch_capture(ns_batch_t b, const double* dt, ns_batch::Entry* 
 }
 
 fc_status ns_batch_step(ns_batch_t b, const double* dt, fc_stream_t stream) {
+  if (fc_status inj = injected("ns_batch_step")) return inj;
   if (!b || !dt) { set_error("ns_batch_step: NULL argument"); return FC_ERR_ARG; }
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) {
@@ -357,10 +474,16 @@ fc_status ns_batch_step(ns_batch_t b, const double* dt, fc_stream_t stream) {
   const int n = (int)b->sims.size();
   for (int i = 0; i < n; ++i)
     if (!(dt[i] > 0)) { set_error("ns_batch_step: dt must be positive"); return FC_ERR_ARG; }
+  for (int i = 0; i < n; ++i)
+    if (b->sims[i]->check_every > 0) {
+      fc_status c = check_flag(b->sims[i], ("ns_batch_step: member " + std::to_string(i)).c_str());
+      if (c) return c;
+    }
   ns_batch::Entry* hit = nullptr;
   for (auto& e : b->cache) {
     bool same = true;
-    for (int i = 0; i < n && same; ++i) same = e.cur_in[i] == b->sims[i]->core.cur && e.dt[i] == dt[i];
+    for (int i = 0; i < n && same; ++i)
+      same = e.cur_in[i] == b->sims[i]->core.cur && e.dt[i] == dt[i] && e.chk[i] == (b->sims[i]->check_every > 0);
     if (same) { hit = &e; break; }
   }
   if (!hit) {
@@ -393,6 +516,7 @@ fc_status ns_batch_info(ns_batch_t b, int* members, int* graph_nodes, int* graph
 
 fc_status ns_diagnostics(ns_sim_t s, double* div_ms, double* wall_u_ms, double* wall_w_ms, double* flow_rate,
                          double* nusselt, fc_stream_t stream) {
+  if (fc_status inj = injected("ns_diagnostics")) return inj;
   fc_status st = check_sim(s, "ns_diagnostics");
   if (st) return st;
   double acc[6];

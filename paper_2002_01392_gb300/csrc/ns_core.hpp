@@ -19,18 +19,25 @@
 
 namespace fcns {
 
+#ifndef FC_LAYOUT_GUARD
+#define FC_LAYOUT_GUARD 0
+#endif
+
 struct NsLayout {
   int Nx, Ny, Nz, Np, Kx, Kxp, nf, L, L1, L2, Lx1, Lx2, Ly1, Ly2;
   bool zdirect;   // L = N' (plain length-N' z transforms)
   long long lines, ntiles, plines;   // lines, tiles of TL lines, padded lines
   size_t es;  // bytes per real
   // byte offsets inside the workspace
-  size_t X[3], DZ, DZZ, V, DY, NL, gradp, diag;
+  size_t X[3], DZ, DZZ, V, DY, NL, gradp, diag, nfin;
   size_t X64[3], d2r, hfr;   // float64 mean-line shadows and real-space z kernels
   int nmean;
   size_t kxo, kyo, kzo, kx, ky, fx, fy, Mr, Mr2, twz, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy;
   size_t tkxo, tkyo, tkzo, tkx, tky, tfx, tfy;   // copies in the simulation's precision
   size_t total;
+#if FC_LAYOUT_GUARD
+  std::vector<std::pair<size_t, size_t>> guards;  // [begin, end) byte ranges between arrays
+#endif
 };
 
 // z transform for continued length Np: Np itself when it is a compiled direct
@@ -76,7 +83,16 @@ inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
   if (p.prec == FC_F64 && (l.L > 576 || p.Nx > 512)) return FC_ERR_UNSUPPORTED;
   const size_t cs = 2 * l.es;
   size_t off = 0;
-  auto take = [&](size_t bytes) { size_t o2 = off; off += (bytes + 255) / 256 * 256; return o2; };
+  // arrays start on 256-byte boundaries; a checking build (FC_LAYOUT_GUARD
+  // bytes > 0) leaves a guard band after every array and records it
+  auto take = [&](size_t bytes) {
+    size_t o2 = off;
+    off += (bytes + 255) / 256 * 256 + FC_LAYOUT_GUARD;
+#if FC_LAYOUT_GUARD
+    l.guards.push_back({o2 + bytes, off});
+#endif
+    return o2;
+  };
   for (int i = 0; i < 3; ++i) l.X[i] = take(cs * l.nf * l.Np * l.plines);
   l.DZ = take(cs * l.nf * l.Nz * l.plines);
   l.DZZ = take(cs * l.nf * l.Nz * l.plines);
@@ -85,6 +101,7 @@ inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
   l.NL = take(cs * l.nf * l.Nz * l.plines);
   l.gradp = take(sizeof(double) * 2 * 4 * l.lines);
   l.diag = take(sizeof(double) * 8);
+  l.nfin = take(sizeof(unsigned long long));
   l.nmean = l.nf == 4 ? 3 : 2;
   for (int i = 0; i < 3; ++i) l.X64[i] = take(16 * (size_t)l.nmean * l.Np);
   l.d2r = take(8 * (size_t)(l.Np + p.Nz - 1));
@@ -198,6 +215,7 @@ struct NsCore {
     if (!s) s = put(l.hfr, hfr.data(), 8 * hfr.size());
     if (!s) s = bk.memset(ws + l.X64[0], 0, 3 * 16 * (size_t)l.nmean * l.Np, nullptr);
     if (!s) s = bk.memset(ws + l.gradp, 0, sizeof(double) * 8 * l.lines, nullptr);
+    if (!s) s = bk.memset(ws + l.nfin, 0, sizeof(unsigned long long), nullptr);
     if (!s) s = bk.memset(ws + l.X[0], 0, l.NL - l.X[0] + 2 * l.es * l.nf * l.Nz * l.plines, nullptr);
     if (!s) s = bk.sync(nullptr);
     return s;
@@ -577,6 +595,23 @@ struct NsCore {
     return s;
   }
   fc_status profiles_any(double* out, void* st) { return f32() ? profiles<float>(out, st) : profiles<double>(out, st); }
+
+  // non-finite values of the current state, added to the device counter at
+  // l.nfin (asynchronous; reset = true zeroes the counter first)
+  template <class T>
+  fc_status count_nonfinite(bool reset, void* st) {
+    fc_status s = reset ? bk.memset(ws + l.nfin, 0, sizeof(unsigned long long), st) : FC_OK;
+    if (!s) {
+      using K = KFinite<T>;
+      typename K::Args a;
+      a.g = zgeom(l.nf); a.X = Xb<T>(cur); a.count = at<unsigned long long>(l.nfin);
+      s = bk.template run<K>(a, l.ntiles, st);
+    }
+    return s;
+  }
+  fc_status count_nonfinite_any(bool reset, void* st) {
+    return f32() ? count_nonfinite<float>(reset, st) : count_nonfinite<double>(reset, st);
+  }
 
   // Autotuner of the lines per CTA: each kernel kind of the RK step is timed
   // with both compiled tile sizes on this simulation's buffers (two timed

@@ -16,6 +16,8 @@
 //   rows   [nf][Nz][Ny][Kx]  complex   same memory seen as x-rows
 //   walls  [2][2][lines]     complex double  tangential grad p at z = 0, Lz
 #pragma once
+#include <cmath>
+
 #include "engine.cuh"
 
 namespace fcns {
@@ -1416,6 +1418,94 @@ struct KMeanInit {
     const C* x = a.X + lay(a.fmap[e], 0, 0, a.g.Np, a.g.ntiles);
     for (int z = tid; z < a.g.Np; z += THREADS)
       a.X64[(long long)e * a.g.Np + z] = make_double2((double)x[z * TL].x, (double)x[z * TL].y);
+  }
+};
+
+// ===========================================================================
+// Non-finite counts (an Inf or NaN in either part of a value counts once per
+// real).  KFinite reads the physical lines (kx < Kx) of a state, every field
+// and every continued row, one tile of TL lines per CTA; KCount reads a flat
+// array of n reals, `per` of them per CTA.  Both add their count to *count.
+// ===========================================================================
+template <class T>
+FC_HD int nonfinite(T v) {
+#if defined(__CUDA_ARCH__)
+  return isfinite(v) ? 0 : 1;
+#else
+  return std::isfinite(v) ? 0 : 1;
+#endif
+}
+
+FC_HD void count_add(unsigned long long* count, unsigned long long n) {
+#if defined(__CUDA_ARCH__)
+  atomicAdd(count, n);
+#else
+  *count += n;
+#endif
+}
+
+template <class T>
+struct KFinite {
+  using C = cx<T>;
+  static constexpr int THREADS = 256, NPHASE = 2, MINB = 1;
+  struct Args {
+    ZGeom g;
+    const C* X;                  // [nf][N'][lines] tiled
+    unsigned long long* count;
+  };
+  struct Regs { unsigned n; };
+  static constexpr size_t smem_bytes = sizeof(unsigned) * THREADS;
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
+    unsigned* red = reinterpret_cast<unsigned*>(sm);
+    if constexpr (P == 0) {
+      R.n = 0;
+      const int li = tid % TL, zr = tid / TL;
+      const long long line = bid * TL + li;
+      if (line < a.g.lines && (int)(line % a.g.Kxp) < a.g.Kx)
+        for (int f = 0; f < a.g.nf; ++f) {
+          const C* x = a.X + lay(f, 0, line, a.g.Np, a.g.ntiles);
+          for (int z = zr; z < a.g.Np; z += THREADS / TL) {
+            const C v = x[z * TL];
+            R.n += nonfinite(v.x) + nonfinite(v.y);
+          }
+        }
+      red[tid] = R.n;
+    } else {
+      if (tid == 0) {
+        unsigned long long s = 0;
+        for (int t = 0; t < THREADS; ++t) s += red[t];
+        if (s) count_add(a.count, s);
+      }
+    }
+  }
+};
+
+template <class T>
+struct KCount {
+  static constexpr int THREADS = 256, NPHASE = 2, MINB = 1;
+  struct Args {
+    const T* x;
+    long long n, per;
+    unsigned long long* count;
+  };
+  struct Regs { unsigned n; };
+  static constexpr size_t smem_bytes = sizeof(unsigned) * THREADS;
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
+    unsigned* red = reinterpret_cast<unsigned*>(sm);
+    if constexpr (P == 0) {
+      R.n = 0;
+      const long long b0 = bid * a.per, b1 = b0 + a.per < a.n ? b0 + a.per : a.n;
+      for (long long i = b0 + tid; i < b1; i += THREADS) R.n += nonfinite(a.x[i]);
+      red[tid] = R.n;
+    } else {
+      if (tid == 0) {
+        unsigned long long s = 0;
+        for (int t = 0; t < THREADS; ++t) s += red[t];
+        if (s) count_add(a.count, s);
+      }
+    }
   }
 };
 

@@ -5,6 +5,7 @@
 // index arithmetic be verified against the oracle without a GPU.
 #pragma once
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <type_traits>
 #include <vector>
 #include "fft_reg.cuh"
@@ -77,25 +78,37 @@ __global__ void __launch_bounds__(K::THREADS, K::MINB) phased_kernel(const typen
 #endif
 
 // CPU execution of the same phases (host-check builds only).
+// Race and initialisation checks of the emulation: threads of a phase run in
+// ascending (order 0) or descending (order 1) thread index, and with poison
+// set, shared memory is filled with 0xFF bytes (NaN as float and double) at
+// the start of every block.  A kernel whose threads exchange shared-memory
+// data without a barrier in between, or read shared memory that their block
+// has not written, gives different results under the two settings.
+inline int& emu_order() { static int v = 0; return v; }
+inline int& emu_poison() { static int v = 0; return v; }
+
 template <class K>
 void phased_emulate(const typename K::Args& a, long long grid, size_t smem_bytes) {
-  std::vector<unsigned char> smem(smem_bytes + 16);
+  std::vector<unsigned char> smem(smem_bytes > 16 ? smem_bytes : 16);
   std::vector<typename K::Regs> regs(K::THREADS);
   using LS = LoopSpec<K>;
+  const bool rev = emu_order() != 0;
+  auto th = [&](int t) { return rev ? K::THREADS - 1 - t : t; };
   for (long long b = 0; b < grid; ++b) {
+    if (emu_poison()) std::fill(smem.begin(), smem.end(), (unsigned char)0xFF);
     SFor<0, LS::LB>::run([&](auto pc) {
       constexpr int p = decltype(pc)::value;
-      for (int t = 0; t < K::THREADS; ++t) call_phase<K, p>(a, smem.data(), t, b, 0, regs[t]);
+      for (int t = 0; t < K::THREADS; ++t) call_phase<K, p>(a, smem.data(), th(t), b, 0, regs[th(t)]);
     });
     if constexpr (LS::on) {
       for (int it = 0; it < LS::NIT; ++it)
         SFor<LS::LB, LS::LE>::run([&](auto pc) {
           constexpr int p = decltype(pc)::value;
-          for (int t = 0; t < K::THREADS; ++t) call_phase<K, p>(a, smem.data(), t, b, it, regs[t]);
+          for (int t = 0; t < K::THREADS; ++t) call_phase<K, p>(a, smem.data(), th(t), b, it, regs[th(t)]);
         });
       SFor<LS::LE, K::NPHASE>::run([&](auto pc) {
         constexpr int p = decltype(pc)::value;
-        for (int t = 0; t < K::THREADS; ++t) call_phase<K, p>(a, smem.data(), t, b, 0, regs[t]);
+        for (int t = 0; t < K::THREADS; ++t) call_phase<K, p>(a, smem.data(), th(t), b, 0, regs[th(t)]);
       });
     }
   }

@@ -9,6 +9,16 @@ in flight (requests of one simulation keep their arrival order; different
 simulations overlap on the device).  Completion is observed with CUDA events,
 so latencies are arrival-to-completion on the host clock.
 
+Errors: a request whose call fails with FC_ERR_CUDA, FC_ERR_NOMEM or
+FC_ERR_TIMEOUT is requeued at the head of the queue, up to ``max_retries``
+times (a failing call enqueues nothing that changes the simulation's state:
+an RK step only replaces the state when all its stages were enqueued).  Other
+errors complete the request with ``error`` set.  With ``check_every`` > 0 the
+resident simulations check their state for non-finite values after every
+``check_every``-th step (``ns_set_finite_check``); a simulation whose check
+failed is quarantined: its later requests complete at once with
+``error = "FC_ERR_NONFINITE"``.
+
 This module only orchestrates calls of the C ABI (through ``api``); every
 step of the work runs in the library's kernels.
 """
@@ -31,13 +41,23 @@ class Request:
     out: object = None        # filled for rhs / project
     t_start: float = -1.0
     t_done: float = -1.0
+    attempts: int = 0         # retries taken
+    error: str | None = None  # status name when the request failed
+
+
+RETRYABLE = ("FC_ERR_CUDA", "FC_ERR_NOMEM", "FC_ERR_TIMEOUT")
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes: int, slots: int = 8):
+    def __init__(self, hbm_budget_bytes: int, slots: int = 8, max_retries: int = 2, check_every: int = 0):
         import torch
         self.torch = torch
         self.budget = int(hbm_budget_bytes)
+        self.max_retries = int(max_retries)
+        self.check_every = int(check_every)
+        self.retried = 0
+        self.failed = 0
+        self.quarantined: set[int] = set()
         self.used = 0
         self.sims: dict[int, api.Sim] = {}
         self.points: dict[int, int] = {}
@@ -61,6 +81,8 @@ class Server:
         self.points[sid] = params.Nx * params.Ny * params.Nz
         if fields is not None:
             sim.set_fields(fields)
+        if self.check_every > 0:
+            sim.set_finite_check(self.check_every)
         return sid
 
     def release(self, sid: int):
@@ -70,25 +92,39 @@ class Server:
 
     # -- execution -------------------------------------------------------
     def _launch(self, r: Request, slot: int, t0: float):
+        """Enqueue r on stream ``slot``; returns the library error of the call
+        (nothing is marked busy then) or None."""
         torch = self.torch
         s = self.streams[slot]
         sim = self.sims[r.sim]
         h = torch.cuda.current_stream()
         s.wait_stream(h)                    # inputs written on the caller's stream
-        with torch.cuda.stream(s):
-            if r.kind == "step":
-                sim.step(r.dt, stream=s)
-            elif r.kind == "project":
-                r.out = sim.project(r.inp, r.dt, stream=s)
-            elif r.kind == "rhs":
-                r.out = sim.rhs(r.inp, stream=s)
-            else:
-                raise ValueError(r.kind)
-            ev = torch.cuda.Event()
-            ev.record(s)
+        try:
+            with torch.cuda.stream(s):
+                if r.kind == "step":
+                    sim.step(r.dt, stream=s)
+                elif r.kind == "project":
+                    r.out = sim.project(r.inp, r.dt, stream=s)
+                elif r.kind == "rhs":
+                    r.out = sim.rhs(r.inp, stream=s)
+                else:
+                    raise ValueError(r.kind)
+                ev = torch.cuda.Event()
+                ev.record(s)
+        except api.FcError as e:
+            return e
         r.t_start = time.perf_counter() - t0
         self.busy[slot] = (r, ev)
         self.inflight_sims.add(r.sim)
+        return None
+
+    def _fail(self, r: Request, name: str, t0: float, done: list):
+        r.error = name
+        r.t_done = time.perf_counter() - t0
+        self.failed += 1
+        if name == "FC_ERR_NONFINITE":
+            self.quarantined.add(r.sim)
+        done.append(r)
 
     def _reap(self, t0: float, done: list):
         for k, b in enumerate(self.busy):
@@ -123,18 +159,31 @@ class Server:
                     blocked.add(r.sim)
                     pending.append(r)
                     continue
+                if r.sim in self.quarantined:
+                    self._fail(r, "FC_ERR_NONFINITE", t0, done)
+                    continue
                 free = next((k for k, b in enumerate(self.busy) if b is None), None)
                 if free is None:
                     pending.appendleft(r)
                     break
-                self._launch(r, free, t0)
+                err = self._launch(r, free, t0)
+                if err is None:
+                    continue
+                if err.name in RETRYABLE and r.attempts < self.max_retries:
+                    r.attempts += 1
+                    self.retried += 1
+                    pending.appendleft(r)
+                else:
+                    self._fail(r, err.name, t0, done)
         wall = time.perf_counter() - t0
-        lat = sorted(r.t_done - r.arrival for r in done)
-        pts = sum(self.points[r.sim] * (3 if r.kind == "step" else 1) for r in done)
+        ok = [r for r in done if r.error is None]
+        lat = sorted(r.t_done - r.arrival for r in ok) or [0.0]
+        pts = sum(self.points[r.sim] * (3 if r.kind == "step" else 1) for r in ok)
         pick = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))]
         return {"requests": len(done), "wall_s": wall, "p50_latency_ms": pick(0.5) * 1e3,
                 "p99_latency_ms": pick(0.99) * 1e3, "grid_points_per_s": pts / wall,
-                "requests_per_s": len(done) / wall, "rejected_admissions": self.rejected,
+                "requests_per_s": len(ok) / wall, "rejected_admissions": self.rejected,
+                "failed": self.failed, "retried": self.retried, "quarantined": len(self.quarantined),
                 "resident": len(self.sims), "hbm_used_GB": self.used / 1e9}
 
     def close(self):

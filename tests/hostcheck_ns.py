@@ -19,7 +19,7 @@ class HostSim:
         self.lib.fchc_ns_create.argtypes = [ctypes.c_void_p]
         for n in ("fchc_ns_set_fields", "fchc_ns_get_fields", "fchc_ns_rhs", "fchc_ns_step", "fchc_ns_project",
                   "fchc_ns_destroy", "fchc_ns_get_state", "fchc_ns_diag_raw", "fchc_ns_interpolate",
-                  "fchc_ns_profiles_raw", "fchc_ns_set_tiles"):
+                  "fchc_ns_profiles_raw", "fchc_ns_set_tiles", "fchc_ns_put_state", "fchc_ns_count_nonfinite"):
             getattr(self.lib, n).argtypes = None
         self.p = ns_params(**kw)
         self.h = self.lib.fchc_ns_create(ctypes.addressof(self.p))
@@ -65,6 +65,22 @@ class HostSim:
 
     def interpolate_from(self, src):
         return self.lib.fchc_ns_interpolate(ctypes.c_void_p(self.h), ctypes.c_void_p(src.h))
+
+    def get_state(self):
+        Kxp = (self.p.Nx // 2 + 1 + 15) // 16 * 16
+        n = self.p.nfields * (self.p.Nz + self.p.C) * self.p.Ny * Kxp
+        out = np.zeros(n, dtype=np.complex64 if self.p.prec == 0 else np.complex128)
+        assert self.lib.fchc_ns_get_state(ctypes.c_void_p(self.h), self._vp(out)) == 0
+        return out
+
+    def put_state(self, st):
+        a = np.ascontiguousarray(st)
+        assert self.lib.fchc_ns_put_state(ctypes.c_void_p(self.h), self._vp(a)) == 0
+
+    def count_nonfinite(self):
+        n = ctypes.c_longlong()
+        assert self.lib.fchc_ns_count_nonfinite(ctypes.c_void_p(self.h), ctypes.byref(n)) == 0
+        return n.value
 
     def step(self, dt):
         assert self.lib.fchc_ns_step(ctypes.c_void_p(self.h), ctypes.c_double(dt)) == 0
