@@ -103,6 +103,7 @@ struct EmuBK {
     return FC_OK;
   }
   fc_status sync(void*) { return FC_OK; }
+  int sms() { return 1; }
   fc_status d2h(void* d, const void* s, size_t b, void*) { std::memcpy(d, s, b); return FC_OK; }
   template <class F>
   fc_status time_ms(F&&, void*, float*) { return FC_ERR_UNSUPPORTED; }  // no timing on the host

@@ -35,6 +35,11 @@ struct DeviceBK {
     return cuda_status(cudaMemsetAsync(dst, v, b, (cudaStream_t)st), "cudaMemsetAsync");
   }
   fc_status sync(void*) { return cuda_status(cudaDeviceSynchronize(), "cudaDeviceSynchronize"); }
+  int sms() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    return cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : 1;
+  }
   // duration of the launches made by f on stream st (synchronous)
   template <class F>
   fc_status time_ms(F&& f, void* st, float* ms) {

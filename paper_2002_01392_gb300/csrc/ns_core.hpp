@@ -128,6 +128,7 @@ struct NsCore {
   unsigned char* ws = nullptr;
   bool own_ws = false;
   int cur = 0;  // index of the state buffer
+  int sms = 1;  // multiprocessors of the device (prefetch distances in blocks)
 
   template <class X> X* at(size_t off) const { return reinterpret_cast<X*>(ws + off); }
 
@@ -136,6 +137,7 @@ struct NsCore {
     p = prm;
     fc_status s = ns_layout(p, &l);
     if (s) return s;
+    sms = bk.sms();
     if (dev_ws) {
       if (bytes < l.total) return FC_ERR_NOMEM;
       ws = static_cast<unsigned char*>(dev_ws);
@@ -274,6 +276,7 @@ struct NsCore {
     a.tiles = (l.lines + LN - 1) / LN;
     const double dz = p.Lz / (p.Nz - 1);
     a.s1 = (T)(1.0 / dz); a.s2 = (T)(1.0 / (dz * dz));
+    a.nblocks = a.tiles * nf; a.pf = (long long)sms * K::MINB;
     return bk.template run<K>(a, a.tiles * nf, st);
   }
   template <class T>
@@ -300,6 +303,7 @@ struct NsCore {
     a.dtj = dtj; a.dif[0] = a.dif[1] = a.dif[2] = p.nu; a.dif[3] = p.kappa;
     a.inject = inject;
     a.tiles = (l.lines + LN - 1) / LN;
+    a.nblocks = a.tiles * nf; a.pf = (long long)sms * K::MINB;
     return bk.template run<K>(a, a.tiles * nf, st);
   }
   template <class T>
@@ -333,6 +337,7 @@ struct NsCore {
     a.g = zgeom(3); a.t = ztab<T>(); a.X = X; a.gradp = at<double2>(l.gradp);
     a.G0 = at<cx<T>>(l.DZ); a.G1 = at<cx<T>>(l.DZZ); a.dtj = dtj;
     a.tiles = (l.lines + LN - 1) / LN;
+    a.nblocks = a.tiles; a.pf = (long long)sms * K::MINB;
     return bk.template run<K>(a, a.tiles, st);
   }
   template <class T>

@@ -66,6 +66,24 @@ FC_HD int lay(long long f, long long z, long long line, long long Z, long long n
   return ((((int)f * (int)ntiles + (l >> 4)) * (int)Z + (int)z) << 4) + (l & (TL - 1));
 }
 
+// lines of a tile row that share one 32-byte L2 sector
+template <class C>
+constexpr int sector_lines() { return sizeof(C) >= 32 ? 1 : 32 / (int)sizeof(C); }
+
+// L2 prefetch of rows r, r + R, ... (< nrows) of `line` of field f in a tiled
+// array of Z rows per tile, issued by the first thread of each 32-byte sector
+template <class C, int JN>
+FC_HD void prefetch_line(const C* base, long long f, long long line, int Z, int nrows, long long ntiles, int r,
+                         int R, int li) {
+  if (li % sector_lines<C>() != 0) return;
+  const C* x = base + lay(f, 0, line, Z, ntiles);
+#pragma unroll
+  for (int j = 0; j < JN; ++j) {
+    const int n = r + R * j;
+    if (n < nrows) prefetch_l2(x + n * TL);
+  }
+}
+
 #if defined(__CUDACC__)
 #define FC_NOINLINE __host__ __device__ __noinline__
 #else
@@ -138,6 +156,7 @@ struct KZDeriv {
     C* DZ;
     C* DZZ;
     long long tiles;
+    long long pf, nblocks;   // prefetch into L2 the input of block bid + pf (0: off)
     T s1, s2;
   };
   struct Regs { C v[L1]; C u[L2]; };
@@ -159,6 +178,11 @@ struct KZDeriv {
         for (int j = 0; j < L1; ++j) {
           const int n = r + L2 * j;
           R.v[j] = (j < JN && valid && n < a.g.Np) ? x[n * TL] : mk<T>(0, 0);
+        }
+        if (a.pf > 0 && bid + a.pf < a.nblocks) {
+          const long long b2 = bid + a.pf, line2 = (b2 % a.tiles) * LINES + li;
+          if (line2 < a.g.lines && (line2 % a.g.Kxp) < a.g.Kx)
+            prefetch_line<C, JN>(a.X, b2 / a.tiles, line2, a.g.Np, a.g.Np, a.g.ntiles, r, L2, li);
         }
         E::template A<-1>(R.v, b0, a.t.tw, r, li);
       }
@@ -226,6 +250,7 @@ struct KZCombine {
     double dtj;
     double dif[4];
     long long tiles;
+    long long pf, nblocks;  // prefetch into L2 the input of block bid + pf (0: off)
     int inject;            // 1: wall injection (RK stage); 0: plain right-hand side
   };
   struct Regs { C v[L1]; C u[L2]; };
@@ -261,6 +286,19 @@ struct KZCombine {
           R.v[j] = val;
           if (n < d) Ev[n] = val;
           if (n >= Nz - d && n < Nz) Ev[DMAX + n - (Nz - d)] = val;
+        }
+        // the rows of Xt, Xj and DZZ read after the filter transforms: into
+        // L2 now, so that their latency overlaps the transforms; and the
+        // input of block bid + pf
+        if (valid) {
+          prefetch_line<C, JN>(a.Xj, f, line, Np, Nz, a.g.ntiles, r, L2, li);
+          prefetch_line<C, JN>(a.DZZ, f, line, Nz, Nz, a.g.ntiles, r, L2, li);
+          if (a.Xt) prefetch_line<C, JN>(a.Xt, f, line, Np, Nz, a.g.ntiles, r, L2, li);
+        }
+        if (a.pf > 0 && bid + a.pf < a.nblocks) {
+          const long long b2 = bid + a.pf, line2 = (b2 % a.tiles) * LINES + li;
+          if (line2 < a.g.lines && (line2 % a.g.Kxp) < a.g.Kx)
+            prefetch_line<C, JN>(a.NL, b2 / a.tiles, line2, Nz, Nz, a.g.ntiles, r, L2, li);
         }
       }
     } else if constexpr (P == 1) {
@@ -433,6 +471,7 @@ struct KZProject {
     double2* gradp;       // [2][2][lines] out
     double dtj;
     long long tiles;
+    long long pf, nblocks;  // prefetch into L2 the input of block bid + pf (0: off)
   };
   struct Regs { C v[L1]; C u[L2]; };
   static constexpr size_t off_M = sizeof(C) * E::BUF;
@@ -520,6 +559,18 @@ struct KZProject {
 
     if constexpr (P == 0) {
       load_mr<T>(sm + off_M, a.t, a.g.Cc * d, tid, THREADS);
+      // w (read by the second transform) into L2 now, and u, v of block
+      // bid + pf
+      if (r < L2) {
+        if (valid) prefetch_line<C, JN>(a.X, 2, line, Np, Np, a.g.ntiles, r, L2, li);
+        if (a.pf > 0 && bid + a.pf < a.nblocks) {
+          const long long line2 = (bid + a.pf) * LINES + li;
+          if (line2 < a.g.lines && (line2 % a.g.Kxp) < a.g.Kx) {
+            prefetch_line<C, JN>(a.X, 0, line2, Np, Np, a.g.ntiles, r, L2, li);
+            prefetch_line<C, JN>(a.X, 1, line2, Np, Np, a.g.ntiles, r, L2, li);
+          }
+        }
+      }
     } else if constexpr (P == 1) {  // input of transform `it`
       if (r < L2) {
         if (it == 0) {  // Y = kx u + ky v
