@@ -404,6 +404,10 @@ def bench_ensemble(api, torch, steps=5, warmup=3, n=64):
         batch.step(dt)
     t = timed(lambda: batch.step(dt), steps)
     info = batch.info()
+    # the variants the autotuner kept, per grid (cached per size: tune(1) only reads them back)
+    variants = {}
+    for sp, sim in zip(specs, sims):
+        variants["%dx%dx%d" % (sp["Nx"], sp["Ny"], sp["Nz"])] = sim.tune(1)
     finite = all(bool(torch.isfinite(s.get_fields()).all().item()) for s in sims)
     batch.close()
     for s in sims:
@@ -422,6 +426,7 @@ def bench_ensemble(api, torch, steps=5, warmup=3, n=64):
     res = {"instances": n, "grids": [list(g) for g in synth.ENSEMBLE_GRIDS], "points": pts,
            "p50_ms": float(np.percentile(t, 50) * 1e3), "p99_ms": float(np.percentile(t, 99) * 1e3),
            "rk_stage_grid_points_per_s": pts * 3 / float(t.mean()), "graph_nodes": info["graph_nodes"],
+           "variants_autotuned": variants,
            "graph_launches_per_step": 1, "finite": finite,
            "plain_fp64_sequential": {"p50_ms": float(np.percentile(t64, 50) * 1e3),
                                      "rk_stage_grid_points_per_s": pts * 3 / float(t64.mean())}}

@@ -311,15 +311,21 @@ fc_status ns_spectrum_shells(ns_sim_t sim, int* nshell, double* dk);
 fc_status ns_interpolate(ns_sim_t dst, ns_sim_t src, fc_stream_t stream);
 
 /*
- * ns_tune -- lines per CTA (tile) of the five kernel kinds of the RK step
- * (z derivatives, stage combine, projection, y inverse, y forward); two tile
- * sizes of each are compiled.  mode 0: the built-in defaults; 1: autotune --
- * time both sizes of each kernel on this simulation's buffers and keep the
- * faster (synchronous; cached per process and size; the state and the wall
- * planes are preserved); 2: set from tiles.  tiles: 5 ints (0 = default,
- * 1 = alternative), read for mode 2, written with the choice if non-NULL.
- * The choice does not change any result (every line is computed the same
- * way whatever the tile).
+ * ns_tune -- kernel variants of the five kernel kinds of the RK step (z
+ * derivatives, stage combine, projection, y inverse, y forward).  Per kind,
+ * bit 0 selects the lines per CTA (tile): two sizes of each kind are
+ * compiled.  For the three z kinds of a float32 simulation whose padded z
+ * length has a second radix schedule compiled (L = 160, 288, 320: the two
+ * factors of the two-pass length-L transform swapped, e.g. 288 = 16 x 18 or
+ * 18 x 16), bit 1 selects that schedule.  mode 0: the built-in defaults
+ * (all 0); 1: autotune -- time every variant of each kernel on this
+ * simulation's buffers and keep the fastest (synchronous; cached per process
+ * and size; the state and the wall planes are preserved); 2: set from tiles
+ * (bits a kind does not have are ignored).  tiles: 5 ints, read for mode 2,
+ * written with the choice if non-NULL.  The tile does not change any result
+ * (every line is computed the same way whatever the tile); the radix
+ * schedule changes the rounding of the float32 transforms only (the same
+ * DFTs, summed in another order).
  */
 fc_status ns_tune(ns_sim_t sim, int mode, int* tiles, fc_stream_t stream);
 
@@ -333,7 +339,8 @@ typedef struct ns_batch* ns_batch_t;
  * ns_batch_create -- group n simulations (created on the current device,
  * each at most once; any sizes, precisions and parameters) so that one RK
  * step of all of them (Sec. 4.4, as rk_step) runs as a single CUDA graph
- * launch.  Autotunes the tiles of every member first (ns_tune mode 1).  The members stay owned by the caller and must outlive the batch;
+ * launch.  Autotunes the tiles and radix schedules of every member first
+ * (ns_tune mode 1).  The members stay owned by the caller and must outlive the batch;
  * the batch copies the array of handles.  FC_ERR_ARG for NULL / repeated
  * members, FC_ERR_STATE for members of another device.
  */

@@ -351,7 +351,8 @@ class Sim:
         return dict(mean=mean, rms=rms, spectrum=spec, dk=dk.value)
 
     def tune(self, mode: int = 1, tiles=None, stream=None):
-        """ns_tune: 0 defaults, 1 autotune, 2 set ``tiles`` (5 ints); returns the choice."""
+        """ns_tune: 0 defaults, 1 autotune, 2 set ``tiles`` (5 ints: bit 0 tile,
+        bit 1 radix schedule of the z kinds); returns the choice."""
         arr = (_c_int * 5)(*(tiles or [0] * 5))
         _check(_lib.ns_tune(self.handle, int(mode), arr, _stream(stream)), "ns_tune")
         return list(arr)

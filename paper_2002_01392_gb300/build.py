@@ -23,7 +23,7 @@ NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--expt-relaxed-constexpr", "-Xc
               "-diag-suppress", "20013", "-I", os.path.join(ROOT, "include")]
 CXX_FLAGS = ["-std=gnu++17", "-O2", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
-CU_SOURCES = ["k_deriv.cu", "k_deriv_f32.cu", "k_deriv_f64.cu", "k_deriv_noalloc.cu", "ns_capi.cu", "k_nsz_float.cu", "k_nsz_double.cu", "k_nsz_float_direct.cu",
+CU_SOURCES = ["k_deriv.cu", "k_deriv_f32.cu", "k_deriv_f64.cu", "k_deriv_noalloc.cu", "ns_capi.cu", "k_nsz_float.cu", "k_nsz_double.cu", "k_nsz_float_direct.cu", "k_nsz_float_alt.cu",
               "k_nsz_double_direct.cu", "k_nsxy_float.cu", "k_nsxy_double.cu",
               "k_nsx_float.cu", "k_nsx_double.cu"]
 CPP_SOURCES = ["capi.cpp", "host_tables.cpp"]

@@ -141,7 +141,7 @@ int fchc_ns_project(void* h, double dt, const void* in, void* out, void* gp) {
 int fchc_ns_step(void* h, double dt) { return ((NsCore<EmuBK>*)h)->step_any(dt, nullptr); }
 int fchc_ns_set_tiles(void* h, const int* tiles) {
   auto* c = (NsCore<EmuBK>*)h;
-  for (int k = 0; k < NsCore<EmuBK>::TK_N; ++k) c->tile[k] = tiles[k] ? 1 : 0;
+  for (int k = 0; k < NsCore<EmuBK>::TK_N; ++k) c->tile[k] = tiles[k] & c->variant_mask(k);
   return 0;
 }
 int fchc_ns_profiles_raw(void* h, double* out) { return ((NsCore<EmuBK>*)h)->profiles_any(out, nullptr); }

@@ -373,7 +373,7 @@ fc_status ns_tune(ns_sim_t s, int mode, int* tiles, fc_stream_t stream) {
     st = c.autotune_any(stream);
   } else if (mode == 2) {
     if (!tiles) { set_error("ns_tune: NULL tiles"); return FC_ERR_ARG; }
-    for (int k = 0; k < c.TK_N; ++k) c.tile[k] = tiles[k] ? 1 : 0;
+    for (int k = 0; k < c.TK_N; ++k) c.tile[k] = tiles[k] & c.variant_mask(k);
   } else {
     set_error("ns_tune: mode must be 0, 1 or 2");
     return FC_ERR_ARG;

@@ -32,7 +32,8 @@ struct NsLayout {
   size_t X[3], DZ, DZZ, V, DY, NL, gradp, diag, nfin;
   size_t X64[3], d2r, hfr;   // float64 mean-line shadows and real-space z kernels
   int nmean;
-  size_t kxo, kyo, kzo, kx, ky, fx, fy, Mr, Mr2, twz, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy;
+  size_t kxo, kyo, kzo, kx, ky, fx, fy, Mr, Mr2, twz, twz2, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy;
+  int L1alt;      // first-pass factor of the alternative z schedule (0: none)
   size_t tkxo, tkyo, tkzo, tkx, tky, tfx, tfy;   // copies in the simulation's precision
   size_t total;
 #if FC_LAYOUT_GUARD
@@ -79,6 +80,11 @@ inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
   l.plines = l.ntiles * TL;
   l.es = p.prec == FC_F32 ? 4 : 8;
   if (!z_shape_for(l.Np, p.Nz, &l.L, &l.L1, &l.L2, &l.zdirect)) return FC_ERR_UNSUPPORTED;
+  l.L1alt = 0;
+#define FC_ZALT(LL, A, B) \
+  if (!l.zdirect && LL == l.L && p.prec == FC_F32) l.L1alt = A;
+  FC_ZSHAPES_ALT(FC_ZALT)
+#undef FC_ZALT
   if (!xy_shape_for(p.Nx, &l.Lx1, &l.Lx2) || !xy_shape_for(p.Ny, &l.Ly1, &l.Ly2)) return FC_ERR_UNSUPPORTED;
   if (p.prec == FC_F64 && (l.L > 576 || p.Nx > 512)) return FC_ERR_UNSUPPORTED;
   const size_t cs = 2 * l.es;
@@ -111,7 +117,7 @@ inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
   l.tkxo = take(l.es * l.Kx); l.tkyo = take(l.es * p.Ny); l.tkzo = take(l.es * l.Np);
   l.tkx = take(l.es * l.Kx); l.tky = take(l.es * p.Ny); l.tfx = take(l.es * l.Kx); l.tfy = take(l.es * p.Ny);
   l.Mr = take(8 * p.C * p.d); l.Mr2 = take(8 * p.C * p.d);
-  l.twz = take(cs * 2 * l.L); l.H1 = take(cs * l.L); l.H2 = take(cs * l.L); l.Hf = take(cs * l.L);
+  l.twz = take(cs * 2 * l.L); l.twz2 = take(cs * 2 * l.L); l.H1 = take(cs * l.L); l.H2 = take(cs * l.L); l.Hf = take(cs * l.L);
   l.chirp = take(cs * l.Np); l.Hbf = take(cs * l.L); l.Hbi = take(cs * l.L);
   l.twx = take(cs * 2 * p.Nx); l.twy = take(cs * 2 * p.Ny);
   l.total = off;
@@ -168,8 +174,10 @@ struct NsCore {
       const int is = (i <= (l.Np - 1) / 2) ? i : i - l.Np;
       kzo[i] = (l.Np % 2 == 0 && i == l.Np / 2) ? 0.0 : twopi * is / (l.Np * dz);
     }
-    std::vector<std::complex<double>> twz, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy;
+    std::vector<std::complex<double>> twz, twz2, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy;
     engine_twiddles(l.L1, l.L2, &twz);
+    if (l.L1alt) engine_twiddles(l.L1alt, l.L / l.L1alt, &twz2);
+    else twz2 = twz;
     deriv_conv_spectra(p.Nz, l.Np, l.L, &H1, &H2);
     filter_conv_spectrum(p.Nz, l.Np, l.L, p.filter_beta, p.filter_2p, &Hf);
     if (l.zdirect) {  // no Bluestein DFTs
@@ -205,6 +213,7 @@ struct NsCore {
     if (!s) s = put(l.Mr, T.Mr.data(), 8 * T.Mr.size());
     if (!s) s = put(l.Mr2, mr2.data(), 8 * mr2.size());
     if (!s) s = putc(l.twz, twz);
+    if (!s) s = putc(l.twz2, twz2);
     if (!s) s = putc(l.H1, H1);
     if (!s) s = putc(l.H2, H2);
     if (!s) s = putc(l.Hf, Hf);
@@ -262,16 +271,23 @@ struct NsCore {
   }
 
   // ------------------------------------------------------------ launchers
-  // Tile choice per kernel kind (lines per CTA): 0 = the built-in default of
-  // shapes.hpp, 1 = its alternative tile_alt (both compiled); see ns_tune.
+  // Variant per kernel kind, see ns_tune: bit 0 = lines per CTA (0: the
+  // built-in default of shapes.hpp, 1: its alternative tile_alt); bit 1 (z
+  // kinds, float32 padded lengths of FC_ZSHAPES_ALT) = the alternative radix
+  // schedule L1 <-> L2.  Every combination is compiled.
   enum { TK_ZD, TK_ZC, TK_ZP, TK_YI, TK_Y1, TK_N };
   int tile[TK_N] = {0, 0, 0, 0, 0};
+  // the variant bits that exist for kind k on this simulation
+  int variant_mask(int k) const { return (k <= TK_ZP && l.L1alt) ? 3 : 1; }
+  // engine twiddles of the schedule whose first pass has length A
+  template <class T>
+  const cx<T>* ztw(int A) const { return at<cx<T>>(A == l.L1 ? l.twz : l.twz2); }
 
   template <class T, int A, int B, int LN, int JN>
   fc_status z_deriv_run(const cx<T>* X, int nf, void* st) {
     using K = KZDeriv<T, A, B, LN, JN>;
     typename K::Args a;
-    a.g = zgeom(nf); a.t = ztab<T>(); a.X = X;
+    a.g = zgeom(nf); a.t = ztab<T>(); a.t.tw = ztw<T>(A); a.X = X;
     a.DZ = at<cx<T>>(l.DZ); a.DZZ = at<cx<T>>(l.DZZ);
     a.tiles = (l.lines + LN - 1) / LN;
     const double dz = p.Lz / (p.Nz - 1);
@@ -282,10 +298,23 @@ struct NsCore {
   template <class T>
   fc_status z_deriv(const cx<T>* X, int nf, void* st) {
     fc_status s = FC_ERR_UNSUPPORTED;
+    if (tile[TK_ZD] & 2) {
+      if constexpr (sizeof(T) == 4) {
+#define FC_ZDA(LL, A, B)                                                                     \
+  if (l.L == LL) {                                                                           \
+    constexpr int LN = zderiv_lines<T, LL>();                                                \
+    return (tile[TK_ZD] & 1) ? z_deriv_run<T, A, B, tile_alt<LN>(), A / 2>(X, nf, st)        \
+                             : z_deriv_run<T, A, B, LN, A / 2>(X, nf, st);                   \
+  }
+        FC_ZSHAPES_ALT(FC_ZDA)
+#undef FC_ZDA
+      }
+      return s;
+    }
 #define FC_ZD(LL, A, B, D)                                                                   \
   if (l.L == LL) {                                                                           \
     constexpr int LN = zderiv_lines<T, LL>();                                                \
-    s = tile[TK_ZD] ? z_deriv_run<T, A, B, tile_alt<LN>(), D ? A : A / 2>(X, nf, st)         \
+    s = (tile[TK_ZD] & 1) ? z_deriv_run<T, A, B, tile_alt<LN>(), D ? A : A / 2>(X, nf, st) \
                     : z_deriv_run<T, A, B, LN, D ? A : A / 2>(X, nf, st);                    \
   }
     FC_ZSHAPES(FC_ZD)
@@ -298,7 +327,7 @@ struct NsCore {
                           int nf, void* st) {
     using K = KZCombine<T, A, B, LN, JN>;
     typename K::Args a;
-    a.g = zgeom(nf); a.t = ztab<T>(); a.NL = NL; a.Xt = Xt; a.Xj = Xj;
+    a.g = zgeom(nf); a.t = ztab<T>(); a.t.tw = ztw<T>(A); a.NL = NL; a.Xt = Xt; a.Xj = Xj;
     a.DZZ = at<cx<T>>(l.DZZ); a.Xout = Xo; a.gradp = at<double2>(l.gradp);
     a.dtj = dtj; a.dif[0] = a.dif[1] = a.dif[2] = p.nu; a.dif[3] = p.kappa;
     a.inject = inject;
@@ -310,10 +339,23 @@ struct NsCore {
   fc_status z_combine(const cx<T>* NL, const cx<T>* Xt, const cx<T>* Xj, cx<T>* Xo, double dtj, int inject,
                       int nf, void* st) {
     fc_status s = FC_ERR_UNSUPPORTED;
+    if (tile[TK_ZC] & 2) {
+      if constexpr (sizeof(T) == 4) {
+#define FC_ZCA(LL, A, B)                                                                                      \
+  if (l.L == LL) {                                                                                            \
+    constexpr int LN = z_lines<T, LL>();                                                                      \
+    return (tile[TK_ZC] & 1) ? z_combine_run<T, A, B, tile_alt<LN>(), A / 2>(NL, Xt, Xj, Xo, dtj, inject, nf, st) \
+                             : z_combine_run<T, A, B, LN, A / 2>(NL, Xt, Xj, Xo, dtj, inject, nf, st);    \
+  }
+        FC_ZSHAPES_ALT(FC_ZCA)
+#undef FC_ZCA
+      }
+      return s;
+    }
 #define FC_ZC(LL, A, B, D)                                                                             \
   if (l.L == LL) {                                                                                     \
     constexpr int LN = z_lines<T, LL>();                                                               \
-    s = tile[TK_ZC] ? z_combine_run<T, A, B, tile_alt<LN>(), D ? A : A / 2>(NL, Xt, Xj, Xo, dtj, inject, nf, st) \
+    s = (tile[TK_ZC] & 1) ? z_combine_run<T, A, B, tile_alt<LN>(), D ? A : A / 2>(NL, Xt, Xj, Xo, dtj, inject, nf, st) \
                     : z_combine_run<T, A, B, LN, D ? A : A / 2>(NL, Xt, Xj, Xo, dtj, inject, nf, st);  \
   }
     FC_ZSHAPES(FC_ZC)
@@ -334,7 +376,7 @@ struct NsCore {
   fc_status z_project_run(cx<T>* X, double dtj, void* st) {
     using K = KZProject<T, A, B, LN, D>;
     typename K::Args a;
-    a.g = zgeom(3); a.t = ztab<T>(); a.X = X; a.gradp = at<double2>(l.gradp);
+    a.g = zgeom(3); a.t = ztab<T>(); a.t.tw = ztw<T>(A); a.X = X; a.gradp = at<double2>(l.gradp);
     a.G0 = at<cx<T>>(l.DZ); a.G1 = at<cx<T>>(l.DZZ); a.dtj = dtj;
     a.tiles = (l.lines + LN - 1) / LN;
     a.nblocks = a.tiles; a.pf = (long long)sms * K::MINB;
@@ -343,10 +385,23 @@ struct NsCore {
   template <class T>
   fc_status z_project(cx<T>* X, double dtj, void* st) {
     fc_status s = FC_ERR_UNSUPPORTED;
+    if (tile[TK_ZP] & 2) {
+      if constexpr (sizeof(T) == 4) {
+#define FC_ZPA(LL, A, B)                                                                 \
+  if (l.L == LL) {                                                                       \
+    constexpr int LN = zproj_lines<T, LL>();                                             \
+    return (tile[TK_ZP] & 1) ? z_project_run<T, A, B, tile_alt<LN>(), false>(X, dtj, st) \
+                             : z_project_run<T, A, B, LN, false>(X, dtj, st);            \
+  }
+        FC_ZSHAPES_ALT(FC_ZPA)
+#undef FC_ZPA
+      }
+      return s;
+    }
 #define FC_ZP(LL, A, B, D)                                                               \
   if (l.L == LL) {                                                                       \
     constexpr int LN = zproj_lines<T, LL>();                                             \
-    s = tile[TK_ZP] ? z_project_run<T, A, B, tile_alt<LN>(), D>(X, dtj, st)              \
+    s = (tile[TK_ZP] & 1) ? z_project_run<T, A, B, tile_alt<LN>(), D>(X, dtj, st)        \
                     : z_project_run<T, A, B, LN, D>(X, dtj, st);                         \
   }
     FC_ZSHAPES(FC_ZP)
@@ -652,8 +707,9 @@ struct NsCore {
     };
     std::array<int, TK_N> pick{};
     for (int k = 0; k < TK_N && !s; ++k) {
-      float best[2] = {3e38f, 3e38f};
-      for (int c = 0; c < 2 && !s; ++c) {
+      float best[4] = {3e38f, 3e38f, 3e38f, 3e38f};
+      const int nv = variant_mask(k) + 1;
+      for (int c = 0; c < nv && !s; ++c) {
         tile[k] = c;
         fc_status w = launch(k);  // warm-up
         if (w == FC_ERR_UNSUPPORTED) continue;  // this tile does not fit the shared memory
@@ -664,7 +720,9 @@ struct NsCore {
           if (!s && ms < best[c]) best[c] = ms;
         }
       }
-      pick[k] = best[1] < best[0] ? 1 : 0;
+      pick[k] = 0;
+      for (int c = 1; c < nv; ++c)
+        if (best[c] < best[pick[k]]) pick[k] = c;
       tile[k] = pick[k];
     }
     if (!s) s = bk.h2d(ws + l.gradp, gp.data(), sizeof(double) * gp.size());

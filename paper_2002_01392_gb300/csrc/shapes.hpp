@@ -22,6 +22,16 @@
 #endif
 #define FC_ZSHAPES(M) FC_ZSHAPES_DIRECT(M) FC_ZSHAPES_PADDED(M)
 
+// Alternative radix schedules of padded z lengths (float32 kernels only): the
+// same length with the first-pass and second-pass factors swapped, M(L, L1,
+// L2).  The autotuner of ns_tune times both schedules (and both tiles) of the
+// z kernels; the default is the FC_ZSHAPES_PADDED one.
+#ifdef FC_HOSTCHECK
+#define FC_ZSHAPES_ALT(M) M(160, 16, 10) M(288, 18, 16)
+#else
+#define FC_ZSHAPES_ALT(M) M(160, 16, 10) M(288, 18, 16) M(320, 20, 16)
+#endif
+
 namespace fcns {
 // lines per CTA of the z kernels and of the y kernels.  float: 8 lines (64
 // contiguous bytes of every z / ky row per CTA); measured on the 1024^2 x 513

@@ -35,7 +35,9 @@ def test_batch_equals_members_alone(api):
     alone = [_make(api, s, "f32")[0] for s in specs]
     batched = [_make(api, s, "f32")[0] for s in specs]
     dts = [2e-4 * (1 + i % 3) for i in range(len(specs))]
-    b = api.Batch(batched)
+    b = api.Batch(batched)      # autotunes every member (tiles and radix schedules)
+    for a_ in alone:            # the same choices (cached per size) for the members run alone
+        a_.tune(1)
     for _ in range(4):
         for sim, dt in zip(alone, dts):
             sim.step(dt)

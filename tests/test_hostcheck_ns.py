@@ -253,6 +253,31 @@ def test_alternative_tiles_match_oracle(Nz):
     hs.close()
 
 
+@pytest.mark.parametrize("Nz,N", [(33, 32), (65, 16)])
+@pytest.mark.parametrize("tiles", [[2, 2, 2, 0, 0], [3, 3, 3, 1, 1]])
+def test_alternative_radix_schedules_match_oracle(Nz, N, tiles):
+    """float32 z kernels with the second radix schedule of their padded length
+    (160 = 16 x 10, 288 = 18 x 16), with both tiles, against the oracle; the
+    first-pass length and the engine twiddles change, the result only by
+    float32 rounding."""
+    kw = dict(nfields=4, nu=3e-3, kappa=3e-3, gamma=1.0)
+    hs = HostSim(Nx=N, Ny=N, Nz=Nz, prec="f32", **kw)
+    hs.set_tiles(tiles)
+    P = ns.Params(N, N, Nz, **kw)
+    v = synth.boussinesq_fields(N, N, Nz, amp=1e-1)
+    hs.set_fields(v)
+    st = ns.to_spectral(v, P)
+    gp = np.zeros((2, 2, N, P.Kx), complex)
+    for _ in range(2):
+        hs.step(1e-3)
+        st, gp = ns.rk_step(st, gp, P, 1e-3)
+    ref = np.stack([ns.to_physical(c, P) for c in st])
+    out = hs.get_fields()
+    for f in range(4):
+        assert _rel(out[f], ref[f]) < 5e-5, f
+    hs.close()
+
+
 def test_general_parameters_match_oracle():
     """Everything away from the defaults at once: exponential filter in x, y
     and z (mode 0), a 4 x 3 x 2 box with Nx != Ny, kappa != nu, gamma = 2.5,
