@@ -7,11 +7,11 @@
 namespace fcns {
 #define FC_INST_Y(NN, A, B)                                                             \
   template struct DevRun<KYInv3<double, A, B, y_lines<double, NN>()>>;                         \
-  template struct DevRun<KYInv3<double, A, B, tile_alt<y_lines<double, NN>()>()>>;             \
+  template struct DevRun<std::conditional_t<y_wide<double, NN>(), KYInv3S<double, A, B, 16>, KYInv3<double, A, B, y_lines_alt<double, NN>()>>>;             \
   template struct DevRun<KY1<double, A, B, y_lines<double, NN>(), -1>>;                        \
-  template struct DevRun<KY1<double, A, B, tile_alt<y_lines<double, NN>()>(), -1>>;            \
+  template struct DevRun<KY1<double, A, B, y_lines_alt<double, NN>(), -1>>;            \
   template struct DevRun<KY1<double, A, B, y_lines<double, NN>(), 1>>;                         \
-  template struct DevRun<KY1<double, A, B, tile_alt<y_lines<double, NN>()>(), 1>>;
+  template struct DevRun<KY1<double, A, B, y_lines_alt<double, NN>(), 1>>;
 FC_XYSHAPES(FC_INST_Y)
 #undef FC_INST_Y
 }  // namespace fcns

@@ -415,9 +415,9 @@ struct NsCore {
     return g;
   }
 
-  template <class T, int A1, int B1, int LN>
+  template <class T, int A1, int B1, int LN, bool ONEBUF = false>
   fc_status y_inv3_run(const cx<T>* A, long long a_fstride, int nf, void* st) {
-    using K = KYInv3<T, A1, B1, LN>;
+    using K = std::conditional_t<ONEBUF, KYInv3S<T, A1, B1, LN>, KYInv3<T, A1, B1, LN>>;
     typename K::Args a;
     a.g = ygeom(); a.tw = at<cx<T>>(l.twy); a.kyo = at<T>(l.tkyo);
     a.A = A; a.a_fstride = a_fstride;
@@ -432,7 +432,7 @@ struct NsCore {
 #define FC_YI(NN, A1, B1)                                                           \
   if (p.Ny == NN) {                                                                \
     constexpr int LN = y_lines<T, NN>();                                           \
-    s = tile[TK_YI] ? y_inv3_run<T, A1, B1, tile_alt<LN>()>(A, a_fstride, nf, st)  \
+    s = tile[TK_YI] ? y_inv3_run<T, A1, B1, y_lines_alt<T, NN>(), y_wide<T, NN>()>(A, a_fstride, nf, st) \
                     : y_inv3_run<T, A1, B1, LN>(A, a_fstride, nf, st);             \
   }
     FC_XYSHAPES(FC_YI)
@@ -456,7 +456,7 @@ struct NsCore {
 #define FC_Y1(NN, A1, B1)                                                                              \
   if (p.Ny == NN) {                                                                                   \
     constexpr int LN = y_lines<T, NN>();                                                              \
-    s = tile[TK_Y1] ? y_one_run<T, SIGN, A1, B1, tile_alt<LN>()>(IN, in_fs, OUT, out_fs, nf, scale, st) \
+    s = tile[TK_Y1] ? y_one_run<T, SIGN, A1, B1, y_lines_alt<T, NN>()>(IN, in_fs, OUT, out_fs, nf, scale, st) \
                     : y_one_run<T, SIGN, A1, B1, LN>(IN, in_fs, OUT, out_fs, nf, scale, st);          \
   }
     FC_XYSHAPES(FC_Y1)

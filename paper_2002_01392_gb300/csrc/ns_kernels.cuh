@@ -830,6 +830,65 @@ struct KYInv3 {
   }
 };
 
+// yinv3 with one exchange buffer (wide tiles: 16 lines = 128 contiguous bytes
+// of every ky row): the three transforms run one after another, and the dy
+// transform reads its input A again from global memory (the same CTA read it
+// one transform earlier, so it comes from L2)
+template <class T, int L1, int L2, int LINES>
+struct KYInv3S {
+  using E = Eng<T, L1, L2, LINES>;
+  using C = cx<T>;
+  static constexpr int THREADS = E::THREADS, NPHASE = 6;
+  static constexpr int MINB = 1;
+  using Args = typename KYInv3<T, L1, L2, LINES>::Args;
+  struct Regs { C v[L1]; C u[L2]; };
+  static constexpr size_t smem_bytes = sizeof(C) * E::BUF;
+
+  template <int P>
+  static FC_HD void phase(const Args& a, unsigned char* sm, int tid, long long bid, Regs& R) {
+    C* b0 = reinterpret_cast<C*>(sm);
+    const int r = tid / LINES, li = tid % LINES;
+    const long long tile = bid % a.tiles;
+    const long long pz = bid / a.tiles;          // f * Nz + z
+    const long long f = pz / a.g.Nz, z = pz % a.g.Nz;
+    const int kx = (int)(tile * LINES + li);
+    const bool valid = kx < a.g.Kx;
+    const int sb = lay(f, z, kx, a.a_fstride, a.g.ntiles), ss = a.g.Kxp * (int)a.a_fstride;
+    const int mb = lay(f, z, kx, a.g.Nz, a.g.ntiles), ms = a.g.Kxp * a.g.Nz;
+    auto mo = [&](int y) { return mb + y * ms; };
+    if constexpr (P == 0 || P == 2 || P == 4) {
+      if (r < L2) {
+#pragma unroll
+        for (int j = 0; j < L1; ++j) {
+          const int ky = r + L2 * j;
+          C x = mk<T>(0, 0);
+          if (valid) {
+            if constexpr (P == 4) {
+              x = a.DZ[mo(ky)];
+            } else {
+              x = a.A[sb + ky * ss];
+              if constexpr (P == 2) {
+                const T k = a.kyo[ky];
+                x = mk<T>(-k * x.y, k * x.x);
+              }
+            }
+          }
+          R.v[j] = x;
+        }
+        E::template A<1>(R.v, b0, a.tw, r, li);
+      }
+    } else {
+      if (r < L1) {
+        E::template B<1>(R.u, b0, r, li);
+        C* out = P == 1 ? a.V : (P == 3 ? a.DY : a.DZ);
+        if (valid)
+#pragma unroll
+          for (int k2 = 0; k2 < L2; ++k2) out[mo(r + L1 * k2)] = cscale(R.u[k2], a.scale);
+      }
+    }
+  }
+};
+
 // y1: one transform per plane, OUT = scale * FFT_y^{SIGN}(IN) (may alias)
 template <class T, int L1, int L2, int LINES, int SIGN>
 struct KY1 {

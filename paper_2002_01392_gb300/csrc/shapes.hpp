@@ -11,7 +11,7 @@
 #ifdef FC_HOSTCHECK
 #define FC_ZSHAPES_DIRECT(M) M(64, 8, 8, true)
 #define FC_ZSHAPES_PADDED(M) M(160, 10, 16, false) M(288, 16, 18, false)
-#define FC_XYSHAPES(M) M(16, 4, 4) M(32, 4, 8)
+#define FC_XYSHAPES(M) M(16, 4, 4) M(32, 4, 8) M(128, 8, 16)
 #else
 #define FC_ZSHAPES_DIRECT(M) \
   M(64, 8, 8, true) M(128, 8, 16, true) M(256, 16, 16, true) M(512, 16, 32, true) M(768, 24, 32, true) M(1024, 32, 32, true)
@@ -54,6 +54,13 @@ template <class T, int N> constexpr int y_lines() {
 // the alternative lines per CTA compiled beside each default (the autotuner
 // of ns_tune times both)
 template <int D> constexpr int tile_alt() { return D >= 8 ? D / 2 : 2 * D; }
+// the alternative tile of the y transforms: float lengths >= 128 widen to 16
+// lines (128 contiguous bytes of every ky row per CTA; the y inverse then runs
+// with one exchange buffer, KYInv3S), else tile_alt
+template <class T, int N> constexpr bool y_wide() { return sizeof(T) == 4 && N >= 128; }
+template <class T, int N> constexpr int y_lines_alt() {
+  return y_wide<T, N>() ? 16 : tile_alt<y_lines<T, N>()>();
+}
 // row-pair jobs per CTA of the x row transforms
 template <int N> constexpr int x_jobs() { return N >= 512 ? 2 : (N >= 128 ? 4 : 8); }
 }  // namespace fcns

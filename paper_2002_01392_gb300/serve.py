@@ -3,7 +3,8 @@
 Requests (ns_rhs, fc_poisson_project, rk_step) arrive at given times for
 simulations that stay resident on the device with their FC tables.  New
 simulations are admitted while their workspace (``ns_workspace_bytes``) fits
-in the HBM budget.  Each request runs on one of ``slots`` CUDA streams as soon
+in the HBM budget (and get the kernel variants the autotuner of ``ns_tune``
+picks for their size).  Each request runs on one of ``slots`` CUDA streams as soon
 as a stream is free and no earlier request for the same simulation is still
 in flight (requests of one simulation keep their arrival order; different
 simulations overlap on the device).  Completion is observed with CUDA events,
@@ -49,9 +50,11 @@ RETRYABLE = ("FC_ERR_CUDA", "FC_ERR_NOMEM", "FC_ERR_TIMEOUT")
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes: int, slots: int = 8, max_retries: int = 2, check_every: int = 0):
+    def __init__(self, hbm_budget_bytes: int, slots: int = 8, max_retries: int = 2, check_every: int = 0,
+                 tune: bool = True):
         import torch
         self.torch = torch
+        self.tune = tune
         self.budget = int(hbm_budget_bytes)
         self.max_retries = int(max_retries)
         self.check_every = int(check_every)
@@ -75,6 +78,8 @@ class Server:
             self.rejected += 1
             return None
         sim = api.Sim(params)
+        if self.tune:
+            sim.tune(1)     # kernel variants timed once per grid size (cached)
         sid = len(self.sims)
         self.sims[sid] = sim
         self.used += need

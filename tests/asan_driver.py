@@ -43,7 +43,8 @@ def main(path):
     from paper_2002_01392_gb300.api import ns_params
     cases = [dict(Nx=32, Ny=32, Nz=33, prec="f64", nu=1e-2, forcing_x=0.1),
              dict(Nx=32, Ny=16, Nz=33, nfields=4, prec="f32", nu=3e-3, kappa=2e-3, gamma=1.0),
-             dict(Nx=16, Ny=16, Nz=39, prec="f32", nu=1e-2)]
+             dict(Nx=16, Ny=16, Nz=39, prec="f32", nu=1e-2),
+             dict(Nx=16, Ny=128, Nz=33, prec="f32", nu=1e-2)]
     for kw in cases:
         p = ns_params(**kw)
         nf = p.nfields
@@ -62,7 +63,7 @@ def main(path):
         vs = np.ascontiguousarray(v[:3])
         po = np.empty_like(vs)
         assert lib.fchc_ns_project(h, ctypes.c_double(1e-3), _vp(vs), _vp(po), _vp(gp)) == 0
-        for tiles in ([0] * 5, [1] * 5):
+        for tiles in ([0] * 5, [1] * 5, [3] * 5):
             t = np.array(tiles, np.int32)
             assert lib.fchc_ns_set_tiles(h, _vp(t)) == 0
             assert lib.fchc_ns_step(h, ctypes.c_double(1e-3)) == 0

@@ -63,19 +63,25 @@ def test_deriv_kernel_race_free(hc, Mr_5_25, Nz, L, Nx, Ny, dtype):
     _both(hc, run)
 
 
-@pytest.mark.parametrize("N,Nz,nf,prec", [(32, 33, 3, "f64"), (16, 33, 4, "f32"), (16, 39, 3, "f32")])
-def test_ns_kernels_race_free(hc, N, Nz, nf, prec):
+@pytest.mark.parametrize("N,Nz,nf,prec,tiles", [(32, 33, 3, "f64", None), (16, 33, 4, "f32", None),
+                                                 (16, 39, 3, "f32", None), (16, 33, 4, "f32", [3, 3, 3, 1, 1]),
+                                                 ((16, 128), 33, 3, "f32", [0, 0, 0, 1, 1])])
+def test_ns_kernels_race_free(hc, N, Nz, nf, prec, tiles):
     """RK3 step (every z / y / x kernel of a stage, the mean line, the
     projection), the right-hand side, the projection call and get_fields; the
-    Nz = 39 case runs the direct length-64 z transforms."""
+    Nz = 39 case runs the direct length-64 z transforms; the last two the
+    alternative tiles and radix schedules, and the wide y tiles (Ny = 128)."""
+    Nx, Ny = (N, N) if isinstance(N, int) else N
     kw = dict(nu=3e-3, kappa=3e-3, gamma=1.0) if nf == 4 else dict(nu=1e-2, forcing_x=0.1)
-    v = synth.boussinesq_fields(N, N, Nz, amp=1e-1) if nf == 4 else synth.channel_velocity(N, N, Nz)
+    v = synth.boussinesq_fields(Nx, Ny, Nz, amp=1e-1) if nf == 4 else synth.channel_velocity(Nx, Ny, Nz)
     g = np.random.default_rng(5)
     vs = v[:3] + 1e-2 * g.standard_normal(v[:3].shape)
 
     def run():
-        hs = HostSim(Nx=N, Ny=N, Nz=Nz, nfields=nf, prec=prec, **kw)
+        hs = HostSim(Nx=Nx, Ny=Ny, Nz=Nz, nfields=nf, prec=prec, **kw)
         try:
+            if tiles:
+                hs.set_tiles(tiles)
             hs.set_fields(v)
             r = hs.rhs(v)
             pv, gp = hs.project(vs, 1e-3)
