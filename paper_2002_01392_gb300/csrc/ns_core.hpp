@@ -379,7 +379,6 @@ struct NsCore {
     a.g = zgeom(3); a.t = ztab<T>(); a.t.tw = ztw<T>(A); a.X = X; a.gradp = at<double2>(l.gradp);
     a.G0 = at<cx<T>>(l.DZ); a.G1 = at<cx<T>>(l.DZZ); a.dtj = dtj;
     a.tiles = (l.lines + LN - 1) / LN;
-    a.nblocks = a.tiles; a.pf = (long long)sms * K::MINB;
     return bk.template run<K>(a, a.tiles, st);
   }
   template <class T>

@@ -471,7 +471,6 @@ struct KZProject {
     double2* gradp;       // [2][2][lines] out
     double dtj;
     long long tiles;
-    long long pf, nblocks;  // prefetch into L2 the input of block bid + pf (0: off)
   };
   struct Regs { C v[L1]; C u[L2]; };
   static constexpr size_t off_M = sizeof(C) * E::BUF;
@@ -559,18 +558,7 @@ struct KZProject {
 
     if constexpr (P == 0) {
       load_mr<T>(sm + off_M, a.t, a.g.Cc * d, tid, THREADS);
-      // w (read by the second transform) into L2 now, and u, v of block
-      // bid + pf
-      if (r < L2) {
-        if (valid) prefetch_line<C, JN>(a.X, 2, line, Np, Np, a.g.ntiles, r, L2, li);
-        if (a.pf > 0 && bid + a.pf < a.nblocks) {
-          const long long line2 = (bid + a.pf) * LINES + li;
-          if (line2 < a.g.lines && (line2 % a.g.Kxp) < a.g.Kx) {
-            prefetch_line<C, JN>(a.X, 0, line2, Np, Np, a.g.ntiles, r, L2, li);
-            prefetch_line<C, JN>(a.X, 1, line2, Np, Np, a.g.ntiles, r, L2, li);
-          }
-        }
-      }
+
     } else if constexpr (P == 1) {  // input of transform `it`
       if (r < L2) {
         if (it == 0) {  // Y = kx u + ky v
