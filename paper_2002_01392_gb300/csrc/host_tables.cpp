@@ -514,6 +514,15 @@ void bluestein_tables(int Np, int L, std::vector<std::complex<double>>* chirp,
   }
 }
 
+void split_twiddles(int N, std::vector<std::complex<double>>* tw) {
+  tw->resize(N / 2 + 1);
+  for (int k = 0; k <= N / 2; ++k) {
+    q c, s;
+    q_sincos2pi(k, N, &c, &s);
+    (*tw)[k] = std::complex<double>((double)c, (double)-s);
+  }
+}
+
 void engine_twiddles(int L1, int L2, std::vector<std::complex<double>>* tw) {
   const int L = L1 * L2;
   tw->resize(2 * L);

@@ -42,6 +42,8 @@ void bluestein_tables(int Np, int L, std::vector<std::complex<double>>* chirp,
 // Twiddles exp(-2 pi i n2 k1 / L), L = L1 L2, stored twice: tw[n2 * L1 + k1]
 // and tw[L + k1 * L2 + n2], so that both thread roles read them contiguously.
 void engine_twiddles(int L1, int L2, std::vector<std::complex<double>>* tw);
+// e^{-2 pi i k / N}, k = 0 .. N/2 (computed in binary128, rounded to double)
+void split_twiddles(int N, std::vector<std::complex<double>>* tw);
 
 // cos / sin of 2 pi num / den, correctly rounded to double from binary128.
 void sincos2pi(long long num, long long den, double* c, double* s);

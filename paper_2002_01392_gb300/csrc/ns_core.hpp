@@ -32,7 +32,7 @@ struct NsLayout {
   size_t X[3], DZ, DZZ, V, DY, NL, gradp, diag, nfin;
   size_t X64[3], d2r, hfr;   // float64 mean-line shadows and real-space z kernels
   int nmean;
-  size_t kxo, kyo, kzo, kx, ky, fx, fy, Mr, Mr2, twz, twz2, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy;
+  size_t kxo, kyo, kzo, kx, ky, fx, fy, Mr, Mr2, twz, twz2, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy, twxh;
   int L1alt;      // first-pass factor of the alternative z schedule (0: none)
   size_t tkxo, tkyo, tkzo, tkx, tky, tfx, tfy;   // copies in the simulation's precision
   size_t total;
@@ -120,6 +120,7 @@ inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
   l.twz = take(cs * 2 * l.L); l.twz2 = take(cs * 2 * l.L); l.H1 = take(cs * l.L); l.H2 = take(cs * l.L); l.Hf = take(cs * l.L);
   l.chirp = take(cs * l.Np); l.Hbf = take(cs * l.L); l.Hbi = take(cs * l.L);
   l.twx = take(cs * 2 * p.Nx); l.twy = take(cs * 2 * p.Ny);
+  l.twxh = take(cs * (p.Nx + p.Nx / 2 + 1));
   l.total = off;
   // every array is indexed with 32-bit element offsets
   if ((double)l.nf * l.Np * l.plines >= 2147483647.0) return FC_ERR_UNSUPPORTED;
@@ -174,7 +175,7 @@ struct NsCore {
       const int is = (i <= (l.Np - 1) / 2) ? i : i - l.Np;
       kzo[i] = (l.Np % 2 == 0 && i == l.Np / 2) ? 0.0 : twopi * is / (l.Np * dz);
     }
-    std::vector<std::complex<double>> twz, twz2, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy;
+    std::vector<std::complex<double>> twz, twz2, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy, twxh;
     engine_twiddles(l.L1, l.L2, &twz);
     if (l.L1alt) engine_twiddles(l.L1alt, l.L / l.L1alt, &twz2);
     else twz2 = twz;
@@ -190,6 +191,12 @@ struct NsCore {
     std::vector<double> d2r, hfr;
     z_kernels_real(p.Nz, l.Np, p.filter_beta, p.filter_2p, &d2r, &hfr);
     engine_twiddles(l.Lx1, l.Lx2, &twx);
+    {  // the x pass's forward half: length-Nx/2 engine, then the even / odd split factors
+      std::vector<std::complex<double>> sp;
+      engine_twiddles(half_l1(l.Lx1, l.Lx2), half_l2(l.Lx1, l.Lx2), &twxh);
+      split_twiddles(p.Nx, &sp);
+      twxh.insert(twxh.end(), sp.begin(), sp.end());
+    }
     engine_twiddles(l.Ly1, l.Ly2, &twy);
     std::vector<float2> mr2(T.Mr.size());
     for (size_t i = 0; i < mr2.size(); ++i) {
@@ -221,6 +228,7 @@ struct NsCore {
     if (!s) s = putc(l.Hbf, Hbf);
     if (!s) s = putc(l.Hbi, Hbi);
     if (!s) s = putc(l.twx, twx);
+    if (!s) s = putc(l.twxh, twxh);
     if (!s) s = putc(l.twy, twy);
     if (!s) s = put(l.d2r, d2r.data(), 8 * d2r.size());
     if (!s) s = put(l.hfr, hfr.data(), 8 * hfr.size());
@@ -486,7 +494,7 @@ struct NsCore {
     if (K::smem_bytes > 227 * 1024) return FC_ERR_UNSUPPORTED;
     typename K::Args a;
     a.Kx = l.Kx; a.Kxp = l.Kxp; a.Ny = p.Ny; a.Nz = p.Nz; a.rows = rows; a.ntiles = l.ntiles;
-    a.tw = at<cx<T>>(l.twx); a.kxo = at<T>(l.tkxo);
+    a.tw = at<cx<T>>(l.twx); a.twh = at<cx<T>>(l.twxh); a.kxo = at<T>(l.tkxo);
     a.V = at<cx<T>>(l.V); a.DY = at<cx<T>>(l.DY); a.DZ = at<cx<T>>(l.DZ); a.NL = at<cx<T>>(l.NL);
     a.forcing = (T)p.forcing_x; a.gamma = (T)p.gamma; a.scale = (T)(1.0 / p.Nx);
     return bk.template run<K>(a, rows, st);

@@ -927,8 +927,14 @@ struct KY1 {
 // X transforms: one CTA per (y, z) row (all fields), row FFTs of length Nx in
 // shared memory; groups of G threads per transform.
 // ===========================================================================
-template <class T, int L1, int L2>
+// factors of the length-Nx/2 transform of the x pass's forward half (real
+// rows split into even / odd samples): L1 halved when even, else L2
+constexpr int half_l1(int L1, int L2) { return L1 % 2 == 0 ? L1 / 2 : L1; }
+constexpr int half_l2(int L1, int L2) { return L1 % 2 == 0 ? L2 : L2 / 2; }
+
+template <class T, int L1_, int L2_>
 struct RowEng {
+  static constexpr int L1 = L1_, L2 = L2_;
   static constexpr int L = L1 * L2;
   static constexpr int G = L1 > L2 ? L1 : L2;
   static constexpr int ROW = L2 + 1;     // padded exchange row
@@ -967,20 +973,24 @@ struct RowEng {
 template <class T, int L1, int L2, int NF>
 struct KXPass {
   using RE = RowEng<T, L1, L2>;
+  // the forward transforms: one length-Nx/2 complex transform per real row
+  using RH = RowEng<T, half_l1(L1, L2), half_l2(L1, L2)>;
   using C = cx<T>;
-  static constexpr int Nx = L1 * L2, G = RE::G, NJOB = 2 * NF, NFWD = (NF + 1) / 2;
+  static constexpr int Nx = L1 * L2, G = RE::G, NJOB = 2 * NF;
+  static_assert(RH::G <= G && RH::BUF <= RE::BUF && Nx / 2 <= RE::BUF, "half-length row engine");
   static constexpr int THREADS = NJOB * G, NPHASE = 8, MINB = 2;
   struct Args {
     int Kx, Kxp, Ny, Nz;
     long long rows;          // Nz * Ny
     long long ntiles;
     const C* tw;             // Nx engine twiddles
+    const C* twh;            // Nx/2 engine twiddles (Nx entries), then e^{-2 pi i k/Nx}, k = 0..Nx/2
     const T* kxo;            // Kx
     const C* V; const C* DY; const C* DZ;   // [NF][rows][Kx]
     C* NL;                                  // [NF][rows][Kx]
     T forcing, gamma, scale;                // scale = 1/Nx
   };
-  struct Regs { C v[L1]; C u[L2]; };
+  struct Regs { C v[L1]; C u[L2]; C vh[RH::L1]; C uh[RH::L2]; };
   // the real rows Pr alias the exchange buffers (phases separate every reuse)
   static constexpr size_t zb_bytes = sizeof(C) * RE::BUF * NJOB;
   static constexpr size_t pr_bytes = sizeof(T) * 4 * NF * Nx;
@@ -1042,36 +1052,36 @@ struct KXPass {
 #pragma unroll
         for (int f = 0; f < NF; ++f) Pr[f * Nx + n] = Nf[f];
       }
-    } else if constexpr (P == 4) {
-      if (q < NFWD && g < L2) {
+    } else if constexpr (P == 4) {  // z_f[m] = N_f[2m] + i N_f[2m+1], one group per field
+      if (q < NF && g < RH::L2) {
 #pragma unroll
-        for (int j = 0; j < L1; ++j) {
-          const int n = g + L2 * j;
-          const T re = Pr[(2 * q) * Nx + n];
-          const T im = (2 * q + 1 < NF) ? Pr[(2 * q + 1) * Nx + n] : T(0);
-          R.v[j] = mk<T>(re, im);
+        for (int j = 0; j < RH::L1; ++j) {
+          const int m = g + RH::L2 * j;
+          R.vh[j] = mk<T>(Pr[q * Nx + 2 * m], Pr[q * Nx + 2 * m + 1]);
         }
       }
     } else if constexpr (P == 5) {
-      if (q < NFWD && g < L2) RE::template A<-1>(R.v, Zb + q * RE::BUF, a.tw, g);
+      if (q < NF && g < RH::L2) RH::template A<-1>(R.vh, Zb + q * RE::BUF, a.twh, g);
     } else if constexpr (P == 6) {
-      if (q < NFWD && g < L1) {
-        RE::template B<-1>(R.u, Zb + q * RE::BUF, g);
-        C* Zn = Zb + (NFWD + q) * RE::BUF;   // natural order spectrum
+      if (q < NF && g < RH::L1) {
+        RH::template B<-1>(R.uh, Zb + q * RE::BUF, g);
+        C* Zn = Zb + (NF + q) * RE::BUF;   // natural order spectrum Z_f (length Nx/2)
 #pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) Zn[g + L1 * k2] = R.u[k2];
+        for (int k2 = 0; k2 < RH::L2; ++k2) Zn[g + RH::L1 * k2] = R.uh[k2];
       }
     } else if constexpr (P == 7) {
-      for (int i = tid; i < NFWD * (Nx / 2 + 1); i += THREADS) {
-        const int qq = i / (Nx / 2 + 1), k = i % (Nx / 2 + 1);
-        const C* Zn = Zb + (NFWD + qq) * RE::BUF;
-        const C zk = Zn[k], zm = Zn[(Nx - k) % Nx];
-        // A = (Z_k + conj Z_{N-k}) / 2,  B = (Z_k - conj Z_{N-k}) / (2i)
-        const C Av = mk<T>((zk.x + zm.x) * T(0.5), (zk.y - zm.y) * T(0.5));
-        const C Bv = mk<T>((zk.y + zm.y) * T(0.5), (zm.x - zk.x) * T(0.5));
-        const long long z = row / a.Ny, yb = (row % a.Ny) * a.Kxp;
-        a.NL[lay(2 * qq, z, yb + k, a.Nz, a.ntiles)] = Av;
-        if (2 * qq + 1 < NF) a.NL[lay(2 * qq + 1, z, yb + k, a.Nz, a.ntiles)] = Bv;
+      // half spectrum of the real row: with E = FFT(N_f[2m]) and
+      // O = FFT(N_f[2m+1]) (length Nx/2, read off Z_f by its Hermitian
+      // parts), X_k = E_k + e^{-2 pi i k/Nx} O_k, k = 0..Nx/2
+      constexpr int H = Nx / 2;
+      const long long z = row / a.Ny, yb = (row % a.Ny) * a.Kxp;
+      for (int i = tid; i < NF * (H + 1); i += THREADS) {
+        const int f = i / (H + 1), k = i % (H + 1);
+        const C* Zn = Zb + (NF + f) * RE::BUF;
+        const C zk = Zn[k % H], zm = Zn[(H - k) % H];
+        const C Ev = mk<T>((zk.x + zm.x) * T(0.5), (zk.y - zm.y) * T(0.5));
+        const C Ov = mk<T>((zk.y + zm.y) * T(0.5), (zm.x - zk.x) * T(0.5));
+        a.NL[lay(f, z, yb + k, a.Nz, a.ntiles)] = cadd(Ev, cmul(a.twh[Nx + k], Ov));
       }
     }
   }
