@@ -558,7 +558,6 @@ struct KZProject {
 
     if constexpr (P == 0) {
       load_mr<T>(sm + off_M, a.t, a.g.Cc * d, tid, THREADS);
-
     } else if constexpr (P == 1) {  // input of transform `it`
       if (r < L2) {
         if (it == 0) {  // Y = kx u + ky v
