@@ -251,6 +251,64 @@ def test_full_size_boussinesq_properties(api):
     sim.close()
 
 
+def _band_limited(Nx, Nz, kmax, seed, xp, dtype):
+    """Four fields sum_{|kx|,|ky| <= kmax} A(z) cos(kx x + ky y) + B(z) sin(...),
+    A, B seeded polynomials times z(1 - z), on an Nx x Nx grid (x = 2 pi i / Nx);
+    xp = numpy or torch (on the GPU)."""
+    g = np.random.default_rng(seed)
+    z = np.linspace(0.0, 1.0, Nz)
+    modes = [(kx, ky) for kx in range(0, kmax + 1) for ky in range(-kmax, kmax + 1) if kx > 0 or ky >= 0]
+    coef = g.uniform(-1, 1, size=(4, len(modes), 2, 3))
+    x = 2 * np.pi * np.arange(Nx) / Nx
+    out = []
+    for f in range(4):
+        acc = None
+        for m, (kx, ky) in enumerate(modes):
+            ph = kx * x[None, :] + ky * x[:, None]                     # [y][x]
+            for part, fn in ((0, np.cos), (1, np.sin)):
+                if kx == 0 and ky == 0 and part == 1:
+                    continue
+                c = coef[f, m, part]
+                prof = 0.1 * z * (1 - z) * (1 + c[0] + c[1] * z + c[2] * z * z) / (1 + kx * kx + ky * ky)
+                if xp is np:
+                    term = prof[:, None, None] * fn(ph)[None]
+                else:
+                    term = (xp.from_numpy(prof).to("cuda", dtype)[:, None, None]
+                            * xp.from_numpy(fn(ph)).to("cuda", dtype)[None])
+                acc = term if acc is None else acc + term
+        out.append(acc)
+    return np.stack(out) if xp is np else xp.stack(out)
+
+
+@pytest.mark.parametrize("Nz", [513, 487])
+def test_full_size_boussinesq_matches_oracle_on_band_limited_fields(api, Nz):
+    """1024 x 1024 x Nz, 4 fields, FP32, autotuned variants as bench.py runs
+    it, one RK3 step, against the FP64 oracle: for fields band-limited to
+    |kx|, |ky| <= 2 the step raises the horizontal bandwidth to 16 at most
+    (each stage's product doubles it), which the 2/3 rule keeps and a
+    64 x 64 grid represents without aliasing, so the exact result on the
+    1024^2 grid restricted to every 16th point is the exact result on the 64^2
+    grid; the oracle computes the latter (Nz = 513: padded N' = 538; 487:
+    direct N' = 512)."""
+    N, Nc, dt = 1024, 64, 1e-3
+    kw = dict(nu=3.162e-4, kappa=3.162e-4, gamma=1.0)
+    sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nfields=4, prec="f32", **kw))
+    sim.tune(1)
+    f = _band_limited(N, Nz, 2, 77 + Nz, torch, torch.float32)
+    sim.set_fields(f)
+    del f
+    sim.step(dt)
+    out = sim.get_fields()[:, :, ::N // Nc, ::N // Nc].cpu().numpy()
+    sim.close()
+    torch.cuda.empty_cache()
+    P = ns.Params(Nc, Nc, Nz, nfields=4, **kw)
+    fc_ = _band_limited(Nc, Nz, 2, 77 + Nz, np, None)
+    st, _ = ns.rk_step(ns.to_spectral(fc_, P), np.zeros((2, 2, Nc, P.Kx), complex), P, dt)
+    ref = np.stack([ns.to_physical(c, P) for c in st])
+    for fi in range(4):
+        assert _rel(out[fi], ref[fi]) < 5e-5, (fi, _rel(out[fi], ref[fi]))
+
+
 def test_diagnostics_boussinesq(api):
     """ns_diagnostics on the GPU vs the oracle's diagnostics after one RK3 step."""
     N, Nz = 32, 33
