@@ -975,8 +975,18 @@ struct KXPass {
   // the forward transforms: one length-Nx/2 complex transform per real row
   using RH = RowEng<T, half_l1(L1, L2), half_l2(L1, L2)>;
   using C = cx<T>;
-  static constexpr int Nx = L1 * L2, G = RE::G, NJOB = 2 * NF;
+  static constexpr int Nx = L1 * L2, G = RE::G, NJOB = 2 * NF, NFWD = (NF + 1) / 2;
   static_assert(RH::G <= G && RH::BUF <= RE::BUF && Nx / 2 <= RE::BUF, "half-length row engine");
+  // forward half: one length-Nx/2 transform per real row (all NF groups) for
+  // Nx >= 1024, where it measured faster (1024^2 x 513 step 232.4 -> 228.4 ms);
+  // else two real rows per length-Nx transform on NFWD groups (Nx = 256:
+  // 0.85 against 0.93 ms per launch).  The host-check build switches at 32,
+  // so that its x lengths (16, 32, 128) run both forms.
+#ifdef FC_HOSTCHECK
+  static constexpr bool HALF = Nx >= 32;
+#else
+  static constexpr bool HALF = Nx >= 1024;
+#endif
   static constexpr int THREADS = NJOB * G, NPHASE = 8, MINB = 2;
   struct Args {
     int Kx, Kxp, Ny, Nz;
@@ -1051,36 +1061,71 @@ struct KXPass {
 #pragma unroll
         for (int f = 0; f < NF; ++f) Pr[f * Nx + n] = Nf[f];
       }
-    } else if constexpr (P == 4) {  // z_f[m] = N_f[2m] + i N_f[2m+1], one group per field
-      if (q < NF && g < RH::L2) {
+    } else if constexpr (HALF) {
+      if constexpr (P == 4) {  // z_f[m] = N_f[2m] + i N_f[2m+1], one group per field
+        if (q < NF && g < RH::L2) {
 #pragma unroll
-        for (int j = 0; j < RH::L1; ++j) {
-          const int m = g + RH::L2 * j;
-          R.vh[j] = mk<T>(Pr[q * Nx + 2 * m], Pr[q * Nx + 2 * m + 1]);
+          for (int j = 0; j < RH::L1; ++j) {
+            const int m = g + RH::L2 * j;
+            R.vh[j] = mk<T>(Pr[q * Nx + 2 * m], Pr[q * Nx + 2 * m + 1]);
+          }
+        }
+      } else if constexpr (P == 5) {
+        if (q < NF && g < RH::L2) RH::template A<-1>(R.vh, Zb + q * RE::BUF, a.twh, g);
+      } else if constexpr (P == 6) {
+        if (q < NF && g < RH::L1) {
+          RH::template B<-1>(R.uh, Zb + q * RE::BUF, g);
+          C* Zn = Zb + (NF + q) * RE::BUF;   // natural order spectrum Z_f (length Nx/2)
+#pragma unroll
+          for (int k2 = 0; k2 < RH::L2; ++k2) Zn[g + RH::L1 * k2] = R.uh[k2];
+        }
+      } else if constexpr (P == 7) {
+        // half spectrum of the real row: with E = FFT(N_f[2m]) and
+        // O = FFT(N_f[2m+1]) (length Nx/2, read off Z_f by its Hermitian
+        // parts), X_k = E_k + e^{-2 pi i k/Nx} O_k, k = 0..Nx/2
+        constexpr int H = Nx / 2;
+        const long long z = row / a.Ny, yb = (row % a.Ny) * a.Kxp;
+        for (int i = tid; i < NF * (H + 1); i += THREADS) {
+          const int f = i / (H + 1), k = i % (H + 1);
+          const C* Zn = Zb + (NF + f) * RE::BUF;
+          const C zk = Zn[k % H], zm = Zn[(H - k) % H];
+          const C Ev = mk<T>((zk.x + zm.x) * T(0.5), (zk.y - zm.y) * T(0.5));
+          const C Ov = mk<T>((zk.y + zm.y) * T(0.5), (zm.x - zk.x) * T(0.5));
+          a.NL[lay(f, z, yb + k, a.Nz, a.ntiles)] = cadd(Ev, cmul(a.twh[Nx + k], Ov));
         }
       }
-    } else if constexpr (P == 5) {
-      if (q < NF && g < RH::L2) RH::template A<-1>(R.vh, Zb + q * RE::BUF, a.twh, g);
-    } else if constexpr (P == 6) {
-      if (q < NF && g < RH::L1) {
-        RH::template B<-1>(R.uh, Zb + q * RE::BUF, g);
-        C* Zn = Zb + (NF + q) * RE::BUF;   // natural order spectrum Z_f (length Nx/2)
+    } else {
+      if constexpr (P == 4) {  // pairs (N_a + i N_b) of real rows
+        if (q < NFWD && g < L2) {
 #pragma unroll
-        for (int k2 = 0; k2 < RH::L2; ++k2) Zn[g + RH::L1 * k2] = R.uh[k2];
-      }
-    } else if constexpr (P == 7) {
-      // half spectrum of the real row: with E = FFT(N_f[2m]) and
-      // O = FFT(N_f[2m+1]) (length Nx/2, read off Z_f by its Hermitian
-      // parts), X_k = E_k + e^{-2 pi i k/Nx} O_k, k = 0..Nx/2
-      constexpr int H = Nx / 2;
-      const long long z = row / a.Ny, yb = (row % a.Ny) * a.Kxp;
-      for (int i = tid; i < NF * (H + 1); i += THREADS) {
-        const int f = i / (H + 1), k = i % (H + 1);
-        const C* Zn = Zb + (NF + f) * RE::BUF;
-        const C zk = Zn[k % H], zm = Zn[(H - k) % H];
-        const C Ev = mk<T>((zk.x + zm.x) * T(0.5), (zk.y - zm.y) * T(0.5));
-        const C Ov = mk<T>((zk.y + zm.y) * T(0.5), (zm.x - zk.x) * T(0.5));
-        a.NL[lay(f, z, yb + k, a.Nz, a.ntiles)] = cadd(Ev, cmul(a.twh[Nx + k], Ov));
+          for (int j = 0; j < L1; ++j) {
+            const int n = g + L2 * j;
+            const T re = Pr[(2 * q) * Nx + n];
+            const T im = (2 * q + 1 < NF) ? Pr[(2 * q + 1) * Nx + n] : T(0);
+            R.v[j] = mk<T>(re, im);
+          }
+        }
+      } else if constexpr (P == 5) {
+        if (q < NFWD && g < L2) RE::template A<-1>(R.v, Zb + q * RE::BUF, a.tw, g);
+      } else if constexpr (P == 6) {
+        if (q < NFWD && g < L1) {
+          RE::template B<-1>(R.u, Zb + q * RE::BUF, g);
+          C* Zn = Zb + (NFWD + q) * RE::BUF;   // natural order spectrum
+#pragma unroll
+          for (int k2 = 0; k2 < L2; ++k2) Zn[g + L1 * k2] = R.u[k2];
+        }
+      } else if constexpr (P == 7) {
+        const long long z = row / a.Ny, yb = (row % a.Ny) * a.Kxp;
+        for (int i = tid; i < NFWD * (Nx / 2 + 1); i += THREADS) {
+          const int qq = i / (Nx / 2 + 1), k = i % (Nx / 2 + 1);
+          const C* Zn = Zb + (NFWD + qq) * RE::BUF;
+          const C zk = Zn[k], zm = Zn[(Nx - k) % Nx];
+          // A = (Z_k + conj Z_{N-k}) / 2,  B = (Z_k - conj Z_{N-k}) / (2i)
+          const C Av = mk<T>((zk.x + zm.x) * T(0.5), (zk.y - zm.y) * T(0.5));
+          const C Bv = mk<T>((zk.y + zm.y) * T(0.5), (zm.x - zk.x) * T(0.5));
+          a.NL[lay(2 * qq, z, yb + k, a.Nz, a.ntiles)] = Av;
+          if (2 * qq + 1 < NF) a.NL[lay(2 * qq + 1, z, yb + k, a.Nz, a.ntiles)] = Bv;
+        }
       }
     }
   }
