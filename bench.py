@@ -194,17 +194,12 @@ def bench_deriv(api, torch, dtype_np, steps, warmup, with_e2e=True):
         "p99_ms": float(np.percentile(lat, 99)), "latency_reps": 200, "grid_points_per_s": pts * steps / total,
         "alg_bytes_per_call": alg_bytes, "alg_GBps": alg_bytes * steps / total / 1e9, "launches": steps,
     }
-    # accuracy vs the FP64 oracle on 64 sampled lines (reported beside the number)
-    from oracle import fc, fc_tables
-    Mr = fc_tables.fc_matrix(5, 25, table_dir=os.path.join(ROOT, "tests", "golden"))
+    # 64 sampled lines of the input and both outputs: the CPU-baseline leg
+    # compares them with the FP64 oracle (reported beside the number)
     g = np.random.default_rng(1)
     B, Nz, Ny, Nx = shape
     bs, ys, xs = g.integers(0, B, 64), g.integers(0, Ny, 64), g.integers(0, Nx, 64)
-    lines = f[bs, :, ys, xs].double().cpu().numpy().T
-    for order, out in ((1, d1), (2, d2)):
-        ref = fc.fc_deriv_z(lines, 1.0, Mr, order, axis=0)
-        o = out[bs, :, ys, xs].double().cpu().numpy().T
-        res[f"rel_l2_err_d{order}_vs_oracle"] = float(np.linalg.norm(o - ref) / np.linalg.norm(ref))
+    res["_samples"] = tuple(t[bs, :, ys, xs].double().cpu().numpy().T for t in (f, d1, d2))
     if with_e2e:
         hf = f.cpu().pin_memory()
         h1 = torch.empty(shape, dtype=tdt).pin_memory()
@@ -514,6 +509,20 @@ def cpu_baseline_deriv(budget_s=12.0):
                       f"FP64 numpy pocketfft, one thread"}
 
 
+def oracle_accuracy(res):
+    """Relative L2 error of the sampled fc_deriv_z output lines of an arm
+    against the FP64 oracle (the CPU-baseline leg: the oracle runs here only)."""
+    samples = res.pop("_samples", None)
+    if samples is None:
+        return
+    from oracle import fc, fc_tables
+    Mr = fc_tables.fc_matrix(5, 25, table_dir=os.path.join(ROOT, "tests", "golden"))
+    lines, o1, o2 = samples
+    for order, o in ((1, o1), (2, o2)):
+        ref = fc.fc_deriv_z(lines, 1.0, Mr, order, axis=0)
+        res[f"rel_l2_err_d{order}_vs_oracle"] = float(np.linalg.norm(o - ref) / np.linalg.norm(ref))
+
+
 def cpu_baseline_rk(budget_s=15.0):
     """The FP64 oracle RK3 Boussinesq step on a 128 x 128 x 129 grid (a bounded
     stand-in for the 1024^2 x 513 step; the cost per point grows like log N)."""
@@ -594,6 +603,7 @@ def main():
         DERIV_SHAPE = (2, 256, 256, 513)
         r = bench_deriv(api, torch, np.float32 if args.profile_case == "deriv32" else np.float64,
                         args.steps, args.warmup, with_e2e=False)
+        r.pop("_samples", None)
         print(json.dumps({"profile_case": args.profile_case, **r}))
         return
     # the companions (RK step, ensemble, serving, float64 and smooth-N' arms) are
@@ -647,6 +657,12 @@ def main():
         out["cpu_baseline"] = cpu_baseline_deriv()
         if out.get("rk_stage"):
             out["rk_stage"]["cpu_baseline"] = cpu_baseline_rk()
+        for arm in (out["fc_deriv_z"]["fp32"], r64, rs):
+            if arm:
+                oracle_accuracy(arm)
+    for arm in (out["fc_deriv_z"]["fp32"], r64, rs):
+        if arm:
+            arm.pop("_samples", None)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
