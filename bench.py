@@ -201,23 +201,25 @@ def bench_deriv(api, torch, dtype_np, steps, warmup, with_e2e=True):
     bs, ys, xs = g.integers(0, B, 64), g.integers(0, Ny, 64), g.integers(0, Nx, 64)
     res["_samples"] = tuple(t[bs, :, ys, xs].double().cpu().numpy().T for t in (f, d1, d2))
     if with_e2e:
+        # end to end through the host-array entry point (fc_deriv_z_host): the
+        # library moves page-locked host arrays through the GPU in slabs, with
+        # the copies in both directions overlapping the kernels; host clock
         hf = f.cpu().pin_memory()
         h1 = torch.empty(shape, dtype=tdt).pin_memory()
         h2 = torch.empty(shape, dtype=tdt).pin_memory()
         n_e2e = max(2, min(steps, 5))
+        api.fc_deriv_z_host(plan, hf, h1, h2)          # staging buffers allocated once
         _barrier_sync(torch)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        t0 = time.perf_counter()
         for _ in range(n_e2e):
-            f.copy_(hf, non_blocking=True)
-            api.fc_deriv_z(plan, f, d1, d2)
-            h1.copy_(d1, non_blocking=True)
-            h2.copy_(d2, non_blocking=True)
-        e1.record(stream)
+            api.fc_deriv_z_host(plan, hf, h1, h2)
         _barrier_sync(torch)
-        te = e0.elapsed_time(e1) * 1e-3
+        te = time.perf_counter() - t0
+        same = bool(torch.equal(h1[:, ::16, ::16], d1[:, ::16, ::16].cpu()) and
+                    torch.equal(h2[:, ::16, ::16], d2[:, ::16, ::16].cpu()))
         res["e2e"] = {"value": replica_value(torch, pts * n_e2e, te), "unit": "grid-points/s",
-                      "h2d_bytes_per_step": es * pts, "d2h_bytes_per_step": 2 * es * pts}
+                      "h2d_bytes_per_step": es * pts, "d2h_bytes_per_step": 2 * es * pts,
+                      "api": "fc_deriv_z_host (host arrays, page-locked)", "bitwise_equal_device_path": same}
     del f, d1, d2
     torch.cuda.empty_cache()
     return res

@@ -146,6 +146,29 @@ fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, 
 fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
                              const void* f, void* df, void* d2f, fc_stream_t stream);
 
+/*
+ * fc_deriv_z_host -- the computation of fc_deriv_z on HOST arrays f, df, d2f
+ * (same layout [batch][Nz][Ny][Nx] and arguments; df or d2f may be NULL).
+ * The library moves slabs of y rows (all z and x of a field, about 64 MB of
+ * input each, an even number of rows) through three rotating device buffers
+ * on three internal streams: the host-to-device copy of one slab, the kernel
+ * of the previous one and the device-to-host copies of the one before run
+ * concurrently.  Results are bitwise those of fc_deriv_z on device copies of
+ * the same arrays.  Synchronous: it starts after the work already queued on
+ * `stream` and returns when the outputs are in host memory.  Host arrays
+ * should be page-locked (cudaHostAlloc / cudaHostRegister) for the copies to
+ * overlap; pageable arrays work at the driver's staged-copy speed.  The
+ * staging buffers (3 x 3 slabs) stay allocated with the plan, per device,
+ * until fc_destroy; calls on one plan run one at a time.
+ */
+fc_status fc_deriv_z_host(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
+                          const void* f, void* df, void* d2f, fc_stream_t stream);
+
+/* fc_deriv_z_host with the slab size in bytes of input chosen by the caller
+ * (at least two y rows are moved at a time). */
+fc_status fc_deriv_z_host_ex(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
+                             const void* f, void* df, void* d2f, size_t slab_bytes, fc_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Navier-Stokes / Boussinesq simulation                                     */
 /* ------------------------------------------------------------------------ */
@@ -409,7 +432,8 @@ fc_status ns_set_finite_check(ns_sim_t sim, int every);
  * also come from the environment variable FCNS_INJECT, a comma-separated
  * list of "entry:status:skip:count" (status by name, e.g. FC_ERR_CUDA, or
  * number), read on the first check.  The entry points that check are
- * fc_setup, fc_deriv_z, fc_deriv_z_noalloc, fc_count_nonfinite, ns_create,
+ * fc_setup, fc_deriv_z, fc_deriv_z_noalloc, fc_deriv_z_host (and _ex),
+ * fc_count_nonfinite, ns_create,
  * ns_set_fields, ns_get_fields, ns_get_state, ns_put_state, ns_rhs,
  * fc_poisson_project, rk_step, ns_diagnostics, ns_profiles, ns_interpolate,
  * ns_tune, ns_check_finite, ns_batch_create and ns_batch_step.

@@ -68,6 +68,8 @@ _sig("ns_batch_info", [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctyp
 _sig("ns_batch_destroy", [_vp])
 _sig("fc_deriv_z", [_vp, _c_int, _c_int, _c_int, _c_int, _c_double, _vp, _vp, _vp, _vp])
 _sig("fc_deriv_z_noalloc", [_vp, _c_int, _c_int, _c_int, _c_int, _c_double, _vp, _vp, _vp, _vp])
+_sig("fc_deriv_z_host", [_vp, _c_int, _c_int, _c_int, _c_int, _c_double, _vp, _vp, _vp, _vp])
+_sig("fc_deriv_z_host_ex", [_vp, _c_int, _c_int, _c_int, _c_int, _c_double, _vp, _vp, _vp, ctypes.c_size_t, _vp])
 _sig("fc_count_nonfinite", [_c_int, _vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong), _vp])
 _sig("ns_check_finite", [_vp, ctypes.POINTER(ctypes.c_longlong), _vp])
 _sig("ns_set_finite_check", [_vp, _c_int])
@@ -79,7 +81,7 @@ EXPORTED = ["fc_status_str", "fc_last_error", "fc_setup", "fc_setup_ex", "fc_pla
             "ns_put_wall_gradp", "ns_rhs", "fc_poisson_project", "rk_step", "ns_diagnostics",
             "ns_batch_create", "ns_batch_step", "ns_batch_info", "ns_batch_destroy", "ns_interpolate",
             "ns_profiles", "ns_spectrum_shells", "ns_tune", "fc_count_nonfinite", "ns_check_finite",
-            "ns_set_finite_check", "fc_inject_failure"]
+            "ns_set_finite_check", "fc_inject_failure", "fc_deriv_z_host", "fc_deriv_z_host_ex"]
 
 
 def _check(status: int, where: str):
@@ -197,6 +199,26 @@ def fc_deriv_z(plan: Plan, f, df=None, d2f=None, Lz: float = 1.0, stream=None):
     B, _, Ny, Nx = f.shape
     _check(_lib.fc_deriv_z(plan.handle, _dtype_code(f), B, Nx, Ny, float(Lz), _ptr(f), _ptr(df), _ptr(d2f),
                            _stream(stream)), "fc_deriv_z")
+    return df, d2f
+
+def fc_deriv_z_host(plan: Plan, f, df=None, d2f=None, Lz: float = 1.0, slab_bytes: int | None = None, stream=None):
+    """fc_deriv_z on CPU tensors [batch][Nz][Ny][Nx] (page-locked for overlapped
+    copies): the library moves them through the GPU in slabs (synchronous)."""
+    if f.dim() == 3:
+        f = f.unsqueeze(0)
+        df = df.unsqueeze(0) if df is not None else None
+        d2f = d2f.unsqueeze(0) if d2f is not None else None
+    if f.dim() != 4 or f.shape[1] != plan.Nz or f.is_cuda:
+        raise ValueError("f must be a CPU tensor [batch][Nz][Ny][Nx] with Nz = plan.Nz")
+    for o in (df, d2f):
+        if o is not None and (o.shape != f.shape or o.dtype != f.dtype or o.is_cuda):
+            raise ValueError("outputs must be CPU tensors matching f in shape and dtype")
+    B, _, Ny, Nx = f.shape
+    args = (plan.handle, _dtype_code(f), B, Nx, Ny, float(Lz), _ptr(f), _ptr(df), _ptr(d2f))
+    if slab_bytes is None:
+        _check(_lib.fc_deriv_z_host(*args, _stream(stream)), "fc_deriv_z_host")
+    else:
+        _check(_lib.fc_deriv_z_host_ex(*args, int(slab_bytes), _stream(stream)), "fc_deriv_z_host_ex")
     return df, d2f
 
 _sig("ns_params_default", [ctypes.POINTER(NsParams)])

@@ -1,4 +1,5 @@
 // C ABI of libfcns: argument validation, plan objects, dispatch to launchers.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdlib>
@@ -214,6 +215,16 @@ fc_status fc_destroy(fc_plan_t plan) {
       cudaDeviceSynchronize();
       cudaFree(t.Mr); cudaFree(t.Mr2); cudaFree(t.tw32); cudaFree(t.tw64);
       cudaFree(t.H1_32); cudaFree(t.H1_64); cudaFree(t.H2_32); cudaFree(t.H2_64);
+      for (auto& slot : t.stage)
+        for (void* b : slot) cudaFree(b);
+      for (int k = 0; k < 3; ++k) {
+        if (t.ev_in[k]) cudaEventDestroy(t.ev_in[k]);
+        if (t.ev_run[k]) cudaEventDestroy(t.ev_run[k]);
+        if (t.ev_out[k]) cudaEventDestroy(t.ev_out[k]);
+      }
+      if (t.st_in) cudaStreamDestroy(t.st_in);
+      if (t.st_run) cudaStreamDestroy(t.st_run);
+      if (t.st_out) cudaStreamDestroy(t.st_out);
     }
     cudaSetDevice(cur);
   }
@@ -307,4 +318,104 @@ extern "C" fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int N
   }
   if (s) return s;
   return launch_deriv_z(*t, plan->data, dtype, batch, (long long)Nx * Ny, Lz, f, df, d2f, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// fc_deriv_z on host arrays: slabs of y rows (all z, all x) are copied in,
+// differentiated and copied out on three streams, so that the copies of one
+// slab overlap the kernel of another and the two copy directions overlap
+// each other.
+// ---------------------------------------------------------------------------
+static fc_status stage_for(DerivDevTables* t, size_t bytes) {
+  fc_status s = FC_OK;
+  if (!t->st_in) {
+    s = cuda_status(cudaStreamCreateWithFlags(&t->st_in, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!s) s = cuda_status(cudaStreamCreateWithFlags(&t->st_run, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!s) s = cuda_status(cudaStreamCreateWithFlags(&t->st_out, cudaStreamNonBlocking), "cudaStreamCreate");
+    for (int k = 0; k < 3 && !s; ++k) {
+      s = cuda_status(cudaEventCreateWithFlags(&t->ev_in[k], cudaEventDisableTiming), "cudaEventCreate");
+      if (!s) s = cuda_status(cudaEventCreateWithFlags(&t->ev_run[k], cudaEventDisableTiming), "cudaEventCreate");
+      if (!s) s = cuda_status(cudaEventCreateWithFlags(&t->ev_out[k], cudaEventDisableTiming), "cudaEventCreate");
+    }
+    if (s) return s;
+  }
+  if (t->stage_bytes >= bytes) return FC_OK;
+  for (auto& slot : t->stage)
+    for (void*& b : slot) {
+      cudaFree(b);
+      b = nullptr;
+    }
+  t->stage_bytes = 0;
+  for (auto& slot : t->stage)
+    for (void*& b : slot) {
+      s = cuda_status(cudaMalloc(&b, bytes), "cudaMalloc(fc_deriv_z_host staging)");
+      if (s) return s;
+    }
+  t->stage_bytes = bytes;
+  return FC_OK;
+}
+
+extern "C" fc_status fc_deriv_z_host_ex(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
+                                        const void* f, void* df, void* d2f, size_t slab_bytes, fc_stream_t stream) {
+  if (fc_status inj = injected("fc_deriv_z_host")) return inj;
+  if (!plan) { set_error("fc_deriv_z_host: NULL plan"); return FC_ERR_ARG; }
+  fc_status s = check_deriv_args(plan->data, plan->deriv, dtype, batch, Nx, Ny, Lz, f, df, d2f, "fc_deriv_z_host");
+  if (s) return s;
+  DerivDevTables* t = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(plan->data.mtx);
+    s = deriv_tables_locked(plan, &t);
+  }
+  if (s) return s;
+  std::lock_guard<std::mutex> hl(plan->data.host_mtx);
+  const size_t es = dtype == FC_F32 ? 4 : 8;
+  const int Nz = plan->data.Nz;
+  const size_t yrow = (size_t)Nz * Nx * es;   // bytes of one y row over all z
+  // slab: an even number of y rows (so that the kernel pairs the same lines
+  // as a call on the whole field), about slab_bytes of input
+  long long Yc = (long long)std::max<size_t>(2, slab_bytes / yrow);
+  Yc -= Yc % 2;
+  if (Yc >= Ny) Yc = Ny;
+  s = stage_for(t, (size_t)Yc * yrow);
+  if (s) return s;
+  // the slabs start after the work already queued on the caller's stream
+  cudaEvent_t e0 = nullptr;
+  s = cuda_status(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming), "cudaEventCreate");
+  if (!s) s = cuda_status(cudaEventRecord(e0, (cudaStream_t)stream), "cudaEventRecord");
+  if (!s) s = cuda_status(cudaStreamWaitEvent(t->st_in, e0, 0), "cudaStreamWaitEvent");
+  const char* fh = static_cast<const char*>(f);
+  char* oh[2] = {static_cast<char*>(df), static_cast<char*>(d2f)};
+  const size_t hp = (size_t)Ny * Nx * es;     // host pitch between z rows
+  long long i = 0;
+  for (int b = 0; b < batch && !s; ++b)
+    for (long long y0 = 0; y0 < Ny && !s; y0 += Yc, ++i) {
+      const long long yc = std::min<long long>(Yc, Ny - y0);
+      const int k = (int)(i % 3);
+      const size_t w = (size_t)yc * Nx * es, off = ((size_t)b * Nz * Ny + (size_t)y0) * Nx * es;
+      if (i >= 3) s = cuda_status(cudaStreamWaitEvent(t->st_in, t->ev_out[k], 0), "cudaStreamWaitEvent");
+      if (!s) s = cuda_status(cudaMemcpy2DAsync(t->stage[k][0], w, fh + off, hp, w, Nz, cudaMemcpyHostToDevice, t->st_in),
+                              "cudaMemcpy2DAsync(H2D)");
+      if (!s) s = cuda_status(cudaEventRecord(t->ev_in[k], t->st_in), "cudaEventRecord");
+      if (!s) s = cuda_status(cudaStreamWaitEvent(t->st_run, t->ev_in[k], 0), "cudaStreamWaitEvent");
+      if (!s) s = launch_deriv_z(*t, plan->data, dtype, 1, (long long)Nx * yc, Lz, t->stage[k][0],
+                                 df ? t->stage[k][1] : nullptr, d2f ? t->stage[k][2] : nullptr, t->st_run);
+      if (!s) s = cuda_status(cudaEventRecord(t->ev_run[k], t->st_run), "cudaEventRecord");
+      if (!s) s = cuda_status(cudaStreamWaitEvent(t->st_out, t->ev_run[k], 0), "cudaStreamWaitEvent");
+      for (int o = 0; o < 2 && !s; ++o)
+        if (oh[o])
+          s = cuda_status(cudaMemcpy2DAsync(oh[o] + off, hp, t->stage[k][1 + o], w, w, Nz, cudaMemcpyDeviceToHost,
+                                            t->st_out), "cudaMemcpy2DAsync(D2H)");
+      if (!s) s = cuda_status(cudaEventRecord(t->ev_out[k], t->st_out), "cudaEventRecord");
+    }
+  // synchronous: the outputs are in host memory on return (also after an error)
+  const fc_status s1 = cuda_status(cudaStreamSynchronize(t->st_in), "cudaStreamSynchronize");
+  const fc_status s2 = cuda_status(cudaStreamSynchronize(t->st_run), "cudaStreamSynchronize");
+  const fc_status s3 = cuda_status(cudaStreamSynchronize(t->st_out), "cudaStreamSynchronize");
+  if (e0) cudaEventDestroy(e0);
+  return s ? s : (s1 ? s1 : (s2 ? s2 : s3));
+}
+
+extern "C" fc_status fc_deriv_z_host(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
+                                     const void* f, void* df, void* d2f, fc_stream_t stream) {
+  return fc_deriv_z_host_ex(plan, dtype, batch, Nx, Ny, Lz, f, df, d2f, (size_t)64 << 20, stream);
 }

@@ -34,6 +34,12 @@ struct DerivDevTables {
   void* H1_64 = nullptr;
   void* H2_32 = nullptr;
   void* H2_64 = nullptr;
+  // staging of fc_deriv_z_host: three rotating slots of (input, d1, d2) slab
+  // buffers of stage_bytes each, and the copy-in / compute / copy-out streams
+  size_t stage_bytes = 0;
+  void* stage[3][3] = {};
+  cudaStream_t st_in = nullptr, st_run = nullptr, st_out = nullptr;
+  cudaEvent_t ev_in[3] = {}, ev_run[3] = {}, ev_out[3] = {};
 };
 
 struct PlanData {
@@ -41,6 +47,7 @@ struct PlanData {
   double ls_residual;
   std::vector<double> Mr;
   std::mutex mtx;
+  std::mutex host_mtx;   // serialises fc_deriv_z_host calls on the plan (shared staging)
   std::vector<DerivDevTables> dev;
 };
 

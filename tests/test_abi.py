@@ -87,6 +87,15 @@ def test_fc_deriv_z_argument_checks_need_no_gpu(api):
     assert api._lib.fc_status_str(st).decode() == "FC_ERR_ARG"
 
 
+def test_fc_deriv_z_host_argument_checks_need_no_gpu(api):
+    plan = api.Plan(5, 25, 33)
+    for fn in ("fc_deriv_z_host", "fc_deriv_z_noalloc"):
+        st = getattr(api._lib, fn)(plan.handle, 0, 1, 4, 4, 1.0, None, None, None, None)
+        assert api._lib.fc_status_str(st).decode() == "FC_ERR_ARG"
+    st = api._lib.fc_deriv_z_host_ex(plan.handle, 0, 1, 4, 4, 1.0, 4096, 4100, None, 1 << 20, None)
+    assert api._lib.fc_status_str(st).decode() == "FC_ERR_ARG"
+
+
 def test_unsupported_length(api):
     plan = api.Plan(5, 25, 700)          # N' + Nz - 1 = 1424 > 1080
     st = api._lib.fc_deriv_z(plan.handle, 0, 1, 4, 4, 1.0, 16, 1 << 40, None, None)

@@ -141,3 +141,32 @@ def test_deriv_parity_d7(api, Mr_7_33, Nz, Nx, Ny, B, dtype):
     fin = f.cpu().numpy().astype(np.float64)
     _check(d1.cpu().numpy(), fin, Mr_7_33, Nz, 1, dtype)
     _check(d2.cpu().numpy(), fin, Mr_7_33, Nz, 2, dtype)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffers_bitwise_device_path(api, dtype, pinned):
+    """fc_deriv_z_host (host arrays moved through the GPU in slabs of y rows on
+    three streams) gives bitwise the device fc_deriv_z result: several slabs
+    per field with a ragged last one, an odd x length (the slab keeps an even
+    number of rows, so the same lines are paired), two fields, page-locked and
+    pageable host arrays, and one output omitted."""
+    Nz, Nx, Ny, B = 129, 37, 23, 2
+    plan = api.Plan(5, 25, Nz)
+    sf = synth.SeparableField(Nx, Ny, Nz, rank=3, seed_offset=11)
+    f = torch.from_numpy(np.stack([sf.field(0), -0.5 * sf.field(0)]).astype(dtype))
+    if pinned:
+        f = f.pin_memory()
+    d1, d2 = torch.empty_like(f.cuda()), torch.empty_like(f.cuda())
+    api.fc_deriv_z(plan, f.cuda(), d1, d2)
+    mk = (lambda: torch.empty_like(f).pin_memory()) if pinned else (lambda: torch.empty_like(f))
+    h1, h2 = mk(), mk()
+    row = Nz * Nx * f.element_size()
+    api.fc_deriv_z_host(plan, f, h1, h2, slab_bytes=6 * row)     # slabs of 6 rows: 6, 6, 6, 5
+    torch.cuda.synchronize()
+    assert torch.equal(h1, d1.cpu()) and torch.equal(h2, d2.cpu())
+    h3 = mk()
+    api.fc_deriv_z_host(plan, f, None, h3)                         # one slab per field, d/dz omitted
+    assert torch.equal(h3, d2.cpu())
+    plan.close()
+
