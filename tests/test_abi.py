@@ -100,3 +100,35 @@ def test_unsupported_length(api):
     plan = api.Plan(5, 25, 700)          # N' + Nz - 1 = 1424 > 1080
     st = api._lib.fc_deriv_z(plan.handle, 0, 1, 4, 4, 1.0, 16, 1 << 40, None, None)
     assert api._lib.fc_status_str(st).decode() == "FC_ERR_UNSUPPORTED"
+
+
+def test_size_limits_need_no_gpu(api):
+    """Largest sizes: every array is indexed with 32-bit element offsets, so
+    fc_deriv_z refuses batch * Nx * Ny >= 2^31 lines and ns_create /
+    ns_workspace_bytes refuse states of >= 2^31 complex values (the
+    1024^2 x 999 Boussinesq state, 4 x 1024 x 1024 x 528 > 2^31); lengths
+    outside the compiled shapes are FC_ERR_UNSUPPORTED, bad parameters
+    FC_ERR_ARG; the benchmark's 1024^2 x 513 Boussinesq case fits."""
+    plan = api.Plan(5, 25, 33)
+    st = api._lib.fc_deriv_z(plan.handle, 0, 3, 1 << 15, 1 << 15, 1.0, 16, 1 << 44, None, None)
+    assert api._lib.fc_status_str(st).decode() == "FC_ERR_UNSUPPORTED"
+    ok = api.ns_workspace_bytes(api.ns_params(Nx=1024, Ny=1024, Nz=513, nfields=4, prec="f32"))
+    assert 60e9 < ok < 90e9
+
+    def status(**kw):
+        import ctypes
+        p = api.ns_params(**kw)
+        n = ctypes.c_size_t()
+        return api._lib.fc_status_str(api._lib.ns_workspace_bytes(ctypes.byref(p), ctypes.byref(n))).decode()
+
+    assert status(Nx=1024, Ny=1024, Nz=999, nfields=4, prec="f32") == "FC_ERR_UNSUPPORTED"   # 2^31 elements
+    assert status(Nx=1024, Ny=1024, Nz=999, nfields=3, prec="f32") == "FC_OK"
+    assert status(Nx=100, Ny=64, Nz=33) == "FC_ERR_UNSUPPORTED"                            # x length not compiled
+    assert status(Nx=64, Ny=64, Nz=743, prec="f64") == "FC_ERR_UNSUPPORTED"                # f64 z length > 576
+    assert status(Nx=64, Ny=64, Nz=1200) == "FC_ERR_UNSUPPORTED"                           # N' + Nz - 1 > 1080
+    assert status(Nx=64, Ny=64, Nz=9) == "FC_ERR_ARG"                                      # Nz < 2d
+    assert status(Nx=64, Ny=64, Nz=33, nfields=5) == "FC_ERR_ARG"
+    assert status(Nx=64, Ny=64, Nz=33, nu=-1.0) == "FC_ERR_ARG"
+    assert status(Nx=64, Ny=64, Nz=33, rk_order=5) == "FC_ERR_ARG"
+    assert status(Nx=64, Ny=64, Nz=10) == "FC_OK"                                          # Nz = 2d
+
