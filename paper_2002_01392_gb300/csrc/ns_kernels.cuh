@@ -450,8 +450,10 @@ struct KZContinue {
 // chirp), or, when N' itself is a compiled length (DIRECT, L = N'), by one
 // length-N' transform each; done one after another through a single exchange
 // buffer; the
-// intermediate lines (Y^, s, sigma, sigma_z) go to two global scratch
-// arrays G0, G1 of [N'][lines] (owned element by element by one thread).
+// intermediate lines (Y^, s, sigma, sigma_z) go to two scratch lines per
+// line: in shared memory when they fit in 24 KB per CTA (float32, short
+// lengths or few lines per CTA), else in two global arrays G0, G1 of
+// [N'][lines] (owned element by element by one thread; they stay in L2).
 // ===========================================================================
 template <class T, int L1, int L2, int LINES, bool DIRECT>
 struct KZProject {
@@ -477,7 +479,13 @@ struct KZProject {
   static constexpr size_t off_W = off_M + sizeof(double) * MRMAX;   // per line: b, t, sigma walls (complex double)
   static constexpr size_t off_E = off_W + sizeof(double) * LINES * 16;
   // per line: Phi and Phi' at the first / last d points
-  static constexpr size_t smem_bytes = off_E + sizeof(C) * LINES * 4 * DMAX;
+  static constexpr size_t off_G = off_E + sizeof(C) * LINES * 4 * DMAX;
+  // scratch lines: N' <= NPC (padded: L >= 2 N' - 1; direct: N' = L)
+  static constexpr int NPC = DIRECT ? L1 * L2 : (L1 * L2) / 2;
+  static constexpr size_t sg_bytes = 2 * sizeof(C) * LINES * NPC;
+  static constexpr bool SG = sizeof(T) == 4 && sg_bytes <= 24 * 1024;
+  static constexpr int GS = SG ? LINES : TL;   // element stride of a scratch line
+  static constexpr size_t smem_bytes = off_G + (SG ? sg_bytes : 0);
 
   // conj(chirp[n]) (1 outside the line)
   static FC_HD C cchirp(const ZTab<T>& t, int n, int Np) {
@@ -497,12 +505,12 @@ struct KZProject {
     if constexpr (K < 2) {
       if constexpr (!DIRECT) val = cmul(val, a.t.chirp[n]);
       if constexpr (K == 0) {
-        g0[n * TL] = val;
+        g0[n * GS] = val;
       } else {
         const T kz = a.t.kzo[n];
         const T k2 = kxo * kxo + kyo * kyo + kz * kz;
         const T inv = k2 > T(0) ? T(1) / k2 : T(0);
-        g0[n * TL] = cscale(cadd(g0[n * TL], cscale(val, kz)), inv);
+        g0[n * GS] = cscale(cadd(g0[n * GS], cscale(val, kz)), inv);
       }
     } else {
       // direct: the inverse DFT is conj(DFT(conj(.)))
@@ -510,14 +518,14 @@ struct KZProject {
       else val = cmul(val, cchirp(a.t, n, Np));
       const C sg = cscale(val, invNp);
       if (it == 2) {
-        g1[n * TL] = sg;
+        g1[n * GS] = sg;
         if (n == 0 || n == Nz - 1) {
           const int o = (n == 0) ? 4 : 6;
           W[o] = (double)sg.x;
           W[o + 1] = (double)sg.y;
         }
       } else {
-        g0[n * TL] = sg;
+        g0[n * GS] = sg;
         if (n == 0 || n == Nz - 1) {
           const C w = xw[n * TL];
           const int o = (n == 0) ? 0 : 2;
@@ -552,8 +560,8 @@ struct KZProject {
     C* xu = a.X + lay(0, 0, line, Np, a.g.ntiles);
     C* xv = a.X + lay(1, 0, line, Np, a.g.ntiles);
     C* xw = a.X + lay(2, 0, line, Np, a.g.ntiles);
-    C* g0 = a.G0 + lay(0, 0, line, Np, a.g.ntiles);
-    C* g1 = a.G1 + lay(0, 0, line, Np, a.g.ntiles);
+    C* g0 = SG ? reinterpret_cast<C*>(sm + off_G) + li : a.G0 + lay(0, 0, line, Np, a.g.ntiles);
+    C* g1 = SG ? reinterpret_cast<C*>(sm + off_G) + LINES * NPC + li : a.G1 + lay(0, 0, line, Np, a.g.ntiles);
     const T invNp = T(1.0 / Np);
 
     if constexpr (P == 0) {
@@ -588,7 +596,7 @@ struct KZProject {
             const int n = r + L2 * j;
             C x = mk<T>(0, 0);
             if (j < JN && valid && n < Np) {
-              x = g0[n * TL];
+              x = g0[n * GS];
               if (it == 3) x = cscale(x, a.t.kzo[n]);
               if constexpr (DIRECT) x.y = -x.y;
               else x = cmul(x, cchirp(a.t, n, Np));
@@ -676,8 +684,8 @@ struct KZProject {
               dph = continuation_value<T>(n - Nz, Ev + 2 * DMAX, Ev + 3 * DMAX, d, a.g.Cc, Ms, Ms2);
             }
             const int o = n * TL;
-            const C sg = g1[o];
-            const C sz = g0[o];
+            const C sg = g1[n * GS];
+            const C sz = g0[n * GS];
             // i k Phi = (-k Phi.y, k Phi.x)
             const C gx = cadd(cscale(sg, kxo), mk<T>(-kxo * ph.y, kxo * ph.x));
             const C gy = cadd(cscale(sg, kyo), mk<T>(-kyo * ph.y, kyo * ph.x));
