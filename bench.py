@@ -53,6 +53,23 @@ def _measured_traffic(key):
     return None
 
 
+def _deriv_alu_roofline(r, clocks, L=1080, Nz=513, C=25, d=5):
+    """fc_deriv_z against the float32 ALU: algorithmic flops per line pair (two
+    real z-lines as one complex line) = three length-L FFTs at 5 L log2 L, two
+    spectrum products (6 flops per complex multiply), the continuation of both
+    lines (2 C d multiply-adds each) and the output scaling, over the
+    CUDA-event time; peak = 152 SMs x 128 FP32 lanes x 2 flops (FMA) x the
+    SM clock sampled under load."""
+    pair = 3 * 5 * L * np.log2(L) + 2 * 6 * L + 2 * 2 * C * d * 2 + 2 * 2 * Nz
+    pairs = r["points"] / Nz / 2
+    achieved = pair * pairs / r["seconds_per_call_mean"] / 1e12
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    return {"bound": "alu", "achieved": float(achieved), "peak": float(peak), "unit": "TFLOP/s",
+            "frac": float(achieved / peak), "flops_per_line_pair": float(pair),
+            "peak_kind": "derived (152 SMs x 128 FP32 lanes x FMA x sampled SM clock)"}
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -651,6 +668,7 @@ def main():
                      "frac": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9 / hbm_peak,
                      "traffic": _measured_traffic("fc_deriv_z_f32"), "peak_kind": peak_kind,
                      "kernel": "fc_deriv_z conv L=1080 FP32, paired lines, registers j >= 16 known zero (phased_kernel<DerivPair<float,30,36,4,16>>)"},
+        "roofline_alu": _deriv_alu_roofline(r32, clk.summary()),
         "e2e": r32.get("e2e"),
         "gpu_launches": r32["launches"],
         "clocks": clk.summary(),
