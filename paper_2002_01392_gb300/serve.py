@@ -51,9 +51,15 @@ RETRYABLE = ("FC_ERR_CUDA", "FC_ERR_NOMEM", "FC_ERR_TIMEOUT")
 
 class Server:
     def __init__(self, hbm_budget_bytes: int, slots: int = 8, max_retries: int = 2, check_every: int = 0,
-                 tune: bool = True):
-        import torch
-        self.torch = torch
+                 tune: bool = True, cuda=None, lib=None):
+        """cuda: the stream / event provider (torch.cuda unless given); lib: the
+        binding module (``api`` unless given) -- both replaceable so that the
+        host logic can be exercised without a GPU."""
+        if cuda is None:
+            import torch
+            cuda = torch.cuda
+        self.cuda = cuda
+        self.lib = lib if lib is not None else api
         self.tune = tune
         self.budget = int(hbm_budget_bytes)
         self.max_retries = int(max_retries)
@@ -62,10 +68,11 @@ class Server:
         self.failed = 0
         self.quarantined: set[int] = set()
         self.used = 0
-        self.sims: dict[int, api.Sim] = {}
+        self.sims: dict = {}
+        self._next_id = 0
         self.points: dict[int, int] = {}
         self.rejected = 0
-        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.streams = [cuda.Stream() for _ in range(slots)]
         self.busy: list[tuple[Request, object] | None] = [None] * slots
         self.inflight_sims: set[int] = set()
 
@@ -73,14 +80,15 @@ class Server:
     def admit(self, params, fields=None) -> int | None:
         """Create a resident simulation if its workspace fits; returns its id
         or None (counted as a rejection)."""
-        need = api.ns_workspace_bytes(params)
+        need = self.lib.ns_workspace_bytes(params)
         if self.used + need > self.budget:
             self.rejected += 1
             return None
-        sim = api.Sim(params)
+        sim = self.lib.Sim(params)
         if self.tune:
             sim.tune(1)     # kernel variants timed once per grid size (cached)
-        sid = len(self.sims)
+        sid = self._next_id  # ids are never reused (a released id may still name old requests)
+        self._next_id += 1
         self.sims[sid] = sim
         self.used += need
         self.points[sid] = params.Nx * params.Ny * params.Nz
@@ -92,20 +100,20 @@ class Server:
 
     def release(self, sid: int):
         sim = self.sims.pop(sid)
-        self.used -= api.ns_workspace_bytes(sim.p)
+        self.used -= self.lib.ns_workspace_bytes(sim.p)
         sim.close()
 
     # -- execution -------------------------------------------------------
     def _launch(self, r: Request, slot: int, t0: float):
         """Enqueue r on stream ``slot``; returns the library error of the call
         (nothing is marked busy then) or None."""
-        torch = self.torch
+        cuda = self.cuda
         s = self.streams[slot]
         sim = self.sims[r.sim]
-        h = torch.cuda.current_stream()
+        h = cuda.current_stream()
         s.wait_stream(h)                    # inputs written on the caller's stream
         try:
-            with torch.cuda.stream(s):
+            with cuda.stream(s):
                 if r.kind == "step":
                     sim.step(r.dt, stream=s)
                 elif r.kind == "project":
@@ -114,9 +122,9 @@ class Server:
                     r.out = sim.rhs(r.inp, stream=s)
                 else:
                     raise ValueError(r.kind)
-                ev = torch.cuda.Event()
+                ev = cuda.Event()
                 ev.record(s)
-        except api.FcError as e:
+        except self.lib.FcError as e:
             return e
         r.t_start = time.perf_counter() - t0
         self.busy[slot] = (r, ev)
@@ -143,12 +151,11 @@ class Server:
     def run(self, requests: list[Request]) -> dict:
         """Serve the requests (sorted by arrival time) in real time; returns
         latency and throughput statistics."""
-        torch = self.torch
         reqs = sorted(requests, key=lambda r: r.arrival)
         pending: collections.deque[Request] = collections.deque()
         done: list[Request] = []
         i = 0
-        torch.cuda.synchronize()
+        self.cuda.synchronize()
         t0 = time.perf_counter()
         while len(done) < len(reqs):
             now = time.perf_counter() - t0
