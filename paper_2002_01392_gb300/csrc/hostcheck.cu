@@ -3,6 +3,7 @@
 // arithmetic and data flow with the oracle.  Not part of libfcns and never
 // loaded by the product path.
 #define FC_HOSTCHECK 1
+#include <chrono>
 #include <complex>
 #include <vector>
 
@@ -105,8 +106,14 @@ struct EmuBK {
   fc_status sync(void*) { return FC_OK; }
   int sms() { return 1; }
   fc_status d2h(void* d, const void* s, size_t b, void*) { std::memcpy(d, s, b); return FC_OK; }
+  // host wall time of the emulated launches (lets the autotuner's logic run on the CPU)
   template <class F>
-  fc_status time_ms(F&&, void*, float*) { return FC_ERR_UNSUPPORTED; }  // no timing on the host
+  fc_status time_ms(F&& f, void*, float* ms) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const fc_status s = f();
+    *ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return s;
+  }
 };
 }  // namespace fcns
 
@@ -165,6 +172,14 @@ int fchc_ns_count_nonfinite(void* h, long long* count) {
   unsigned long long n = 0;
   if (!s) s = c->bk.d2h(&n, c->ws + c->l.nfin, sizeof(n), nullptr);
   *count = (long long)n;
+  return s;
+}
+// ns_tune mode 1 on the CPU: every variant timed by host wall clock; the
+// choice is written to tiles (5 ints)
+int fchc_ns_autotune(void* h, int* tiles) {
+  auto* c = (NsCore<EmuBK>*)h;
+  const fc_status s = c->autotune_any(nullptr);
+  for (int k = 0; k < NsCore<EmuBK>::TK_N; ++k) tiles[k] = c->tile[k];
   return s;
 }
 // thread order inside a phase (0 ascending, 1 descending) and shared-memory

@@ -19,7 +19,7 @@ class HostSim:
         self.lib.fchc_ns_create.argtypes = [ctypes.c_void_p]
         for n in ("fchc_ns_set_fields", "fchc_ns_get_fields", "fchc_ns_rhs", "fchc_ns_step", "fchc_ns_project",
                   "fchc_ns_destroy", "fchc_ns_get_state", "fchc_ns_diag_raw", "fchc_ns_interpolate",
-                  "fchc_ns_profiles_raw", "fchc_ns_set_tiles", "fchc_ns_put_state", "fchc_ns_count_nonfinite"):
+                  "fchc_ns_profiles_raw", "fchc_ns_set_tiles", "fchc_ns_put_state", "fchc_ns_count_nonfinite", "fchc_ns_autotune"):
             getattr(self.lib, n).argtypes = None
         self.p = ns_params(**kw)
         self.h = self.lib.fchc_ns_create(ctypes.addressof(self.p))
@@ -76,6 +76,11 @@ class HostSim:
     def put_state(self, st):
         a = np.ascontiguousarray(st)
         assert self.lib.fchc_ns_put_state(ctypes.c_void_p(self.h), self._vp(a)) == 0
+
+    def autotune(self):
+        out = np.zeros(5, dtype=np.int32)
+        assert self.lib.fchc_ns_autotune(ctypes.c_void_p(self.h), self._vp(out)) == 0
+        return [int(x) for x in out]
 
     def count_nonfinite(self):
         n = ctypes.c_longlong()

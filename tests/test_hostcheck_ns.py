@@ -300,6 +300,35 @@ def test_wide_y_tiles_bitwise_and_match_oracle():
     assert _rel(outs[1], ref) < 1e-5
 
 
+def test_autotuner_keeps_state_and_caches():
+    """ns_tune mode 1 run on the CPU emulation (variants timed by host wall
+    clock): the choice stays within each kind's variants (tile bit; radix bit
+    only for the z kinds of float32 padded lengths with a second schedule),
+    the state and the wall planes are left as they were (the step afterwards
+    equals the step of an untuned twin run with the same variants), and a
+    second simulation of the same size gets the cached choice."""
+    N, Nz = 16, 33
+    kw = dict(nu=1e-2, forcing_x=0.1)
+    v = synth.channel_velocity(N, N, Nz)
+    hs = HostSim(Nx=N, Ny=N, Nz=Nz, prec="f32", **kw)
+    hs.set_fields(v)
+    hs.step(1e-3)                       # non-zero wall planes before tuning
+    st0 = hs.get_state()
+    choice = hs.autotune()
+    assert all(0 <= c <= 3 for c in choice[:3]) and all(c in (0, 1) for c in choice[3:])
+    assert np.array_equal(hs.get_state(), st0)
+    hs.step(1e-3)
+    twin = HostSim(Nx=N, Ny=N, Nz=Nz, prec="f32", **kw)
+    twin.set_fields(v)
+    twin.step(1e-3)                     # defaults, as hs before tuning
+    twin.set_tiles(choice)
+    twin.step(1e-3)
+    assert np.array_equal(hs.get_fields(), twin.get_fields())
+    assert twin.autotune() == choice    # cached per size
+    hs.close()
+    twin.close()
+
+
 def test_general_parameters_match_oracle():
     """Everything away from the defaults at once: exponential filter in x, y
     and z (mode 0), a 4 x 3 x 2 box with Nx != Ny, kappa != nu, gamma = 2.5,
