@@ -148,6 +148,9 @@ fc_status fc_setup_ex(int d, int C, int Nz, int M, int n_os, fc_plan_t* out) {
   if (!build_fc_tables(d, C, M, n_os, &T)) { delete p; set_error("fc_setup: table construction failed"); return FC_ERR_ARG; }
   p->data.d = d; p->data.C = C; p->data.Nz = Nz; p->data.Np = Nz + C;
   p->data.M = M; p->data.n_os = n_os; p->data.ls_residual = T.ls_residual;
+  // per-device tables are handed out by address and used outside the plan's
+  // lock: the vector never reallocates (one entry per device, at most 64)
+  p->data.dev.reserve(64);
   p->data.Mr = T.Mr;
   // transform length: N' itself when it is one of the compiled (smooth)
   // lengths -- the paper's choice of N' (Sec. 6, Sec. 7 tables) -- else the
@@ -251,6 +254,10 @@ static fc_status deriv_tables_locked(fc_plan* plan, DerivDevTables** out) {
   if (s) return s;
   for (auto& t : plan->data.dev)
     if (t.device == dev) { *out = &t; return FC_OK; }
+  if (plan->data.dev.size() >= plan->data.dev.capacity()) {
+    set_error("fc_deriv_z: more devices than the plan supports (64)");
+    return FC_ERR_UNSUPPORTED;
+  }
   DerivDevTables t;
   t.device = dev;
   t.L = plan->deriv.L;

@@ -51,7 +51,6 @@ struct PlanData {
   std::vector<DerivDevTables> dev;
 };
 
-fc_status deriv_tables_for_device(PlanData* p, DerivDevTables** out);
 
 // host copies of the derivative tables of one plan, in both precisions
 struct PlanHostTables {
