@@ -44,7 +44,8 @@ def main(path):
     cases = [dict(Nx=32, Ny=32, Nz=33, prec="f64", nu=1e-2, forcing_x=0.1),
              dict(Nx=32, Ny=16, Nz=33, nfields=4, prec="f32", nu=3e-3, kappa=2e-3, gamma=1.0),
              dict(Nx=16, Ny=16, Nz=39, prec="f32", nu=1e-2),
-             dict(Nx=16, Ny=128, Nz=33, prec="f32", nu=1e-2)]
+             dict(Nx=16, Ny=128, Nz=33, prec="f32", nu=1e-2),
+             dict(Nx=16, Ny=16, Nz=513, nfields=4, prec="f32", nu=3.162e-4, kappa=3.162e-4, gamma=1.0)]
     for kw in cases:
         p = ns_params(**kw)
         nf = p.nfields
@@ -80,7 +81,7 @@ def main(path):
         ns = int(math.floor(math.hypot(kxm, kym) / min(2 * math.pi / p.Lx, 2 * math.pi / p.Ly) + 0.5)) + 1
         prof = np.empty((nf, p.Nz, 2 + ns))
         assert lib.fchc_ns_profiles_raw(h, _vp(prof)) == 0
-        if p.Nx == p.Ny == 16:  # restart on a grid twice as fine in x and y
+        if p.Nx == p.Ny == 16 and p.Nz < 100:  # restart on a grid twice as fine in x and y
             p2 = ns_params(**dict(kw, Nx=32, Ny=32))
             h2 = ctypes.c_void_p(lib.fchc_ns_create(ctypes.addressof(p2)))
             assert h2.value

@@ -300,6 +300,31 @@ def test_wide_y_tiles_bitwise_and_match_oracle():
     assert _rel(outs[1], ref) < 1e-5
 
 
+@pytest.mark.parametrize("tiles", [[0, 0, 0, 0, 0], [1, 1, 1, 1, 1]])
+def test_padded_1080_boussinesq_matches_oracle(tiles):
+    """The z kernels at the benchmark's transform length (Nz = 513, N' = 538,
+    L = 1080 = 30 x 36: 4-line z derivatives, 8-line stage combine and
+    projection, and their alternative tiles), float32 Boussinesq, two RK3
+    steps on a 16 x 16 horizontal grid against the oracle."""
+    N, Nz = 16, 513
+    kw = dict(nu=3.162e-4, kappa=3.162e-4, gamma=1.0)
+    hs = HostSim(Nx=N, Ny=N, Nz=Nz, nfields=4, prec="f32", **kw)
+    hs.set_tiles(tiles)
+    P = ns.Params(N, N, Nz, nfields=4, **kw)
+    v = synth.boussinesq_fields(N, N, Nz, amp=1e-1)
+    hs.set_fields(v)
+    st = ns.to_spectral(v, P)
+    gp = np.zeros((2, 2, N, P.Kx), complex)
+    for _ in range(2):
+        hs.step(1e-3)
+        st, gp = ns.rk_step(st, gp, P, 1e-3)
+    ref = np.stack([ns.to_physical(c, P) for c in st])
+    out = hs.get_fields()
+    for f in range(4):
+        assert _rel(out[f], ref[f]) < 5e-5, (f, _rel(out[f], ref[f]))
+    hs.close()
+
+
 def test_autotuner_keeps_state_and_caches():
     """ns_tune mode 1 run on the CPU emulation (variants timed by host wall
     clock): the choice stays within each kind's variants (tile bit; radix bit
