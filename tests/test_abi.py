@@ -85,6 +85,10 @@ def test_fc_deriv_z_argument_checks_need_no_gpu(api):
     # overlapping input and output
     st = api._lib.fc_deriv_z(plan.handle, 0, 1, 4, 4, 1.0, 4096, 4100, None, None)
     assert api._lib.fc_status_str(st).decode() == "FC_ERR_ARG"
+    # empty batches / grids are argument errors (nothing is launched or written)
+    for b, nx, ny in ((0, 4, 4), (1, 0, 4), (1, 4, 0), (-1, 4, 4)):
+        st = api._lib.fc_deriv_z(plan.handle, 0, b, nx, ny, 1.0, 16, 1 << 40, None, None)
+        assert api._lib.fc_status_str(st).decode() == "FC_ERR_ARG", (b, nx, ny)
 
 
 def test_fc_deriv_z_host_argument_checks_need_no_gpu(api):
