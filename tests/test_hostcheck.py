@@ -66,3 +66,29 @@ def test_deriv_kernel_phases_match_oracle(hc, Mr_5_25, Nz, L, Nx, Ny, B, dtype):
         if dtype == 1:
             rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
             assert rel < 1e-11 * max(1.0, (Np / 128) ** (2 * (order - 1))), (order, rel)
+
+
+def test_deriv_kernel_converges_to_exact_derivative(hc, Mr_5_25):
+    """Against the exact z-derivatives of the separable workload field (its z
+    profiles are degree-16 Chebyshev series): the float64 kernel has the
+    oracle's discretisation error (to the float64 parity bound), and it falls at
+    least like h^(d-1) = h^4 for d/dz (boundary order of the d = 5 FC-Gram
+    continuation) and h^3 for d2/dz2 from Nz = 129 to 513."""
+    errs = {}
+    for Nz, L in ((129, 288), (513, 1080)):
+        sf = synth.SeparableField(6, 3, Nz, seed_offset=4)
+        f = np.ascontiguousarray(sf.field(0)[None])
+        d1, d2 = np.zeros_like(f), np.zeros_like(f)
+        assert hc.fchc_deriv_z(1, L, _vp(Mr_5_25), 5, 25, Nz, 1, 6, 3, ctypes.c_double(1.0),
+                               _vp(f), _vp(d1), _vp(d2)) == 0
+        for order, out in ((1, d1), (2, d2)):
+            ex = sf.field(order)[None]
+            ke = np.linalg.norm(out - ex) / np.linalg.norm(ex)
+            oe = np.linalg.norm(fc.fc_deriv_z(f, 1.0, Mr_5_25, order, axis=1) - ex) / np.linalg.norm(ex)
+            # the two differ by at most the kernel's float64 parity bound
+            assert abs(ke - oe) <= rel_bound_f64(order, Nz + 25), (Nz, order, ke, oe)
+            errs[(Nz, order)] = ke
+    h_ratio = 512 / 128
+    assert errs[(129, 1)] / errs[(513, 1)] >= h_ratio ** 4 * 0.8
+    assert errs[(129, 2)] / errs[(513, 2)] >= h_ratio ** 3 * 0.8
+
