@@ -9,7 +9,7 @@
 #pragma once
 
 #ifdef FC_HOSTCHECK
-#define FC_ZSHAPES_DIRECT(M) M(64, 8, 8, true)
+#define FC_ZSHAPES_DIRECT(M) M(64, 8, 8, true) M(512, 16, 32, true)
 #define FC_ZSHAPES_PADDED(M) M(160, 10, 16, false) M(288, 16, 18, false) M(1080, 30, 36, false)
 #define FC_XYSHAPES(M) M(16, 4, 4) M(32, 4, 8) M(128, 8, 16)
 #else

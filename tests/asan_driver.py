@@ -45,7 +45,8 @@ def main(path):
              dict(Nx=32, Ny=16, Nz=33, nfields=4, prec="f32", nu=3e-3, kappa=2e-3, gamma=1.0),
              dict(Nx=16, Ny=16, Nz=39, prec="f32", nu=1e-2),
              dict(Nx=16, Ny=128, Nz=33, prec="f32", nu=1e-2),
-             dict(Nx=16, Ny=16, Nz=513, nfields=4, prec="f32", nu=3.162e-4, kappa=3.162e-4, gamma=1.0)]
+             dict(Nx=16, Ny=16, Nz=513, nfields=4, prec="f32", nu=3.162e-4, kappa=3.162e-4, gamma=1.0),
+             dict(Nx=16, Ny=16, Nz=487, prec="f64", nu=3.162e-4)]
     for kw in cases:
         p = ns_params(**kw)
         nf = p.nfields

@@ -59,32 +59,39 @@ def test_rk3_steps_match_oracle(chan):
     assert _rel(hs.get_fields(), ref) < 1e-13
 
 
-@pytest.mark.parametrize("prec,tol,tol_rhs", [("f64", 1e-12, 1e-12), ("f32", 2e-5, 5e-4)])
-def test_direct_length_steps_match_oracle(prec, tol, tol_rhs):
-    """N' = Nz + C = 64 is itself a compiled transform length: z derivatives and
-    the filter become spectral multipliers of length N' and the projection's
-    DFTs plain length-N' transforms (no padding, no Bluestein).  The float32
-    right-hand side carries nu d2/dz2, whose rounding floor is eps (k_max/k)^2
-    ~ 1e-4 here."""
-    N, Nz = 16, 39
-    hs = HostSim(Nx=N, Ny=N, Nz=Nz, nu=1e-2, forcing_x=0.1, prec=prec)
-    P = ns.Params(N, N, Nz, nu=1e-2, forcing_x=0.1)
-    v = synth.channel_velocity(N, N, Nz)
+@pytest.mark.parametrize("Nz,nu,dt,prec,tol,tol_rhs", [(39, 1e-2, 1e-3, "f64", 1e-12, 1e-12),
+                                                       (39, 1e-2, 1e-3, "f32", 2e-5, 5e-4),
+                                                       (487, 3.162e-4, 1e-4, "f64", 1e-12, 1e-11),
+                                                       (487, 3.162e-4, 1e-4, "f32", 2e-5, 5e-3)])
+def test_direct_length_steps_match_oracle(Nz, nu, dt, prec, tol, tol_rhs):
+    """N' = Nz + C = 64 or 512 (the paper-shaped smooth companion) is itself a
+    compiled transform length: z derivatives and the filter become spectral
+    multipliers of length N' and the projection's DFTs plain length-N'
+    transforms (no padding, no Bluestein).  The right-hand side carries
+    nu d2/dz2, whose rounding floor is eps (k_max/k)^2: ~1e-4 in float32 at
+    N' = 64, ~1e-3 at N' = 512.  The explicit step needs dt nu k_max^2 = O(1)
+    at most (k_max = pi (Nz - 1)): at Nz = 487 with nu = 1e-2 and dt = 1e-3
+    the top z modes grow from rounding by orders of magnitude per step, so the
+    larger grid runs at the Rayleigh-Benard viscosity with dt = 1e-4."""
+    N = 16
+    hs = HostSim(Nx=N, Ny=N, Nz=Nz, nu=nu, forcing_x=10 * nu, prec=prec)
+    P = ns.Params(N, N, Nz, nu=nu, forcing_x=10 * nu)
+    v = synth.channel_velocity(N, N, Nz, nu=nu)
     assert _rel(hs.rhs(v), ns.ns_rhs(v, P)) < tol_rhs
     g = np.random.default_rng(3)
     z = synth.z_grid(Nz)
     vs = v + 0.2 * (z * (1 - z))[None, :, None, None] * g.standard_normal((3, 1, N, N))
     hs.set_fields(v)
-    out, gp = hs.project(vs, 1e-3)
-    ref, gref = ns.poisson_project(vs, P, 1e-3)
+    out, gp = hs.project(vs, dt)
+    ref, gref = ns.poisson_project(vs, P, dt)
     assert _rel(out, ref) < tol
     assert _rel(gp, gref) < 10 * tol
     hs.set_fields(v)
     st = ns.to_spectral(v, P)
     gp = np.zeros((2, 2, N, P.Kx), complex)
     for _ in range(2):
-        hs.step(1e-3)
-        st, gp = ns.rk_step(st, gp, P, 1e-3)
+        hs.step(dt)
+        st, gp = ns.rk_step(st, gp, P, dt)
     ref = np.stack([ns.to_physical(c, P) for c in st])
     assert _rel(hs.get_fields(), ref) < tol
     hs.close()

@@ -66,13 +66,15 @@ def test_deriv_kernel_race_free(hc, Mr_5_25, Nz, L, Nx, Ny, dtype):
 @pytest.mark.parametrize("N,Nz,nf,prec,tiles", [(32, 33, 3, "f64", None), (16, 33, 4, "f32", None),
                                                  (16, 39, 3, "f32", None), (16, 33, 4, "f32", [3, 3, 3, 1, 1]),
                                                  ((16, 128), 33, 3, "f32", [0, 0, 0, 1, 1]),
-                                                 (16, 513, 4, "f32", None), (16, 513, 4, "f32", [1, 1, 1, 1, 1])])
+                                                 (16, 513, 4, "f32", None), (16, 513, 4, "f32", [1, 1, 1, 1, 1]),
+                                                 (16, 487, 4, "f32", None)])
 def test_ns_kernels_race_free(hc, N, Nz, nf, prec, tiles):
     """RK3 step (every z / y / x kernel of a stage, the mean line, the
     projection), the right-hand side, the projection call and get_fields; the
     Nz = 39 case runs the direct length-64 z transforms; then the alternative
-    tiles and radix schedules, the wide y tiles (Ny = 128), and the
-    benchmark's z length 1080 (Nz = 513) with both tiles."""
+    tiles and radix schedules, the wide y tiles (Ny = 128), the benchmark's
+    z length 1080 (Nz = 513) with both tiles, and the direct length 512
+    (Nz = 487)."""
     Nx, Ny = (N, N) if isinstance(N, int) else N
     kw = dict(nu=3e-3, kappa=3e-3, gamma=1.0) if nf == 4 else dict(nu=1e-2, forcing_x=0.1)
     v = synth.boussinesq_fields(Nx, Ny, Nz, amp=1e-1) if nf == 4 else synth.channel_velocity(Nx, Ny, Nz)
