@@ -136,3 +136,19 @@ def test_size_limits_need_no_gpu(api):
     assert status(Nx=64, Ny=64, Nz=33, rk_order=5) == "FC_ERR_ARG"
     assert status(Nx=64, Ny=64, Nz=10) == "FC_OK"                                          # Nz = 2d
 
+
+def test_host_array_binding_checks_need_no_gpu(api):
+    """fc_deriv_z_host through the binding: shapes and dtypes are checked
+    before the library is called."""
+    import torch
+    plan = api.Plan(5, 25, 33)
+    f = torch.zeros(2, 33, 4, 6)
+    with pytest.raises(ValueError):
+        api.fc_deriv_z_host(plan, torch.zeros(2, 32, 4, 6), torch.zeros(2, 32, 4, 6))   # Nz != plan.Nz
+    with pytest.raises(ValueError):
+        api.fc_deriv_z_host(plan, f, torch.zeros(2, 33, 4, 5))                          # output shape
+    with pytest.raises(ValueError):
+        api.fc_deriv_z_host(plan, f, torch.zeros(2, 33, 4, 6, dtype=torch.float64))    # output dtype
+    with pytest.raises(TypeError):
+        api.fc_deriv_z_host(plan, f.to(torch.int32), None, torch.zeros(2, 33, 4, 6, dtype=torch.int32))
+
