@@ -395,7 +395,7 @@ fc_status ns_batch_create(ns_sim_t* sims, int n, ns_batch_t* out) {
     for (int j = 0; j < i; ++j)
       if (sims[j] == sims[i]) { set_error("ns_batch_create: a simulation appears twice"); return FC_ERR_ARG; }
   }
-  for (int i = 0; i < n; ++i) {  // tile sizes of every member picked by measurement (cached per size)
+  for (int i = 0; i < n; ++i) {  // kernel variants of every member picked by measurement (cached per size)
     fc_status t = sims[i]->core.autotune_any(nullptr);
     if (t) return t;
   }

@@ -680,9 +680,11 @@ struct NsCore {
     return f32() ? count_nonfinite<float>(reset, st) : count_nonfinite<double>(reset, st);
   }
 
-  // Autotuner of the lines per CTA: each kernel kind of the RK step is timed
-  // with both compiled tile sizes on this simulation's buffers (two timed
-  // launches each after a warm-up) and the faster kept.  The state and the
+  // Autotuner of the kernel variants: each kernel kind of the RK step is
+  // timed with every compiled variant (lines per CTA; for the z kinds of
+  // float32 padded lengths also the second radix schedule) on this
+  // simulation's buffers (two timed launches each after a warm-up) and the
+  // fastest kept.  The state and the
   // wall planes are preserved (the projection runs on a spare buffer; the
   // planes it writes are restored).  Results are cached per process by size,
   // so instances of equal sizes are tuned once.
