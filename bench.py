@@ -70,6 +70,36 @@ def _deriv_alu_roofline(r, clocks, L=1080, Nz=513, C=25, d=5):
             "peak_kind": "derived (152 SMs x 128 FP32 lanes x FMA x sampled SM clock)"}
 
 
+def measure_alu_peaks(api, torch, iters=4096, reps=5):
+    """Arithmetic-pipe ceilings measured on this GPU with the library's probe
+    kernel (fc_alu_probe: independent chains of one instruction kind on every
+    SM, full occupancy), best of ``reps`` CUDA-event-timed launches after one
+    warm-up each.  Per kind: lane operations per second (a packed two-wide
+    instruction counts two) and, for the fused multiply-adds, flop/s
+    (2 per lane operation)."""
+    sink = torch.empty(256, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+    for kind in ("ffma", "fadd", "ffma2", "fadd2", "dfma"):
+        it = iters if kind != "dfma" else max(64, iters // 32)
+        api.alu_probe(kind, it, sink)
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ops = api.alu_probe(kind, it, sink)
+            e1.record(stream)
+            e1.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3
+            best = t if best is None else min(best, t)
+        rate = ops / best
+        out[kind] = {"lane_ops_per_s": rate, "tflops": (2 * rate if kind in ("ffma", "ffma2", "dfma") else rate) / 1e12,
+                     "ms": best * 1e3}
+    out["how"] = ("fc_alu_probe: 8 x SMs blocks x 256 threads, 8 independent chains per thread, "
+                  "best of %d launches (CUDA events)" % reps)
+    return out
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):

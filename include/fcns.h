@@ -441,6 +441,29 @@ fc_status ns_set_finite_check(ns_sim_t sim, int every);
  */
 fc_status fc_inject_failure(const char* entry, fc_status status, long long skip, long long count);
 
+/* ------------------------------------------------------------------------ */
+/* Measurement                                                                */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * fc_alu_probe -- arithmetic-pipe throughput probe (no counterpart in the
+ * paper: it measures the float32 / float64 ceilings against which the
+ * transform kernels' rooflines are stated).  Launches, on `stream`, one
+ * kernel of 8 x (SM count) blocks of 256 threads, each thread running 8
+ * independent chains of `iters` x 16 instructions of one kind:
+ *   kind 0 FFMA (float32 fused multiply-add), 1 FADD (float32 add),
+ *        2 FFMA2 (packed 2 x float32 fused multiply-add), 3 FADD2 (packed
+ *        2 x float32 add), 4 DFMA (float64 fused multiply-add).
+ *   iters    >= 1.
+ *   sink     device pointer to 256 floats (written only in a case that
+ *            cannot occur; keeps the work alive).
+ *   lane_ops host pointer (may be NULL): receives the number of scalar lane
+ *            operations the launch performs (two per packed instruction
+ *            and thread); the caller times the launch with CUDA events.
+ * Asynchronous; FC_ERR_ARG for a kind outside 0..4, iters < 1 or NULL sink.
+ */
+fc_status fc_alu_probe(int kind, int iters, void* sink, double* lane_ops, fc_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

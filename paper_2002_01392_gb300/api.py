@@ -74,6 +74,7 @@ _sig("fc_count_nonfinite", [_c_int, _vp, ctypes.c_longlong, ctypes.POINTER(ctype
 _sig("ns_check_finite", [_vp, ctypes.POINTER(ctypes.c_longlong), _vp])
 _sig("ns_set_finite_check", [_vp, _c_int])
 _sig("fc_inject_failure", [ctypes.c_char_p, _c_int, ctypes.c_longlong, ctypes.c_longlong])
+_sig("fc_alu_probe", [_c_int, _c_int, _vp, ctypes.POINTER(_c_double), _vp])
 
 EXPORTED = ["fc_status_str", "fc_last_error", "fc_setup", "fc_setup_ex", "fc_plan_matrix", "fc_plan_info",
             "fc_destroy", "fc_deriv_z", "fc_deriv_z_noalloc", "ns_params_default", "ns_workspace_bytes", "ns_create", "ns_destroy",
@@ -81,7 +82,7 @@ EXPORTED = ["fc_status_str", "fc_last_error", "fc_setup", "fc_setup_ex", "fc_pla
             "ns_put_wall_gradp", "ns_rhs", "fc_poisson_project", "rk_step", "ns_diagnostics",
             "ns_batch_create", "ns_batch_step", "ns_batch_info", "ns_batch_destroy", "ns_interpolate",
             "ns_profiles", "ns_spectrum_shells", "ns_tune", "fc_count_nonfinite", "ns_check_finite",
-            "ns_set_finite_check", "fc_inject_failure", "fc_deriv_z_host", "fc_deriv_z_host_ex"]
+            "ns_set_finite_check", "fc_inject_failure", "fc_deriv_z_host", "fc_deriv_z_host_ex", "fc_alu_probe"]
 
 
 def _check(status: int, where: str):
@@ -114,6 +115,18 @@ def count_nonfinite(t, stream=None) -> int:
     if st not in (0, STATUS["FC_ERR_NONFINITE"]):
         _check(st, "fc_count_nonfinite")
     return n.value
+
+
+ALU_KINDS = {"ffma": 0, "fadd": 1, "ffma2": 2, "fadd2": 3, "dfma": 4}
+
+
+def alu_probe(kind: str, iters: int, sink, stream=None) -> float:
+    """Enqueue the arithmetic-pipe probe kernel (fc_alu_probe); returns the lane
+    operations it performs (the caller times it with CUDA events)."""
+    ops = _c_double(0.0)
+    _check(_lib.fc_alu_probe(ALU_KINDS[kind], int(iters), _ptr(sink), ctypes.byref(ops), _stream(stream)),
+           "fc_alu_probe")
+    return ops.value
 
 
 def _stream(stream=None) -> int:

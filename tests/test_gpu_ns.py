@@ -24,6 +24,20 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def _wall_err(out, ref):
+    """Largest error on the wall rows z = 0 and z = Lz (where the continuation
+    and the boundary-condition injection act), per field relative to that
+    field's largest value, maximised over the fields: an error confined to the
+    walls can hide inside a relative L2 norm over every point."""
+    out = np.asarray(out, dtype=np.float64)
+    worst = 0.0
+    for f in range(ref.shape[0]):
+        scale = max(np.abs(ref[f]).max(), 1e-300)
+        for s in (0, ref.shape[1] - 1):
+            worst = max(worst, float(np.abs(out[f, s] - ref[f, s]).max() / scale))
+    return worst
+
+
 def _cuda(x, dt=torch.float64):
     return torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dt)
 
@@ -60,7 +74,9 @@ def test_cfg0_fields_roundtrip(cfg0):
 def test_cfg0_rhs(cfg0):
     sim, P, v = cfg0
     out = sim.rhs(_cuda(v)).cpu().numpy()
-    assert _rel(out, ns.ns_rhs(v, P)) < 1e-11
+    ref = ns.ns_rhs(v, P)
+    assert _rel(out, ref) < 1e-11
+    assert _wall_err(out, ref) < 1e-11
 
 
 def test_cfg0_projection(cfg0):
@@ -73,6 +89,7 @@ def test_cfg0_projection(cfg0):
     out = sim.project(_cuda(vs), 1e-3, gradp_out=gp).cpu().numpy()
     ref, gref = ns.poisson_project(vs, P, 1e-3)
     assert _rel(out, ref) < 1e-11
+    assert _wall_err(out, ref) < 1e-11
     assert _rel(gp.cpu().numpy(), gref) < 1e-11
     # wall-normal velocity after projection is zero to round-off (Sec. 6)
     assert np.abs(out[2][[0, -1]]).max() < 1e-13
@@ -86,6 +103,7 @@ def test_cfg0_rk3_steps(cfg0):
     out = sim.get_fields().cpu().numpy()
     ref, gref, _ = _oracle_steps(v, P, 1e-3, 3)
     assert _rel(out, ref) < 1e-11
+    assert _wall_err(out, ref) < 1e-11
     # grad p = grad phi / dt_j carries 1/dt_j (down to 3/dt): its rounding is a
     # velocity-scale rounding divided by dt_j, so it is measured on that scale
     dgp = sim.wall_gradp().cpu().numpy() - gref
@@ -146,6 +164,7 @@ def test_channel_float32(api, N, Nz):
     out = sim.get_fields().cpu().numpy()
     ref, _, _ = _oracle_steps(v, P, 1e-3, 2)
     assert _rel(out, ref) < 1e-5
+    assert _wall_err(out, ref) < 1e-5
     sim.close()
 
 
@@ -161,6 +180,7 @@ def test_boussinesq_float32(api, N, Nz):
     ref, _, _ = _oracle_steps(f, P, 2e-3, 1)
     for c in range(4):
         assert _rel(out[c], ref[c]) < 5e-5, c
+    assert _wall_err(out, ref) < 5e-5
     sim.close()
 
 
@@ -180,7 +200,9 @@ def test_direct_length_channel_matches_oracle(api, N, Nz):
     for _ in range(3):
         sim.step(1e-3)
     ref, gref, _ = _oracle_steps(v, P, 1e-3, 3)
-    assert _rel(sim.get_fields().cpu().numpy(), ref) < 1e-11
+    out = sim.get_fields().cpu().numpy()
+    assert _rel(out, ref) < 1e-11
+    assert _wall_err(out, ref) < 1e-11
     assert _rel(sim.wall_gradp().cpu().numpy(), gref) < 1e-9
     sim.close()
 
@@ -307,6 +329,7 @@ def test_full_size_boussinesq_matches_oracle_on_band_limited_fields(api, Nz):
     ref = np.stack([ns.to_physical(c, P) for c in st])
     for fi in range(4):
         assert _rel(out[fi], ref[fi]) < 5e-5, (fi, _rel(out[fi], ref[fi]))
+    assert _wall_err(out, ref) < 5e-5
 
 
 def test_diagnostics_boussinesq(api):
@@ -481,7 +504,9 @@ def test_every_z_length_one_step(api, Nz, prec, tol):
     sim.set_fields(_cuda(v, sim.dtype))
     sim.step(1e-4)
     ref, _, _ = _oracle_steps(v, P, 1e-4, 1)
-    assert _rel(sim.get_fields().cpu().numpy(), ref) < tol
+    out = sim.get_fields().cpu().numpy()
+    assert _rel(out, ref) < tol
+    assert _wall_err(out, ref) < tol
     sim.close()
 
 
@@ -498,6 +523,8 @@ def test_general_parameters_match_oracle(api):
     for _ in range(2):
         sim.step(2e-3)
     ref, gref, _ = _oracle_steps(f, P, 2e-3, 2)
-    assert _rel(sim.get_fields().cpu().numpy(), ref) < 1e-11
+    out = sim.get_fields().cpu().numpy()
+    assert _rel(out, ref) < 1e-11
+    assert _wall_err(out, ref) < 1e-11
     assert _rel(sim.wall_gradp().cpu().numpy(), gref) < 1e-9
     sim.close()

@@ -68,6 +68,52 @@ def test_conduction_state_is_exactly_fixed(Mr_5_25):
     assert ns.nusselt(st2 + 0.0, p) == (1.0, 1.0)
 
 
+@pytest.mark.parametrize("Lz", [1.0, 2.0])
+def test_nusselt_closed_form(Mr_5_25, Lz):
+    """Sec. 7 Nusselt number with reading B2, Nu = 1 - <d_z theta>/gamma at each
+    wall.  theta = a z (Lz - z) + c z^2 (Lz - z) + (zero horizontal mean part)
+    is a polynomial of degree 3 < d in z, differentiated exactly by FC-Gram, so
+    <d_z theta> = a Lz at z = 0 and -a Lz - c Lz^2 at z = Lz, and
+    Nu = (1 - a Lz / gamma, 1 + (a Lz + c Lz^2) / gamma).  The cubic term makes
+    the two walls differ, gamma != 1 exposes a misplaced 1/gamma, the
+    x, y-varying part exposes a sum in place of a mean, and a w with wall
+    gradients of its own exposes a wrong field."""
+    N, Nz, gamma, a, c = 16, 33, 2.5, 0.8, -0.3
+    p = ns.Params(N, N, Nz, nfields=4, nu=1e-3, kappa=1e-3, gamma=gamma, Lz=Lz, Mr=Mr_5_25)
+    z = synth.z_grid(Nz, Lz)
+    x = np.arange(N) * 2 * np.pi / N
+    Z, Y, X = np.meshgrid(z, x, x, indexing="ij")
+    f = np.zeros((4, Nz, N, N))
+    f[2] = 0.7 * Z * (Lz - Z)
+    f[3] = a * Z * (Lz - Z) + c * Z ** 2 * (Lz - Z) + 0.4 * np.cos(2 * X + Y) * Z ** 2 * (Lz - Z)
+    nu0, nu1 = ns.nusselt(ns.to_spectral(f, p), p)
+    assert abs(nu0 - (1 - a * Lz / gamma)) < 1e-9
+    assert abs(nu1 - (1 + (a * Lz + c * Lz ** 2) / gamma)) < 1e-9
+
+
+def test_flow_rate_is_the_grid_point_mean_of_u(Mr_5_25):
+    """Sec. 6 channel diagnostic: the flow rate reported is the mean of u over
+    the Nx Ny Nz physical grid points (both walls included), not a quadrature of
+    the continuous profile.  For the laminar profile U = F z (1 - z)/(2 nu) on
+    z_s = s/(Nz - 1) that mean is F/(2 nu) (Nz - 2)/(6 (Nz - 1)) in closed form
+    (sum of s/M - s^2/M^2 over s = 0..M, M = Nz - 1, divided by Nz), which tends
+    to the continuous flow rate F/(12 nu) as Nz grows.  A zero-mean x, y
+    fluctuation of u and nonzero v, w must not change it."""
+    nu, F = 1e-2, 0.1
+    for Nz in (17, 33, 65):
+        p = ns.Params(16, 8, Nz, nu=nu, forcing_x=F, Mr=Mr_5_25)
+        v = synth.poiseuille(16, 8, Nz, F=F, nu=nu)
+        z = synth.z_grid(Nz)
+        x = np.arange(16) * 2 * np.pi / 16
+        v[0] += 0.3 * np.cos(x)[None, None, :] * (z * (1 - z))[:, None, None]
+        v[1] += 0.2
+        v[2] += (z ** 2)[:, None, None]
+        q = ns.flow_rate(ns.to_spectral(v, p), p)
+        exact = F / (2 * nu) * (Nz - 2) / (6 * (Nz - 1))
+        assert abs(q - exact) < 1e-12 * exact, (Nz, q, exact)
+        assert abs(exact - F / (12 * nu)) < F / (12 * nu) * 2.0 / (Nz - 1)
+
+
 def test_projection_wall_normal_velocity_is_roundoff(Mr_5_25):
     """After projection w = 0 at the walls to round-off (Sec. 6: <w^2|wall> ~ 1e-35)."""
     p = ns.Params(32, 32, 33, nu=1e-2, Mr=Mr_5_25)
