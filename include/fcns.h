@@ -123,22 +123,31 @@ fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, 
 
 /*
  * fc_deriv_z_noalloc -- the same computation and arguments as fc_deriv_z,
- * for callers that cannot let the library allocate device memory: code that
- * runs while a CUDA graph is being captured (cudaMalloc cannot be captured),
- * applications whose device memory belongs to a host framework or a fixed
- * arena and that forbid allocations by plug-ins, and latency-critical loops
- * that cannot take cudaMalloc's implicit synchronisation.  The paper has no
- * counterpart; this is a deployment variant of fc_deriv_z.
+ * for callers that cannot let the library allocate device memory:
+ * applications whose device memory belongs to a host framework or to a
+ * fixed-size arena and that forbid allocations by plug-ins, and programs
+ * running under a device-memory budget that a library must not grow.
+ * (fc_deriv_z allocates its tables with cudaMalloc on the first call of a
+ * plan on a device.)  The paper has no counterpart; this is a deployment
+ * variant of fc_deriv_z, and its results are bitwise those of fc_deriv_z.
  *   - Calls no cudaMalloc, cudaFree or other allocating routine.  The plan's
- *     tables (continuation matrix, kernel spectrum, twiddles) are copied on
- *     the caller's stream into one fixed 96 KiB static device array that
- *     every GPU loading the library reserves until the process exits.
+ *     tables (continuation matrix, kernel spectra, twiddles) live in one
+ *     fixed 96 KiB static device array that every GPU loading the library
+ *     reserves until the process exits.
  *   - The first call on each device looks up that array's device address
- *     (cudaGetSymbolAddress) with the device current; make that first call
- *     before any stream capture on that device.
- *   - Every call shares the array and overwrites all of it that it reads;
- *     calls whose copies and kernels overlap on the GPU (other streams,
- *     other host threads) race on it and must be serialised by the caller.
+ *     (cudaGetSymbolAddress) with the device current and keeps it for the
+ *     life of the process: resetting the device (cudaDeviceReset) after that
+ *     first call is not supported.
+ *   - When the plan or the precision differs from those of the previous call
+ *     on the device, the call first copies the plan's tables into the array
+ *     on `stream` from the plan's (pageable) host memory; such a copy waits
+ *     for the work already queued on `stream` before the call returns.  A
+ *     call with the same plan and precision as the previous call on the
+ *     device copies nothing and only enqueues the kernel.
+ *   - Every call shares the array and the tables stay there after the call:
+ *     calls whose copies and kernels can overlap on the GPU (on other
+ *     streams, from other host threads) race on it and must be serialised by
+ *     the caller.
  *   - A plan whose tables would not fit the 96 KiB array returns
  *     FC_ERR_UNSUPPORTED (the compiled transform lengths, up to 1080, need
  *     at most 78 KiB); arguments are checked as in fc_deriv_z.

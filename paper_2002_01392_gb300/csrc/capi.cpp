@@ -144,6 +144,8 @@ fc_status fc_setup_ex(int d, int C, int Nz, int M, int n_os, fc_plan_t* out) {
   }
   fc_plan* p = new (std::nothrow) fc_plan;
   if (!p) return FC_ERR_NOMEM;
+  static std::atomic<unsigned long long> next_serial{1};
+  p->deriv.serial = next_serial.fetch_add(1);
   FcTables T;
   if (!build_fc_tables(d, C, M, n_os, &T)) { delete p; set_error("fc_setup: table construction failed"); return FC_ERR_ARG; }
   p->data.d = d; p->data.C = C; p->data.Nz = Nz; p->data.Np = Nz + C;

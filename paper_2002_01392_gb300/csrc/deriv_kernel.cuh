@@ -34,7 +34,10 @@ namespace fcns {
 // JN: registers j >= JN of the input (indices r + L2 j) are known to be zero
 // (N' <= L2 JN, the padded case) and no output lies there, so their loads,
 // continuation checks and stores are left out at compile time.
-template <class T, int L1_, int L2_, int LINES_, int JN_ = L1_>
+// SYM: the kernels sit on the whole window |j| <= N' - 1 (L >= 2 N' - 1, or
+// L = N'), so H1 is purely imaginary and H2 purely real: the spectrum
+// products are two real multiplies per value instead of a complex multiply.
+template <class T, int L1_, int L2_, int LINES_, int JN_ = L1_, bool SYM = false>
 struct DerivPair {
   using E = Eng<T, L1_, L2_, LINES_>;
   using C = cx<T>;
@@ -70,7 +73,8 @@ struct DerivPair {
   static constexpr size_t off_E = off_b1 + sizeof(C) * E::BUF;
   static constexpr size_t smem_bytes = off_E + sizeof(C) * LINES * 2 * DMAX;
 
-  // continuation value jj of a complex line: M_r f_last + M_l f_first
+  // continuation value jj of a complex line: M_r f_last + M_l f_first, with
+  // compensated sums in both precisions (float-float / double-double)
   static DERIV_NOINLINE C cont_cplx(int jj, const C* first, const C* last, int d, int Cc, const double* Ms,
                                     const float2* Ms2) {
     if constexpr (sizeof(T) == 4) {
@@ -85,13 +89,15 @@ struct DerivPair {
       }
       return mk<T>(ff_round(re), ff_round(im));
     } else {
-      double re = 0, im = 0;
+      dd re{0.0, 0.0}, im{0.0, 0.0};
       for (int i = 0; i < d; ++i) {
         const double m1 = Ms[jj * d + i], m2 = Ms[(Cc - 1 - jj) * d + (d - 1 - i)];
-        re += m1 * last[i].x + m2 * first[i].x;
-        im += m1 * last[i].y + m2 * first[i].y;
+        dd_fma(re, m1, last[i].x);
+        dd_fma(im, m1, last[i].y);
+        dd_fma(re, m2, first[i].x);
+        dd_fma(im, m2, first[i].y);
       }
-      return mk<T>((T)re, (T)im);
+      return mk<T>((T)dd_round(re), (T)dd_round(im));
     }
   }
 
@@ -160,7 +166,12 @@ struct DerivPair {
 #pragma unroll
             for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = b1[E::bidx(r, k2, li)];
           }
-          E::mulH(R.u, o == 0 ? a.H1 : a.H2, r);
+          if constexpr (SYM) {
+            if (o == 0) E::mulH_imag(R.u, a.H1, r);
+            else E::mulH_real(R.u, a.H2, r);
+          } else {
+            E::mulH(R.u, o == 0 ? a.H1 : a.H2, r);
+          }
           E::template Bi<1>(R.u, bo, a.tw, r, li);
         }
       }

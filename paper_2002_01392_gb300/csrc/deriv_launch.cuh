@@ -9,10 +9,10 @@
 namespace fcns {
 
 
-template <class T, int L1, int L2, int LINES, int JN>
+template <class T, int L1, int L2, int LINES, int JN, bool SYM>
 fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long long lines, double Lz,
                     const void* f, void* df, void* d2f, cudaStream_t stream) {
-  using K = DerivPair<T, L1, L2, LINES, JN>;
+  using K = DerivPair<T, L1, L2, LINES, JN, SYM>;
   static_assert(K::smem_bytes <= 227 * 1024, "shared memory budget");
   typename K::Args a;
   a.f = static_cast<const T*>(f);
@@ -60,12 +60,16 @@ fc_status launch_deriv_typed(const DerivDevTables& t, const PlanData& p, int bat
                              const void* f, void* df, void* d2f, cudaStream_t stream) {
   constexpr bool F = sizeof(T) == 4;
 // the padded case (N' <= L2 (L1/2 + 1)) runs the variant whose upper input
-// registers are known zeros
-#define FC_CASE(LL, A, B, LF, LD)                                                              \
-  case LL:                                                                                     \
-    if (p.Np <= B * (A / 2 + 1))                                                               \
-      return run_deriv<T, A, B, F ? LF : LD, A / 2 + 1>(t, p, batch, lines, Lz, f, df, d2f, stream); \
-    return run_deriv<T, A, B, F ? LF : LD, A>(t, p, batch, lines, Lz, f, df, d2f, stream);
+// registers are known zeros; with L >= 2 N' - 1 (or L = N') the kernel
+// spectra are purely imaginary / real (symmetric placement, host_tables)
+  const bool sym = t.L == p.Np || t.L >= 2 * p.Np - 1;
+#define FC_CASE(LL, A, B, LF, LD)                                                                          \
+  case LL:                                                                                                 \
+    if (p.Np <= B * (A / 2 + 1))                                                                           \
+      return sym ? run_deriv<T, A, B, F ? LF : LD, A / 2 + 1, true>(t, p, batch, lines, Lz, f, df, d2f, stream) \
+                 : run_deriv<T, A, B, F ? LF : LD, A / 2 + 1, false>(t, p, batch, lines, Lz, f, df, d2f, stream); \
+    return sym ? run_deriv<T, A, B, F ? LF : LD, A, true>(t, p, batch, lines, Lz, f, df, d2f, stream)       \
+               : run_deriv<T, A, B, F ? LF : LD, A, false>(t, p, batch, lines, Lz, f, df, d2f, stream);
   switch (t.L) {
     FC_CASE(64, 8, 8, 16, 8)
     FC_CASE(96, 8, 12, 16, 8)

@@ -90,6 +90,23 @@ struct Eng {
       u[k2] = cmul(u[k2], H[k1 + L1 * k2]);
     }
   }
+  // u[k2] *= i Im(H[k1 + L1 k2]) for a purely imaginary H (odd real kernel)
+  static FC_HD void mulH_imag(C (&u)[L2], const C* H, int k1) {
+#pragma unroll
+    for (int k2 = 0; k2 < L2; ++k2) {
+      if (k2 % 6 == 0) FC_FENCE();
+      const T g = H[k1 + L1 * k2].y;
+      u[k2] = mk<T>(-g * u[k2].y, g * u[k2].x);
+    }
+  }
+  // u[k2] *= Re(H[k1 + L1 k2]) for a purely real H (even real kernel)
+  static FC_HD void mulH_real(C (&u)[L2], const C* H, int k1) {
+#pragma unroll
+    for (int k2 = 0; k2 < L2; ++k2) {
+      if (k2 % 6 == 0) FC_FENCE();
+      u[k2] = cscale(u[k2], H[k1 + L1 * k2].x);
+    }
+  }
   // inverse-direction A: thread n2 -> v[n1] = x[n2 + L2 n1]
   template <int SIGN>
   static FC_HD void Ai(C (&v)[L1], const C* buf, int n2, int li) {

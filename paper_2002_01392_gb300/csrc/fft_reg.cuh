@@ -49,6 +49,41 @@ template <int SIGN, class C> __host__ __device__ __forceinline__ C mul_si(C a) {
   if (SIGN > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
   return r;
 }
+// a * s + c for complex a, c and real s: one fused multiply-add per component
+// (one packed 2 x fp32 instruction on sm_100 family parts)
+template <class C, class S> __host__ __device__ __forceinline__ C cfma_s(C a, S s, C c) {
+  C r; r.x = a.x * s + c.x; r.y = a.y * s + c.y; return r;
+}
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+template <> __device__ __forceinline__ float2 cfma_s<float2, float>(float2 a, float s, float2 c) {
+  return __ffma2_rn(a, make_float2(s, s), c);
+}
+#endif
+// t + SIGN i s d for complex t, d and real s, as two scalar fused
+// multiply-adds (the rotation by i swaps the components, which a packed
+// instruction cannot do without extra moves)
+template <int SIGN, class C, class S> __host__ __device__ __forceinline__ C add_rot(C t, C d, S s) {
+  C r;
+#if defined(__CUDA_ARCH__)
+  if constexpr (sizeof(S) == 4) {
+    r.x = __fmaf_rn(S(-SIGN) * s, d.y, t.x);
+    r.y = __fmaf_rn(S(SIGN) * s, d.x, t.y);
+  } else {
+    r.x = fma(S(-SIGN) * s, d.y, t.x);
+    r.y = fma(S(SIGN) * s, d.x, t.y);
+  }
+#else
+  r.x = t.x + S(-SIGN) * s * d.y;
+  r.y = t.y + S(SIGN) * s * d.x;
+#endif
+  return r;
+}
+// t + SIGN i d (no scaling): two scalar adds
+template <int SIGN, class C> __host__ __device__ __forceinline__ C add_i(C t, C d) {
+  C r;
+  if (SIGN > 0) { r.x = t.x - d.y; r.y = t.y + d.x; } else { r.x = t.x + d.y; r.y = t.y - d.x; }
+  return r;
+}
 
 // ---------------------------------------------------------------------------
 // compile-time cos / sin of 2 pi num / den
@@ -109,15 +144,14 @@ template <int SIGN, class T> struct Radix<2, SIGN, T> {
 };
 template <int SIGN, class T> struct Radix<3, SIGN, T> {
   __host__ __device__ __forceinline__ static void run(cx<T>* v) {
-    constexpr T h = T(0.5);
     constexpr T s = T(0.86602540378443864676372317075294);  // sin(2 pi / 3)
     cx<T> a = v[0], b = v[1], c = v[2];
     cx<T> t1 = cadd(b, c);
-    cx<T> t2 = csub(a, cscale(t1, h));
-    cx<T> t3 = cscale(mul_si<SIGN>(csub(b, c)), s);
+    cx<T> dd = csub(b, c);
+    cx<T> t2 = cfma_s(t1, T(-0.5), a);   // a - t1 / 2
     v[0] = cadd(a, t1);
-    v[1] = cadd(t2, t3);
-    v[2] = csub(t2, t3);
+    v[1] = add_rot<SIGN>(t2, dd, s);      // t2 + SIGN i s (b - c)
+    v[2] = add_rot<-SIGN>(t2, dd, s);
   }
 };
 template <int SIGN, class T> struct Radix<4, SIGN, T> {
@@ -137,13 +171,13 @@ template <int SIGN, class T> struct Radix<5, SIGN, T> {
     cx<T> a0 = v[0];
     cx<T> p1 = cadd(v[1], v[4]), m1 = csub(v[1], v[4]);
     cx<T> p2 = cadd(v[2], v[3]), m2 = csub(v[2], v[3]);
-    cx<T> r1 = cadd(a0, cadd(cscale(p1, c1), cscale(p2, c2)));
-    cx<T> r2 = cadd(a0, cadd(cscale(p1, c2), cscale(p2, c1)));
-    cx<T> i1 = mul_si<SIGN>(cadd(cscale(m1, s1), cscale(m2, s2)));
-    cx<T> i2 = mul_si<SIGN>(csub(cscale(m1, s2), cscale(m2, s1)));
+    cx<T> r1 = cfma_s(p2, c2, cfma_s(p1, c1, a0));      // a0 + c1 p1 + c2 p2
+    cx<T> r2 = cfma_s(p2, c1, cfma_s(p1, c2, a0));      // a0 + c2 p1 + c1 p2
+    cx<T> i1 = cfma_s(m2, s2, cscale(m1, s1));          // s1 m1 + s2 m2
+    cx<T> i2 = cfma_s(m2, -s1, cscale(m1, s2));         // s2 m1 - s1 m2
     v[0] = cadd(a0, cadd(p1, p2));
-    v[1] = cadd(r1, i1); v[4] = csub(r1, i1);
-    v[2] = cadd(r2, i2); v[3] = csub(r2, i2);
+    v[1] = add_i<SIGN>(r1, i1); v[4] = add_i<-SIGN>(r1, i1);
+    v[2] = add_i<SIGN>(r2, i2); v[3] = add_i<-SIGN>(r2, i2);
   }
 };
 
@@ -283,21 +317,59 @@ struct ff {
   float hi, lo;
 };
 
-// s += (mhi + mlo) * x, exactly up to float-float rounding.
+// s += (mhi + mlo) * x, exactly up to float-float rounding.  On the device
+// every operation of the error-free product / sum is an explicitly rounded
+// intrinsic: the compiler must not contract p into the following sum (an
+// FMA there would make t differ from s.hi + p and the correction term
+// meaningless).
 __host__ __device__ __forceinline__ void ff_fma(ff& s, float mhi, float mlo, float x) {
-  const float p = mhi * x;
 #if defined(__CUDA_ARCH__)
+  const float p = __fmul_rn(mhi, x);
   const float e = __fmaf_rn(mhi, x, -p);
+  const float t = __fadd_rn(s.hi, p);
+  const float z = __fsub_rn(t, s.hi);
+  const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s.hi = t;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(__fadd_rn(err, e), __fmul_rn(mlo, x)));
 #else
+  const float p = mhi * x;
   const float e = (float)((double)mhi * (double)x - (double)p);  // exact: 48-bit product
-#endif
   const float t = s.hi + p;
   const float z = t - s.hi;
   const float err = (s.hi - (t - z)) + (p - z);
   s.hi = t;
   s.lo += err + e + mlo * x;
+#endif
 }
 
 __host__ __device__ __forceinline__ float ff_round(const ff& s) { return s.hi + s.lo; }
+
+// The same compensated sum in double (a "double-double" accumulator): the
+// float64 path's continuation product, whose weights reach 4e3 and cancel, so
+// that plain double sums would put ~1e-12 |f| of rounding into the continued
+// values, which the second derivative amplifies near the walls.
+struct dd {
+  double hi, lo;
+};
+__host__ __device__ __forceinline__ void dd_fma(dd& s, double m, double x) {
+#if defined(__CUDA_ARCH__)
+  const double p = __dmul_rn(m, x);
+  const double e = __fma_rn(m, x, -p);
+  const double t = __dadd_rn(s.hi, p);
+  const double z = __dsub_rn(t, s.hi);
+  const double err = __dadd_rn(__dsub_rn(s.hi, __dsub_rn(t, z)), __dsub_rn(p, z));
+  s.hi = t;
+  s.lo = __dadd_rn(s.lo, __dadd_rn(err, e));
+#else
+  const double p = m * x;
+  const double e = fma(m, x, -p);
+  const double t = s.hi + p;
+  const double z = t - s.hi;
+  const double err = (s.hi - (t - z)) + (p - z);
+  s.hi = t;
+  s.lo += err + e;
+#endif
+}
+__host__ __device__ __forceinline__ double dd_round(const dd& s) { return s.hi + s.lo; }
 
 }  // namespace fcns

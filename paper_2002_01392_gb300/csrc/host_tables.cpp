@@ -11,6 +11,9 @@
 #include "host_tables.hpp"
 
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace fcns {
 
@@ -353,9 +356,29 @@ static bool build_fc_tables_in(int d, int C, int M, int n_os, FcTables* out) {
 
 bool build_fc_tables(int d, int C, int M, int n_os, FcTables* out) {
   if (d < 2 || d > 10 || C < d || C > 64 || M < 1 || n_os < 1) return false;
-  // binary128 reproduces the d = 5 tables to double precision; larger d needs
-  // the double-binary128 arithmetic
-  return d <= 5 ? build_fc_tables_in<q>(d, C, M, n_os, out) : build_fc_tables_in<qq>(d, C, M, n_os, out);
+  // Double-binary128 arithmetic (~67 digits) for every (d, C): binary128
+  // alone leaves the (5, 25) fits ~17 correct digits, so about two thirds of
+  // the entries round to the neighbouring double, and the continuation's
+  // cancellation (row sums up to 1.2e4) turns those ulps into 1e-12 of the
+  // continued values.  With ~67 digits every entry is the correctly rounded
+  // double.  The tables of a (d, C, M, n_os) are built once per process.
+  static std::mutex mtx;
+  static std::map<std::tuple<int, int, int, int>, FcTables> cache;
+  const auto key = std::make_tuple(d, C, M, n_os);
+  {
+    std::lock_guard<std::mutex> lk(mtx);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *out = it->second;
+      return true;
+    }
+  }
+  FcTables T;
+  if (!build_fc_tables_in<qq>(d, C, M, n_os, &T)) return false;
+  std::lock_guard<std::mutex> lk(mtx);
+  cache.emplace(key, T);
+  *out = T;
+  return true;
 }
 
 // direct DFT helpers on binary128 with a root table
@@ -403,7 +426,12 @@ void deriv_conv_spectra(int Nz, int Np, int L, std::vector<std::complex<double>>
   }
   Roots rn(Np);
   const q twopi = 2 * q_pi();
-  const int jlo = -(Np - 1), jhi = Nz - 1;
+  // With L >= 2 N' - 1 the kernels are placed on the whole window
+  // |j| <= N' - 1 (zeros between): d1 is odd and d2 even on it, so their
+  // spectra are purely imaginary and purely real.  The outputs n < Nz only
+  // use j in [-(N'-1), Nz-1], so they are the same either way.
+  const bool sym = conv_symmetric(Np, L);
+  const int jlo = -(Np - 1), jhi = sym ? Np - 1 : Nz - 1;
   std::vector<q> d1(jhi - jlo + 1), d2(jhi - jlo + 1);
   for (int j = jlo; j <= jhi; ++j) {
     q s1 = 0, s2 = 0;
@@ -421,6 +449,11 @@ void deriv_conv_spectra(int Nz, int Np, int L, std::vector<std::complex<double>>
   }
   kernel_spectrum(d1, jlo, L, H1);
   kernel_spectrum(d2, jlo, L, H2);
+  if (sym)
+    for (int k = 0; k < L; ++k) {
+      (*H1)[k] = std::complex<double>(0.0, (*H1)[k].imag());
+      (*H2)[k] = std::complex<double>((*H2)[k].real(), 0.0);
+    }
 }
 
 void filter_conv_spectrum(int Nz, int Np, int L, double beta, double two_p,
@@ -438,7 +471,10 @@ void filter_conv_spectrum(int Nz, int Np, int L, double beta, double two_p,
     for (int l = 0; l < Np; ++l) (*Hf)[l] = std::complex<double>((double)(fz[l] / (q)Np), 0.0);
     return;
   }
-  const int jlo = -(Np - 1), jhi = Nz - 1;
+  // symmetric placement as in deriv_conv_spectra: the kernel is even, its
+  // spectrum real
+  const bool sym = conv_symmetric(Np, L);
+  const int jlo = -(Np - 1), jhi = sym ? Np - 1 : Nz - 1;
   std::vector<q> h(jhi - jlo + 1);
   for (int j = jlo; j <= jhi; ++j) {
     q s = 0;
@@ -450,6 +486,8 @@ void filter_conv_spectrum(int Nz, int Np, int L, double beta, double two_p,
     h[j - jlo] = s / (q)Np;
   }
   kernel_spectrum(h, jlo, L, Hf);
+  if (sym)
+    for (int k = 0; k < L; ++k) (*Hf)[k] = std::complex<double>((*Hf)[k].real(), 0.0);
 }
 
 void z_kernels_real(int Nz, int Np, double beta, double two_p, std::vector<double>* d2, std::vector<double>* hf) {

@@ -16,14 +16,23 @@ struct FcTables {
 // M_r = A_r Q_r^T.  Returns false on invalid sizes.
 bool build_fc_tables(int d, int C, int M, int n_os, FcTables* out);
 
+// Whether the circular kernels of the z operators can be placed on the whole
+// symmetric window |j| <= N' - 1 (L >= 2 N' - 1) or are the multipliers of
+// length N' itself (L = N'): then the spectra of the derivative kernels are
+// purely imaginary (d/dz) and purely real (d2/dz2, the filter).
+inline bool conv_symmetric(int Np, int L) { return L == Np || L >= 2 * Np - 1; }
+
 // Spectra (length L, with 1/L) of the circular kernels of d/dz and d2/dz2 on
 // the N'-periodic unit grid (first Nz outputs valid).  L >= N' + Nz - 1
 // (padded circular convolution) or L = N' (the multipliers i k, -k^2 / N').
+// When conv_symmetric(N', L), H1 has zero real parts and H2 zero imaginary
+// parts.
 void deriv_conv_spectra(int Nz, int Np, int L, std::vector<std::complex<double>>* H1,
                         std::vector<std::complex<double>>* H2);
 
 // Spectrum (length L, with 1/L) of the circular kernel of the z filter
-// fz(l) = exp(-beta (|l_s| / (N'/2))^{2p}) on the N'-periodic grid.
+// fz(l) = exp(-beta (|l_s| / (N'/2))^{2p}) on the N'-periodic grid (real
+// when conv_symmetric(N', L)).
 void filter_conv_spectrum(int Nz, int Np, int L, double beta, double two_p,
                           std::vector<std::complex<double>>* Hf);
 

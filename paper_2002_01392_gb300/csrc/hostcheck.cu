@@ -12,10 +12,10 @@
 
 namespace fcns {
 
-template <class T, int L1, int L2, int LINES, int JN>
-static int emu_deriv(const double* Mr, int d, int Cc, int Nz, int batch, long long lines, double Lz,
-                     const T* f, T* df, T* d2f) {
-  using K = DerivPair<T, L1, L2, LINES, JN>;
+template <class T, int L1, int L2, int LINES, int JN, bool SYM>
+static int emu_deriv_k(const double* Mr, int d, int Cc, int Nz, int batch, long long lines, double Lz,
+                       const T* f, T* df, T* d2f) {
+  using K = DerivPair<T, L1, L2, LINES, JN, SYM>;
   const int L = L1 * L2;
   std::vector<std::complex<double>> H1, H2, tw;
   deriv_conv_spectra(Nz, Nz + Cc, L, &H1, &H2);
@@ -41,6 +41,16 @@ static int emu_deriv(const double* Mr, int d, int Cc, int Nz, int batch, long lo
   a.pf_dist = 3;
   phased_emulate<K>(a, a.tiles * batch, K::smem_bytes);
   return 0;
+}
+
+// the variant fc_deriv_z launches: symmetric kernel spectra when L >= 2 N' - 1 or L = N'
+template <class T, int L1, int L2, int LINES, int JN>
+static int emu_deriv(const double* Mr, int d, int Cc, int Nz, int batch, long long lines, double Lz,
+                     const T* f, T* df, T* d2f) {
+  const int L = L1 * L2, Np = Nz + Cc;
+  if (L == Np || L >= 2 * Np - 1)
+    return emu_deriv_k<T, L1, L2, LINES, JN, true>(Mr, d, Cc, Nz, batch, lines, Lz, f, df, d2f);
+  return emu_deriv_k<T, L1, L2, LINES, JN, false>(Mr, d, Cc, Nz, batch, lines, Lz, f, df, d2f);
 }
 
 }  // namespace fcns

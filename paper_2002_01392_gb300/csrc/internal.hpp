@@ -54,6 +54,7 @@ struct PlanData {
 
 // host copies of the derivative tables of one plan, in both precisions
 struct PlanHostTables {
+  unsigned long long serial = 0;  // unique per plan in the process (never reused)
   int L = 0, L1 = 0, L2 = 0;
   std::vector<std::complex<double>> tw;
   std::vector<float2> tw32, Mr2, H1_32, H2_32;

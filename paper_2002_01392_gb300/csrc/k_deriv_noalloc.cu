@@ -1,16 +1,18 @@
 // fc_deriv_z_noalloc: fc_deriv_z without any device allocation.
 //
-// fc_deriv_z keeps its continuation matrix, kernel spectrum and twiddles in
+// fc_deriv_z keeps its continuation matrix, kernel spectra and twiddles in
 // device memory that the library allocates with cudaMalloc the first time a
 // plan is used on a device.  Some callers cannot have the library allocate:
-// code running while a CUDA graph is being captured (cudaMalloc is not
-// capturable), applications whose device memory is owned by a host framework
-// or a fixed-size arena and that forbid allocations by plug-ins, and
-// latency-critical loops that cannot afford cudaMalloc's implicit device
-// synchronisation.  This entry point instead keeps those tables in one
-// file-scope static device array of fixed size (kNoAllocBytes = 96 KiB, reserved by
-// every GPU that loads the library until the process exits) and copies the
-// plan's tables into it on the caller's stream before every launch.
+// applications whose device memory belongs to a host framework or to a
+// fixed-size arena and that forbid allocations by plug-ins, and programs run
+// under a device-memory budget that a library must not grow.  This entry point
+// instead keeps those tables in one file-scope static device array of fixed
+// size (kNoAllocBytes = 96 KiB, reserved by every GPU that loads the library
+// until the process exits).  A call whose plan and precision differ from the
+// tables the array holds on this device copies the plan's tables into it on
+// the caller's stream first; a call with the same plan and precision as the
+// previous call on the device launches the kernel at once.
+#include <mutex>
 #include <mutex>
 
 #include "internal.hpp"
@@ -26,6 +28,10 @@ static __device__ __align__(256) unsigned char g_deriv_scratch[kNoAllocBytes];
 
 std::mutex g_mtx;
 void* g_scratch_addr[kMaxDevices] = {};
+// which tables the array holds per device: the plan's serial number and the
+// precision of the last upload (0: none, or an upload that failed part-way)
+unsigned long long g_loaded_serial[kMaxDevices] = {};
+int g_loaded_dtype[kMaxDevices] = {};
 
 // Device address of g_deriv_scratch on the current device (the host-side
 // symbol is only a stand-in and must never be passed to a kernel).
@@ -71,16 +77,25 @@ extern "C" fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batc
   s = scratch_address(dev, &base);
   if (s) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  const void* H1src = dtype == FC_F32 ? (const void*)h.H1_32.data() : (const void*)h.H1_64.data();
-  const void* H2src = dtype == FC_F32 ? (const void*)h.H2_32.data() : (const void*)h.H2_64.data();
-  const void* Tsrc = dtype == FC_F32 ? (const void*)h.tw32.data() : (const void*)h.tw64.data();
-  // every table is overwritten in full, so nothing left by an earlier call is read
-  s = cuda_status(cudaMemcpyAsync(base + oMr, plan->data.Mr.data(), sizeof(double) * nMr, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(Mr)");
-  if (!s) s = cuda_status(cudaMemcpyAsync(base + oMr2, h.Mr2.data(), sizeof(float2) * nMr, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(Mr2)");
-  if (!s) s = cuda_status(cudaMemcpyAsync(base + oH1, H1src, cs * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(H1)");
-  if (!s) s = cuda_status(cudaMemcpyAsync(base + oH2, H2src, cs * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(H2)");
-  if (!s) s = cuda_status(cudaMemcpyAsync(base + oTw, Tsrc, cs * 2 * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(tw)");
-  if (s) return s;
+  {
+    std::lock_guard<std::mutex> lk(g_mtx);
+    if (g_loaded_serial[dev] != h.serial || g_loaded_dtype[dev] != (int)dtype) {
+      g_loaded_serial[dev] = 0;
+      const void* H1src = dtype == FC_F32 ? (const void*)h.H1_32.data() : (const void*)h.H1_64.data();
+      const void* H2src = dtype == FC_F32 ? (const void*)h.H2_32.data() : (const void*)h.H2_64.data();
+      const void* Tsrc = dtype == FC_F32 ? (const void*)h.tw32.data() : (const void*)h.tw64.data();
+      // every table the kernel reads is overwritten in full, so nothing left
+      // by an earlier call with other tables is read
+      s = cuda_status(cudaMemcpyAsync(base + oMr, plan->data.Mr.data(), sizeof(double) * nMr, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(Mr)");
+      if (!s) s = cuda_status(cudaMemcpyAsync(base + oMr2, h.Mr2.data(), sizeof(float2) * nMr, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(Mr2)");
+      if (!s) s = cuda_status(cudaMemcpyAsync(base + oH1, H1src, cs * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(H1)");
+      if (!s) s = cuda_status(cudaMemcpyAsync(base + oH2, H2src, cs * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(H2)");
+      if (!s) s = cuda_status(cudaMemcpyAsync(base + oTw, Tsrc, cs * 2 * h.L, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(tw)");
+      if (s) return s;
+      g_loaded_serial[dev] = h.serial;
+      g_loaded_dtype[dev] = (int)dtype;
+    }
+  }
   DerivDevTables t;
   t.device = dev;
   t.L = h.L;

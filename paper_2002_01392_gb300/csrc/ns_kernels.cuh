@@ -96,7 +96,8 @@ constexpr int MRMAX = 640;
 
 // C continuation value jj (point Nz + jj) of a complex line from its first /
 // last d values (Sec. 3 continuation formula; right matrix M_r, left matrix
-// its row/column reversal).  float32: compensated float-float products.
+// its row/column reversal), with compensated sums: float-float products in
+// float32, double-double in float64 (the weights reach 4e3 and cancel).
 template <class T>
 FC_NOINLINE cx<T> continuation_value(int jj, const cx<T>* first, const cx<T>* last, int d, int Cc,
                                      const double* Ms, const float2* Ms2) {
@@ -112,14 +113,16 @@ FC_NOINLINE cx<T> continuation_value(int jj, const cx<T>* first, const cx<T>* la
     }
     return mk<T>(ff_round(re), ff_round(im));
   } else {
-    double re = 0, im = 0;
+    dd re{0.0, 0.0}, im{0.0, 0.0};
     for (int i = 0; i < d; ++i) {
       const double m1 = Ms[jj * d + i];
       const double m2 = Ms[(Cc - 1 - jj) * d + (d - 1 - i)];
-      re += m1 * last[i].x + m2 * first[i].x;
-      im += m1 * last[i].y + m2 * first[i].y;
+      dd_fma(re, m1, last[i].x);
+      dd_fma(im, m1, last[i].y);
+      dd_fma(re, m2, first[i].x);
+      dd_fma(im, m2, first[i].y);
     }
-    return mk<T>((T)re, (T)im);
+    return mk<T>((T)dd_round(re), (T)dd_round(im));
   }
 }
 
@@ -199,7 +202,9 @@ struct KZDeriv {
 #pragma unroll
             for (int k2 = 0; k2 < L2; ++k2) R.u[k2] = b1[E::bidx(r, k2, li)];
           }
-          E::mulH(R.u, o == 0 ? a.t.H1 : a.t.H2, r);
+          // the NS lengths satisfy L >= 2 N' - 1 (or L = N'): H1 imaginary, H2 real
+          if (o == 0) E::mulH_imag(R.u, a.t.H1, r);
+          else E::mulH_real(R.u, a.t.H2, r);
           E::template Bi<1>(R.u, o == 0 ? b0 : b1, a.t.tw, r, li);
         }
       }
@@ -313,7 +318,7 @@ struct KZCombine {
     } else if constexpr (P == 2) {
       if (r < L1) {
         E::template B<-1>(R.u, b0, r, li);
-        E::mulH(R.u, a.t.Hf, r);
+        E::mulH_real(R.u, a.t.Hf, r);   // even filter kernel: real spectrum
         E::template Bi<1>(R.u, b0, a.t.tw, r, li);
       }
     } else if constexpr (P == 3) {
@@ -1356,13 +1361,15 @@ struct KMean {
     const int Nz = a.g.Nz, Np = a.g.Np, d = a.g.d, Cc = a.g.Cc;
     const int jlo = -(Np - 1);
     auto cont = [&](const double2* x, int jj) {
-      double re = 0, im = 0;
+      dd re{0.0, 0.0}, im{0.0, 0.0};
       for (int i = 0; i < d; ++i) {
         const double m1 = a.Mr[jj * d + i], m2 = a.Mr[(Cc - 1 - jj) * d + (d - 1 - i)];
-        re += m1 * x[Nz - d + i].x + m2 * x[i].x;
-        im += m1 * x[Nz - d + i].y + m2 * x[i].y;
+        dd_fma(re, m1, x[Nz - d + i].x);
+        dd_fma(im, m1, x[Nz - d + i].y);
+        dd_fma(re, m2, x[i].x);
+        dd_fma(im, m2, x[i].y);
       }
-      return make_double2(re, im);
+      return make_double2(dd_round(re), dd_round(im));
     };
     if constexpr (P == 0) {
       const C* src = a.NL + lay(f, 0, 0, Nz, a.g.ntiles);

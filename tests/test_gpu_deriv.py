@@ -19,13 +19,26 @@ def api():
     return a
 
 
+def _wall_rows_error(out, ref, xext, kmax, order, axis):
+    """Largest error on the wall rows (z index 0 and Nz - 1, where the
+    continuation acts) in the pointwise form of the rounding model: relative to
+    max |x_ext| k_max^p."""
+    o = np.moveaxis(np.asarray(out, dtype=np.float64), axis, 0)
+    r = np.moveaxis(ref, axis, 0)
+    worst = max(np.abs(o[0] - r[0]).max(), np.abs(o[-1] - r[-1]).max())
+    return float(worst / (np.abs(xext).max() * kmax ** order))
+
+
 def _check(out, f64, Mr, Nz, order, dtype):
     ref = fc.fc_deriv_z(f64, 1.0, Mr, order, axis=-3)
-    xnorm = np.linalg.norm(fc.extend(f64, Mr, axis=-3))
+    xext = fc.extend(f64, Mr, axis=-3)
+    xnorm = np.linalg.norm(xext)
     kmax = np.pi * (Nz - 1)
     amp = fc_amplification(Mr)
     en = normalized_error(out, ref, xnorm, kmax, order)
     assert en < amp * norm_bound(dtype, Nz), (order, en)
+    ew = _wall_rows_error(out, ref, xext, kmax, order, axis=-3)
+    assert ew < amp * norm_bound(dtype, Nz), (order, ew)
     if dtype == np.float64:
         rel = rel_l2(out, ref)
         assert rel < amp * rel_bound_f64(order, Nz + Mr.shape[0]), (order, rel)
@@ -124,6 +137,9 @@ def test_full_size_sampled_lines(api, Mr_5_25, dtype):
         xnorm = np.linalg.norm(fc.extend(lines, Mr_5_25, axis=0))
         en = normalized_error(out, ref, xnorm, np.pi * (Nz - 1), order)
         assert en < norm_bound(dtype, Nz), (order, en)
+        xext = fc.extend(lines, Mr_5_25, axis=0)
+        ew = _wall_rows_error(out, ref, xext, np.pi * (Nz - 1), order, axis=0)
+        assert ew < norm_bound(dtype, Nz), (order, ew)
         if dtype == np.float64:
             assert rel_l2(out, ref) < rel_bound_f64(order, Nz + 25)
 

@@ -355,6 +355,61 @@ def test_diagnostics_boussinesq(api):
     sim.close()
 
 
+@pytest.mark.parametrize("kind,N,Nz", [("rb", 32, 33), ("rb", 128, 129), ("channel", 64, 65)])
+def test_diagnostics_float32_errors(api, kind, N, Nz):
+    """Error of every float32 diagnostic against the FP64 oracle after one RK3
+    step (Sec. 6 and 7 diagnostics), on the scale where it is meaningful.
+    Flow rate and Nusselt number come from the (kx, ky) = (0, 0) line, which
+    the float32 path carries in float64: relative error <= 1e-7 (flow rate;
+    the nonlinear term that feeds the mean line is float32) and absolute
+    <= 1e-9 (Nu ~ 1).  Horizontal-mean, r.m.s. and shell-spectrum profiles:
+    <= 1e-6 of their largest value (float32 products over the grid).  The
+    divergence and the wall mean squares of u and w are quadratic in
+    quantities that vanish in the exact solution, so in float32 they sit at
+    the rounding floor: each is within (eps32 v_max k_z,max)^2 (divergence) or
+    (eps32 v_max)^2 (wall values) of the oracle, plus 1e-3 relative for the
+    wall slip of the Boussinesq runs, which is above that floor (measured:
+    flow rate 1.3e-8 - 3.1e-8, Nu 2e-12 - 1.3e-11, profiles <= 2e-7, wall slip
+    0.12 - 0.28 %)."""
+    eps = float(np.finfo(np.float32).eps)
+    if kind == "rb":
+        kw = dict(nu=3.162e-3, kappa=3.162e-3, gamma=1.0, nfields=4)
+        f = synth.boussinesq_fields(N, N, Nz, amp=1e-1)
+        f[0] += 0.3 * (synth.z_grid(Nz) * (1 - synth.z_grid(Nz)))[:, None, None]
+        dt = 2e-3
+    else:
+        kw = dict(nu=1e-2, forcing_x=0.1)
+        f = synth.channel_velocity(N, N, Nz, nu=1e-2)
+        dt = 1e-3
+    f = f.astype(np.float32).astype(np.float64)
+    P = ns.Params(N, N, Nz, **kw)
+    sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, prec="f32", **kw))
+    sim.set_fields(_cuda(f, torch.float32))
+    sim.step(dt)
+    d = sim.diagnostics()
+    pr = sim.profiles()
+    sim.close()
+    _, _, st = _oracle_steps(f, P, dt, 1)
+    vmax = float(np.abs(f[:3]).max())
+    kz_max = np.pi * (Nz - 1)
+    div = (ns.divergence_phys(st, P) ** 2).mean()
+    wu, _, ww = ns.wall_mean_squares(st, P)
+    assert abs(d["flow_rate"] - ns.flow_rate(st, P)) <= 1e-7 * abs(ns.flow_rate(st, P))
+    if kind == "rb":
+        nb, nt = ns.nusselt(st, P)
+        assert abs(d["nusselt"] - 0.5 * (nb + nt)) <= 1e-9
+        assert abs(d["wall_u_ms"] - wu) <= 1e-3 * wu + (eps * vmax) ** 2
+    else:
+        assert abs(d["wall_u_ms"] - wu) <= (eps * vmax) ** 2
+    assert abs(d["wall_w_ms"] - ww) <= (eps * vmax) ** 2
+    assert abs(d["div_ms"] - div) <= (eps * vmax * kz_max) ** 2
+    mean, rms = ns.profiles(st, P)
+    E, _ = ns.shell_spectrum(st, P)
+    assert np.abs(pr["mean"] - mean).max() <= 1e-6 * np.abs(mean).max()
+    assert np.abs(pr["rms"] - rms).max() <= 1e-6 * rms.max()
+    assert np.abs(pr["spectrum"] - E).max() <= 1e-6 * E.max()
+
+
 def test_float32_mean_flow_island_long_run(api):
     """2000 float32 RK3 steps of a decaying mean profile u = 0.5 sin(pi z) with
     weak fluctuations: the mean-flow line, accumulated in float64, stays within

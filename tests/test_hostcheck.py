@@ -65,7 +65,7 @@ def test_deriv_kernel_phases_match_oracle(hc, Mr_5_25, Nz, L, Nx, Ny, B, dtype):
         assert en < norm_bound(npdt, Nz), (order, en)
         if dtype == 1:
             rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
-            assert rel < 1e-11 * max(1.0, (Np / 128) ** (2 * (order - 1))), (order, rel)
+            assert rel < rel_bound_f64(order, Np), (order, rel)
 
 
 def test_deriv_kernel_converges_to_exact_derivative(hc, Mr_5_25):

@@ -1,12 +1,15 @@
 """fc_deriv_z_noalloc: the allocation-free variant of fc_deriv_z.
 
-Some callers cannot let a library call cudaMalloc (graph capture in
-progress, device memory owned by a host framework, latency-critical loops).
-For them fc_deriv_z_noalloc keeps the plan's tables in a fixed static device
-array instead of library-allocated device memory.  This file checks, through
-the C ABI, that it returns what fc_deriv_z returns, on two calls in a row
-with different plans (so the second call must have replaced the first call's
-tables).  It is named to run after every other test file.
+Some callers cannot let a library call cudaMalloc: applications whose device
+memory belongs to a host framework or to a fixed arena, and programs run
+under a device-memory budget.  For them fc_deriv_z_noalloc keeps the plan's
+tables in a fixed static device array instead of library-allocated device
+memory.  This file checks, through the C ABI, that its outputs are bitwise
+those of fc_deriv_z (the same kernel on the same tables), on calls in a row
+with different plans (each must replace the previous call's tables) and with
+the same plan again (the tables are already in place and nothing is copied),
+and that those calls allocate no device memory.  It is named to run after
+every other test file.
 """
 import ctypes
 
@@ -14,7 +17,6 @@ import numpy as np
 import pytest
 
 import synth
-from numerics import norm_bound
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -39,9 +41,8 @@ def _call(api, name, plan, f, d1, d2):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
-def test_noalloc_matches_fc_deriv_z_on_two_calls(api, dtype):
+def test_noalloc_matches_fc_deriv_z_on_calls_in_a_row(api, dtype):
     cases = [(129, 40, 6, 2), (513, 33, 8, 1)]          # two plans: different tables
-    outs = []
     inputs = []
     for Nz, Nx, Ny, B in cases:
         sf = synth.SeparableField(Nx, Ny, Nz, seed_offset=Nz)
@@ -49,19 +50,31 @@ def test_noalloc_matches_fc_deriv_z_on_two_calls(api, dtype):
         base = sf.field(0) + np.sin(3 * z + 1)[:, None, None]
         f = torch.from_numpy(np.stack([base * (b + 1) for b in range(B)])).to("cuda", dtype)
         inputs.append((api.Plan(5, 25, Nz), f))
-    # two no-alloc calls in a row, then the reference entry point
-    for plan, f in inputs:
-        d1, d2 = torch.empty_like(f), torch.empty_like(f)
-        _call(api, "fc_deriv_z_noalloc", plan, f, d1, d2)
-        outs.append((d1, d2))
+    outs = [(torch.empty_like(f), torch.empty_like(f)) for _, f in inputs]
+    again = (torch.empty_like(inputs[1][1]), torch.empty_like(inputs[1][1]))
     torch.cuda.synchronize()
+    # set-up calls on this device: resolve the array's address and load both
+    # kernels (lazy module loading may take device memory for their code)
+    for (plan, f), (o1, o2) in zip(inputs, outs):
+        _call(api, "fc_deriv_z_noalloc", plan, f, o1, o2)
+    for o1, o2 in outs + [again]:
+        o1.fill_(np.nan)
+        o2.fill_(np.nan)
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    # two calls in a row with different plans (each replaces the other's
+    # tables), then the same plan again (nothing to copy)
+    for (plan, f), (o1, o2) in zip(inputs, outs):
+        _call(api, "fc_deriv_z_noalloc", plan, f, o1, o2)
+    _call(api, "fc_deriv_z_noalloc", inputs[1][0], inputs[1][1], *again)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    # the reference entry point (allocates its own tables on first use)
     for (plan, f), (n1, n2) in zip(inputs, outs):
         r1, r2 = torch.empty_like(f), torch.empty_like(f)
         _call(api, "fc_deriv_z", plan, f, r1, r2)
         torch.cuda.synchronize()
-        Nz = f.shape[1]
-        kmax = np.pi * (Nz - 1)
-        fnorm = float(f.double().norm())
-        for o, (a, b) in enumerate(((n1, r1), (n2, r2)), start=1):
-            err = float((a.double() - b.double()).norm()) / (fnorm * kmax ** o)
-            assert err <= norm_bound(np.float32 if dtype == torch.float32 else np.float64, Nz), (o, err)
+        assert torch.equal(n1, r1) and torch.equal(n2, r2)
+        if plan is inputs[1][0]:
+            assert torch.equal(again[0], r1) and torch.equal(again[1], r2)
