@@ -10,6 +10,15 @@ in flight (requests of one simulation keep their arrival order; different
 simulations overlap on the device).  Completion is observed with CUDA events,
 so latencies are arrival-to-completion on the host clock.
 
+Simulations can also arrive and leave while the loop runs: an "admit"
+request (params, initial fields, and a name in ``sim``) creates the
+simulation as soon as its workspace fits in what the resident simulations
+leave of the HBM budget, waiting for releases if it does not fit yet; a
+"release" request frees a simulation once its earlier requests are done.
+Later requests may name a simulation admitted mid-run by the name of its
+admission; they wait for it.  An admission that can never fit (nothing left
+to release) fails with FC_ERR_NOMEM.
+
 Errors: a request whose call fails with FC_ERR_CUDA, FC_ERR_NOMEM or
 FC_ERR_TIMEOUT is requeued at the head of the queue, up to ``max_retries``
 times (a failing call enqueues nothing that changes the simulation's state:
@@ -34,8 +43,8 @@ from . import api
 
 @dataclasses.dataclass
 class Request:
-    kind: str                 # "rhs" | "project" | "step"
-    sim: int                  # resident simulation id
+    kind: str                 # "rhs" | "project" | "step" | "admit" | "release"
+    sim: object               # resident simulation id, or the name given at its mid-run admission
     arrival: float = 0.0      # seconds from the start of the run
     dt: float = 1e-3
     inp: object = None        # device tensor for rhs / project (physical fields)
@@ -44,6 +53,9 @@ class Request:
     t_done: float = -1.0
     attempts: int = 0         # retries taken
     error: str | None = None  # status name when the request failed
+    params: object = None     # "admit": the simulation's ns_params (inp: its initial fields or None)
+    points: int = 0           # grid points of the simulation it ran on (set at launch)
+    sid: int | None = None    # the simulation id it ran on (set at launch)
 
 
 RETRYABLE = ("FC_ERR_CUDA", "FC_ERR_NOMEM", "FC_ERR_TIMEOUT")
@@ -75,6 +87,9 @@ class Server:
         self.streams = [cuda.Stream() for _ in range(slots)]
         self.busy: list[tuple[Request, object] | None] = [None] * slots
         self.inflight_sims: set[int] = set()
+        self.names: dict = {}          # name of a mid-run admission -> simulation id
+        self.admitted_midrun = 0
+        self.released_midrun = 0
 
     # -- admission -------------------------------------------------------
     def admit(self, params, fields=None) -> int | None:
@@ -104,12 +119,13 @@ class Server:
         sim.close()
 
     # -- execution -------------------------------------------------------
-    def _launch(self, r: Request, slot: int, t0: float):
+    def _launch(self, r: Request, slot: int, t0: float, sid: int):
         """Enqueue r on stream ``slot``; returns the library error of the call
         (nothing is marked busy then) or None."""
         cuda = self.cuda
         s = self.streams[slot]
-        sim = self.sims[r.sim]
+        sim = self.sims[sid]
+        r.points = self.points[sid]
         h = cuda.current_stream()
         s.wait_stream(h)                    # inputs written on the caller's stream
         try:
@@ -128,7 +144,8 @@ class Server:
             return e
         r.t_start = time.perf_counter() - t0
         self.busy[slot] = (r, ev)
-        self.inflight_sims.add(r.sim)
+        self.inflight_sims.add(sid)
+        r.sid = sid
         return None
 
     def _fail(self, r: Request, name: str, t0: float, done: list):
@@ -136,7 +153,9 @@ class Server:
         r.t_done = time.perf_counter() - t0
         self.failed += 1
         if name == "FC_ERR_NONFINITE":
-            self.quarantined.add(r.sim)
+            sid = self._resolve(r)
+            if sid is not None:
+                self.quarantined.add(sid)
         done.append(r)
 
     def _reap(self, t0: float, done: list):
@@ -145,8 +164,32 @@ class Server:
                 r = b[0]
                 r.t_done = time.perf_counter() - t0
                 done.append(r)
-                self.inflight_sims.discard(r.sim)
+                self.inflight_sims.discard(r.sid)
                 self.busy[k] = None
+
+    def _resolve(self, r: Request):
+        """The simulation id a request refers to (None: named, not admitted yet)."""
+        if r.kind == "admit":
+            return None
+        if isinstance(r.sim, int) and r.sim in self.sims:
+            return r.sim
+        return self.names.get(r.sim)
+
+    def _admit_or_release(self, r: Request, sid, t0: float, done: list) -> bool:
+        """Handle an "admit" / "release" request now if it can run; returns
+        False if it must wait (admission: not enough budget yet)."""
+        if r.kind == "admit":
+            if self.used + self.lib.ns_workspace_bytes(r.params) > self.budget:
+                return False
+            new = self.admit(r.params, r.inp)
+            self.names[r.sim] = new
+            self.admitted_midrun += 1
+        else:
+            self.release(sid)
+            self.released_midrun += 1
+        r.t_start = r.t_done = time.perf_counter() - t0
+        done.append(r)
+        return True
 
     def run(self, requests: list[Request]) -> dict:
         """Serve the requests (sorted by arrival time) in real time; returns
@@ -163,22 +206,39 @@ class Server:
                 pending.append(reqs[i])
                 i += 1
             self._reap(t0, done)
-            # dispatch in arrival order; a request waits while its simulation is in flight
-            blocked: set[int] = set()
+            # dispatch in arrival order; a request waits while its simulation is in
+            # flight, or (named) not admitted yet, or behind an earlier request for it
+            blocked: set = set()
+            progress = False
             for _ in range(len(pending)):
                 r = pending.popleft()
-                if r.sim in self.inflight_sims or r.sim in blocked:
-                    blocked.add(r.sim)
+                key = r.sim
+                sid = self._resolve(r)
+                if sid is None and r.kind != "admit" and isinstance(key, int):
+                    self._fail(r, "FC_ERR_STATE", t0, done)     # no such resident simulation
+                    progress = True
+                    continue
+                if key in blocked or (sid is not None and sid in self.inflight_sims) or \
+                        (sid is None and r.kind != "admit"):
+                    blocked.add(key)
                     pending.append(r)
                     continue
-                if r.sim in self.quarantined:
+                if r.kind in ("admit", "release"):
+                    if self._admit_or_release(r, sid, t0, done):
+                        progress = True
+                    else:
+                        blocked.add(key)
+                        pending.append(r)
+                    continue
+                if sid in self.quarantined:
                     self._fail(r, "FC_ERR_NONFINITE", t0, done)
                     continue
                 free = next((k for k, b in enumerate(self.busy) if b is None), None)
                 if free is None:
                     pending.appendleft(r)
                     break
-                err = self._launch(r, free, t0)
+                err = self._launch(r, free, t0, sid)
+                progress = True
                 if err is None:
                     continue
                 if err.name in RETRYABLE and r.attempts < self.max_retries:
@@ -187,16 +247,24 @@ class Server:
                     pending.appendleft(r)
                 else:
                     self._fail(r, err.name, t0, done)
+            # nothing in flight, nothing still to arrive and nothing dispatched in
+            # this pass: what is left waits for an admission that cannot fit
+            # (FC_ERR_NOMEM) or names a simulation never admitted (FC_ERR_STATE)
+            if pending and not progress and i == len(reqs) and all(b is None for b in self.busy):
+                for r in list(pending):
+                    pending.remove(r)
+                    self._fail(r, "FC_ERR_NOMEM" if r.kind == "admit" else "FC_ERR_STATE", t0, done)
         wall = time.perf_counter() - t0
-        ok = [r for r in done if r.error is None]
+        ok = [r for r in done if r.error is None and r.kind not in ("admit", "release")]
         lat = sorted(r.t_done - r.arrival for r in ok) or [0.0]
-        pts = sum(self.points[r.sim] * (3 if r.kind == "step" else 1) for r in ok)
+        pts = sum(r.points * (3 if r.kind == "step" else 1) for r in ok)
         pick = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))]
         return {"requests": len(done), "wall_s": wall, "p50_latency_ms": pick(0.5) * 1e3,
                 "p99_latency_ms": pick(0.99) * 1e3, "grid_points_per_s": pts / wall,
                 "requests_per_s": len(ok) / wall, "rejected_admissions": self.rejected,
                 "failed": self.failed, "retried": self.retried, "quarantined": len(self.quarantined),
-                "resident": len(self.sims), "hbm_used_GB": self.used / 1e9}
+                "resident": len(self.sims), "hbm_used_GB": self.used / 1e9,
+                "admitted_midrun": self.admitted_midrun, "released_midrun": self.released_midrun}
 
     def close(self):
         for sid in list(self.sims):

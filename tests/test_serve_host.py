@@ -157,3 +157,31 @@ def test_nonfinite_quarantines_and_other_errors_fail_at_once(serve):
     assert reqs[4].error == "FC_ERR_ARG" and reqs[4].attempts == 0
     assert reqs[5].error is None
     assert stats["quarantined"] == 1 and stats["failed"] == 4 and stats["retried"] == 0
+
+
+def test_admission_and_release_while_running(serve):
+    """A simulation that arrives while the loop runs is admitted once a release
+    frees enough of the budget; requests naming it wait for it; a release waits
+    for the simulation's earlier requests; an admission that can never fit
+    fails with FC_ERR_NOMEM and requests naming it with FC_ERR_STATE, as do
+    requests for a simulation already released."""
+    srv = _server(serve, budget=100)
+    a = srv.admit(FakeParams(60))
+    reqs = [serve.Request(kind="step", sim=a, arrival=0.0, dt=1.0),
+            serve.Request(kind="admit", sim="B", arrival=0.0, params=FakeParams(60)),
+            serve.Request(kind="step", sim="B", arrival=0.0, dt=2.0),
+            serve.Request(kind="release", sim=a, arrival=0.0),
+            serve.Request(kind="step", sim="B", arrival=0.0, dt=3.0),
+            serve.Request(kind="admit", sim="C", arrival=0.0, params=FakeParams(200)),
+            serve.Request(kind="step", sim="C", arrival=0.0),
+            serve.Request(kind="step", sim=a, arrival=0.001)]
+    stats = srv.run(reqs)
+    assert [r.error for r in reqs[:5]] == [None] * 5
+    b = srv.names["B"]
+    assert [w for (s, w) in FakeLib.log if s == a] == [("step", 1.0)]
+    assert [w for (s, w) in FakeLib.log if s == b] == [("step", 2.0), ("step", 3.0)]
+    assert reqs[5].error == "FC_ERR_NOMEM" and reqs[6].error == "FC_ERR_STATE"
+    assert reqs[7].error == "FC_ERR_STATE"
+    assert stats["admitted_midrun"] == 1 and stats["released_midrun"] == 1
+    assert srv.used == 60 and list(srv.sims) == [b]
+    srv.close()
