@@ -116,7 +116,10 @@ fc_status fc_destroy(fc_plan_t plan);
  *          At least one of df, d2f must be non-NULL; outputs must not
  *          overlap f.
  *   stream CUDA stream for the launch.
- * Needs no workspace.  FC_ERR_UNSUPPORTED when N' + Nz - 1 exceeds 1080.
+ * Needs no workspace.  Transform length: N' itself when it is a compiled
+ * smooth length (64, 128, 256, 512, 768, 1024, 1536), else the smallest
+ * compiled length >= N' + Nz - 1 (up to 1536); FC_ERR_UNSUPPORTED when
+ * neither exists.
  */
 fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
                      const void* f, void* df, void* d2f, fc_stream_t stream);
@@ -132,7 +135,7 @@ fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, 
  * variant of fc_deriv_z, and its results are bitwise those of fc_deriv_z.
  *   - Calls no cudaMalloc, cudaFree or other allocating routine.  The plan's
  *     tables (continuation matrix, kernel spectra, twiddles) live in one
- *     fixed 96 KiB static device array that every GPU loading the library
+ *     fixed 128 KiB static device array that every GPU loading the library
  *     reserves until the process exits.
  *   - The first call on each device looks up that array's device address
  *     (cudaGetSymbolAddress) with the device current and keeps it for the
@@ -148,9 +151,10 @@ fc_status fc_deriv_z(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, 
  *     calls whose copies and kernels can overlap on the GPU (on other
  *     streams, from other host threads) race on it and must be serialised by
  *     the caller.
- *   - A plan whose tables would not fit the 96 KiB array returns
- *     FC_ERR_UNSUPPORTED (the compiled transform lengths, up to 1080, need
- *     at most 78 KiB); arguments are checked as in fc_deriv_z.
+ *   - A plan whose tables would not fit the 128 KiB array returns
+ *     FC_ERR_UNSUPPORTED (the tables of every compiled transform length fit:
+ *     at most 100 KiB, float64 at length 1536); arguments are checked as in
+ *     fc_deriv_z.
  */
 fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, int Ny, double Lz,
                              const void* f, void* df, void* d2f, fc_stream_t stream);
@@ -218,11 +222,11 @@ fc_status ns_workspace_bytes(const ns_params* p, size_t* bytes);
  * cudaMalloc and frees it in ns_destroy.  Creation uploads tables with
  * synchronous copies on the current device.
  * z transforms: when N' = Nz + C is itself a compiled length (64, 128, 256,
- * 512, 768, 1024 -- the paper's choice of smooth N') the z derivatives and
+ * 512, 768, 1024, 1536 -- the paper's choice of smooth N') the z derivatives and
  * filter are length-N' spectral multipliers and the projection's DFTs plain
  * length-N' transforms; otherwise they are circular convolutions and
  * Bluestein DFTs on a padded length L >= max(N' + Nz - 1, 2 N' - 1) (160,
- * 288, 320, 576 or 1080).  FC_ERR_UNSUPPORTED when no compiled length fits,
+ * 288, 320, 576, 1080 or 1152).  FC_ERR_UNSUPPORTED when no compiled length fits,
  * Nx or Ny is not one of 16, 32, 64, 96, 128, 192, 256, 512, 1024, or, in
  * double precision, L > 576 or Nx > 512.
  */

@@ -65,6 +65,7 @@ struct DerivPair {
     const C* tw;          // engine twiddles
     long long pf_dist;    // prefetch into L2 the input of block bid + pf_dist (0: off)
     long long nblocks;    // grid size
+    int vec;              // 1: every line pair is one aligned 2-element vector (even line count)
   };
   struct Regs { C v[L1]; C u[L2]; };
 
@@ -127,8 +128,12 @@ struct DerivPair {
           C x = mk<T>(0, 0);
           if (n < a.Nz) {
             const T* p = a.f + base + (long long)n * a.zstride;
-            if (va) x.x = p[0];
-            if (vb) x.y = p[1];
+            if (a.vec) {
+              if (va) x = *reinterpret_cast<const C*>(p);
+            } else {
+              if (va) x.x = p[0];
+              if (vb) x.y = p[1];
+            }
           }
           R.v[j] = x;
           if (n < a.d) Ev[n] = x;
@@ -188,8 +193,12 @@ struct DerivPair {
             const int n = r + L2 * j;
             if (n < a.Nz) {
               T* p = out + base + (long long)n * a.zstride;
-              p[0] = R.v[j].x * sc;
-              if (vb) p[1] = R.v[j].y * sc;
+              if (a.vec) {
+                *reinterpret_cast<C*>(p) = cscale(R.v[j], sc);
+              } else {
+                p[0] = R.v[j].x * sc;
+                if (vb) p[1] = R.v[j].y * sc;
+              }
             }
           }
         }

@@ -2,6 +2,7 @@
 // precision instantiates it: the kernels of all compiled lengths).
 #pragma once
 #include <atomic>
+#include <cstdint>
 
 #include "deriv_kernel.cuh"
 #include "internal.hpp"
@@ -49,6 +50,10 @@ fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long 
   static int sms = 0;
   if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 0;
   a.nblocks = grid;
+  // pairs start at even lines: with an even line count (and 2-element aligned
+  // arrays, as device allocations are) each pair is one aligned vector
+  const uintptr_t al = 2 * sizeof(T);
+  a.vec = (lines % 2 == 0 && ((uintptr_t)f | (uintptr_t)df | (uintptr_t)d2f) % al == 0) ? 1 : 0;
   a.pf_dist = (L1 * L2 < 1000) ? (long long)sms * K::MINB : 0;
   kern<<<(unsigned)grid, K::THREADS, K::smem_bytes, stream>>>(a);
   return cuda_status(cudaGetLastError(), "fc_deriv_z launch");
@@ -84,6 +89,8 @@ fc_status launch_deriv_typed(const DerivDevTables& t, const PlanData& p, int bat
     FC_CASE(768, 24, 32, 4, 2)
     FC_CASE(1024, 32, 32, 4, 2)
     FC_CASE(1080, 30, 36, 4, 2)
+    FC_CASE(1152, 32, 36, 4, 2)
+    FC_CASE(1536, 32, 48, 2, 1)
     default:
       return FC_ERR_UNSUPPORTED;
   }

@@ -55,14 +55,28 @@ struct Eng {
     return w;
   }
 
+  // twiddle loads in groups of TG, one group ahead of their use: the first
+  // group is issued before the register DFT (its latency overlaps the DFT),
+  // each later one while the previous group is multiplied and stored
+  static constexpr int TG = 6;
   // A: thread n2 with v[n1] = x[n2 + L2 n1]
   template <int SIGN>
   static FC_HD void A(C (&v)[L1], C* buf, const C* tw, int n2, int li) {
+    C t[TG];
+#pragma unroll
+    for (int i = 0; i < TG; ++i) t[i] = i < L1 ? twidA<SIGN>(tw, n2, i) : mk<T>(0, 0);
     dft_reg<L1, SIGN, T>(v);
 #pragma unroll
-    for (int k1 = 0; k1 < L1; ++k1) {
-      if (k1 % 6 == 0) FC_FENCE();
-      buf[bidx(k1, n2, li)] = cmul(v[k1], twidA<SIGN>(tw, n2, k1));
+    for (int g = 0; g < L1; g += TG) {
+      C tn[TG];
+#pragma unroll
+      for (int i = 0; i < TG; ++i) tn[i] = (g + TG + i < L1) ? twidA<SIGN>(tw, n2, g + TG + i) : mk<T>(0, 0);
+      FC_FENCE();
+#pragma unroll
+      for (int i = 0; i < TG; ++i)
+        if (g + i < L1) buf[bidx(g + i, n2, li)] = cmul(v[g + i], t[i]);
+#pragma unroll
+      for (int i = 0; i < TG; ++i) t[i] = tn[i];
     }
   }
   // B: thread k1 -> u[k2] = X[k1 + L1 k2]
@@ -75,37 +89,55 @@ struct Eng {
   // inverse-direction B: thread k1 holds u[k2] = X[k1 + L1 k2]; stores for Ai
   template <int SIGN>
   static FC_HD void Bi(C (&u)[L2], C* buf, const C* tw, int k1, int li) {
+    C t[TG];
+#pragma unroll
+    for (int i = 0; i < TG; ++i) t[i] = i < L2 ? twid<SIGN>(tw, i, k1) : mk<T>(0, 0);
     dft_reg<L2, SIGN, T>(u);
 #pragma unroll
-    for (int n2 = 0; n2 < L2; ++n2) {
-      if (n2 % 6 == 0) FC_FENCE();
-      buf[bidx(k1, n2, li)] = cmul(u[n2], twid<SIGN>(tw, n2, k1));
+    for (int g = 0; g < L2; g += TG) {
+      C tn[TG];
+#pragma unroll
+      for (int i = 0; i < TG; ++i) tn[i] = (g + TG + i < L2) ? twid<SIGN>(tw, g + TG + i, k1) : mk<T>(0, 0);
+      FC_FENCE();
+#pragma unroll
+      for (int i = 0; i < TG; ++i)
+        if (g + i < L2) buf[bidx(k1, g + i, li)] = cmul(u[g + i], t[i]);
+#pragma unroll
+      for (int i = 0; i < TG; ++i) t[i] = tn[i];
     }
   }
-  // u[k2] *= H[k1 + L1 k2], in chunks so the table loads are not all live at once
-  static FC_HD void mulH(C (&u)[L2], const C* H, int k1) {
+  // u[k2] *= h(H[k1 + L1 k2]): the table loads in groups of TG, one group
+  // ahead of their use (so that not all of them are live at once, and each
+  // group's latency overlaps the previous group's products)
+  template <class F>
+  static FC_HD void mulH_by(C (&u)[L2], const C* H, int k1, F&& mul) {
+    C t[TG];
 #pragma unroll
-    for (int k2 = 0; k2 < L2; ++k2) {
-      if (k2 % 6 == 0) FC_FENCE();
-      u[k2] = cmul(u[k2], H[k1 + L1 * k2]);
+    for (int i = 0; i < TG; ++i) t[i] = i < L2 ? H[k1 + L1 * i] : mk<T>(0, 0);
+#pragma unroll
+    for (int g = 0; g < L2; g += TG) {
+      C tn[TG];
+#pragma unroll
+      for (int i = 0; i < TG; ++i) tn[i] = (g + TG + i < L2) ? H[k1 + L1 * (g + TG + i)] : mk<T>(0, 0);
+      FC_FENCE();
+#pragma unroll
+      for (int i = 0; i < TG; ++i)
+        if (g + i < L2) u[g + i] = mul(u[g + i], t[i]);
+#pragma unroll
+      for (int i = 0; i < TG; ++i) t[i] = tn[i];
     }
+  }
+  // u[k2] *= H[k1 + L1 k2]
+  static FC_HD void mulH(C (&u)[L2], const C* H, int k1) {
+    mulH_by(u, H, k1, [](C a, C h) { return cmul(a, h); });
   }
   // u[k2] *= i Im(H[k1 + L1 k2]) for a purely imaginary H (odd real kernel)
   static FC_HD void mulH_imag(C (&u)[L2], const C* H, int k1) {
-#pragma unroll
-    for (int k2 = 0; k2 < L2; ++k2) {
-      if (k2 % 6 == 0) FC_FENCE();
-      const T g = H[k1 + L1 * k2].y;
-      u[k2] = mk<T>(-g * u[k2].y, g * u[k2].x);
-    }
+    mulH_by(u, H, k1, [](C a, C h) { return mk<T>(-h.y * a.y, h.y * a.x); });
   }
   // u[k2] *= Re(H[k1 + L1 k2]) for a purely real H (even real kernel)
   static FC_HD void mulH_real(C (&u)[L2], const C* H, int k1) {
-#pragma unroll
-    for (int k2 = 0; k2 < L2; ++k2) {
-      if (k2 % 6 == 0) FC_FENCE();
-      u[k2] = cscale(u[k2], H[k1 + L1 * k2].x);
-    }
+    mulH_by(u, H, k1, [](C a, C h) { return cscale(a, h.x); });
   }
   // inverse-direction A: thread n2 -> v[n1] = x[n2 + L2 n1]
   template <int SIGN>

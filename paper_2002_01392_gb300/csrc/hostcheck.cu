@@ -39,6 +39,7 @@ static int emu_deriv_k(const double* Mr, int d, int Cc, int Nz, int batch, long 
 
   a.nblocks = a.tiles * batch;
   a.pf_dist = 3;
+  a.vec = lines % 2 == 0 ? 1 : 0;
   phased_emulate<K>(a, a.tiles * batch, K::smem_bytes);
   return 0;
 }

@@ -11,7 +11,7 @@ const std::vector<EngineShape>& engine_shapes() {
   static const std::vector<EngineShape> s = {
       {64, 8, 8},     {96, 8, 12},    {128, 8, 16},   {160, 10, 16},  {192, 12, 16}, {256, 16, 16},
       {288, 16, 18},  {320, 16, 20},  {512, 16, 32},  {576, 24, 24},  {768, 24, 32}, {1024, 32, 32},
-      {1080, 30, 36}};
+      {1080, 30, 36}, {1152, 32, 36}, {1536, 32, 48}};
   return s;
 }
 

@@ -7,7 +7,7 @@
 // fixed-size arena and that forbid allocations by plug-ins, and programs run
 // under a device-memory budget that a library must not grow.  This entry point
 // instead keeps those tables in one file-scope static device array of fixed
-// size (kNoAllocBytes = 96 KiB, reserved by every GPU that loads the library
+// size (kNoAllocBytes = 128 KiB, reserved by every GPU that loads the library
 // until the process exits).  A call whose plan and precision differ from the
 // tables the array holds on this device copies the plan's tables into it on
 // the caller's stream first; a call with the same plan and precision as the
@@ -20,7 +20,7 @@
 namespace fcns {
 namespace {
 
-constexpr size_t kNoAllocBytes = 96 * 1024;
+constexpr size_t kNoAllocBytes = 128 * 1024;
 constexpr int kMaxDevices = 64;
 
 // Shared by every call on a device; holds the tables of the last call.
@@ -67,7 +67,7 @@ extern "C" fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batc
   const size_t oMr = 0, oMr2 = align256(sizeof(double) * nMr), oH1 = oMr2 + align256(sizeof(float2) * nMr);
   const size_t oH2 = oH1 + align256(cs * h.L), oTw = oH2 + align256(cs * h.L), need = oTw + align256(cs * 2 * h.L);
   if (need > kNoAllocBytes) {
-    set_error("fc_deriv_z_noalloc: tables of this plan exceed the 96 KiB static scratch");
+    set_error("fc_deriv_z_noalloc: tables of this plan exceed the 128 KiB static scratch");
     return FC_ERR_UNSUPPORTED;
   }
   int dev = -1;

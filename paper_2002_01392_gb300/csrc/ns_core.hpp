@@ -80,6 +80,8 @@ inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
   l.plines = l.ntiles * TL;
   l.es = p.prec == FC_F32 ? 4 : 8;
   if (!z_shape_for(l.Np, p.Nz, &l.L, &l.L1, &l.L2, &l.zdirect)) return FC_ERR_UNSUPPORTED;
+  // the float64 mean-line kernel keeps two continued lines in shared memory
+  if (l.Np > KMean<float>::NPMAX) return FC_ERR_UNSUPPORTED;
   l.L1alt = 0;
 #define FC_ZALT(LL, A, B) \
   if (!l.zdirect && LL == l.L && p.prec == FC_F32) l.L1alt = A;

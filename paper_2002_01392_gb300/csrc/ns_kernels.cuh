@@ -1332,7 +1332,9 @@ namespace fcns {
 template <class T>
 struct KMean {
   using C = cx<T>;
-  static constexpr int THREADS = 256, NPHASE = 4, MINB = 1, NPMAX = 1200;
+  // NPMAX: the longest continued line held in shared memory (two lines); it
+  // covers every compiled z length (N' <= 1536), and ns_layout refuses longer
+  static constexpr int THREADS = 256, NPHASE = 4, MINB = 1, NPMAX = 1536;
   struct Args {
     ZGeom g;
     const double* Mr;       // C x d

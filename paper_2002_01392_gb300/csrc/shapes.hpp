@@ -9,14 +9,16 @@
 #pragma once
 
 #ifdef FC_HOSTCHECK
-#define FC_ZSHAPES_DIRECT(M) M(64, 8, 8, true) M(512, 16, 32, true)
+#define FC_ZSHAPES_DIRECT(M) M(64, 8, 8, true) M(512, 16, 32, true) M(1536, 32, 48, true)
 #define FC_ZSHAPES_PADDED(M) M(160, 10, 16, false) M(288, 16, 18, false) M(1080, 30, 36, false)
 #define FC_XYSHAPES(M) M(16, 4, 4) M(32, 4, 8) M(128, 8, 16)
 #else
 #define FC_ZSHAPES_DIRECT(M) \
-  M(64, 8, 8, true) M(128, 8, 16, true) M(256, 16, 16, true) M(512, 16, 32, true) M(768, 24, 32, true) M(1024, 32, 32, true)
+  M(64, 8, 8, true) M(128, 8, 16, true) M(256, 16, 16, true) M(512, 16, 32, true) M(768, 24, 32, true) \
+  M(1024, 32, 32, true) M(1536, 32, 48, true)
 #define FC_ZSHAPES_PADDED(M) \
-  M(160, 10, 16, false) M(288, 16, 18, false) M(320, 16, 20, false) M(576, 24, 24, false) M(1080, 30, 36, false)
+  M(160, 10, 16, false) M(288, 16, 18, false) M(320, 16, 20, false) M(576, 24, 24, false) M(1080, 30, 36, false) \
+  M(1152, 32, 36, false)
 #define FC_XYSHAPES(M) \
   M(16, 4, 4) M(32, 4, 8) M(64, 8, 8) M(96, 8, 12) M(128, 8, 16) M(192, 12, 16) M(256, 16, 16) M(512, 16, 32) M(1024, 32, 32)
 #endif

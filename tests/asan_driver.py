@@ -46,7 +46,8 @@ def main(path):
              dict(Nx=16, Ny=16, Nz=39, prec="f32", nu=1e-2),
              dict(Nx=16, Ny=128, Nz=33, prec="f32", nu=1e-2),
              dict(Nx=16, Ny=16, Nz=513, nfields=4, prec="f32", nu=3.162e-4, kappa=3.162e-4, gamma=1.0),
-             dict(Nx=16, Ny=16, Nz=487, prec="f64", nu=3.162e-4)]
+             dict(Nx=16, Ny=16, Nz=487, prec="f64", nu=3.162e-4),
+             dict(Nx=16, Ny=16, Nz=1511, prec="f32", nu=3.162e-4)]     # N' = 1536, the longest line
     for kw in cases:
         p = ns_params(**kw)
         nf = p.nfields

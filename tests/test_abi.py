@@ -103,7 +103,7 @@ def test_fc_deriv_z_host_argument_checks_need_no_gpu(api):
 
 
 def test_unsupported_length(api):
-    plan = api.Plan(5, 25, 700)          # N' + Nz - 1 = 1424 > 1080
+    plan = api.Plan(5, 25, 800)          # N' + Nz - 1 = 1624 > 1536, N' = 825 not a compiled length
     st = api._lib.fc_deriv_z(plan.handle, 0, 1, 4, 4, 1.0, 16, 1 << 40, None, None)
     assert api._lib.fc_status_str(st).decode() == "FC_ERR_UNSUPPORTED"
 
@@ -131,7 +131,7 @@ def test_size_limits_need_no_gpu(api):
     assert status(Nx=1024, Ny=1024, Nz=999, nfields=3, prec="f32") == "FC_OK"
     assert status(Nx=100, Ny=64, Nz=33) == "FC_ERR_UNSUPPORTED"                            # x length not compiled
     assert status(Nx=64, Ny=64, Nz=743, prec="f64") == "FC_ERR_UNSUPPORTED"                # f64 z length > 576
-    assert status(Nx=64, Ny=64, Nz=1200) == "FC_ERR_UNSUPPORTED"                           # N' + Nz - 1 > 1080
+    assert status(Nx=64, Ny=64, Nz=1200) == "FC_ERR_UNSUPPORTED"                           # 2 N' - 1 > 1152, N' = 1225
     assert status(Nx=64, Ny=64, Nz=9) == "FC_ERR_ARG"                                      # Nz < 2d
     assert status(Nx=64, Ny=64, Nz=33, nfields=5) == "FC_ERR_ARG"
     assert status(Nx=64, Ny=64, Nz=33, nu=-1.0) == "FC_ERR_ARG"

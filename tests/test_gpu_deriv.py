@@ -46,8 +46,10 @@ def _check(out, f64, Mr, Nz, order, dtype):
 
 @pytest.mark.parametrize("Nz,Nx,Ny,B", [(10, 33, 1, 1), (33, 20, 6, 3), (33, 1, 1, 1), (65, 40, 3, 1),
                                          (129, 33, 5, 2), (257, 24, 2, 1), (513, 17, 2, 1), (513, 64, 16, 2),
-                                         # smooth N' = Nz + 25 (64, 512, 1024): transform length N' itself
-                                         (39, 21, 4, 2), (487, 33, 3, 1), (999, 16, 3, 1)])
+                                         # smooth N' = Nz + 25 (64, 512, 1024, 1536): transform length N' itself
+                                         (39, 21, 4, 2), (487, 33, 3, 1), (999, 16, 3, 1), (1511, 8, 2, 1),
+                                         # padded length 1152 (N' + Nz - 1 = 1124)
+                                         (550, 16, 2, 1)])
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_deriv_parity_small(api, Mr_5_25, Nz, Nx, Ny, B, dtype):
     plan = api.Plan(5, 25, Nz)

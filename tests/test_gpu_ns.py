@@ -207,6 +207,42 @@ def test_direct_length_channel_matches_oracle(api, N, Nz):
     sim.close()
 
 
+def test_d7_channel_float32_at_nz513(api, Mr_7_33):
+    """d = 7, C = 33 at Nz = 513 (N' = 546): the padded length must reach
+    2 N' - 1 = 1091, so the step runs on the 1152 = 32 x 36 transforms; one
+    float32 RK3 step of the channel workload against the oracle with the
+    same tables (float32 bound of the float32 channel tests)."""
+    N, Nz, nu, dt = 16, 513, 3.162e-4, 1e-5
+    sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, d=7, C=33, nu=nu, forcing_x=10 * nu, prec="f32"))
+    P = ns.Params(N, N, Nz, d=7, C=33, nu=nu, forcing_x=10 * nu, Mr=Mr_7_33)
+    v = synth.channel_velocity(N, N, Nz, nu=nu).astype(np.float32).astype(np.float64)
+    sim.set_fields(_cuda(v, torch.float32))
+    sim.step(dt)
+    out = sim.get_fields().cpu().numpy()
+    ref, _, _ = _oracle_steps(v, P, dt, 1)
+    assert _rel(out, ref) < 3e-5
+    assert _wall_err(out, ref) < 3e-5
+    sim.close()
+
+
+def test_direct_length_1536_float32(api):
+    """N' = Nz + 25 = 1536 (Nz = 1511), the largest smooth N' of the paper's
+    runs: direct length-1536 = 32 x 48 z transforms; one float32 RK3 step of
+    the channel workload against the oracle (dt nu k_max^2 = 7e-3 keeps the
+    explicit viscous term stable at this resolution)."""
+    N, Nz, nu, dt = 16, 1511, 3.162e-4, 1e-6
+    sim = api.Sim(api.ns_params(Nx=N, Ny=N, Nz=Nz, nu=nu, forcing_x=10 * nu, prec="f32"))
+    P = ns.Params(N, N, Nz, nu=nu, forcing_x=10 * nu)
+    v = synth.channel_velocity(N, N, Nz, nu=nu).astype(np.float32).astype(np.float64)
+    sim.set_fields(_cuda(v, torch.float32))
+    sim.step(dt)
+    out = sim.get_fields().cpu().numpy()
+    ref, _, _ = _oracle_steps(v, P, dt, 1)
+    assert _rel(out, ref) < 3e-5
+    assert _wall_err(out, ref) < 3e-5
+    sim.close()
+
+
 def test_d7_channel_matches_oracle(api, Mr_7_33):
     """d = 7, C = 33 (N' = 66) on the 32 x 32 x 33 channel: right-hand side and
     three RK3 steps vs the oracle with the same tables; float64 floor scaled by
