@@ -53,21 +53,19 @@ def _measured_traffic(key):
     return None
 
 
-def _deriv_alu_roofline(r, clocks, L=1080, Nz=513, C=25, d=5):
-    """fc_deriv_z against the float32 ALU: algorithmic flops per line pair (two
-    real z-lines as one complex line) = three length-L FFTs at 5 L log2 L, two
-    spectrum products (6 flops per complex multiply), the continuation of both
-    lines (2 C d multiply-adds each) and the output scaling, over the
-    CUDA-event time; peak = 152 SMs x 128 FP32 lanes x 2 flops (FMA) x the
-    SM clock sampled under load."""
+def _deriv_alu_roofline(r, peak_tflops, peak_kind, L=1080, Nz=513, C=25, d=5):
+    """fc_deriv_z against the arithmetic pipe: algorithmic flops per line pair
+    (two real z-lines as one complex line) = three length-L FFTs at
+    5 L log2 L, two spectrum products (6 flops per complex multiply), the
+    continuation of both lines (2 C d multiply-adds each) and the output
+    scaling, over the CUDA-event time; peak = the fused multiply-add rate of the
+    arm's precision measured on this GPU (fc_alu_probe, 2 flops per lane
+    operation)."""
     pair = 3 * 5 * L * np.log2(L) + 2 * 6 * L + 2 * 2 * C * d * 2 + 2 * 2 * Nz
     pairs = r["points"] / Nz / 2
     achieved = pair * pairs / r["seconds_per_call_mean"] / 1e12
-    mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
-    return {"bound": "alu", "achieved": float(achieved), "peak": float(peak), "unit": "TFLOP/s",
-            "frac": float(achieved / peak), "flops_per_line_pair": float(pair),
-            "peak_kind": "derived (152 SMs x 128 FP32 lanes x FMA x sampled SM clock)"}
+    return {"bound": "alu", "achieved": float(achieved), "peak": float(peak_tflops), "unit": "TFLOP/s",
+            "frac": float(achieved / peak_tflops), "flops_per_line_pair": float(pair), "peak_kind": peak_kind}
 
 
 def measure_alu_peaks(api, torch, iters=4096, reps=5):
@@ -453,6 +451,54 @@ def bench_cufft64(api, torch, steps, warmup):
     return res
 
 
+def band_limited_fields(Nx, Nz, seed, torch=None, kmax=2):
+    """Four fields sum_{|kx|,|ky| <= kmax} A(z) cos(kx x + ky y) + B(z) sin(...)
+    on an Nx x Nx grid (x = 2 pi i / Nx), A, B seeded polynomials times
+    z(1 - z) / (1 + k^2); on the device (float32) when torch is given, else a
+    float64 numpy array."""
+    g = np.random.default_rng(seed)
+    z = np.linspace(0.0, 1.0, Nz)
+    modes = [(kx, ky) for kx in range(0, kmax + 1) for ky in range(-kmax, kmax + 1) if kx > 0 or ky >= 0]
+    coef = g.uniform(-1, 1, size=(4, len(modes), 2, 3))
+    x = 2 * np.pi * np.arange(Nx) / Nx
+    out = []
+    for f in range(4):
+        acc = None
+        for m, (kx, ky) in enumerate(modes):
+            ph = kx * x[None, :] + ky * x[:, None]
+            for part, fn in ((0, np.cos), (1, np.sin)):
+                if kx == 0 and ky == 0 and part == 1:
+                    continue
+                c = coef[f, m, part]
+                prof = 0.1 * z * (1 - z) * (1 + c[0] + c[1] * z + c[2] * z * z) / (1 + kx * kx + ky * ky)
+                if torch is None:
+                    term = prof[:, None, None] * fn(ph)[None]
+                else:
+                    term = (torch.from_numpy(prof).to("cuda", torch.float32)[:, None, None]
+                            * torch.from_numpy(fn(ph)).to("cuda", torch.float32)[None])
+                acc = term if acc is None else acc + term
+        out.append(acc)
+    return np.stack(out) if torch is None else torch.stack(out)
+
+
+def rk_accuracy(res):
+    """Relative L2 error per field of the band-limited full-size RK3 step of
+    bench_rk against the oracle's 64^2 step (the CPU leg)."""
+    smp = res.pop("_err_sample", None) if res else None
+    if not smp:
+        return
+    from oracle import ns
+    Nz, kw = smp["Nz"], smp["kw"]
+    P = ns.Params(64, 64, Nz, nfields=4, **kw)
+    fc_ = band_limited_fields(64, Nz, smp["seed"])
+    st, _ = ns.rk_step(ns.to_spectral(fc_, P), np.zeros((2, 2, 64, P.Kx), complex), P, smp["dt"])
+    ref = np.stack([ns.to_physical(c, P) for c in st])
+    res["rel_l2_err_vs_oracle_per_field"] = [float(np.linalg.norm(smp["out"][f] - ref[f]) / np.linalg.norm(ref[f]))
+                                             for f in range(4)]
+    res["error_sample"] = ("one RK3 step of fields band-limited to |kx|,|ky| <= 2 at full size, every "
+                           "Nx/64-th point against the oracle's 64^2 step (exact restriction)")
+
+
 RK_SHAPE = (1024, 1024, 513)
 
 
@@ -501,6 +547,19 @@ def bench_rk(api, torch, steps, warmup, with_e2e=True, shape=None, tune=True):
     out = sim.get_fields()
     res["finite"] = bool(torch.isfinite(out).all().item())
     res["w_wall_rel"] = float(out[2, [0, -1]].abs().max().item() / max(out[:3].abs().max().item(), 1e-300))
+    # error against the oracle, untimed: one step of fields band-limited to
+    # |kx|, |ky| <= 2, whose exact result on every (Nx/64)-th point is the exact
+    # result of the 64^2 grid the oracle can run (each stage's product at most
+    # doubles the bandwidth, which stays inside the 2/3 rule of a 64^2 grid);
+    # the comparison runs in the CPU leg (rk_accuracy)
+    if Nx % 64 == 0 and Nx == Ny:
+        fb = band_limited_fields(Nx, Nz, seed=77 + Nz, torch=torch)
+        sim.set_fields(fb)
+        del fb
+        sim.step(dt)
+        r = Nx // 64
+        res["_err_sample"] = {"Nz": Nz, "dt": dt, "seed": 77 + Nz, "kw": kw,
+                              "out": sim.get_fields()[:, :, ::r, ::r].double().cpu().numpy()}
     if with_e2e:
         hp = torch.from_numpy(host).pin_memory()
         ho = torch.empty_like(hp).pin_memory()
@@ -710,8 +769,74 @@ def bench_serving(api, torch, rate=2000.0, duration=2.0, resident=48, slots=8):
     stats.update({"arrival_rate_per_s": rate, "duration_s": duration, "slots": slots,
                   "grids": [list(x) for x in grids], "mix": "50/50 fc_poisson_project / rk_step"})
     srv.close()
+    # error sample (compared with the oracle in the CPU leg): per grid size, one
+    # projection and one RK3 step of a simulation as served, from its fields
+    smp = []
+    for Nx, Ny, Nz in grids:
+        p = api.ns_params(Nx=Nx, Ny=Ny, Nz=Nz, nu=5e-3, forcing_x=5e-2, prec="f32")
+        v = synth.channel_velocity(Nx, Ny, Nz, nu=5e-3, seed_offset=2000).astype(np.float32)
+        vs = synth.channel_velocity(Nx, Ny, Nz, nu=5e-3, seed_offset=3000).astype(np.float32)
+        sim = api.Sim(p)
+        sim.set_fields(torch.from_numpy(v).cuda())
+        proj = sim.project(torch.from_numpy(vs).cuda(), 2e-4).double().cpu().numpy()
+        sim.set_fields(torch.from_numpy(v).cuda())
+        sim.step(2e-4)
+        smp.append(((Nx, Ny, Nz), v, vs, proj, sim.get_fields().double().cpu().numpy()))
+        sim.close()
+    stats["_err_samples"] = smp
     torch.cuda.empty_cache()
     return stats
+
+
+def serving_capacity(api, torch, grids, reps=10):
+    """GPU time of one request of each kind alone (CUDA events, after warm-up)
+    per grid size, and the request rate one GPU sustains for the served mix
+    (50/50 projection / RK3 step, grids uniform) with one request at a time:
+    1 / (mean request time).  Concurrent streams overlap small requests, so
+    the served rate can exceed it somewhat; far above it is impossible."""
+    import synth
+    stream = torch.cuda.current_stream()
+    per = {}
+    for Nx, Ny, Nz in grids:
+        sim = api.Sim(api.ns_params(Nx=Nx, Ny=Ny, Nz=Nz, nu=5e-3, forcing_x=5e-2, prec="f32"))
+        sim.tune(1)
+        v = torch.from_numpy(synth.channel_velocity(Nx, Ny, Nz, nu=5e-3).astype(np.float32)).cuda()
+        sim.set_fields(v)
+        out = {}
+        for kind, fn in (("project", lambda: sim.project(v, 2e-4)), ("step", lambda: sim.step(2e-4))):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            out[kind] = e0.elapsed_time(e1) / reps
+        per["%dx%dx%d" % (Nx, Ny, Nz)] = out
+        sim.close()
+    mean_ms = float(np.mean([t for g in per.values() for t in g.values()]))
+    return {"request_gpu_ms": per, "mean_request_gpu_ms": mean_ms, "sustainable_req_per_s_one_at_a_time": 1e3 / mean_ms}
+
+
+def serving_accuracy(res):
+    """Relative L2 error against the oracle of one projection and one RK3 step
+    per grid size of the served simulations (the CPU leg)."""
+    smp = res.pop("_err_samples", None) if res else None
+    if not smp:
+        return
+    from oracle import ns
+    errs = {}
+    for (Nx, Ny, Nz), v, vs, proj, step in smp:
+        P = ns.Params(Nx, Ny, Nz, nu=5e-3, forcing_x=5e-2)
+        v64, vs64 = v.astype(np.float64), vs.astype(np.float64)
+        ref_p, _ = ns.poisson_project(vs64, P, 2e-4)
+        st, _ = ns.rk_step(ns.to_spectral(v64, P), np.zeros((2, 2, Ny, P.Kx), complex), P, 2e-4)
+        ref_s = np.stack([ns.to_physical(c, P) for c in st])
+        errs["%dx%dx%d" % (Nx, Ny, Nz)] = {
+            "project": float(np.linalg.norm(proj - ref_p) / np.linalg.norm(ref_p)),
+            "rk_step": float(np.linalg.norm(step - ref_s) / np.linalg.norm(ref_s))}
+    res["rel_l2_err_vs_oracle"] = errs
 
 
 class OracleDerivSample:
@@ -935,6 +1060,10 @@ def main():
         ens = bench_ensemble(api, torch)
         srv = bench_serving(api, torch)
         srv_low = bench_serving(api, torch, rate=300.0)
+        srv["capacity"] = serving_capacity(api, torch, ((64, 64, 65), (128, 128, 129), (256, 256, 257)))
+    alu = measure_alu_peaks(api, torch)
+    if r64:
+        r64["roofline_alu"] = _deriv_alu_roofline(r64, alu["dfma"]["tflops"], "measured DFMA rate (fc_alu_probe)")
     value = replica_value(torch, r32["points"] * args.steps, r32["seconds_total"])
     ms_per_step = _max_over_ranks(torch, r32["seconds_total"]) / args.steps * 1e3
     out = {
@@ -957,8 +1086,10 @@ def main():
                      "peak": hbm_peak, "unit": "GB/s",
                      "frac": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9 / hbm_peak,
                      "traffic": _measured_traffic("fc_deriv_z_f32"), "peak_kind": peak_kind,
-                     "kernel": "fc_deriv_z conv L=1080 FP32, paired lines, registers j >= 16 known zero (phased_kernel<DerivPair<float,30,36,4,16>>)"},
-        "roofline_alu": _deriv_alu_roofline(r32, clk.summary()),
+                     "kernel": "fc_deriv_z conv L=1080 FP32, paired lines, real-valued kernel spectra, registers j >= 16 known zero (phased_kernel<DerivPair<float,30,36,4,16,1>>)",
+                     "algorithmic_bytes_per_point": 12, "traffic_source": "profiles/traffic.txt (ncu, small case scaled x6)"},
+        "roofline_alu": _deriv_alu_roofline(r32, alu["ffma"]["tflops"], "measured FFMA rate (fc_alu_probe)"),
+        "alu_peaks_measured": alu,
         "e2e": r32.get("e2e"),
         "gpu_launches": r32["launches"],
         "clocks": clk.summary(),
@@ -972,11 +1103,20 @@ def main():
                 oracle_accuracy(arm)
         if ens:
             ensemble_accuracy(ens)
+        rk_accuracy(out.get("rk_stage"))
+        rk_accuracy(out.get("rk_stage_smooth_Np512_1024x1024x487"))
+        serving_accuracy(out.get("serving_poisson_2000_per_s"))
     for arm in (out["fc_deriv_z"]["fp32"], r64, rs):
         if arm:
             arm.pop("_samples", None)
     if ens:
         ens.pop("_err_samples", None)
+    for arm in (out.get("rk_stage"), out.get("rk_stage_smooth_Np512_1024x1024x487")):
+        if arm:
+            arm.pop("_err_sample", None)
+    for arm in (out.get("serving_poisson_2000_per_s"), out.get("serving_poisson_300_per_s")):
+        if arm:
+            arm.pop("_err_samples", None)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
