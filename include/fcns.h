@@ -162,7 +162,7 @@ fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, 
 /*
  * fc_deriv_z_host -- the computation of fc_deriv_z on HOST arrays f, df, d2f
  * (same layout [batch][Nz][Ny][Nx] and arguments; df or d2f may be NULL).
- * The library moves slabs of y rows (all z and x of a field, about 64 MB of
+ * The library moves slabs of y rows (all z and x of a field, about 256 MB of
  * input each, an even number of rows) through three rotating device buffers
  * on three internal streams: the host-to-device copy of one slab, the kernel
  * of the previous one and the device-to-host copies of the one before run
