@@ -27,9 +27,9 @@ paper, Sec. 6 table of channel runs and Sec. 7 table of convection runs):
   coefficients N(0,1) 2^(-n/2), n <= 16 (exact z-derivatives in closed form).
 * Boussinesq: theta = 1e-3 eta(x,y) sin(pi z / Lz), velocity = 1e-3 times a
   channel-type solenoidal fluctuation (no mean flow).
-* App. A noise: curl-eigenfunction perturbations from the Chandrasekhar-Reid
-  functions g_m (poloidal) and sin(m pi (z' + 1/2)) (toroidal), the paper's
-  initial-perturbation recipe (``chandrasekhar_reid_noise``).
+* App. A noise: only the uniform phase draws (``noise_draws``); the
+  curl-eigenfunction field built from them is method arithmetic (the library's
+  ``fc_noise`` and the oracle's ``noise_field``).
 """
 from __future__ import annotations
 
@@ -157,87 +157,15 @@ def poiseuille(Nx: int, Ny: int, Nz: int, F: float, nu: float, Lz: float = 1.0) 
 
 
 # ----------------------------------------------------------------------------
-# App. A: random solenoidal no-slip noise from curl eigenfunctions
+# App. A: the random draws of the curl-eigenfunction perturbation
 # ----------------------------------------------------------------------------
 
-def chandrasekhar_reid_lambdas(count: int) -> np.ndarray:
-    """lambda_m, m = 1..count, of the Chandrasekhar-Reid functions g_m (App. A):
-    the roots of g_m'(+-1/2) = 0, i.e. tanh(l/2) + tan(l/2) = 0 for odd m
-    (even g_m) and tanh(l/2) - tan(l/2) = 0 for even m (odd g_m).  With
-    t = l/2: odd m has its root where tan t ~ -1 on (j pi - pi/2, j pi),
-    j = (m + 1)/2; even m where tan t ~ +1 on (j pi, j pi + pi/2), j = m/2."""
-    from scipy.optimize import brentq
-    out = np.empty(count)
-    eps = 1e-12
-    for m in range(1, count + 1):
-        if m % 2 == 1:
-            j = (m + 1) // 2
-            f = lambda t: np.tanh(t) + np.tan(t)
-            lo, hi = j * np.pi - np.pi / 2 + eps, j * np.pi - eps
-        else:
-            j = m // 2
-            f = lambda t: np.tanh(t) - np.tan(t)
-            lo, hi = j * np.pi + eps, j * np.pi + np.pi / 2 - eps
-        out[m - 1] = 2 * brentq(f, lo, hi, xtol=1e-15, maxiter=200)
-    return out
-
-
-def _cr_g(m: int, lam: float, zp: np.ndarray):
-    """g_m(z') and dg_m/dz' (App. A), z' in [-1/2, 1/2]."""
-    if m % 2 == 1:
-        g = np.cosh(lam * zp) / np.cosh(lam / 2) - np.cos(lam * zp) / np.cos(lam / 2)
-        dg = lam * (np.sinh(lam * zp) / np.cosh(lam / 2) + np.sin(lam * zp) / np.cos(lam / 2))
-    else:
-        g = np.sinh(lam * zp) / np.sinh(lam / 2) - np.sin(lam * zp) / np.sin(lam / 2)
-        dg = lam * (np.cosh(lam * zp) / np.sinh(lam / 2) - np.cos(lam * zp) / np.sin(lam / 2))
-    return g, dg
-
-
-def chandrasekhar_reid_noise(Nx: int, Ny: int, Nz: int, Lx: float = 2 * np.pi, Ly: float = 2 * np.pi,
-                             Lz: float = 1.0, seed_offset: int = 0, kperp2=(4.0, 25.0), mrange=(2, 5),
-                             slopes=(-4.0, -3.0)) -> np.ndarray:
-    """Random solenoidal velocity vanishing at z = 0, Lz (App. A), shape
-    [3][Nz][Ny][Nx], scaled to max |v| = 1:
-        q = curl curl(phi z_hat) + curl(psi z_hat),
-        phi = sum a_nlm e^{i(kx x + ky y)} g_m(z'),
-        psi = sum b_nlm e^{i(kx x + ky y)} sin(m pi (z' + 1/2)),  z' = z/Lz - 1/2,
-    with random phases, kperp2[0] <= kx^2 + ky^2 <= kperp2[1], mrange[0] <= m
-    <= mrange[1], |a| ~ k^slopes[0], |b| ~ k^slopes[1], k^2 = kx^2 + ky^2 +
-    lambda_m^2 (App. A: k^-4 and k^-3, velocity spectrum ~ k^-2).  Each
-    mode's real part is divergence-free and vanishes with its normal
-    derivative structure at the walls (g_m(+-1/2) = g_m'(+-1/2) = 0)."""
-    g = rng(3, seed_offset)
-    z = z_grid(Nz, Lz)
-    zp = z / Lz - 0.5
-    lams = chandrasekhar_reid_lambdas(mrange[1])
-    out = np.zeros((3, Nz, Ny, Nx))
-    x = np.arange(Nx) * Lx / Nx
-    y = np.arange(Ny) * Ly / Ny
-    nmax = int(np.ceil(np.sqrt(kperp2[1]) * Lx / (2 * np.pi)))
-    lmax = int(np.ceil(np.sqrt(kperp2[1]) * Ly / (2 * np.pi)))
-    for n in range(-nmax, nmax + 1):
-        kx = 2 * np.pi * n / Lx
-        for l in range(0, lmax + 1):        # half plane: the real part supplies the conjugate modes
-            if l == 0 and n < 0:
-                continue
-            ky = 2 * np.pi * l / Ly
-            kp2 = kx * kx + ky * ky
-            if not (kperp2[0] <= kp2 <= kperp2[1]):
-                continue
-            E = np.exp(1j * (kx * x[None, :] + ky * y[:, None]))          # [Ny][Nx]
-            for m in range(mrange[0], mrange[1] + 1):
-                lam = lams[m - 1]
-                k = np.sqrt(kp2 + lam * lam)
-                a = k ** slopes[0] * np.exp(2j * np.pi * g.uniform())
-                b = k ** slopes[1] * np.exp(2j * np.pi * g.uniform())
-                gm, dgm = _cr_g(m, lam, zp)
-                sm = np.sin(m * np.pi * (zp + 0.5))
-                # curl curl(phi z) = (d_x d_z phi, d_y d_z phi, -(d_xx + d_yy) phi); curl(psi z) = (d_y psi, -d_x psi, 0)
-                cz = dgm / Lz
-                out[0] += np.real((1j * kx * a * cz)[:, None, None] * E[None] + (1j * ky * b * sm)[:, None, None] * E[None])
-                out[1] += np.real((1j * ky * a * cz)[:, None, None] * E[None] - (1j * kx * b * sm)[:, None, None] * E[None])
-                out[2] += np.real((kp2 * a * gm)[:, None, None] * E[None])
-    return out / np.abs(out).max()
+def noise_draws(count: int, seed_offset: int = 0) -> np.ndarray:
+    """The 2 * count uniform numbers in [0, 1) of an App. A perturbation with
+    count (n, l, m) modes (two phases per mode, in mode order); the field
+    itself is built by the library (``fc_noise``) and by the oracle from
+    these draws."""
+    return rng(3, seed_offset).uniform(size=2 * count)
 
 
 # ----------------------------------------------------------------------------
