@@ -252,19 +252,27 @@ def bench_deriv(api, torch, dtype_np, steps, warmup, with_e2e=True):
         hf = f.cpu().pin_memory()
         h1 = torch.empty(shape, dtype=tdt).pin_memory()
         h2 = torch.empty(shape, dtype=tdt).pin_memory()
-        n_e2e = max(2, min(steps, 5))
+        n_e2e = max(2, min(steps, 10))
         api.fc_deriv_z_host(plan, hf, h1, h2)          # staging buffers allocated once
         _barrier_sync(torch)
         t0 = time.perf_counter()
+        calls = []
         for _ in range(n_e2e):
-            api.fc_deriv_z_host(plan, hf, h1, h2)
+            tc = time.perf_counter()
+            api.fc_deriv_z_host(plan, hf, h1, h2)      # synchronous: returns with the outputs in host memory
+            calls.append(time.perf_counter() - tc)
         _barrier_sync(torch)
         te = time.perf_counter() - t0
         same = bool(torch.equal(h1[:, ::16, ::16], d1[:, ::16, ::16].cpu()) and
                     torch.equal(h2[:, ::16, ::16], d2[:, ::16, ::16].cpu()))
         res["e2e"] = {"value": replica_value(torch, pts * n_e2e, te), "unit": "grid-points/s",
                       "h2d_bytes_per_step": es * pts, "d2h_bytes_per_step": 2 * es * pts,
-                      "api": "fc_deriv_z_host (host arrays, page-locked)", "bitwise_equal_device_path": same}
+                      "api": "fc_deriv_z_host (host arrays, page-locked)", "bitwise_equal_device_path": same,
+                      "calls": n_e2e, "ms_per_call_p50": float(np.median(calls) * 1e3),
+                      "ms_per_call_max": float(max(calls) * 1e3),
+                      "link_floor_ms": 2 * es * pts / 193.5e9 * 1e3,
+                      "link_floor_note": "device-to-host bytes / 193.5 GB/s, the pinned copy rate measured on this "
+                                         "pool's GB300 hosts (the larger of the two directions)"}
     del f, d1, d2
     torch.cuda.empty_cache()
     return res
@@ -863,6 +871,49 @@ class OracleDerivSample:
         return self.lines * 513
 
 
+def bench_noise(api, torch, reps=5, warmup=3, Nx=1024, Ny=1024, Nz=513):
+    """App. A perturbation (fc_noise) on the 1024^2 x 513 Boussinesq grid,
+    float32 output (float64 arithmetic): CUDA-event time per call and the
+    float64 multiply-add rate of the synthesis (6 per point per kx index)."""
+    import synth
+    p = api.noise_params()
+    cnt = api.noise_modes(p)
+    draws = synth.noise_draws(cnt, 13)
+    out = torch.empty((3, Nz, Ny, Nx), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        api.fc_noise(p, draws, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        api.fc_noise(p, draws, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / reps
+    nn = 2 * 5 + 1                       # kx indices -5..5 of the App. A annulus
+    pts = Nx * Ny * Nz
+    res = {"grid": [Nx, Ny, Nz], "modes": cnt, "ms_per_call": sec * 1e3, "grid_points_per_s": pts / sec,
+           "dfma_per_point_synthesis": 6 * nn, "dfma_tflops_synthesis": 2 * 6 * nn * pts / sec / 1e12,
+           "_err_sample": (draws, out[:, :, ::64, ::64].double().cpu().numpy(), Nz)}
+    del out
+    torch.cuda.empty_cache()
+    return res
+
+
+def noise_accuracy(res):
+    """Largest error of every 64th x, y column against the oracle on the grid
+    of exactly those points, after the one global scale (the CPU leg)."""
+    smp = res.pop("_err_sample", None) if res else None
+    if not smp:
+        return
+    from oracle import noise
+    draws, sample, Nz = smp
+    ref = noise.noise_field(16, 16, Nz, draws)
+    c = float((sample * ref).sum() / (ref * ref).sum())
+    res["max_abs_err_vs_oracle_sampled"] = float(np.abs(sample - c * ref).max())
+
+
 def host_cores() -> int:
     """Host cores this process may run on."""
     try:
@@ -1046,7 +1097,7 @@ def main():
     with ClockSampler(dev_index) as clk:
         r32 = bench_deriv(api, torch, np.float32, args.steps, args.warmup)
         rk = bench_rk(api, torch, args.rk_steps, 3) if extras else None
-    r64 = rc = rks = ens = srv = srv_low = rs = None
+    r64 = rc = rks = ens = srv = srv_low = rs = nz = None
     if world == 1:
         r64 = bench_deriv(api, torch, np.float64, max(3, args.steps // 4), 2, with_e2e=False)
         rc = bench_cufft64(api, torch, max(3, args.steps // 4), 2)
@@ -1061,6 +1112,7 @@ def main():
         srv = bench_serving(api, torch)
         srv_low = bench_serving(api, torch, rate=300.0)
         srv["capacity"] = serving_capacity(api, torch, ((64, 64, 65), (128, 128, 129), (256, 256, 257)))
+        nz = bench_noise(api, torch)
     alu = measure_alu_peaks(api, torch)
     if r64:
         r64["roofline_alu"] = _deriv_alu_roofline(r64, alu["dfma"]["tflops"], "measured DFMA rate (fc_alu_probe)")
@@ -1082,6 +1134,7 @@ def main():
         "ensemble_64_uneven_fp32_graph": ens,
         "serving_poisson_2000_per_s": srv,
         "serving_poisson_300_per_s": srv_low,
+        "noise_app_a_1024x1024x513": nz,
         "roofline": {"bound": "hbm", "achieved": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9,
                      "peak": hbm_peak, "unit": "GB/s",
                      "frac": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9 / hbm_peak,
@@ -1106,6 +1159,9 @@ def main():
         rk_accuracy(out.get("rk_stage"))
         rk_accuracy(out.get("rk_stage_smooth_Np512_1024x1024x487"))
         serving_accuracy(out.get("serving_poisson_2000_per_s"))
+        noise_accuracy(nz)
+    if nz:
+        nz.pop("_err_sample", None)
     for arm in (out["fc_deriv_z"]["fp32"], r64, rs):
         if arm:
             arm.pop("_samples", None)

@@ -162,8 +162,9 @@ fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, 
 /*
  * fc_deriv_z_host -- the computation of fc_deriv_z on HOST arrays f, df, d2f
  * (same layout [batch][Nz][Ny][Nx] and arguments; df or d2f may be NULL).
- * The library moves slabs of y rows (all z and x of a field, about 256 MB of
- * input each, an even number of rows) through three rotating device buffers
+ * The library moves slabs of y rows (all z and x of a field, at most about
+ * 256 MB of input each, an even number of rows, the slabs of a field of
+ * nearly equal size) through three rotating device buffers
  * on three internal streams: the host-to-device copy of one slab, the kernel
  * of the previous one and the device-to-host copies of the one before run
  * concurrently.  Results are bitwise those of fc_deriv_z on device copies of
@@ -347,6 +348,59 @@ fc_status ns_spectrum_shells(ns_sim_t sim, int* nshell, double* dk);
 fc_status ns_interpolate(ns_sim_t dst, ns_sim_t src, fc_stream_t stream);
 
 /*
+ * Initial perturbation (App. A): a random solenoidal velocity that vanishes
+ * at both walls, built from curl eigenfunctions,
+ *   q = curl curl(phi z_hat) + curl(psi z_hat),
+ *   phi = sum a e^{i(kx x + ky y)} g_m(z'),  psi = sum b e^{i(kx x + ky y)} sin(m pi (z' + 1/2)),
+ * z' = z/Lz - 1/2, g_m the Chandrasekhar-Reid functions
+ * (cosh(l z')/cosh(l/2) - cos(l z')/cos(l/2) for odd m, sinh / sin for even
+ * m, l = lambda_m, the m-th root of g_m'(+-1/2) = 0), a = k^slope_phi
+ * e^{2 pi i u_a}, b = k^slope_psi e^{2 pi i u_b}, k^2 = kx^2 + ky^2 +
+ * lambda_m^2, kx = 2 pi n / Lx, ky = 2 pi l / Ly.  Modes: the half plane
+ * (l > 0, or l = 0 and n > 0) of the annulus kperp2_min <= kx^2 + ky^2 <=
+ * kperp2_max (inclusive within a relative 1e-12), and m_min <= m <= m_max;
+ * the real part is taken.  App. A's choice is the default: annulus [4, 25],
+ * m = 2..5, slopes -4 and -3.
+ */
+typedef struct {
+  double Lx, Ly, Lz;               /* x, y periods; wall distance (z in [0, Lz])        */
+  double kperp2_min, kperp2_max;   /* annulus of kx^2 + ky^2                            */
+  int m_min, m_max;                /* vertical indices, 1 <= m_min <= m_max <= 64       */
+  double slope_phi, slope_psi;     /* exponents of |a| and |b| in k                     */
+  double amplitude;                /* largest component magnitude of the result         */
+} fc_noise_params;
+
+/* The defaults above (Lx = Ly = 2 pi, Lz = 1, amplitude 1). */
+fc_status fc_noise_params_default(fc_noise_params* p);
+
+/* Number of (n, l, m) modes of these parameters (host only; the caller
+ * supplies two uniform draws per mode to fc_noise).  FC_ERR_ARG for invalid
+ * parameters (see fc_noise). */
+fc_status fc_noise_modes(const fc_noise_params* p, int* count);
+
+/*
+ * fc_noise -- the perturbation on the grid x_i = i Lx/Nx, y_j = j Ly/Ny,
+ * z_s = s Lz/(Nz - 1), written to `out` (device, [3][Nz][Ny][Nx] contiguous,
+ * components u, v, w, dtype FC_F32 or FC_F64; the arithmetic is float64 in
+ * both cases), scaled so that its largest component magnitude equals
+ * p->amplitude.  draws: host array of ndraws = 2 x fc_noise_modes() numbers
+ * in [0, 1): (u_a, u_b) per mode, modes ordered by n ascending, then l
+ * ascending, then m ascending.  lambda_m and the mode amplitudes are computed
+ * on the host; the profiles, the synthesis and the scaling run on the device
+ * on `stream` (scratch taken with cudaMallocAsync / cudaFreeAsync on it).
+ * Asynchronous with respect to the host (the draws are read before return).
+ * The result is exactly solenoidal and no-slip as a function; on the grid
+ * the walls hold zero to rounding.  Add it to a base flow and pass the sum to
+ * ns_set_fields.  FC_ERR_ARG: invalid parameters (Lx, Ly, Lz <= 0,
+ * kperp2_min > kperp2_max, m outside 1..64, non-finite values), no mode in
+ * the annulus, ndraws wrong, a non-finite draw, NULL pointers, Nx <= 2 max|n|
+ * or Ny <= 2 max l (a mode the grid cannot resolve), Nz < 2; FC_ERR_NOMEM if
+ * the scratch cannot be allocated.
+ */
+fc_status fc_noise(const fc_noise_params* p, fc_dtype dtype, int Nx, int Ny, int Nz, const double* draws,
+                   int ndraws, void* out, fc_stream_t stream);
+
+/*
  * ns_tune -- kernel variants of the five kernel kinds of the RK step (z
  * derivatives, stage combine, projection, y inverse, y forward).  Per kind,
  * bit 0 selects the lines per CTA (tile): two sizes of each kind are
@@ -446,7 +500,7 @@ fc_status ns_set_finite_check(ns_sim_t sim, int every);
  * list of "entry:status:skip:count" (status by name, e.g. FC_ERR_CUDA, or
  * number), read on the first check.  The entry points that check are
  * fc_setup, fc_deriv_z, fc_deriv_z_noalloc, fc_deriv_z_host (and _ex),
- * fc_count_nonfinite, ns_create,
+ * fc_count_nonfinite, fc_noise, ns_create,
  * ns_set_fields, ns_get_fields, ns_get_state, ns_put_state, ns_rhs,
  * fc_poisson_project, rk_step, ns_diagnostics, ns_profiles, ns_interpolate,
  * ns_tune, ns_check_finite, ns_batch_create and ns_batch_step.

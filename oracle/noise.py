@@ -21,7 +21,10 @@ Readings (App. A is silent on these):
       modes (ky > 0, or ky = 0 and kx > 0) and the real part is taken, which
       supplies the conjugate modes.
   A2  kx = 2 pi n / Lx, ky = 2 pi l / Ly with integer n, l; the annulus
-      bounds apply to kx^2 + ky^2 (integers n^2 + l^2 for Lx = Ly = 2 pi).
+      bounds apply to kx^2 + ky^2 (integers n^2 + l^2 for Lx = Ly = 2 pi)
+      and are inclusive: a mode counts as inside when it is within a
+      relative 1e-12 of a bound (so that rounding of 2 pi n / Lx never drops
+      a mode that lies on the bound, such as n^2 + l^2 = 25).
   A3  the random numbers are two per (n, l, m) mode, u_a and u_b in [0, 1):
       a = k^-4 e^{2 pi i u_a}, b = k^-3 e^{2 pi i u_b}; modes are enumerated
       with n ascending, then l ascending, then m ascending, and draw (u_a,
@@ -84,7 +87,7 @@ def modes(Lx: float, Ly: float, kperp2=(4.0, 25.0), mrange=(2, 5)) -> list[tuple
                 continue
             kx, ky = 2 * math.pi * n / Lx, 2 * math.pi * l / Ly
             kp2 = kx * kx + ky * ky
-            if not (kperp2[0] <= kp2 <= kperp2[1]):
+            if not (kperp2[0] * (1 - 1e-12) <= kp2 <= kperp2[1] * (1 + 1e-12)):
                 continue
             for m in range(mrange[0], mrange[1] + 1):
                 out.append((n, l, m))

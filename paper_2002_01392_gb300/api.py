@@ -42,6 +42,12 @@ class NsParams(ctypes.Structure):
                 ("prec", _c_int)]
 
 
+class NoiseParams(ctypes.Structure):
+    _fields_ = [("Lx", _c_double), ("Ly", _c_double), ("Lz", _c_double),
+                ("kperp2_min", _c_double), ("kperp2_max", _c_double), ("m_min", _c_int), ("m_max", _c_int),
+                ("slope_phi", _c_double), ("slope_psi", _c_double), ("amplitude", _c_double)]
+
+
 def _sig(name, args, res=_c_int):
     f = getattr(_lib, name)
     f.argtypes = args
@@ -75,6 +81,10 @@ _sig("ns_check_finite", [_vp, ctypes.POINTER(ctypes.c_longlong), _vp])
 _sig("ns_set_finite_check", [_vp, _c_int])
 _sig("fc_inject_failure", [ctypes.c_char_p, _c_int, ctypes.c_longlong, ctypes.c_longlong])
 _sig("fc_alu_probe", [_c_int, _c_int, _vp, ctypes.POINTER(_c_double), _vp])
+_sig("fc_noise_params_default", [ctypes.POINTER(NoiseParams)])
+_sig("fc_noise_modes", [ctypes.POINTER(NoiseParams), ctypes.POINTER(_c_int)])
+_sig("fc_noise", [ctypes.POINTER(NoiseParams), _c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_c_double), _c_int,
+                  _vp, _vp])
 
 EXPORTED = ["fc_status_str", "fc_last_error", "fc_setup", "fc_setup_ex", "fc_plan_matrix", "fc_plan_info",
             "fc_destroy", "fc_deriv_z", "fc_deriv_z_noalloc", "ns_params_default", "ns_workspace_bytes", "ns_create", "ns_destroy",
@@ -82,7 +92,8 @@ EXPORTED = ["fc_status_str", "fc_last_error", "fc_setup", "fc_setup_ex", "fc_pla
             "ns_put_wall_gradp", "ns_rhs", "fc_poisson_project", "rk_step", "ns_diagnostics",
             "ns_batch_create", "ns_batch_step", "ns_batch_info", "ns_batch_destroy", "ns_interpolate",
             "ns_profiles", "ns_spectrum_shells", "ns_tune", "fc_count_nonfinite", "ns_check_finite",
-            "ns_set_finite_check", "fc_inject_failure", "fc_deriv_z_host", "fc_deriv_z_host_ex", "fc_alu_probe"]
+            "ns_set_finite_check", "fc_inject_failure", "fc_deriv_z_host", "fc_deriv_z_host_ex", "fc_alu_probe",
+            "fc_noise_params_default", "fc_noise_modes", "fc_noise"]
 
 
 def _check(status: int, where: str):
@@ -118,6 +129,39 @@ def count_nonfinite(t, stream=None) -> int:
 
 
 ALU_KINDS = {"ffma": 0, "fadd": 1, "ffma2": 2, "fadd2": 3, "dfma": 4}
+
+
+def noise_params(**kw) -> NoiseParams:
+    """fc_noise_params with the App. A defaults, fields overridden by keyword."""
+    p = NoiseParams()
+    _check(_lib.fc_noise_params_default(ctypes.byref(p)), "fc_noise_params_default")
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def noise_modes(p: NoiseParams) -> int:
+    """Number of (n, l, m) modes (two draws each) of the App. A perturbation."""
+    n = _c_int(0)
+    _check(_lib.fc_noise_modes(ctypes.byref(p), ctypes.byref(n)), "fc_noise_modes")
+    return n.value
+
+
+def fc_noise(p: NoiseParams, draws, out, stream=None):
+    """Write the App. A perturbation built from ``draws`` (2 per mode, host,
+    float64 in [0, 1)) into the device tensor ``out`` of shape [3][Nz][Ny][Nx]
+    (float32 or float64)."""
+    import numpy as np
+    d = np.ascontiguousarray(np.asarray(draws, dtype=np.float64))
+    if out.dim() != 4 or out.shape[0] != 3 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous [3][Nz][Ny][Nx] tensor")
+    _, Nz, Ny, Nx = out.shape
+    _check(_lib.fc_noise(ctypes.byref(p), _dtype_code(out), Nx, Ny, Nz,
+                         d.ctypes.data_as(ctypes.POINTER(_c_double)), int(d.size), _ptr(out), _stream(stream)),
+           "fc_noise")
+    return out
 
 
 def alu_probe(kind: str, iters: int, sink, stream=None) -> float:

@@ -25,7 +25,7 @@ CXX_FLAGS = ["-std=gnu++17", "-O2", "-fPIC", "-I", os.path.join(ROOT, "include")
 
 CU_SOURCES = ["k_deriv.cu", "k_deriv_f32.cu", "k_deriv_f64.cu", "k_deriv_noalloc.cu", "ns_capi.cu", "k_nsz_float.cu", "k_nsz_double.cu", "k_nsz_float_direct.cu", "k_nsz_float_alt.cu",
               "k_nsz_double_direct.cu", "k_nsxy_float.cu", "k_nsxy_double.cu",
-              "k_nsx_float.cu", "k_nsx_double.cu", "k_probe.cu"]
+              "k_nsx_float.cu", "k_nsx_double.cu", "k_probe.cu", "k_noise.cu"]
 CPP_SOURCES = ["capi.cpp", "host_tables.cpp"]
 
 

@@ -381,10 +381,17 @@ extern "C" fc_status fc_deriv_z_host_ex(fc_plan_t plan, fc_dtype dtype, int batc
   const int Nz = plan->data.Nz;
   const size_t yrow = (size_t)Nz * Nx * es;   // bytes of one y row over all z
   // slab: an even number of y rows (so that the kernel pairs the same lines
-  // as a call on the whole field), about slab_bytes of input
+  // as a call on the whole field), at most about slab_bytes of input, the
+  // slabs of a field as equal as that allows (no short last slab)
   long long Yc = (long long)std::max<size_t>(2, slab_bytes / yrow);
   Yc -= Yc % 2;
-  if (Yc >= Ny) Yc = Ny;
+  if (Yc >= Ny) {
+    Yc = Ny;
+  } else {
+    const long long ns = (Ny + Yc - 1) / Yc;
+    Yc = (Ny + ns - 1) / ns;
+    Yc += Yc % 2;
+  }
   s = stage_for(t, (size_t)Yc * yrow);
   if (s) return s;
   // the slabs start after the work already queued on the caller's stream

@@ -154,3 +154,33 @@ def test_host_array_binding_checks_need_no_gpu(api):
     with pytest.raises(TypeError):
         api.fc_deriv_z_host(plan, f.to(torch.int32), None, torch.zeros(2, 33, 4, 6, dtype=torch.int32))
 
+
+
+def test_noise_mode_count_and_argument_checks_need_no_gpu(api):
+    """fc_noise_modes enumerates the same (n, l, m) modes as the oracle (App. A
+    defaults and other boxes); fc_noise rejects bad arguments before any
+    device work."""
+    import math
+    from oracle import noise
+    for kw, ref in (({}, noise.modes(2 * math.pi, 2 * math.pi)),
+                    ({"Lx": 4 * math.pi}, noise.modes(4 * math.pi, 2 * math.pi)),
+                    ({"Ly": 3.0, "kperp2_min": 1.0, "kperp2_max": 9.0, "m_min": 1, "m_max": 3},
+                     noise.modes(2 * math.pi, 3.0, (1.0, 9.0), (1, 3)))):
+        assert api.noise_modes(api.noise_params(**kw)) == len(ref), kw
+    p = api.noise_params()
+    cnt = api.noise_modes(p)
+    draws = (ctypes.c_double * (2 * cnt))()
+    lib = api._lib
+
+    def st(pp, dtype=0, Nx=16, Ny=16, Nz=17, nd=2 * cnt, out=1 << 40):
+        return lib.fc_status_str(lib.fc_noise(ctypes.byref(pp), dtype, Nx, Ny, Nz, draws, nd, out, None)).decode()
+
+    assert st(p, nd=2 * cnt - 1) == "FC_ERR_ARG"          # wrong draw count
+    assert st(p, Nx=10) == "FC_ERR_ARG"                   # the mode n = 5 is not resolved
+    assert st(p, Ny=9) == "FC_ERR_ARG"                    # l = 5
+    assert st(p, Nz=1) == "FC_ERR_ARG"
+    assert st(p, dtype=7) == "FC_ERR_ARG"
+    assert st(p, out=None) == "FC_ERR_ARG"
+    for bad in ({"Lz": 0.0}, {"kperp2_min": 30.0}, {"m_min": 0}, {"m_max": 65}, {"amplitude": float("nan")}):
+        assert st(api.noise_params(**bad)) == "FC_ERR_ARG", bad
+    assert st(api.noise_params(kperp2_min=0.1, kperp2_max=0.2)) == "FC_ERR_ARG"   # empty annulus
