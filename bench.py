@@ -1082,6 +1082,7 @@ def main():
         shape = {"rk-small": (256, 256, 513), "rk-mid": (1024, 1024, 33), "rk-full": None,
                  "rk-smooth": (1024, 1024, 487)}[args.profile_case]
         r = bench_rk(api, torch, args.steps, args.warmup, with_e2e=False, shape=shape, tune=not args.no_tune)
+        r.pop("_err_sample", None)
         print(json.dumps({"profile_case": args.profile_case, **r}))
         return
     if args.profile_case:
