@@ -314,6 +314,34 @@ fc_status ns_diagnostics(ns_sim_t sim, double* div_ms, double* wall_u_ms, double
                          double* flow_rate, double* nusselt, fc_stream_t stream);
 
 /*
+ * ns_set_diag_series -- time series of the ns_diagnostics quantities (the
+ * flow-rate and Nusselt-number histories of Sec. 6 and 7) kept on the
+ * device: after every `every`-th rk_step the diagnostic sums of the new state
+ * are computed on the step's stream into the next of 4096 device slots, with
+ * no synchronisation and no host copy (recording stops when the slots are
+ * full).  every = 0 stops recording.  Every call clears the series and
+ * restarts the step count.  ns_batch_step does not record.  FC_ERR_ARG for
+ * every < 0.  Each recorded step costs one z-derivative pass and one
+ * reduction (as ns_diagnostics) and overwrites the work buffers.
+ */
+fc_status ns_set_diag_series(ns_sim_t sim, int every);
+
+/*
+ * ns_get_diag_series -- copy the first min(max, recorded) entries of the
+ * series to host memory, synchronously (the copy is enqueued on `stream`,
+ * which must be the stream of the recorded steps or ordered after them):
+ * values[5 i + 0 .. 4] = div_ms, wall_u_ms, wall_w_ms, flow_rate, nusselt of
+ * entry i (the definitions and normalisation of ns_diagnostics: the values
+ * ns_diagnostics returns for that state, up to the order of the float64
+ * atomic additions of the reduction); steps[i] (may be
+ * NULL) = its step number counted from ns_set_diag_series; *count (may be
+ * NULL) = the number of entries recorded.  FC_ERR_ARG for max < 0 or a NULL
+ * values with max > 0.
+ */
+fc_status ns_get_diag_series(ns_sim_t sim, int max, double* values, long long* steps, int* count,
+                             fc_stream_t stream);
+
+/*
  * ns_profiles -- horizontal statistics of the current state (Sec. 6 r.m.s.
  * velocity profiles and spectra; Sec. 7 temperature profiles), synchronous,
  * host outputs (each may be NULL), by Parseval from the state's physical rows:

@@ -81,6 +81,9 @@ _sig("ns_check_finite", [_vp, ctypes.POINTER(ctypes.c_longlong), _vp])
 _sig("ns_set_finite_check", [_vp, _c_int])
 _sig("fc_inject_failure", [ctypes.c_char_p, _c_int, ctypes.c_longlong, ctypes.c_longlong])
 _sig("fc_alu_probe", [_c_int, _c_int, _vp, ctypes.POINTER(_c_double), _vp])
+_sig("ns_set_diag_series", [_vp, _c_int])
+_sig("ns_get_diag_series", [_vp, _c_int, ctypes.POINTER(_c_double), ctypes.POINTER(ctypes.c_longlong),
+                            ctypes.POINTER(_c_int), _vp])
 _sig("fc_noise_params_default", [ctypes.POINTER(NoiseParams)])
 _sig("fc_noise_modes", [ctypes.POINTER(NoiseParams), ctypes.POINTER(_c_int)])
 _sig("fc_noise", [ctypes.POINTER(NoiseParams), _c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_c_double), _c_int,
@@ -93,7 +96,7 @@ EXPORTED = ["fc_status_str", "fc_last_error", "fc_setup", "fc_setup_ex", "fc_pla
             "ns_batch_create", "ns_batch_step", "ns_batch_info", "ns_batch_destroy", "ns_interpolate",
             "ns_profiles", "ns_spectrum_shells", "ns_tune", "fc_count_nonfinite", "ns_check_finite",
             "ns_set_finite_check", "fc_inject_failure", "fc_deriv_z_host", "fc_deriv_z_host_ex", "fc_alu_probe",
-            "fc_noise_params_default", "fc_noise_modes", "fc_noise"]
+            "fc_noise_params_default", "fc_noise_modes", "fc_noise", "ns_set_diag_series", "ns_get_diag_series"]
 
 
 def _check(status: int, where: str):
@@ -445,6 +448,29 @@ class Sim:
         vals = [_c_double() for _ in range(5)]
         _check(_lib.ns_diagnostics(self.handle, *[ctypes.byref(v) for v in vals], _stream(stream)), "ns_diagnostics")
         return dict(zip(["div_ms", "wall_u_ms", "wall_w_ms", "flow_rate", "nusselt"], (v.value for v in vals)))
+
+    def set_diag_series(self, every: int):
+        """ns_set_diag_series: record the diagnostics on the device after every
+        ``every``-th step (0: off); clears the series."""
+        _check(_lib.ns_set_diag_series(self.handle, int(every)), "ns_set_diag_series")
+
+    def diag_series(self, stream=None):
+        """ns_get_diag_series: dict of step numbers and the five diagnostics per
+        recorded step (numpy arrays; synchronous)."""
+        import numpy as np
+        n = _c_int(0)
+        _check(_lib.ns_get_diag_series(self.handle, 0, None, None, ctypes.byref(n), _stream(stream)),
+               "ns_get_diag_series")
+        vals = np.zeros((max(n.value, 1), 5))
+        steps = np.zeros(max(n.value, 1), dtype=np.int64)
+        _check(_lib.ns_get_diag_series(self.handle, n.value, vals.ctypes.data_as(ctypes.POINTER(_c_double)),
+                                       steps.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), ctypes.byref(n),
+                                       _stream(stream)), "ns_get_diag_series")
+        vals, steps = vals[:n.value], steps[:n.value]
+        out = {"step": steps}
+        for i, k in enumerate(["div_ms", "wall_u_ms", "wall_w_ms", "flow_rate", "nusselt"]):
+            out[k] = vals[:, i]
+        return out
 
     def close(self):
         if getattr(self, "handle", None):

@@ -1,4 +1,5 @@
 // Navier-Stokes entry points of the C ABI (GPU backend of NsCore).
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -75,7 +76,27 @@ struct ns_sim {
   int check_every = 0;
   long long nsteps = 0;
   unsigned long long* hflag = nullptr;
+  // diagnostic series: after every diag_every-th rk_step the diagnostic sums
+  // of the new state go to the next device slot; diag_at[i] = its step number
+  int diag_every = 0;
+  long long diag_steps = 0;
+  std::vector<long long> diag_at;
 };
+
+// ns_diagnostics' normalisation of the six device sums
+static void diag_scale(const ns_params& p, const double* acc, double* out5) {
+  const double n2 = (double)p.Nx * p.Ny * (double)p.Nx * p.Ny;
+  out5[0] = acc[0] / n2 / p.Nz;
+  out5[1] = acc[1] / n2 / 2.0;
+  out5[2] = acc[2] / n2 / 2.0;
+  out5[3] = acc[3] / ((double)p.Nx * p.Ny) / p.Nz;
+  if (p.nfields == 4 && p.gamma != 0.0) {
+    const double m0 = acc[4] / ((double)p.Nx * p.Ny), m1 = acc[5] / ((double)p.Nx * p.Ny);
+    out5[4] = 0.5 * ((1.0 - m0 / p.gamma) + (1.0 - m1 / p.gamma));
+  } else {
+    out5[4] = 0.0;
+  }
+}
 
 static fc_status check_enqueue(ns_sim* s, cudaStream_t st) {
   fc_status r = s->core.count_nonfinite_any(false, st);
@@ -244,7 +265,40 @@ fc_status rk_step(ns_sim_t s, double dt, fc_stream_t stream) {
   st = check_flag(s, "rk_step");
   if (!st) st = s->core.step_any(dt, stream);
   if (!st && s->check_every > 0 && ++s->nsteps % s->check_every == 0) st = check_enqueue(s, (cudaStream_t)stream);
+  if (!st && s->diag_every > 0 && ++s->diag_steps % s->diag_every == 0 && (int)s->diag_at.size() < NS_DIAG_SLOTS) {
+    st = s->core.diag_record_any((int)s->diag_at.size(), stream);
+    if (!st) s->diag_at.push_back(s->diag_steps);
+  }
   return st;
+}
+
+fc_status ns_set_diag_series(ns_sim_t s, int every) {
+  fc_status st = check_sim(s, "ns_set_diag_series");
+  if (st) return st;
+  if (every < 0) { set_error("ns_set_diag_series: every must be >= 0"); return FC_ERR_ARG; }
+  s->diag_every = every;
+  s->diag_steps = 0;
+  s->diag_at.clear();
+  return FC_OK;
+}
+
+fc_status ns_get_diag_series(ns_sim_t s, int max, double* values, long long* steps, int* count, fc_stream_t stream) {
+  fc_status st = check_sim(s, "ns_get_diag_series");
+  if (st) return st;
+  if (max < 0 || (max > 0 && !values)) { set_error("ns_get_diag_series: max >= 0 and values non-NULL"); return FC_ERR_ARG; }
+  const int n = std::min(max, (int)s->diag_at.size());
+  if (count) *count = (int)s->diag_at.size();
+  if (n == 0) return FC_OK;
+  std::vector<double> acc(8 * (size_t)n);
+  st = cuda_status(cudaMemcpyAsync(acc.data(), s->core.ws + s->core.l.dser, sizeof(double) * acc.size(),
+                                   cudaMemcpyDeviceToHost, (cudaStream_t)stream), "cudaMemcpyAsync(diagnostic series)");
+  if (!st) st = cuda_status(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+  if (st) return st;
+  for (int i = 0; i < n; ++i) {
+    diag_scale(s->core.p, &acc[8 * (size_t)i], values + 5 * (size_t)i);
+    if (steps) steps[i] = s->diag_at[i];
+  }
+  return FC_OK;
 }
 
 fc_status ns_set_finite_check(ns_sim_t s, int every) {
@@ -527,20 +581,13 @@ fc_status ns_diagnostics(ns_sim_t s, double* div_ms, double* wall_u_ms, double* 
   double acc[6];
   st = s->core.diagnostics_any(acc, stream);
   if (st) return st;
-  const ns_params& p = s->core.p;
-  const double n2 = (double)p.Nx * p.Ny * (double)p.Nx * p.Ny;
-  if (div_ms) *div_ms = acc[0] / n2 / p.Nz;
-  if (wall_u_ms) *wall_u_ms = acc[1] / n2 / 2.0;
-  if (wall_w_ms) *wall_w_ms = acc[2] / n2 / 2.0;
-  if (flow_rate) *flow_rate = acc[3] / ((double)p.Nx * p.Ny) / p.Nz;
-  if (nusselt) {
-    if (p.nfields == 4 && p.gamma != 0.0) {
-      const double m0 = acc[4] / ((double)p.Nx * p.Ny), m1 = acc[5] / ((double)p.Nx * p.Ny);
-      *nusselt = 0.5 * ((1.0 - m0 / p.gamma) + (1.0 - m1 / p.gamma));
-    } else {
-      *nusselt = 0.0;
-    }
-  }
+  double v[5];
+  diag_scale(s->core.p, acc, v);
+  if (div_ms) *div_ms = v[0];
+  if (wall_u_ms) *wall_u_ms = v[1];
+  if (wall_w_ms) *wall_w_ms = v[2];
+  if (flow_rate) *flow_rate = v[3];
+  if (nusselt) *nusselt = v[4];
   return FC_OK;
 }
 

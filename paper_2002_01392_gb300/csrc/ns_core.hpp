@@ -29,7 +29,7 @@ struct NsLayout {
   long long lines, ntiles, plines;   // lines, tiles of TL lines, padded lines
   size_t es;  // bytes per real
   // byte offsets inside the workspace
-  size_t X[3], DZ, DZZ, V, DY, NL, gradp, diag, nfin;
+  size_t X[3], DZ, DZZ, V, DY, NL, gradp, diag, nfin, dser;
   size_t X64[3], d2r, hfr;   // float64 mean-line shadows and real-space z kernels
   int nmean;
   size_t kxo, kyo, kzo, kx, ky, fx, fy, Mr, Mr2, twz, twz2, H1, H2, Hf, chirp, Hbf, Hbi, twx, twy, twxh;
@@ -66,6 +66,9 @@ inline bool xy_shape_for(int N, int* L1, int* L2) {
 #undef FC_XYPICK
   return ok;
 }
+
+// slots of the device-side diagnostic series (ns_set_diag_series)
+constexpr int NS_DIAG_SLOTS = 4096;
 
 inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
   if (p.Nx < 2 || p.Ny < 2 || p.Nz < 2 * p.d || p.d < 2 || p.d > DMAX || p.C < p.d || p.C > 64 ||
@@ -109,6 +112,7 @@ inline fc_status ns_layout(const ns_params& p, NsLayout* o) {
   l.NL = take(cs * l.nf * l.Nz * l.plines);
   l.gradp = take(sizeof(double) * 2 * 4 * l.lines);
   l.diag = take(sizeof(double) * 8);
+  l.dser = take(sizeof(double) * 8 * NS_DIAG_SLOTS);
   l.nfin = take(sizeof(unsigned long long));
   l.nmean = l.nf == 4 ? 3 : 2;
   for (int i = 0; i < 3; ++i) l.X64[i] = take(16 * (size_t)l.nmean * l.Np);
@@ -828,6 +832,24 @@ struct NsCore {
   }
   fc_status diagnostics_any(double out[6], void* st) {
     return f32() ? diagnostics<float>(out, st) : diagnostics<double>(out, st);
+  }
+  // the same sums into slot `slot` of the device-side series (asynchronous)
+  template <class T>
+  fc_status diag_record(int slot, void* st) {
+    double* acc = at<double>(l.dser) + 8 * (size_t)slot;
+    fc_status s = bk.memset(acc, 0, sizeof(double) * 8, st);
+    if (!s) s = z_deriv<T>(Xb<T>(cur), l.nf, st);
+    if (!s) {
+      using K = KDiag<T>;
+      typename K::Args a;
+      a.g = zgeom(l.nf); a.t = ztab<T>(); a.Nx = p.Nx;
+      a.X = Xb<T>(cur); a.DZ = buf<T>(l.DZ); a.acc = acc;
+      s = bk.template run<K>(a, l.ntiles, st);
+    }
+    return s;
+  }
+  fc_status diag_record_any(int slot, void* st) {
+    return f32() ? diag_record<float>(slot, st) : diag_record<double>(slot, st);
   }
   size_t state_bytes() const { return 2 * l.es * l.nf * l.Np * l.plines; }
   // wall planes: internal [2][2][Ny][Kxp] <-> public [2][2][Ny][Kx] (complex double)

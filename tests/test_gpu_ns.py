@@ -619,3 +619,35 @@ def test_general_parameters_match_oracle(api):
     assert _wall_err(out, ref) < 1e-11
     assert _rel(sim.wall_gradp().cpu().numpy(), gref) < 1e-9
     sim.close()
+
+
+def test_diag_series_equals_synchronous_diagnostics(api):
+    """ns_set_diag_series / ns_get_diag_series: the device-recorded diagnostics
+    after every 2nd step are the values ns_diagnostics returns for the same
+    states (Boussinesq, float32, Nu and flow rate included), up to the order of
+    the reduction's float64 atomic additions."""
+    import synth
+    p = api.ns_params(Nx=32, Ny=32, Nz=33, nfields=4, prec="f32", nu=1e-2, kappa=1e-2, gamma=1.0)
+    v = synth.boussinesq_fields(32, 32, 33, seed_offset=5).astype(np.float32)
+    a, b = api.Sim(p), api.Sim(p)
+    for s_ in (a, b):
+        s_.set_fields(torch.from_numpy(v).cuda())
+    a.set_diag_series(2)
+    ref = []
+    for k in range(1, 8):
+        a.step(1e-3)
+        b.step(1e-3)
+        if k % 2 == 0:
+            ref.append(b.diagnostics())
+    ser = a.diag_series()
+    assert list(ser["step"]) == [2, 4, 6]
+    for i, r in enumerate(ref):
+        for key, val in r.items():
+            assert abs(ser[key][i] - val) <= 1e-12 * abs(val) + 1e-300, (i, key)
+    a.set_diag_series(0)
+    a.step(1e-3)
+    assert len(a.diag_series()["step"]) == 0
+    with pytest.raises(api.FcError):
+        a.set_diag_series(-1)
+    a.close()
+    b.close()
