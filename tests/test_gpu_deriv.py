@@ -180,7 +180,7 @@ def test_host_buffers_bitwise_device_path(api, dtype, pinned):
     mk = (lambda: torch.empty_like(f).pin_memory()) if pinned else (lambda: torch.empty_like(f))
     h1, h2 = mk(), mk()
     row = Nz * Nx * f.element_size()
-    api.fc_deriv_z_host(plan, f, h1, h2, slab_bytes=6 * row)     # slabs of 6 rows: 6, 6, 6, 5
+    api.fc_deriv_z_host(plan, f, h1, h2, slab_bytes=6 * row)     # slabs: 2, 6, 6, 6, 3 rows, then 6, 6, 6, 5
     torch.cuda.synchronize()
     assert torch.equal(h1, d1.cpu()) and torch.equal(h2, d2.cpu())
     h3 = mk()
