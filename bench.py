@@ -1035,8 +1035,8 @@ def main():
     ap.add_argument("--no-rk", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="profile cases: default tiles, no autotuning launches")
     ap.add_argument("--profile-case", default=None,
-                    choices=["deriv32", "deriv64", "rk-small", "rk-mid", "rk-full", "rk-smooth"],
-                    help="small single-kernel case for ncu (deriv: fc_deriv_z on 2x256x256x513; rk-*: one RK3 grid), no e2e / CPU leg")
+                    choices=["deriv32", "deriv64", "rk-small", "rk-mid", "rk-full", "rk-smooth", "noise"],
+                    help="small single-kernel case for ncu (deriv: fc_deriv_z on 2x256x256x513; rk-*: one RK3 grid; noise: fc_noise on 256x256x513), no e2e / CPU leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1078,6 +1078,11 @@ def main():
     from paper_2002_01392_gb300 import api
     dev_index = torch.cuda.current_device()
     hbm_peak, peak_kind = _peaks()
+    if args.profile_case == "noise":
+        r = bench_noise(api, torch, reps=args.steps, warmup=args.warmup, Nx=256, Ny=256, Nz=513)
+        r.pop("_err_sample", None)
+        print(json.dumps({"profile_case": args.profile_case, **r}))
+        return
     if args.profile_case and args.profile_case.startswith("rk"):
         shape = {"rk-small": (256, 256, 513), "rk-mid": (1024, 1024, 33), "rk-full": None,
                  "rk-smooth": (1024, 1024, 487)}[args.profile_case]
