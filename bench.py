@@ -552,6 +552,20 @@ def bench_rk(api, torch, steps, warmup, with_e2e=True, shape=None, tune=True):
     stage_s = float(times.mean()) / 3
     res["roofline_stage"] = {"bound": "hbm", "model_bytes_per_point": 288, "achieved": 288 * pts / stage_s / 1e9,
                              "peak": hbm_peak, "unit": "GB/s", "frac": 288 * pts / stage_s / 1e9 / hbm_peak}
+    if tune and any(tiles):
+        # what the autotuner buys: the same steps with the built-in default variants
+        sim.tune(0)
+        sim.step(dt)
+        torch.cuda.synchronize()
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        for _ in range(steps):
+            sim.step(dt)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        res["default_variants_ms_per_step"] = d0.elapsed_time(d1) / steps
+        res["autotune_speedup"] = res["default_variants_ms_per_step"] / (total / steps * 1e3)
+        sim.tune(1)                          # back to the tuned variants (cached)
     out = sim.get_fields()
     res["finite"] = bool(torch.isfinite(out).all().item())
     res["w_wall_rel"] = float(out[2, [0, -1]].abs().max().item() / max(out[:3].abs().max().item(), 1e-300))
@@ -663,8 +677,18 @@ def bench_ensemble(api, torch, steps=5, warmup=3, n=64):
         outs.append(pl.to_physical(st).cpu().numpy())
     samples["cufft_f64"] = outs
 
-    # FP32, one graph launch per step of all members
+    # FP32, one graph launch per step of all members: first with every member
+    # on the built-in default variants (what the autotuner buys), then tuned
     sims = make("f32")
+    batch = api.Batch(sims)
+    for s_ in sims:
+        s_.tune(0)
+    for _ in range(warmup):
+        batch.step(dt)
+    tdef = timed(lambda: batch.step(dt), steps)
+    batch.close()
+    for s_ in sims:
+        s_.tune(1)
     batch = api.Batch(sims)
     for _ in range(warmup):
         batch.step(dt)
@@ -716,6 +740,8 @@ def bench_ensemble(api, torch, steps=5, warmup=3, n=64):
 
     res = {"instances": n, "grids": [list(g) for g in synth.ENSEMBLE_GRIDS], "points": pts,
            **arm(t), "graph_nodes": info["graph_nodes"], "variants_autotuned": variants,
+           "fp32_graph_default_variants": arm(tdef),
+           "autotune_speedup": float(np.percentile(tdef, 50) / np.percentile(t, 50)),
            "graph_launches_per_step": 1, "finite": finite,
            "fp32_sequential": arm(t32), "fp64_library_sequential": arm(t64),
            "fp64_cufft_plain_sequential": dict(arm(tcu), what="PlainCufftNS: torch.fft (cuFFT) float64 + "
