@@ -37,11 +37,16 @@ namespace fcns {
 // SYM: the kernels sit on the whole window |j| <= N' - 1 (L >= 2 N' - 1, or
 // L = N'), so H1 is purely imaginary and H2 purely real: the spectrum
 // products are two real multiplies per value instead of a complex multiply.
-template <class T, int L1_, int L2_, int LINES_, int JN_ = L1_, bool SYM = false>
+// JI: register rows j < JI hold only indices n = r + L2 j below Nz - DMAX
+// (the launcher picks JI > 0 only when Nz is large enough for that): their
+// loads and stores need no bounds check and they hold no continuation or end
+// values (row 0 still keeps the first d values).
+template <class T, int L1_, int L2_, int LINES_, int JN_ = L1_, bool SYM = false, int JI = 0>
 struct DerivPair {
   using E = Eng<T, L1_, L2_, LINES_>;
   using C = cx<T>;
   static constexpr int L1 = L1_, L2 = L2_, LINES = LINES_, JN = JN_;
+  static_assert(JI <= JN_, "interior rows lie among the loaded rows");
   static constexpr int THREADS = E::THREADS, NPHASE = 4;
   static constexpr int MINB = THREADS <= 160 ? 3 : (THREADS <= 320 ? 2 : 1);
   static constexpr int MR_MAX = 640;
@@ -126,7 +131,7 @@ struct DerivPair {
           }
           const int n = r + L2 * j;
           C x = mk<T>(0, 0);
-          if (n < a.Nz) {
+          if (j < JI || n < a.Nz) {
             const T* p = a.f + base + (long long)n * a.zstride;
             if (a.vec) {
               if (va) x = *reinterpret_cast<const C*>(p);
@@ -136,8 +141,10 @@ struct DerivPair {
             }
           }
           R.v[j] = x;
-          if (n < a.d) Ev[n] = x;
-          if (n >= a.Nz - a.d && n < a.Nz) Ev[DMAX + n - (a.Nz - a.d)] = x;
+          if (j == 0 || j >= JI) {
+            if (n < a.d) Ev[n] = x;
+            if (j >= JI && n >= a.Nz - a.d && n < a.Nz) Ev[DMAX + n - (a.Nz - a.d)] = x;
+          }
         }
       }
     } else if constexpr (P == 1) {
@@ -151,7 +158,7 @@ struct DerivPair {
       }
       if (r < L2) {
 #pragma unroll
-        for (int j = 0; j < JN; ++j) {
+        for (int j = JI; j < JN; ++j) {
           const int n = r + L2 * j;
           if (n >= a.Nz && n < a.Np) R.v[j] = cont_cplx(n - a.Nz, Ev, Ev + DMAX, a.d, a.Cc, Ms, Ms2);
         }
@@ -191,7 +198,7 @@ struct DerivPair {
 #pragma unroll
           for (int j = 0; j < JN; ++j) {
             const int n = r + L2 * j;
-            if (n < a.Nz) {
+            if (j < JI || n < a.Nz) {
               T* p = out + base + (long long)n * a.zstride;
               if (a.vec) {
                 *reinterpret_cast<C*>(p) = cscale(R.v[j], sc);

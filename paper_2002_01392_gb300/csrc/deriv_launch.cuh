@@ -10,10 +10,10 @@
 namespace fcns {
 
 
-template <class T, int L1, int L2, int LINES, int JN, bool SYM>
+template <class T, int L1, int L2, int LINES, int JN, bool SYM, int JI = 0>
 fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long long lines, double Lz,
                     const void* f, void* df, void* d2f, cudaStream_t stream) {
-  using K = DerivPair<T, L1, L2, LINES, JN, SYM>;
+  using K = DerivPair<T, L1, L2, LINES, JN, SYM, JI>;
   static_assert(K::smem_bytes <= 227 * 1024, "shared memory budget");
   typename K::Args a;
   a.f = static_cast<const T*>(f);
@@ -68,6 +68,13 @@ fc_status launch_deriv_typed(const DerivDevTables& t, const PlanData& p, int bat
 // registers are known zeros; with L >= 2 N' - 1 (or L = N') the kernel
 // spectra are purely imaginary / real (symmetric placement, host_tables)
   const bool sym = t.L == p.Np || t.L >= 2 * p.Np - 1;
+  // float32 at L = 1080 (the length every Nz from 481 to 551 with C <= 64 is
+  // given): register rows 0..12 (n <= 467) lie below Nz - 10 whenever
+  // Nz >= 481, so they run without bounds checks (DerivPair JI)
+  if constexpr (F) {
+    if (t.L == 1080 && sym && p.Np <= 36 * 16 && p.Nz >= 481)
+      return run_deriv<T, 30, 36, 4, 16, true, 13>(t, p, batch, lines, Lz, f, df, d2f, stream);
+  }
 #define FC_CASE(LL, A, B, LF, LD)                                                                          \
   case LL:                                                                                                 \
     if (p.Np <= B * (A / 2 + 1))                                                                           \
