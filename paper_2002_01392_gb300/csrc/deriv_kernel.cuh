@@ -41,7 +41,10 @@ namespace fcns {
 // (the launcher picks JI > 0 only when Nz is large enough for that): their
 // loads and stores need no bounds check and they hold no continuation or end
 // values (row 0 still keeps the first d values).
-template <class T, int L1_, int L2_, int LINES_, int JN_ = L1_, bool SYM = false, int JI = 0>
+// FULL: every tile holds LINES whole pairs and every pair is one aligned
+// vector (the launcher checks: even line count, a multiple of 2 LINES, aligned
+// arrays), so the per-element pair checks are left out.
+template <class T, int L1_, int L2_, int LINES_, int JN_ = L1_, bool SYM = false, int JI = 0, bool FULL = false>
 struct DerivPair {
   using E = Eng<T, L1_, L2_, LINES_>;
   using C = cx<T>;
@@ -118,7 +121,7 @@ struct DerivPair {
     const long long field = bid / a.tiles;
     const long long pair = (bid % a.tiles) * LINES + li;
     const long long la = 2 * pair;                 // first line of the pair
-    const bool va = la < a.lines, vb = la + 1 < a.lines;
+    const bool va = FULL || la < a.lines, vb = FULL || la + 1 < a.lines;
     const long long base = field * a.bstride + la;
 
     if constexpr (P == 0) {
@@ -133,7 +136,7 @@ struct DerivPair {
           C x = mk<T>(0, 0);
           if (j < JI || n < a.Nz) {
             const T* p = a.f + base + (long long)n * a.zstride;
-            if (a.vec) {
+            if (FULL || a.vec) {
               if (va) x = *reinterpret_cast<const C*>(p);
             } else {
               if (va) x.x = p[0];
@@ -200,7 +203,7 @@ struct DerivPair {
             const int n = r + L2 * j;
             if (j < JI || n < a.Nz) {
               T* p = out + base + (long long)n * a.zstride;
-              if (a.vec) {
+              if (FULL || a.vec) {
                 *reinterpret_cast<C*>(p) = cscale(R.v[j], sc);
               } else {
                 p[0] = R.v[j].x * sc;

@@ -10,10 +10,10 @@
 namespace fcns {
 
 
-template <class T, int L1, int L2, int LINES, int JN, bool SYM, int JI = 0>
+template <class T, int L1, int L2, int LINES, int JN, bool SYM, int JI = 0, bool FULL = false>
 fc_status run_deriv(const DerivDevTables& t, const PlanData& p, int batch, long long lines, double Lz,
                     const void* f, void* df, void* d2f, cudaStream_t stream) {
-  using K = DerivPair<T, L1, L2, LINES, JN, SYM, JI>;
+  using K = DerivPair<T, L1, L2, LINES, JN, SYM, JI, FULL>;
   static_assert(K::smem_bytes <= 227 * 1024, "shared memory budget");
   typename K::Args a;
   a.f = static_cast<const T*>(f);
@@ -72,8 +72,13 @@ fc_status launch_deriv_typed(const DerivDevTables& t, const PlanData& p, int bat
   // given): register rows 0..12 (n <= 467) lie below Nz - 10 whenever
   // Nz >= 481, so they run without bounds checks (DerivPair JI)
   if constexpr (F) {
-    if (t.L == 1080 && sym && p.Np <= 36 * 16 && p.Nz >= 481)
-      return run_deriv<T, 30, 36, 4, 16, true, 13>(t, p, batch, lines, Lz, f, df, d2f, stream);
+    if (t.L == 1080 && sym && p.Np <= 36 * 16 && p.Nz >= 481) {
+      // whole tiles of aligned pair vectors: no per-element pair checks (FULL)
+      const uintptr_t al = 2 * sizeof(T);
+      const bool full = lines % 8 == 0 && ((uintptr_t)f | (uintptr_t)df | (uintptr_t)d2f) % al == 0;
+      return full ? run_deriv<T, 30, 36, 4, 16, true, 13, true>(t, p, batch, lines, Lz, f, df, d2f, stream)
+                  : run_deriv<T, 30, 36, 4, 16, true, 13>(t, p, batch, lines, Lz, f, df, d2f, stream);
+    }
   }
 #define FC_CASE(LL, A, B, LF, LD)                                                                          \
   case LL:                                                                                                 \

@@ -12,10 +12,10 @@
 
 namespace fcns {
 
-template <class T, int L1, int L2, int LINES, int JN, bool SYM, int JI = 0>
+template <class T, int L1, int L2, int LINES, int JN, bool SYM, int JI = 0, bool FULL = false>
 static int emu_deriv_k(const double* Mr, int d, int Cc, int Nz, int batch, long long lines, double Lz,
                        const T* f, T* df, T* d2f) {
-  using K = DerivPair<T, L1, L2, LINES, JN, SYM, JI>;
+  using K = DerivPair<T, L1, L2, LINES, JN, SYM, JI, FULL>;
   const int L = L1 * L2;
   std::vector<std::complex<double>> H1, H2, tw;
   deriv_conv_spectra(Nz, Nz + Cc, L, &H1, &H2);
@@ -52,7 +52,8 @@ static int emu_deriv(const double* Mr, int d, int Cc, int Nz, int batch, long lo
   // the interior-row form fc_deriv_z runs for float32 at L = 1080, Nz >= 481
   if constexpr (sizeof(T) == 4 && L1 == 30 && L2 == 36 && JN == 16)
     if (L >= 2 * Np - 1 && Nz >= 481)
-      return emu_deriv_k<T, L1, L2, LINES, JN, true, 13>(Mr, d, Cc, Nz, batch, lines, Lz, f, df, d2f);
+      return lines % 8 == 0 ? emu_deriv_k<T, L1, L2, LINES, JN, true, 13, true>(Mr, d, Cc, Nz, batch, lines, Lz, f, df, d2f)
+                            : emu_deriv_k<T, L1, L2, LINES, JN, true, 13>(Mr, d, Cc, Nz, batch, lines, Lz, f, df, d2f);
   if (L == Np || L >= 2 * Np - 1)
     return emu_deriv_k<T, L1, L2, LINES, JN, true>(Mr, d, Cc, Nz, batch, lines, Lz, f, df, d2f);
   return emu_deriv_k<T, L1, L2, LINES, JN, false>(Mr, d, Cc, Nz, batch, lines, Lz, f, df, d2f);
