@@ -1171,7 +1171,7 @@ def main():
                      "peak": hbm_peak, "unit": "GB/s",
                      "frac": r32["alg_bytes_per_call"] / r32["seconds_per_call_mean"] / 1e9 / hbm_peak,
                      "traffic": _measured_traffic("fc_deriv_z_f32"), "peak_kind": peak_kind,
-                     "kernel": "fc_deriv_z conv L=1080 FP32, paired lines, real-valued kernel spectra, registers j >= 16 known zero, rows j < 13 without bounds checks (phased_kernel<DerivPair<float,30,36,4,16,1,13>>)",
+                     "kernel": "fc_deriv_z conv L=1080 FP32, paired lines, real-valued kernel spectra, registers j >= 16 known zero, rows j < 13 without bounds checks, whole tiles (phased_kernel<DerivPair<float,30,36,4,16,1,13,1>>)",
                      "algorithmic_bytes_per_point": 12, "traffic_source": "profiles/traffic.txt (ncu, small case scaled x6)"},
         "roofline_alu": _deriv_alu_roofline(r32, alu["ffma"]["tflops"], "measured FFMA rate (fc_alu_probe)"),
         "alu_peaks_measured": alu,
