@@ -245,7 +245,7 @@ def bench_deriv(api, torch, dtype_np, steps, warmup, with_e2e=True):
     B, Nz, Ny, Nx = shape
     bs, ys, xs = g.integers(0, B, 64), g.integers(0, Ny, 64), g.integers(0, Nx, 64)
     res["_samples"] = tuple(t[bs, :, ys, xs].double().cpu().numpy().T for t in (f, d1, d2))
-    if with_e2e:
+    def e2e():
         # end to end through the host-array entry point (fc_deriv_z_host): the
         # library moves page-locked host arrays through the GPU in slabs, with
         # the copies in both directions overlapping the kernels; host clock
@@ -265,16 +265,31 @@ def bench_deriv(api, torch, dtype_np, steps, warmup, with_e2e=True):
         te = time.perf_counter() - t0
         same = bool(torch.equal(h1[:, ::16, ::16], d1[:, ::16, ::16].cpu()) and
                     torch.equal(h2[:, ::16, ::16], d2[:, ::16, ::16].cpu()))
-        res["e2e"] = {"value": replica_value(torch, pts * n_e2e, te), "unit": "grid-points/s",
-                      "h2d_bytes_per_step": es * pts, "d2h_bytes_per_step": 2 * es * pts,
-                      "api": "fc_deriv_z_host (host arrays, page-locked)", "bitwise_equal_device_path": same,
-                      "calls": n_e2e, "ms_per_call_p50": float(np.median(calls) * 1e3),
-                      "ms_per_call_max": float(max(calls) * 1e3),
-                      "link_floor_ms": 2 * es * pts / 193.5e9 * 1e3,
-                      "link_floor_note": "device-to-host bytes / 193.5 GB/s, the pinned copy rate measured on this "
-                                         "pool's GB300 hosts (the larger of the two directions)"}
-    del f, d1, d2
-    torch.cuda.empty_cache()
+        return {"value": replica_value(torch, pts * n_e2e, te), "unit": "grid-points/s",
+                "h2d_bytes_per_step": es * pts, "d2h_bytes_per_step": 2 * es * pts,
+                "api": "fc_deriv_z_host (host arrays, page-locked)", "bitwise_equal_device_path": same,
+                "calls": n_e2e, "ms_per_call_p50": float(np.median(calls) * 1e3),
+                "ms_per_call_max": float(max(calls) * 1e3),
+                "link_floor_ms": 2 * es * pts / 193.5e9 * 1e3,
+                "link_floor_note": "device-to-host bytes / 193.5 GB/s, the pinned copy rate measured on this "
+                                   "pool's GB300 hosts (the larger of the two directions)",
+                "clock_sampling": "off during this measurement (nvidia-smi queries stall host copies)"}
+
+    def finish():
+        nonlocal f, d1, d2
+        out = e2e() if with_e2e else None
+        del f, d1, d2
+        torch.cuda.empty_cache()
+        return out
+
+    if with_e2e == "defer":
+        # the caller runs the host-array measurement later (outside the clock
+        # sampling, whose nvidia-smi queries were measured to stall host copies)
+        res["_e2e"] = finish
+        return res
+    e = finish()
+    if e is not None:
+        res["e2e"] = e
     return res
 
 
@@ -1127,8 +1142,12 @@ def main():
     # single-GPU context: with several replicas only the headline is timed
     extras = world == 1 and not args.no_rk
     with ClockSampler(dev_index) as clk:
-        r32 = bench_deriv(api, torch, np.float32, args.steps, args.warmup)
+        r32 = bench_deriv(api, torch, np.float32, args.steps, args.warmup, with_e2e="defer")
+    r32["e2e"] = r32.pop("_e2e")()
+    with ClockSampler(dev_index) as clk_rk:
         rk = bench_rk(api, torch, args.rk_steps, 3) if extras else None
+    if rk:
+        rk["clocks"] = clk_rk.summary()
     r64 = rc = rks = ens = srv = srv_low = rs = nz = None
     if world == 1:
         r64 = bench_deriv(api, torch, np.float64, max(3, args.steps // 4), 2, with_e2e=False)

@@ -188,3 +188,34 @@ def test_host_buffers_bitwise_device_path(api, dtype, pinned):
     assert torch.equal(h3, d2.cpu())
     plan.close()
 
+
+
+def test_length_1080_paths_agree_bitwise(api, Mr_5_25):
+    """At L = 1080 (Nz = 513) the float32 launcher picks among three forms of
+    the same kernel: whole tiles of aligned pair vectors (line count a
+    multiple of 8), bounds-checked pairs (other even line counts), and
+    element loads (arrays not 8-byte aligned).  All compute the same
+    arithmetic, so lines they share agree bitwise."""
+    Nz = 513
+    plan = api.Plan(5, 25, Nz)
+    sf = synth.SeparableField(16, 8, Nz, seed_offset=3)
+    f = torch.from_numpy(sf.field(0).astype(np.float32)).cuda()          # 128 lines: whole tiles
+    d1, d2 = torch.empty_like(f), torch.empty_like(f)
+    api.fc_deriv_z(plan, f, d1, d2)
+    # the first 6 lines of every z row: 6 lines, not a multiple of 8
+    g = f[:, 0, :6].contiguous().reshape(Nz, 1, 6)
+    e1, e2 = torch.empty_like(g), torch.empty_like(g)
+    api.fc_deriv_z(plan, g, e1, e2)
+    # the same 128 lines in buffers offset by one float (4-byte aligned only)
+    buf = torch.empty(Nz * 128 + 1, device="cuda")
+    h = buf[1:].view(Nz, 8, 16)
+    h.copy_(f)
+    ob1, ob2 = torch.empty(Nz * 128 + 1, device="cuda"), torch.empty(Nz * 128 + 1, device="cuda")
+    o1, o2 = ob1[1:].view(Nz, 8, 16), ob2[1:].view(Nz, 8, 16)
+    api.fc_deriv_z(plan, h, o1, o2)
+    torch.cuda.synchronize()
+    assert torch.equal(o1, d1) and torch.equal(o2, d2)
+    assert torch.equal(e1.reshape(Nz, 6), d1[:, 0, :6]) and torch.equal(e2.reshape(Nz, 6), d2[:, 0, :6])
+    f64 = sf.field(0)[None].astype(np.float32).astype(np.float64)
+    _check(d1[None].cpu().numpy(), f64, Mr_5_25, Nz, 1, np.float32)
+    _check(d2[None].cpu().numpy(), f64, Mr_5_25, Nz, 2, np.float32)
