@@ -25,6 +25,18 @@
 
 namespace fcns {
 
+// float32 input loads cached in L2 only (float64: through L1, measured 11 %
+// faster there; the host-check build: a plain load)
+template <class X>
+FC_HD X ld_stream(const X* p) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (std::is_same_v<X, float> || std::is_same_v<X, float2>) return __ldcg(p);
+  else return *p;
+#else
+  return *p;
+#endif
+}
+
 // fc_deriv_z with two adjacent real z-lines packed as one complex line
 // x = a + i b.  The derivative kernels d1, d2 of the N'-periodic grid are
 // real, so one forward transform X = FFT_L(x) serves both lines and
@@ -135,12 +147,14 @@ struct DerivPair {
           const int n = r + L2 * j;
           C x = mk<T>(0, 0);
           if (j < JI || n < a.Nz) {
+            // streamed once: cached in L2 only, so that it does not evict the
+            // twiddle and spectrum tables from L1
             const T* p = a.f + base + (long long)n * a.zstride;
             if (FULL || a.vec) {
-              if (va) x = *reinterpret_cast<const C*>(p);
+              if (va) x = ld_stream(reinterpret_cast<const C*>(p));
             } else {
-              if (va) x.x = p[0];
-              if (vb) x.y = p[1];
+              if (va) x.x = ld_stream(p);
+              if (vb) x.y = ld_stream(p + 1);
             }
           }
           R.v[j] = x;
