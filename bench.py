@@ -814,7 +814,7 @@ def bench_serving(api, torch, rate=2000.0, duration=2.0, resident=48, slots=8):
     for r in reqs:
         if r.kind == "project":
             r.inp = inputs[r.sim]
-    stats = srv.run(reqs)
+    stats = srv.run(reqs, max_wall_s=300.0)
     stats.update({"arrival_rate_per_s": rate, "duration_s": duration, "slots": slots,
                   "grids": [list(x) for x in grids], "mix": "50/50 fc_poisson_project / rk_step"})
     srv.close()
@@ -1010,8 +1010,12 @@ def _on_all_cores(worker, args_of_rank, cores):
     single-threaded); returns (total units, wall seconds of the slowest)."""
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.map(worker, [args_of_rank(i) for i in range(cores)])
+        # bounded: a worker that dies (e.g. out of host memory) must not hang the bench
+        res = pool.map_async(worker, [args_of_rank(i) for i in range(cores)]).get(timeout=POOL_TIMEOUT_S)
     return sum(r[0] for r in res), max(r[1] for r in res)
+
+
+POOL_TIMEOUT_S = 300.0
 
 
 _REF = {}
@@ -1090,11 +1094,12 @@ def main():
         import multiprocessing as mp
         cores = host_cores()
         with mp.get_context("spawn").Pool(cores, initializer=_ref_init) as pool:
-            pool.map(_ref_step, range(cores))                  # tables / fields built, first call
+            pool.map_async(_ref_step, range(cores)).get(timeout=POOL_TIMEOUT_S)   # tables / fields built, first call
             for _ in range(args.warmup):
-                pool.map(_ref_step, range(cores))
+                pool.map_async(_ref_step, range(cores)).get(timeout=POOL_TIMEOUT_S)
             t0 = time.perf_counter()
-            pts = sum(sum(pool.map(_ref_step, range(cores))) for _ in range(args.steps))
+            pts = sum(sum(pool.map_async(_ref_step, range(cores)).get(timeout=POOL_TIMEOUT_S))
+                      for _ in range(args.steps))
             dt = time.perf_counter() - t0
         val = pts / dt
         cb = {"value": val, "unit": "grid-points/s", "cores": cores, "kind": "oracle",
@@ -1199,18 +1204,30 @@ def main():
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline_deriv()
+        # the CPU leg (oracle baselines and errors): a failure here is reported
+        # in the line, never lost with it
+        def leg(name, fn):
+            try:
+                fn()
+            except Exception as e:                      # noqa: BLE001
+                out.setdefault("cpu_leg_errors", {})[name] = f"{type(e).__name__}: {e}"[:300]
+
+        def set_cpu():
+            out["cpu_baseline"] = cpu_baseline_deriv()
+        leg("cpu_baseline", set_cpu)
         if out.get("rk_stage"):
-            out["rk_stage"]["cpu_baseline"] = cpu_baseline_rk()
+            def set_rk_cpu():
+                out["rk_stage"]["cpu_baseline"] = cpu_baseline_rk()
+            leg("rk_cpu_baseline", set_rk_cpu)
         for arm in (out["fc_deriv_z"]["fp32"], r64, rs):
             if arm:
-                oracle_accuracy(arm)
+                leg("oracle_accuracy", lambda arm=arm: oracle_accuracy(arm))
         if ens:
-            ensemble_accuracy(ens)
-        rk_accuracy(out.get("rk_stage"))
-        rk_accuracy(out.get("rk_stage_smooth_Np512_1024x1024x487"))
-        serving_accuracy(out.get("serving_poisson_2000_per_s"))
-        noise_accuracy(nz)
+            leg("ensemble_accuracy", lambda: ensemble_accuracy(ens))
+        leg("rk_accuracy", lambda: rk_accuracy(out.get("rk_stage")))
+        leg("rk_smooth_accuracy", lambda: rk_accuracy(out.get("rk_stage_smooth_Np512_1024x1024x487")))
+        leg("serving_accuracy", lambda: serving_accuracy(out.get("serving_poisson_2000_per_s")))
+        leg("noise_accuracy", lambda: noise_accuracy(nz))
     if nz:
         nz.pop("_err_sample", None)
     for arm in (out["fc_deriv_z"]["fp32"], r64, rs):

@@ -191,9 +191,11 @@ class Server:
         done.append(r)
         return True
 
-    def run(self, requests: list[Request]) -> dict:
+    def run(self, requests: list[Request], max_wall_s: float | None = None) -> dict:
         """Serve the requests (sorted by arrival time) in real time; returns
-        latency and throughput statistics."""
+        latency and throughput statistics.  With ``max_wall_s``, requests not
+        yet launched when that much time has passed complete at once with
+        ``error = "FC_ERR_TIMEOUT"`` (those in flight still finish)."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         pending: collections.deque[Request] = collections.deque()
         done: list[Request] = []
@@ -202,6 +204,16 @@ class Server:
         t0 = time.perf_counter()
         while len(done) < len(reqs):
             now = time.perf_counter() - t0
+            if max_wall_s is not None and now > max_wall_s:
+                while i < len(reqs):
+                    pending.append(reqs[i])
+                    i += 1
+                while pending:
+                    self._fail(pending.popleft(), "FC_ERR_TIMEOUT", t0, done)
+                self._reap(t0, done)
+                if len(done) < len(reqs):
+                    time.sleep(1e-4)
+                continue
             while i < len(reqs) and reqs[i].arrival <= now:
                 pending.append(reqs[i])
                 i += 1

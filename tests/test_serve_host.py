@@ -185,3 +185,15 @@ def test_admission_and_release_while_running(serve):
     assert stats["admitted_midrun"] == 1 and stats["released_midrun"] == 1
     assert srv.used == 60 and list(srv.sims) == [b]
     srv.close()
+
+
+def test_wall_limit_times_out_unlaunched_requests(serve):
+    """With max_wall_s = 0 every request not yet launched completes at once
+    with FC_ERR_TIMEOUT (nothing is launched)."""
+    srv = _server(serve, budget=10 ** 9)
+    sid = srv.admit(FakeParams(1))
+    reqs = [serve.Request(kind="step", sim=sid, arrival=0.0) for _ in range(5)]
+    st = srv.run(reqs, max_wall_s=0.0)
+    assert st["requests"] == 5 and st["failed"] == 5
+    assert all(r.error == "FC_ERR_TIMEOUT" for r in reqs)
+    assert not [w for (s, w) in FakeLib.log if s == sid]
