@@ -164,7 +164,9 @@ fc_status fc_deriv_z_noalloc(fc_plan_t plan, fc_dtype dtype, int batch, int Nx, 
  * (same layout [batch][Nz][Ny][Nx] and arguments; df or d2f may be NULL).
  * The library moves slabs of y rows (all z and x of a field, at most about
  * 256 MB of input each, an even number of rows, the slabs of a field of
- * nearly equal size) through three rotating device buffers
+ * nearly equal size; the first slab of a call about a quarter of that, so
+ * that the device-to-host copies start sooner) through three rotating device
+ * buffers
  * on three internal streams: the host-to-device copy of one slab, the kernel
  * of the previous one and the device-to-host copies of the one before run
  * concurrently.  Results are bitwise those of fc_deriv_z on device copies of
