@@ -11,12 +11,12 @@
 //   the annulus kperp2_min <= kx^2 + ky^2 <= kperp2_max and m_min <= m <= m_max;
 //   the real part, scaled to a largest component magnitude of `amplitude`.
 //
-// Four launches, all in float64 arithmetic: the vertical profiles of every
+// Five launches, all in float64 arithmetic: the vertical profiles of every
 // horizontal mode (sum over m), the e^{i kx x} / e^{i ky y} tables (exact
 // argument reduction: the phase 2 pi n i / Nx is taken modulo 2 pi in
 // integers), the synthesis (one block per (z, y) row: first the sums over the
-// modes that share kx, then one real sum over kx per point), and the scaling
-// by the largest magnitude (a block-max reduction into one device word).
+// modes that share kx, then one real sum over kx per point), the largest
+// magnitude (a block-max reduction into one device word) and the scaling.
 #include "internal.hpp"
 
 #include <cmath>
