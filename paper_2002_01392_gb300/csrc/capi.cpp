@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "host_tables.hpp"
+#include "slabs.hpp"
 #include "internal.hpp"
 
 namespace fcns {
@@ -380,18 +381,8 @@ extern "C" fc_status fc_deriv_z_host_ex(fc_plan_t plan, fc_dtype dtype, int batc
   const size_t es = dtype == FC_F32 ? 4 : 8;
   const int Nz = plan->data.Nz;
   const size_t yrow = (size_t)Nz * Nx * es;   // bytes of one y row over all z
-  // slab: an even number of y rows (so that the kernel pairs the same lines
-  // as a call on the whole field), at most about slab_bytes of input, the
-  // slabs of a field as equal as that allows (no short last slab)
-  long long Yc = (long long)std::max<size_t>(2, slab_bytes / yrow);
-  Yc -= Yc % 2;
-  if (Yc >= Ny) {
-    Yc = Ny;
-  } else {
-    const long long ns = (Ny + Yc - 1) / Yc;
-    Yc = (Ny + ns - 1) / ns;
-    Yc += Yc % 2;
-  }
+  std::vector<Slab> slabs;
+  const long long Yc = plan_slabs(batch, Ny, yrow, slab_bytes, &slabs);
   s = stage_for(t, (size_t)Yc * yrow);
   if (s) return s;
   // the slabs start after the work already queued on the caller's stream
@@ -402,25 +393,6 @@ extern "C" fc_status fc_deriv_z_host_ex(fc_plan_t plan, fc_dtype dtype, int batc
   const char* fh = static_cast<const char*>(f);
   char* oh[2] = {static_cast<char*>(df), static_cast<char*>(d2f)};
   const size_t hp = (size_t)Ny * Nx * es;     // host pitch between z rows
-  // the first slab of the call is about a quarter of the others (an even row
-  // count), so that the device-to-host copies, the busiest of the three
-  // streams, start sooner; the rest of that field is split into equal slabs
-  struct Slab { int b; long long y0, yc; };
-  std::vector<Slab> slabs;
-  for (int b = 0; b < batch; ++b) {
-    long long y0 = 0;
-    if (b == 0 && Yc < Ny) {
-      long long first = std::max<long long>(2, Yc / 4);
-      first -= first % 2;
-      slabs.push_back({0, 0, first});
-      y0 = first;
-    }
-    const long long rest = Ny - y0, ns = (rest + Yc - 1) / Yc;
-    long long each = ns > 0 ? (rest + ns - 1) / ns : 0;
-    each += each % 2;
-    if (each > Yc) each = Yc;
-    for (; y0 < Ny; y0 += each) slabs.push_back({b, y0, std::min<long long>(each, Ny - y0)});
-  }
   long long i = 0;
   for (size_t si = 0; si < slabs.size() && !s; ++si, ++i) {
     {  // slab si in staging slot i % 3

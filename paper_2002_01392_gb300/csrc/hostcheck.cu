@@ -9,6 +9,7 @@
 
 #include "deriv_kernel.cuh"
 #include "host_tables.hpp"
+#include "slabs.hpp"
 
 namespace fcns {
 
@@ -62,6 +63,21 @@ static int emu_deriv(const double* Mr, int d, int Cc, int Nz, int batch, long lo
 }  // namespace fcns
 
 using namespace fcns;
+
+// The slab plan of fc_deriv_z_host: out[3 i + 0..2] = field, first y row, rows
+// of slab i (at most max slabs); returns the staging rows, *n the slab count.
+extern "C" long long fchc_slab_plan(int batch, long long Ny, size_t yrow, size_t slab_bytes, long long* out, int max,
+                                    int* n) {
+  std::vector<Slab> sl;
+  const long long Yc = plan_slabs(batch, Ny, yrow, slab_bytes, &sl);
+  *n = (int)sl.size();
+  for (int i = 0; i < (int)sl.size() && i < max; ++i) {
+    out[3 * i] = sl[i].b;
+    out[3 * i + 1] = sl[i].y0;
+    out[3 * i + 2] = sl[i].yc;
+  }
+  return Yc;
+}
 
 // Emulate fc_deriv_z for transform length L (must be one of the compiled
 // shapes and >= N' + Nz - 1).  dtype 0 = float, 1 = double.

@@ -94,3 +94,34 @@ def test_deriv_kernel_converges_to_exact_derivative(hc, Mr_5_25):
     assert errs[(129, 1)] / errs[(513, 1)] >= h_ratio ** 4 * 0.8
     assert errs[(129, 2)] / errs[(513, 2)] >= h_ratio ** 3 * 0.8
 
+
+
+@pytest.mark.parametrize("batch,Ny,rows_per_slab", [(3, 512, 242), (2, 23, 6), (1, 23, 6), (1, 7, 100), (2, 9, 2),
+                                                    (4, 1024, 7), (1, 2, 2), (3, 513, 64)])
+def test_host_array_slab_plan(hc, batch, Ny, rows_per_slab):
+    """fc_deriv_z_host's slabs cover every y row of every field exactly once,
+    in order; every slab but a field's last has an even row count and starts
+    on an even row (the kernel pairs the same lines as on the whole field); no
+    slab exceeds the staging rows, which stay within the requested bytes
+    (rounded to an even count, at least 2); the first slab of the call is at
+    most about a quarter of the staging rows."""
+    yrow = 513 * 37 * 4
+    out = (ctypes.c_longlong * 30000)()
+    n = ctypes.c_int()
+    hc.fchc_slab_plan.restype = ctypes.c_longlong
+    hc.fchc_slab_plan.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_size_t, ctypes.c_size_t,
+                                  ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    Yc = hc.fchc_slab_plan(batch, Ny, yrow, rows_per_slab * yrow, out, 10000, ctypes.byref(n))
+    slabs = [tuple(out[3 * i:3 * i + 3]) for i in range(n.value)]
+    assert 0 < Yc <= max(2, rows_per_slab + rows_per_slab % 2) or Yc == Ny
+    for b in range(batch):
+        mine = [(y0, yc) for (bb, y0, yc) in slabs if bb == b]
+        assert [y0 for y0, _ in mine] == [sum(yc for _, yc in mine[:k]) for k in range(len(mine))]
+        assert sum(yc for _, yc in mine) == Ny
+        for k, (y0, yc) in enumerate(mine):
+            assert 0 < yc <= Yc and y0 % 2 == 0
+            if k < len(mine) - 1:
+                assert yc % 2 == 0
+    if Yc < Ny:
+        assert slabs[0][2] <= max(2, Yc // 4)
+    assert [bb for bb, _, _ in slabs] == sorted(bb for bb, _, _ in slabs)
