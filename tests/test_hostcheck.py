@@ -46,7 +46,9 @@ def test_deriv_kernel_d7_matches_oracle(hc, Mr_7_33, Nz, L, Nx, Ny, B):
                                            (39, 64, 9, 3, 2),
                                            (129, 288, 33, 1, 1), (513, 1080, 17, 2, 1), (513, 1080, 8, 2, 2),
                                            # the smallest Nz that L = 1080 serves with C = 25 (need 1025)
-                                           (501, 1080, 8, 2, 1)])
+                                           (501, 1080, 8, 2, 1),
+                                           # an odd line count: element loads of the last pair
+                                           (513, 1080, 9, 3, 1)])
 @pytest.mark.parametrize("dtype", [0, 1])
 def test_deriv_kernel_phases_match_oracle(hc, Mr_5_25, Nz, L, Nx, Ny, B, dtype):
     sf = synth.SeparableField(Nx, Ny, Nz, rank=3, seed_offset=Nz)
