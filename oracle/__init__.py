@@ -12,7 +12,8 @@ or equation it follows.  Where the paper is silent or inconsistent, the
 reading taken is stated in the docstring of the module that takes it
 (``fc_tables``: geometry, bandwidth and precision of the fits; ``fc``: grid,
 Nyquist treatment and truncation; ``ns``: signs, filter normalisation, stage
-steps, pressure units, mean mode, injection and Nusselt definition).
+steps, pressure units, mean mode, injection and Nusselt definition;
+``noise``: the App. A perturbation's mode set, draws and scaling).
 
 Parity status: every function is pinned by a test in ``tests/test_oracle_*``
 against closed forms, invariants, brute-force sums or the paper's printed
