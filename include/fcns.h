@@ -424,8 +424,9 @@ fc_status fc_noise_modes(const fc_noise_params* p, int* count);
  * ns_set_fields.  FC_ERR_ARG: invalid parameters (Lx, Ly, Lz <= 0,
  * kperp2_min > kperp2_max, m outside 1..64, non-finite values), no mode in
  * the annulus, ndraws wrong, a non-finite draw, NULL pointers, Nx <= 2 max|n|
- * or Ny <= 2 max l (a mode the grid cannot resolve), Nz < 2; FC_ERR_NOMEM if
- * the scratch cannot be allocated.
+ * or Ny <= 2 max l (a mode the grid cannot resolve), Nz < 2;
+ * FC_ERR_UNSUPPORTED for more than 511 kx indices on each side of the annulus
+ * (max |n| > 511); FC_ERR_NOMEM if the scratch cannot be allocated.
  */
 fc_status fc_noise(const fc_noise_params* p, fc_dtype dtype, int Nx, int Ny, int Nz, const double* draws,
                    int ndraws, void* out, fc_stream_t stream);

@@ -279,6 +279,10 @@ extern "C" fc_status fc_noise(const fc_noise_params* p, fc_dtype dtype, int Nx, 
     set_error("fc_noise: the grid must resolve every mode (Nx > 2 max|n|, Ny > 2 max l)");
     return FC_ERR_ARG;
   }
+  if (2 * md.nmax + 1 > 1024) {   // the synthesis keeps 3 x (2 nmax + 1) complex sums in 48 KB of shared memory
+    set_error("fc_noise: at most 511 kx indices on each side of the annulus");
+    return FC_ERR_UNSUPPORTED;
+  }
   if ((long long)Nz * Ny > 0x7fffffffLL || 3LL * Nz * Ny * Nx > (1LL << 40)) {
     set_error("fc_noise: grid too large");
     return FC_ERR_ARG;

@@ -184,3 +184,9 @@ def test_noise_mode_count_and_argument_checks_need_no_gpu(api):
     for bad in ({"Lz": 0.0}, {"kperp2_min": 30.0}, {"m_min": 0}, {"m_max": 65}, {"amplitude": float("nan")}):
         assert st(api.noise_params(**bad)) == "FC_ERR_ARG", bad
     assert st(api.noise_params(kperp2_min=0.1, kperp2_max=0.2)) == "FC_ERR_ARG"   # empty annulus
+    # max |n| = 600 > 511: refused before any device work (grid and draws sized to pass the other checks)
+    big = api.noise_params(kperp2_min=599.5 ** 2, kperp2_max=600.0 ** 2, m_min=2, m_max=2)
+    nb = api.noise_modes(big)
+    big_draws = (ctypes.c_double * (2 * nb))()
+    assert lib.fc_status_str(lib.fc_noise(ctypes.byref(big), 0, 1300, 1300, 17, big_draws, 2 * nb, 1 << 40,
+                                          None)).decode() == "FC_ERR_UNSUPPORTED"
